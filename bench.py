@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: Gcell-updates/s of one dual-parameter FWI gradient (forward + adjoint).
+
+One step = one ``misfit_and_gradient`` call over the 540x290-cell (20-cell CPML inside),
+32-shot, nt = 2000, 100-receiver, 400 MHz layered + blob workload: the forward time loop
+(Algorithm 1) with the full wavefield stored, the L2 misfit (Eq. objective) and the adjoint
+time loop (Algorithm 2) accumulating the zero-lag gradients.  A cell-update is one cell
+advanced one time step in one shot, counted once for the forward and once for the adjoint:
+2 * N * nt * nshots per step.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload.  Under torchrun every rank runs its own 32-shot batch
+(independent shots, no data-path collective: weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s (fwd+adjoint) and s per dual-param FWI iteration vs HBM roofline"
+UNIT = "Gcell-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM bytes (read + write) per cell-step of one launch, from `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
+# gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
+NCU_TRAFFIC_PER_CELL_STEP: dict = {}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nshots", type=int, default=32)
+    ap.add_argument("--nt", type=int, default=2000)
+    ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch")
+    ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def workload(rank: int, nshots: int, nt: int):
+    from paper_2506_20513_gb300 import workloads as W
+    return W.multishot_layered(seed=1000 + rank, nshots=nshots, nt=nt)
+
+
+def cpu_sample_shots(requested: int) -> int:
+    if requested > 0:
+        return requested
+    cores = os.cpu_count() or 1
+    try:
+        mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+    except (ValueError, OSError):
+        mem_gb = 16.0
+    # the oracle keeps each shot's FP64 wavefield history (~2.5 GB here) per thread
+    return max(1, min(8, cores, int(mem_gb * 0.4 / 2.6)))
+
+
+def run_oracle_sample(wl, shots: int):
+    """Time the FP64 oracle gradient of `shots` shots (one OpenMP thread per shot)."""
+    from oracle import oracle as O
+    g = wl.grid
+    wav = np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (shots, 1, g.nt))
+    obs = np.zeros((shots, g.nt, wl.nrec))
+    t0 = time.perf_counter()
+    O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl.src[:shots], wav, wl.rec[:shots], obs,
+                          nthreads=shots)
+    dt = time.perf_counter() - t0
+    cells = 2 * g.ncells * g.nt * shots
+    return cells / dt / 1e9, dt
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wl = workload(0, args.nshots, args.nt)
+    shots = cpu_sample_shots(args.cpu_shots)
+    for _ in range(args.warmup):
+        run_oracle_sample(wl, shots)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, t = run_oracle_sample(wl, shots)
+        vals.append(v)
+        times.append(t)
+    value = 2 * wl.grid.ncells * wl.grid.nt * shots * args.steps / sum(times) / 1e9
+    sample = (f"{shots} of {wl.nshots} shots per step (full {wl.grid.nx}x{wl.grid.ny} grid, "
+              f"nt {wl.grid.nt}, forward + adjoint gradient), FP64 C oracle, one thread per shot")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "grid": f"{wl.grid.nx}x{wl.grid.ny}",
+                   "shots_per_step": shots, "nt": wl.grid.nt, "nrec": wl.nrec},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": shots, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_tag():
+    p = os.path.join(ROOT, "paper_2506_20513_gb300", "csrc", "gf_tile_kernels.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def algorithmic_bytes_per_launch(kind: str, wl, K: int) -> float:
+    """Compulsory HBM bytes of one tile-kernel launch of K steps over all cells and shots:
+    fields Ez, Hx, Hy read and written once (24 B), the model read once per cell (8 B,
+    shared by the shots), CPML memories read and written in the strips (2 arrays x 8 B),
+    plus per step: forward, the Ez history write (4 B); adjoint, the history read (4 B,
+    K + 1 slots) and the per-shot gradient pair read and written once (16 B)."""
+    g = wl.grid
+    N, S = g.ncells, wl.nshots
+    w = 2 * g.npml + 1
+    strip_cells = w * g.ny + w * g.nx
+    base = S * N * 24 + 8 * N + S * strip_cells * 16
+    if kind == "fwd":
+        return base + S * N * 4 * K
+    return base + S * N * (16 + 4 * (K + 1))
+
+
+def ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2506_20513_gb300 import FDTD, Tiling, _lib
+    from paper_2506_20513_gb300.fdtd import ricker
+
+    wl = workload(rank, args.nshots, args.nt)
+    g = wl.grid
+    tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
+    fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=tiling)
+    t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
+    eps_t, sig_t = t32(wl.eps_true), t32(wl.sig_true)
+    eps0, sig0 = t32(wl.eps_init), t32(wl.sig_init)
+    obs = fd.forward_model(eps_t, sig_t, wav)
+    fd.status()
+
+    def step():
+        return fd.misfit_and_gradient(eps0, sig0, wav, obs)
+
+    for _ in range(args.warmup):
+        step()
+    fd.status()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier()
+    clocks.start()
+    lib, ctx = fd.lib, fd.ctx
+    launches0 = lib.gf_kernel_launches(ctx)
+    lib.gf_profile(ctx, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        J, ge, gs = step()
+    e1.record()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    gpu_launches = lib.gf_kernel_launches(ctx) - launches0
+    import ctypes
+    prof = {}
+    for name, kind in (("fwd", _lib.GF_KERNEL_FWD), ("adj", _lib.GF_KERNEL_ADJ),
+                       ("aux", _lib.GF_KERNEL_AUX)):
+        tot, cnt = ctypes.c_double(), ctypes.c_longlong()
+        lib.gf_profile_read(ctx, kind, ctypes.byref(tot), ctypes.byref(cnt))
+        prof[name] = (tot.value, cnt.value)
+    lib.gf_profile(ctx, 0)
+    clk = clocks.stop()
+    fd.status()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = wl.cell_updates() * args.steps * world
+    value = cells / (ms / 1e3) / 1e9
+
+    # roofline of the dominant tile kernel (its own launches, CUDA events on its stream)
+    K = tiling.steps if tiling and tiling.steps else 4
+    dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
+    tot_ms, cnt = prof[dom]
+    nt = g.nt
+    # launches of K steps except a possibly shorter last one: use the mean steps per launch
+    per_launch_steps = nt / max(1, cnt / args.steps)
+    algo = algorithmic_bytes_per_launch(dom, wl, per_launch_steps)
+    avg_s = tot_ms / 1e3 / max(1, cnt)
+    peak, peak_kind = hbm_peak()
+    achieved = algo / avg_s / 1e9
+    key = f"{dom}@{kernel_source_tag()}@{g.nx}x{g.ny}x{wl.nshots}@{args.tile or 'default'}"
+    tpc = NCU_TRAFFIC_PER_CELL_STEP.get(key)
+    traffic = tpc * wl.nshots * g.ncells * per_launch_steps if tpc else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom}_tile",
+            "peak_source": f"hbm_gbs of {peak_kind}",
+            "avg_launch_us": avg_s * 1e6, "launches": cnt,
+            "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        h = lambda t: t.detach().to("cpu").pin_memory()
+        he, hs, hw, ho = h(eps0), h(sig0), h(wav), h(obs)
+        fd.misfit_and_gradient(he, hs, hw, ho)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Jh, geh, gsh = fd.misfit_and_gradient(he, hs, hw, ho)
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for x in (he, hs, hw, ho))
+        d2h = Jh.numel() * 8 + geh.numel() * 4 + gsh.numel() * 4
+        e2e = {"value": cells / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        shots = cpu_sample_shots(args.cpu_shots)
+        v, t = run_oracle_sample(wl, shots)
+        cpu = {"value": v, "unit": UNIT, "cores": shots, "kind": "oracle",
+               "sample": (f"{shots} of {wl.nshots} shots, full grid and nt, forward + adjoint "
+                          f"gradient, FP64 C oracle, one thread per shot, {t:.1f} s")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": f"{g.nx}x{g.ny}", "npml": g.npml,
+                       "shots_per_gpu": wl.nshots, "nt": g.nt, "nrec": wl.nrec,
+                       "cell_updates_per_step": wl.cell_updates() * world,
+                       "s_per_gradient": ms / args.steps / 1e3,
+                       "tiling": args.tile or "default 56,24,4",
+                       "l2": "inputs larger than L2: each step streams the "
+                             f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
+                             "history through HBM",
+                       "parallelism": f"shots x{world} (independent per GPU)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    fd.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * gprfwi.h -- C ABI of the GB300 (sm_103a) library for the hot path of dual-parameter GPR
+ * full waveform inversion (arXiv 2506.20513): the 2-D TM Maxwell FDTD time loop with CPML
+ * absorbing boundaries and its exact discrete adjoint with zero-lag gradients.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid.      Arrays are [ny][nx], x (horizontal) fastest, y (depth) second, FP32.  The
+ *            absorbing layer (npml cells on each side) lies INSIDE the arrays, as the
+ *            paper's model arrays do (Sec. 3.1, the demo strips pmlthick cells before
+ *            saving).  Ez lives on integer nodes, Hx at (i, j+1/2), Hy at (i+1/2, j)
+ *            (Sec. 2.1, Eqs. 3-5).  The outermost ring of Ez nodes is a PEC wall behind
+ *            the CPML and is never updated.
+ * Model.     eps_r (relative permittivity, >= 1) and sigma (conductivity in S/m, >= 0),
+ *            both [ny][nx].  Cells with sigma > 100 S/m are perfect conductors (Sec. 3.2,
+ *            coefficient listing).  Relative permeability is 1.
+ * Shots.     A context holds nshots independent experiments ("step" in the paper's
+ *            Table 1; every kernel carries a shot index, Sec. 3.2).  Each shot has nsrc
+ *            z-polarised line sources and nrec receivers given as cell indices (i, j).
+ * Wavelet.   Device FP32 [nshots][nsrc][nt]: w^n is injected into Ez^{n+1} as
+ *            Ez(src) -= Cb(src) w^n / (dx dy)  (Sec. 3.2, hertzian-dipole listing with
+ *            dl = dz = 1).
+ * Traces.    Device FP32 [nshots][nt][nrec]: d^n = Ez^n sampled before the updates of
+ *            step n (Algorithm 1, stage 1), so d^0 = 0.
+ * Pointers.  Every array argument of a compute call is a DEVICE pointer on the context's
+ *            device unless stated otherwise.  The caller owns every argument buffer; the
+ *            library never frees or retains them beyond the call.  Calls are asynchronous
+ *            on the given stream (a cudaStream_t passed as void*, NULL = legacy default
+ *            stream) and return after enqueueing.
+ * Errors.    Every call returns 0 (GF_OK) or a negative GF_E* code; gf_last_error() gives
+ *            a one-line message.  Host-side argument errors are detected before anything
+ *            is enqueued.  Errors found on the device (invalid model values, non-finite
+ *            traces, exhausted bounded waits) are recorded in a device status word that
+ *            gf_status() reads.  No call throws, traps or aborts.
+ * Threads.   A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef GPRFWI_H
+#define GPRFWI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GF_OK 0
+#define GF_EINVAL (-1)     /* bad argument: shape, index, NULL pointer, eps_r < 1, sigma < 0 */
+#define GF_ECFL (-2)       /* time step violates the CFL bound (Sec. 2.1, Eq. cfl) */
+#define GF_ENOMEM (-3)     /* device allocation failed or caller workspace too small */
+#define GF_ECUDA (-4)      /* a CUDA runtime call failed (message in gf_last_error) */
+#define GF_ENONFINITE (-5) /* non-finite trace or gradient detected on the device */
+#define GF_ETIMEOUT (-6)   /* a bounded device-side wait ran out */
+#define GF_ESTATE (-7)     /* call out of order (e.g. adjoint without a saved forward) */
+
+/* Padded grid and CPML description (Sec. 4 parameter tables: dx, nx, ny, dt, pmlthick;
+ * CPML grading per the convolutional PML of Roden & Gedney, which the paper names only as
+ * "PML" kernels, Sec. 3.2). */
+typedef struct gf_grid_desc {
+    int32_t nx, ny;        /* array size in cells, CPML included */
+    int32_t npml;          /* CPML width in cells on each side (0 = PEC box) */
+    int32_t nt;            /* number of time steps */
+    double dx, dy, dt;     /* cell size (m) and time step (s) */
+    int32_t pml_order;     /* grading exponent m (e.g. 3) */
+    double pml_sigma_max;  /* S/m; <= 0 selects 0.8 (m+1) / (eta0 d sqrt(pml_eps_ref)) */
+    double pml_kappa_max;  /* >= 1 */
+    double pml_alpha_max;  /* S/m (complex-frequency shift, linear taper to 0 at depth) */
+    double pml_eps_ref;    /* reference relative permittivity of the sigma_max default */
+} gf_grid_desc;
+
+/* Acquisition geometry (Sec. 3.2 source / receiver listings; Table 1 source_location,
+ * receiver_location, step, nsrc, nrx).  HOST pointers, copied during gf_create. */
+typedef struct gf_acquisition {
+    int32_t nshots;         /* >= 1 */
+    int32_t nsrc;           /* sources per shot, 1..8 */
+    int32_t nrec;           /* receivers per shot, >= 1 */
+    const int32_t* src_ij;  /* [nshots][nsrc][2] cell indices (i, j), 1 <= i <= nx-2 ... */
+    const int32_t* rec_ij;  /* [nshots][nrec][2] cell indices, same range (off the ring) */
+} gf_acquisition;
+
+typedef struct gf_ctx gf_ctx;
+
+/* Wavefield storage for the adjoint (the forward wavefield store of Algorithm 1, stage 7). */
+#define GF_STORE_FULL 0 /* every Ez^n of every shot kept in the workspace */
+
+/* Create a context on CUDA device `device`: validates the grid (CFL, Eq. cfl) and the
+ * geometry, builds the CPML profiles in FP64 on the host and uploads them with the
+ * geometry (device memory owned by the context, freed by gf_destroy).  No workspace is
+ * allocated here.  *out is set to NULL on failure; the returned code says why. */
+int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq, int device);
+
+/* Free everything the context owns (never a caller workspace).  NULL is accepted. */
+void gf_destroy(gf_ctx* ctx);
+
+/* Message of the last error on this context (static text for ctx == NULL). */
+const char* gf_last_error(const gf_ctx* ctx);
+
+/* Bytes of device workspace that gf_misfit_and_gradient / gf_forward with saving need for
+ * the given storage mode (GF_STORE_FULL: nshots * nt * nx * ny * 4 bytes of wavefield plus
+ * the time-stepping state).  forward_only != 0 gives the smaller forward-only figure. */
+int gf_workspace_size(const gf_ctx* ctx, int store_mode, int forward_only, size_t* bytes);
+
+/* Hand the context a caller-owned device workspace (>= gf_workspace_size bytes, 256-byte
+ * aligned).  The caller keeps ownership and must keep it alive and unused by others while
+ * calls on this context are in flight.  Without it the library allocates its own workspace
+ * with cudaMalloc on first use (freed by gf_destroy).  ws == NULL reverts to that. */
+int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
+
+/* Time-blocking options: tile interior width/height in cells and time steps per launch
+ * (0 = keep the current value).  Rejects shapes whose shared-memory footprint does not fit. */
+int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
+
+/* forward_model(eps_r, sigma, sources, receivers) -> traces (Algorithm 1 for all shots).
+ * traces: [nshots][nt][nrec] written.  illum: optional [ny][nx], receives the illumination
+ * sum over shots and n = 1..nt of (Ez^n)^2 (NULL to skip).  Nothing is kept for an adjoint. */
+int gf_forward_model(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
+                     float* traces, float* illum, void* stream);
+
+/* Forward run that also stores the wavefield (mode GF_STORE_FULL) in the workspace for a
+ * later gf_adjoint on the same model, wavelet and stream. */
+int gf_forward(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
+               float* traces, float* illum, int store_mode, void* stream);
+
+/* Adjoint run (Algorithm 2) of the last gf_forward, driven by the trace cotangent
+ * resid = dL/dtraces [nshots][nt][nrec].  Writes g_eps_r = dL/deps_r and g_sigma =
+ * dL/dsigma (per S/m), [ny][nx], summed over shots: the discrete zero-lag gradients
+ * -sum_n lam^{n+1} (Ez^{n+1} - Ez^n) eps0/dt and -sum_n lam^{n+1} (Ez^{n+1} + Ez^n)/2 with
+ * lam = Cb * adjoint(Ez) (Sec. 2.1, Eqs. grad_eps and grad_sigma).  Either output may be
+ * NULL.  Returns GF_ESTATE if no stored forward exists. */
+int gf_adjoint(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* resid,
+               float* g_eps_r, float* g_sigma, void* stream);
+
+/* misfit_and_gradient(eps_r, sigma, observed) -> J, g_eps_r, g_sigma: the L2 misfit
+ * J = 1/2 sum_{s,n,r} (d - o)^2 (Sec. 2.1, Eq. objective) written as one FP64 value to
+ * *misfit (device), and its exact gradients as in gf_adjoint.  observed: [nshots][nt][nrec].
+ * traces (optional, may be NULL) receives the modelled data.  Equivalent to gf_forward +
+ * residual + gf_adjoint, enqueued on one stream. */
+int gf_misfit_and_gradient(gf_ctx* ctx, const float* eps_r, const float* sigma,
+                           const float* wavelet, const float* observed, double* misfit,
+                           float* g_eps_r, float* g_sigma, float* traces, void* stream);
+
+/* Synchronise `stream` and return the device status word (GF_OK or the first device-side
+ * error since the last gf_status call), then clear it. */
+int gf_status(gf_ctx* ctx, void* stream);
+
+/* Host helper: Ricker wavelet w(n dt) = amp (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2),
+ * tau = n dt - sqrt(2)/f0, n = 0..nt-1, into the HOST array out[nt] (the paper's
+ * source_amplitudes = ['ricker', amplitude, f0], Sec. 4 tables). */
+int gf_ricker(float* out, int nt, double dt, double f0, double amp);
+
+/* Kernel families for the profiling counters below. */
+#define GF_KERNEL_FWD 0 /* temporally blocked forward tile kernel (Algorithm 1) */
+#define GF_KERNEL_ADJ 1 /* temporally blocked adjoint tile kernel (Algorithm 2) */
+#define GF_KERNEL_AUX 2 /* model check, residual / misfit, shot sums */
+
+/* Number of kernels this context has launched since gf_create (all families). */
+long long gf_kernel_launches(const gf_ctx* ctx);
+
+/* enable != 0: from now on bracket every kernel launch with CUDA events on its stream (no
+ * synchronisation is added); enable == 0 stops and drops what was recorded. */
+int gf_profile(gf_ctx* ctx, int enable);
+
+/* Synchronise on the recorded events and return, for one kernel family, the summed device
+ * time in milliseconds and the number of launches recorded since the last read (or since
+ * profiling was enabled); the family's record is then cleared. */
+int gf_profile_read(gf_ctx* ctx, int kind, double* ms_total, long long* launches);
+
+/* Library version string. */
+const char* gf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPRFWI_H */

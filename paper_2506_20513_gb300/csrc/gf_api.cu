@@ -1,0 +1,571 @@
+// gf_api.cu -- host runtime behind the C ABI of include/gprfwi.h.
+//
+// Owns argument validation (CFL, Eq. cfl; geometry; sizes), the CPML profiles (built here in
+// FP64 and uploaded as FP32), the workspace layout, and the launch sequence of the forward
+// (Algorithm 1) and adjoint (Algorithm 2) time loops.  Every step of the path runs in the
+// kernels of gf_tile_kernels.cu and gf_misc_kernels.cu; nothing is computed on the host
+// except the model-independent CPML profiles and the Ricker helper.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/gprfwi.h"
+#include "gf_internal.cuh"
+
+namespace {
+
+constexpr double kEps0 = 8.8541878128e-12;  // F/m
+constexpr double kMu0 = 1.25663706212e-6;   // H/m
+constexpr double kC0 = 299792458.0;         // m/s
+constexpr int kMisfitBlocks = 1024;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Offsets (bytes) of the workspace regions.
+struct Layout {
+    size_t status, partial, stA, stB, illum, traces, resid, grad, hist, total;
+};
+
+}  // namespace
+
+struct gf_ctx {
+    gf_grid_desc g;
+    int nshots, nsrc, nrec, device;
+    long long N;
+    float* d_prof = nullptr;  // [12][max(nx, ny)] profiles (x: 6 arrays, y: 6 arrays)
+    int* d_src = nullptr;     // [nshots][nsrc]
+    int* d_rec = nullptr;     // [nshots][nrec]
+    gf::AxisProfile px{}, py{};
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    bool have_forward = false;
+    int tile_w = 56, tile_h = 24, K = 4;
+    size_t smem_optin = 0;
+    long long launches = 0;
+    bool profiling = false;
+    // per kernel family: recorded (start, stop) event pairs not yet read
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
+    std::vector<cudaEvent_t> ev_pool;
+    char err[512] = {0};
+};
+
+namespace {
+
+int fail(gf_ctx* c, int code, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int cuda_fail(gf_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, GF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GF_CUDA(ctx, call, what)                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, (what)); \
+    } while (0)
+
+cudaEvent_t take_event(gf_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch one kernel (a callable returning cudaError_t) of family `kind`, counting it and,
+// when profiling, bracketing it with events on `st`.
+template <class F>
+cudaError_t launch(gf_ctx* c, int kind, cudaStream_t st, F&& f) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        cudaEventRecord(e0, st);
+    }
+    cudaError_t e = f();
+    if (c->profiling) {
+        cudaEventRecord(e1, st);
+        c->prof_ev[kind].emplace_back(e0, e1);
+    }
+    if (e == cudaSuccess) ++c->launches;
+    return e;
+}
+
+void drop_profile(gf_ctx* c) {
+    for (auto& v : c->prof_ev) {
+        for (auto& pr : v) {
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        v.clear();
+    }
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// CPML profile of one node at depth u = rho / (npml d) in (0, 1] (convolutional PML,
+// Roden & Gedney): graded sigma, kappa, alpha; recursive-convolution coefficients b, c.
+void cpml_node(const gf_grid_desc& g, double d, double u, double& a, double& b, double& c) {
+    if (u <= 0.0) {
+        a = 1.0 / d;
+        b = 0.0;
+        c = 0.0;
+        return;
+    }
+    const double m = g.pml_order;
+    double smax = g.pml_sigma_max;
+    if (smax <= 0.0) smax = 0.8 * (m + 1.0) / (sqrt(kMu0 / kEps0) * d * sqrt(g.pml_eps_ref));
+    const double um = pow(u, m);
+    const double sig = smax * um;
+    const double kap = 1.0 + (g.pml_kappa_max - 1.0) * um;
+    const double alp = g.pml_alpha_max * (1.0 - u);
+    b = exp(-(sig / kap + alp) * g.dt / kEps0);
+    c = sig > 0.0 ? sig * (b - 1.0) / (sig * kap + kap * kap * alp) / d : 0.0;
+    a = 1.0 / (kap * d);
+}
+
+// Six FP32 arrays of length n for one axis: aE, bE, cE (integer nodes), aH, bH, cH
+// (half nodes i + 1/2).  Depth is measured from the edge of the physical part
+// [npml, n - 1 - npml].
+void axis_profiles(const gf_grid_desc& g, int n, double d, float* out, int stride) {
+    const double lo = g.npml, hi = n - 1 - g.npml;
+    for (int i = 0; i < n; ++i) {
+        for (int h = 0; h < 2; ++h) {
+            const double pos = i + 0.5 * h;
+            double rho = 0.0;
+            if (pos < lo) rho = lo - pos;
+            if (pos > hi) rho = pos - hi;
+            const double u = g.npml > 0 ? rho / g.npml : 0.0;
+            double a, b, c;
+            cpml_node(g, d, u, a, b, c);
+            out[(3 * h + 0) * stride + i] = (float)a;
+            out[(3 * h + 1) * stride + i] = (float)b;
+            out[(3 * h + 2) * stride + i] = (float)c;
+        }
+    }
+}
+
+Layout layout_of(const gf_ctx* c, bool forward_only) {
+    Layout L{};
+    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    const size_t tr = sizeof(float) * (size_t)c->nshots * c->g.nt * c->nrec;
+    size_t o = 0;
+    L.status = o; o = align_up(o + sizeof(int));
+    L.partial = o; o = align_up(o + sizeof(double) * kMisfitBlocks);
+    L.stA = o; o = align_up(o + gf::kNumFields * field);
+    L.stB = o; o = align_up(o + gf::kNumFields * field);
+    L.illum = o; o = align_up(o + field);
+    L.traces = o; o = align_up(o + tr);
+    if (forward_only) {
+        L.resid = L.grad = L.hist = 0;
+        L.total = o;
+        return L;
+    }
+    L.resid = o; o = align_up(o + tr);
+    L.grad = o; o = align_up(o + 2 * field);
+    L.hist = o; o = align_up(o + field * (size_t)c->g.nt);
+    L.total = o;
+    return L;
+}
+
+int ensure_workspace(gf_ctx* c, bool forward_only) {
+    const Layout L = layout_of(c, forward_only);
+    if (c->ws && c->ws_bytes >= L.total) return GF_OK;
+    if (c->ws && !c->ws_owned)
+        return fail(c, GF_ENOMEM, "caller workspace has %zu bytes, %zu needed", c->ws_bytes, L.total);
+    if (c->ws) {
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GF_ENOMEM, "cudaMalloc(%zu) failed: %s", L.total, cudaGetErrorString(e));
+    }
+    c->ws = (char*)p;
+    c->ws_bytes = L.total;
+    c->ws_owned = true;
+    c->have_forward = false;
+    GF_CUDA(c, cudaMemset(c->ws + L.status, 0, sizeof(int)), "clear status");
+    return GF_OK;
+}
+
+gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
+    gf::TileParams p{};
+    p.nx = c->g.nx;
+    p.ny = c->g.ny;
+    p.npml = c->g.npml;
+    p.nt = c->g.nt;
+    p.nshots = c->nshots;
+    p.nsrc = c->nsrc;
+    p.nrec = c->nrec;
+    p.N = c->N;
+    p.dt_eps0 = (float)(c->g.dt / kEps0);
+    p.ch = (float)(c->g.dt / kMu0);
+    p.src_scale = (float)(1.0 / (c->g.dx * c->g.dy));
+    p.geps = (float)(kEps0 / c->g.dt);
+    p.px = c->px;
+    p.py = c->py;
+    p.src_cell = c->d_src;
+    p.rec_cell = c->d_rec;
+    p.status = (int*)(c->ws + L.status);
+    p.tile_w = c->tile_w;
+    p.tile_h = c->tile_h;
+    p.tiles_x = (c->g.nx + c->tile_w - 1) / c->tile_w;
+    return p;
+}
+
+int tiles_of(const gf_ctx* c) {
+    return ((c->g.nx + c->tile_w - 1) / c->tile_w) * ((c->g.ny + c->tile_h - 1) / c->tile_h);
+}
+
+int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                float* traces, float* illum, bool store, cudaStream_t st) {
+    if (!eps_r || !sigma || !wavelet) return fail(c, GF_EINVAL, "NULL model or wavelet pointer");
+    int rc = ensure_workspace(c, !store);
+    if (rc) return rc;
+    const Layout L = layout_of(c, !store);
+    gf::TileParams p = base_params(c, L);
+    p.eps_r = eps_r;
+    p.sigma = sigma;
+    p.wavelet = wavelet;
+    p.traces = traces ? traces : (float*)(c->ws + L.traces);
+    p.hist = store ? (float*)(c->ws + L.hist) : nullptr;
+    p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
+    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    float* st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear state");
+    if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, field, st), "clear illumination");
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_check_model(eps_r, sigma, c->N, p.status, st); }), "check_model");
+    const int tiles = tiles_of(c);
+    int cur = 0;
+    for (int n0 = 0; n0 < c->g.nt; n0 += c->K) {
+        p.n0 = n0;
+        p.K = std::min(c->K, c->g.nt - n0);
+        p.st_in = st_buf[cur];
+        p.st_out = st_buf[cur ^ 1];
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, tiles, st); }), "fwd_tile");
+        cur ^= 1;
+    }
+    if (illum)
+        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.illum, c->nshots, c->N, illum, p.status, st); }), "sum illum");
+    c->have_forward = store;
+    return GF_OK;
+}
+
+int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* resid,
+                float* g_eps_r, float* g_sigma, cudaStream_t st) {
+    const Layout L = layout_of(c, false);
+    gf::TileParams p = base_params(c, L);
+    p.eps_r = eps_r;
+    p.sigma = sigma;
+    p.resid = resid;
+    p.hist = (float*)(c->ws + L.hist);
+    p.grad = (float*)(c->ws + L.grad);
+    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    float* st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear adjoint state");
+    GF_CUDA(c, cudaMemsetAsync(p.grad, 0, 2 * field, st), "clear gradients");
+    const int tiles = tiles_of(c);
+    int cur = 0;
+    for (int n1 = c->g.nt - 1; n1 >= 0; n1 -= c->K) {
+        const int k = std::min(c->K, n1 + 1);
+        p.n0 = n1 - k + 1;
+        p.K = k;
+        p.st_in = st_buf[cur];
+        p.st_out = st_buf[cur ^ 1];
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, tiles, st); }), "adj_tile");
+        cur ^= 1;
+    }
+    if (g_eps_r)
+        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.grad, c->nshots, c->N, g_eps_r, p.status, st); }), "sum g_eps_r");
+    if (g_sigma)
+        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                    return gf::launch_sum_shots(p.grad + (size_t)c->nshots * c->N, c->nshots, c->N,
+                                                g_sigma, p.status, st);
+                }),
+                "sum g_sigma");
+    return GF_OK;
+}
+
+int check_tiling(gf_ctx* c, int tw, int th, int K) {
+    if (tw < 1 || th < 1 || K < 1 || K > 64)
+        return fail(c, GF_EINVAL, "tile %dx%d, K=%d out of range", tw, th, K);
+    const size_t f = gf::fwd_tile_smem_bytes(tw, th, K), a = gf::adj_tile_smem_bytes(tw, th, K);
+    if (std::max(f, a) > c->smem_optin)
+        return fail(c, GF_EINVAL, "tile %dx%d with K=%d needs %zu bytes of shared memory (> %zu)",
+                    tw, th, K, std::max(f, a), c->smem_optin);
+    return GF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gf_version(void) { return "gprfwi-gb300 0.1 (sm_103a)"; }
+
+const char* gf_last_error(const gf_ctx* ctx) {
+    return ctx ? ctx->err : "no context (gf_create failed before allocating one)";
+}
+
+int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq, int device) {
+    if (!out) return GF_EINVAL;
+    *out = nullptr;
+    if (!grid || !acq || !acq->src_ij || !acq->rec_ij) return GF_EINVAL;
+    const gf_grid_desc& g = *grid;
+    if (g.nx < 3 || g.ny < 3 || g.nt < 1 || g.npml < 0 || 2 * g.npml > g.nx - 2 ||
+        2 * g.npml > g.ny - 2 || !(g.dx > 0) || !(g.dy > 0) || !(g.dt > 0) || g.pml_order < 0 ||
+        !(g.pml_kappa_max >= 1.0) || !(g.pml_alpha_max >= 0.0) || !(g.pml_eps_ref > 0.0))
+        return GF_EINVAL;
+    if ((long long)g.nx * g.ny > (1LL << 31) - 1) return GF_EINVAL;
+    // Eq. cfl with the vacuum speed of light (eps_r >= 1 everywhere).
+    const double dtmax = 1.0 / (kC0 * sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy)));
+    if (g.dt > dtmax) return GF_ECFL;
+    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1)
+        return GF_EINVAL;
+    auto inside = [&](const int32_t* ij) {
+        return ij[0] >= 1 && ij[0] <= g.nx - 2 && ij[1] >= 1 && ij[1] <= g.ny - 2;
+    };
+    std::vector<int> src((size_t)acq->nshots * acq->nsrc), rec((size_t)acq->nshots * acq->nrec);
+    for (size_t k = 0; k < src.size(); ++k) {
+        if (!inside(acq->src_ij + 2 * k)) return GF_EINVAL;
+        src[k] = acq->src_ij[2 * k + 1] * g.nx + acq->src_ij[2 * k];
+    }
+    for (size_t k = 0; k < rec.size(); ++k) {
+        if (!inside(acq->rec_ij + 2 * k)) return GF_EINVAL;
+        rec[k] = acq->rec_ij[2 * k + 1] * g.nx + acq->rec_ij[2 * k];
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return GF_ECUDA;
+    }
+    DeviceGuard guard(device);
+    gf_ctx* c = new gf_ctx();
+    c->g = g;
+    c->nshots = acq->nshots;
+    c->nsrc = acq->nsrc;
+    c->nrec = acq->nrec;
+    c->device = device;
+    c->N = (long long)g.nx * g.ny;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)optin;
+    const int stride = std::max(g.nx, g.ny);
+    std::vector<float> prof(12 * (size_t)stride, 0.f);
+    axis_profiles(g, g.nx, g.dx, prof.data(), stride);
+    axis_profiles(g, g.ny, g.dy, prof.data() + 6 * (size_t)stride, stride);
+    cudaError_t e = cudaMalloc(&c->d_prof, prof.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_src, src.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_rec, rec.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_prof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(c->d_rec, rec.data(), rec.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        size_t mx = std::max(gf::fwd_tile_smem_bytes(1, 1, 1), (size_t)optin);
+        e = gf::configure_tile_kernels(mx, mx);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gf_destroy(c);
+        return GF_ECUDA;
+    }
+    float* P = c->d_prof;
+    const size_t S = stride;
+    c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
+    c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
+    if (check_tiling(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
+        gf_destroy(c);
+        return GF_EINVAL;
+    }
+    *out = c;
+    return GF_OK;
+}
+
+void gf_destroy(gf_ctx* c) {
+    if (!c) return;
+    DeviceGuard guard(c->device);
+    drop_profile(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->ws_owned && c->ws) cudaFree(c->ws);
+    cudaFree(c->d_prof);
+    cudaFree(c->d_src);
+    cudaFree(c->d_rec);
+    delete c;
+}
+
+int gf_workspace_size(const gf_ctx* c, int store_mode, int forward_only, size_t* bytes) {
+    if (!c || !bytes) return GF_EINVAL;
+    if (store_mode != GF_STORE_FULL) return GF_EINVAL;
+    *bytes = layout_of(c, forward_only != 0).total;
+    return GF_OK;
+}
+
+int gf_set_workspace(gf_ctx* c, void* ws, size_t bytes) {
+    if (!c) return GF_EINVAL;
+    if (ws && ((uintptr_t)ws % kAlign)) return fail(c, GF_EINVAL, "workspace not 256-byte aligned");
+    DeviceGuard guard(c->device);
+    if (c->ws_owned && c->ws) cudaFree(c->ws);
+    c->ws = (char*)ws;
+    c->ws_bytes = ws ? bytes : 0;
+    c->ws_owned = false;
+    c->have_forward = false;
+    if (ws) {
+        if (bytes < layout_of(c, true).total)
+            return fail(c, GF_ENOMEM, "workspace of %zu bytes is below the forward minimum", bytes);
+        GF_CUDA(c, cudaMemset(c->ws, 0, sizeof(int)), "clear status");
+    }
+    return GF_OK;
+}
+
+int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
+    if (!c) return GF_EINVAL;
+    const int tw = tile_w > 0 ? tile_w : c->tile_w, th = tile_h > 0 ? tile_h : c->tile_h;
+    const int k = K > 0 ? K : c->K;
+    int rc = check_tiling(c, tw, th, k);
+    if (rc) return rc;
+    c->tile_w = tw;
+    c->tile_h = th;
+    c->K = k;
+    return GF_OK;
+}
+
+int gf_forward_model(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                     float* traces, float* illum, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
+    DeviceGuard guard(c->device);
+    return run_forward(c, eps_r, sigma, wavelet, traces, illum, false, (cudaStream_t)stream);
+}
+
+int gf_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+               float* traces, float* illum, int store_mode, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (store_mode != GF_STORE_FULL) return fail(c, GF_EINVAL, "unknown store mode %d", store_mode);
+    if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
+    DeviceGuard guard(c->device);
+    return run_forward(c, eps_r, sigma, wavelet, traces, illum, true, (cudaStream_t)stream);
+}
+
+int gf_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* resid,
+               float* g_eps_r, float* g_sigma, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!eps_r || !sigma || !resid) return fail(c, GF_EINVAL, "NULL model or residual pointer");
+    if (!c->have_forward) return fail(c, GF_ESTATE, "gf_adjoint needs a stored gf_forward first");
+    DeviceGuard guard(c->device);
+    return run_adjoint(c, eps_r, sigma, resid, g_eps_r, g_sigma, (cudaStream_t)stream);
+}
+
+int gf_misfit_and_gradient(gf_ctx* c, const float* eps_r, const float* sigma,
+                           const float* wavelet, const float* observed, double* misfit,
+                           float* g_eps_r, float* g_sigma, float* traces, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!observed || !misfit) return fail(c, GF_EINVAL, "NULL observed or misfit pointer");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = run_forward(c, eps_r, sigma, wavelet, traces, nullptr, true, st);
+    if (rc) return rc;
+    const Layout L = layout_of(c, false);
+    float* tr = traces ? traces : (float*)(c->ws + L.traces);
+    float* resid = (float*)(c->ws + L.resid);
+    const long long count = (long long)c->nshots * c->g.nt * c->nrec;
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                return gf::launch_residual_misfit(tr, observed, resid, count,
+                                                  (double*)(c->ws + L.partial), kMisfitBlocks,
+                                                  (int*)(c->ws + L.status), st);
+            }),
+            "residual_misfit");
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                return gf::launch_finish_misfit((double*)(c->ws + L.partial), kMisfitBlocks, misfit, st);
+            }),
+            "finish_misfit");
+    return run_adjoint(c, eps_r, sigma, resid, g_eps_r, g_sigma, st);
+}
+
+int gf_status(gf_ctx* c, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!c->ws) return GF_OK;
+    DeviceGuard guard(c->device);
+    GF_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream), "synchronize");
+    int s = 0;
+    GF_CUDA(c, cudaMemcpy(&s, c->ws, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    GF_CUDA(c, cudaMemset(c->ws, 0, sizeof(int)), "clear status");
+    if (s & gf::kStatusBadModel)
+        return fail(c, GF_EINVAL, "model has eps_r < 1, sigma < 0 or non-finite values");
+    if (s & gf::kStatusNonFinite) return fail(c, GF_ENONFINITE, "non-finite traces or gradients");
+    return GF_OK;
+}
+
+long long gf_kernel_launches(const gf_ctx* c) { return c ? c->launches : 0; }
+
+int gf_profile(gf_ctx* c, int enable) {
+    if (!c) return GF_EINVAL;
+    DeviceGuard guard(c->device);
+    drop_profile(c);
+    c->profiling = enable != 0;
+    return GF_OK;
+}
+
+int gf_profile_read(gf_ctx* c, int kind, double* ms_total, long long* launches) {
+    if (!c || kind < 0 || kind > 2 || !ms_total || !launches) return GF_EINVAL;
+    DeviceGuard guard(c->device);
+    double total = 0.0;
+    auto& v = c->prof_ev[kind];
+    for (auto& pr : v) {
+        GF_CUDA(c, cudaEventSynchronize(pr.second), "event synchronize");
+        float ms = 0.f;
+        GF_CUDA(c, cudaEventElapsedTime(&ms, pr.first, pr.second), "event elapsed");
+        total += ms;
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    *ms_total = total;
+    *launches = (long long)v.size();
+    v.clear();
+    return GF_OK;
+}
+
+int gf_ricker(float* out, int nt, double dt, double f0, double amp) {
+    if (!out || nt < 0 || !(dt > 0) || !(f0 > 0)) return GF_EINVAL;
+    const double t0 = sqrt(2.0) / f0, pi = 3.14159265358979323846;
+    for (int n = 0; n < nt; ++n) {
+        const double tau = n * dt - t0;
+        const double z = pi * pi * f0 * f0 * tau * tau;
+        out[n] = (float)(amp * (1.0 - 2.0 * z) * exp(-z));
+    }
+    return GF_OK;
+}
+
+}  // extern "C"

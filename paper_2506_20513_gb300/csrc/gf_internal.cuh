@@ -1,0 +1,69 @@
+// gf_internal.cuh -- types shared by the host runtime and the sm_103a kernels of libgprfwi.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace gf {
+
+constexpr int kMaxSrc = 8;       // sources per shot
+constexpr int kThreads = 256;    // threads per tile CTA
+constexpr int kNumFields = 7;    // Ez, Hx, Hy, psiEx, psiEy, psiHx, psiHy (or their adjoints)
+
+// Device-status bits (OR-ed into the workspace status word by kernels).
+constexpr int kStatusBadModel = 1;   // eps_r < 1, sigma < 0 or non-finite model value
+constexpr int kStatusNonFinite = 2;  // non-finite trace or gradient
+
+// CPML profiles of one axis (FP32, uploaded once per context).  For a node at index i:
+//   a = 1 / (kappa * d), b = exp(-(sigma/kappa + alpha) dt / eps0),
+//   c = sigma (b - 1) / (sigma kappa + kappa^2 alpha) / d  (0 outside the CPML),
+// "E" arrays at integer nodes, "H" arrays at the half node i + 1/2.
+struct AxisProfile {
+    const float *aE, *bE, *cE, *aH, *bH, *cH;
+};
+
+// Everything one tile launch needs.  State arrays are packed as [kNumFields][nshots][N].
+struct TileParams {
+    int nx, ny, npml, nt, nshots, nsrc, nrec;
+    long long N;         // nx * ny
+    float dt_eps0;       // dt / eps0
+    float ch;            // dt / mu0
+    float src_scale;     // 1 / (dx dy)
+    float geps;          // eps0 / dt (zero-lag eps_r gradient scale)
+    AxisProfile px, py;
+    const float* eps_r;
+    const float* sigma;
+    const float* wavelet;   // [nshots][nsrc][nt]
+    const int* src_cell;    // [nshots][nsrc] linear cell index j*nx+i
+    const int* rec_cell;    // [nshots][nrec]
+    const float* st_in;     // time-stepping state at the start of the launch
+    float* st_out;          // state at the end of the launch (other ping-pong buffer)
+    float* hist;            // [nshots][nt][N]: slot n holds Ez^{n+1}; NULL = not stored
+    float* traces;          // forward: [nshots][nt][nrec] output
+    const float* resid;     // adjoint: [nshots][nt][nrec] trace cotangent
+    float* illum;           // forward: [nshots][N] accumulated (NULL = skip)
+    float* grad;            // adjoint: [2][nshots][N] accumulated
+    int n0, K;              // first time step of the launch, steps in the launch
+    int tile_w, tile_h;     // interior tile size; the staged tile has a K-cell halo
+    int tiles_x;
+    int* status;
+};
+
+// Host-side launchers (one per kernel family).
+cudaError_t launch_fwd_tile(const TileParams& p, int tiles, cudaStream_t st);
+cudaError_t launch_adj_tile(const TileParams& p, int tiles, cudaStream_t st);
+size_t fwd_tile_smem_bytes(int tile_w, int tile_h, int K);
+size_t adj_tile_smem_bytes(int tile_w, int tile_h, int K);
+cudaError_t configure_tile_kernels(size_t max_fwd, size_t max_adj);
+
+cudaError_t launch_check_model(const float* eps_r, const float* sigma, long long N, int* status,
+                               cudaStream_t st);
+cudaError_t launch_residual_misfit(const float* traces, const float* observed, float* resid,
+                                   long long count, double* partial, int nblocks, int* status,
+                                   cudaStream_t st);
+cudaError_t launch_finish_misfit(const double* partial, int nblocks, double* misfit,
+                                 cudaStream_t st);
+cudaError_t launch_sum_shots(const float* per_shot, int nshots, long long N, float* out,
+                             int* status, cudaStream_t st);
+
+}  // namespace gf

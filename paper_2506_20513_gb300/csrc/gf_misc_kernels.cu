@@ -1,0 +1,108 @@
+// gf_misc_kernels.cu -- small HBM-bound helpers: model validation, residual + L2 misfit
+// (Eq. objective), and the sum of per-shot gradients.
+#include "gf_internal.cuh"
+
+namespace gf {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+// eps_r >= 1, sigma >= 0 and both finite (the physical ranges the paper clamps to, Sec. 3.1).
+__global__ void check_model_kernel(const float* __restrict__ eps_r, const float* __restrict__ sigma,
+                                   long long N, int* status) {
+    int bad = 0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const float e = eps_r[c], s = sigma[c];
+        bad |= !(e >= 1.0f && s >= 0.0f && isfinite(e) && isfinite(s));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusBadModel);
+}
+
+// resid = traces - observed; per-block partial sums of resid^2 / 2 in FP64 (fixed order).
+__global__ void residual_misfit_kernel(const float* __restrict__ traces,
+                                       const float* __restrict__ observed, float* resid,
+                                       long long count, double* partial, int* status) {
+    __shared__ double red[kRedThreads];
+    double acc = 0.0;
+    int bad = 0;
+    for (long long k = blockIdx.x * (long long)kRedThreads + threadIdx.x; k < count;
+         k += (long long)gridDim.x * kRedThreads) {
+        const float r = traces[k] - observed[k];
+        resid[k] = r;
+        bad |= !isfinite(r);
+        acc += 0.5 * (double)r * (double)r;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
+}
+
+__global__ void finish_misfit_kernel(const double* partial, int nblocks, double* misfit) {
+    __shared__ double red[kRedThreads];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += kRedThreads) acc += partial[k];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *misfit = red[0];
+}
+
+// out[c] = sum_s per_shot[s][c] in shot order (deterministic), 4 cells per thread.
+__global__ void sum_shots_kernel(const float* __restrict__ per_shot, int nshots, long long N,
+                                 float* __restrict__ out, int* status) {
+    int bad = 0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int s = 0; s < nshots; ++s) acc += per_shot[(long long)s * N + c];
+        out[c] = acc;
+        bad |= !isfinite(acc);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusNonFinite);
+}
+
+int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_check_model(const float* eps_r, const float* sigma, long long N, int* status,
+                               cudaStream_t st) {
+    check_model_kernel<<<grid_for(N, 256), 256, 0, st>>>(eps_r, sigma, N, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_misfit(const float* traces, const float* observed, float* resid,
+                                   long long count, double* partial, int nblocks, int* status,
+                                   cudaStream_t st) {
+    residual_misfit_kernel<<<nblocks, kRedThreads, 0, st>>>(traces, observed, resid, count,
+                                                            partial, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_misfit(const double* partial, int nblocks, double* misfit,
+                                 cudaStream_t st) {
+    finish_misfit_kernel<<<1, kRedThreads, 0, st>>>(partial, nblocks, misfit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_shots(const float* per_shot, int nshots, long long N, float* out,
+                             int* status, cudaStream_t st) {
+    sum_shots_kernel<<<grid_for(N, 256), 256, 0, st>>>(per_shot, nshots, N, out, status);
+    return cudaGetLastError();
+}
+
+}  // namespace gf

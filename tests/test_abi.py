@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/gprfwi.h declares, and its host-side validation and helpers behave (no compute)."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2506_20513_gb300 import _lib, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gprfwi.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_20513_gb300 import build as B
+    return _lib.load(B.build_library())
+
+
+def header_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gf_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_what_binding_lists():
+    assert header_symbols() == sorted(_lib.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+    assert lib.gf_version().startswith(b"gprfwi-gb300")
+
+
+def _create(lib, g, src, rec, nshots=1):
+    gd = _lib.GridDesc(g.nx, g.ny, g.npml, g.nt, g.dx, g.dy, g.dt, g.pml_order, g.pml_sigma_max,
+                       g.pml_kappa_max, g.pml_alpha_max, g.pml_eps_ref)
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    rec = np.ascontiguousarray(rec, dtype=np.int32)
+    acq = _lib.Acquisition(nshots, src.shape[1], rec.shape[1],
+                           src.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                           rec.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    ctx = ctypes.c_void_p()
+    rc = lib.gf_create(ctypes.byref(ctx), ctypes.byref(gd), ctypes.byref(acq), 0)
+    if rc == 0:
+        lib.gf_destroy(ctx)
+    else:
+        assert not ctx.value
+    return rc
+
+
+def test_create_rejects_cfl_violation(lib):
+    g = W.GridSpec(nx=40, ny=30, npml=5, nt=10, dx=0.01, dy=0.01, dt=1.001 * W.cfl_dt_max(0.01, 0.01))
+    assert _create(lib, g, [[[10, 10]]], [[[20, 12]]]) == _lib.GF_ECFL
+
+
+@pytest.mark.parametrize("src,rec", [
+    ([[[0, 10]]], [[[20, 12]]]),     # source on the PEC ring
+    ([[[10, 10]]], [[[39, 12]]]),    # receiver on the PEC ring
+    ([[[10, 30]]], [[[20, 12]]]),    # outside the grid
+    ([[[10, 10]] * 9], [[[20, 12]]]),  # more than 8 sources per shot
+])
+def test_create_rejects_bad_geometry(lib, src, rec):
+    g = W.GridSpec(nx=40, ny=30, npml=5, nt=10, dx=0.01, dy=0.01, dt=0.9 * W.cfl_dt_max(0.01, 0.01))
+    assert _create(lib, g, src, rec) == _lib.GF_EINVAL
+
+
+def test_create_rejects_bad_grid(lib):
+    ok = dict(nx=40, ny=30, npml=5, nt=10, dx=0.01, dy=0.01, dt=1e-12)
+    for bad in (dict(nt=0), dict(npml=15), dict(dx=0.0), dict(nx=2), dict(pml_kappa_max=0.5)):
+        g = W.GridSpec(**{**ok, **bad})
+        assert _create(lib, g, [[[10, 10]]], [[[20, 12]]]) == _lib.GF_EINVAL, bad
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.gf_create(None, None, None, 0) == _lib.GF_EINVAL
+    assert lib.gf_forward_model(None, None, None, None, None, None, None) == _lib.GF_EINVAL
+    assert lib.gf_status(None, None) == _lib.GF_EINVAL
+    lib.gf_destroy(None)
+    assert lib.gf_last_error(None)
+
+
+def test_ricker_helper_closed_form(lib):
+    """The host helper follows the Ricker closed form: peak at t0 = sqrt(2)/f0, zeros at
+    t0 +- 1/(sqrt(2) pi f0)."""
+    from paper_2506_20513_gb300.fdtd import ricker
+    f0, dt, nt = 250e6, 1e-12, 20000
+    w = ricker(f0, dt, nt, amp=3.0)
+    t0 = math.sqrt(2) / f0
+    assert w[int(round(t0 / dt))] == pytest.approx(3.0, rel=1e-6)
+    nz = int((t0 + 1 / (math.sqrt(2) * math.pi * f0)) / dt)
+    assert w[nz] > 0 > w[nz + 1]
+    n = np.arange(nt) * dt - t0
+    z = (math.pi * f0 * n) ** 2
+    np.testing.assert_allclose(w, 3.0 * (1 - 2 * z) * np.exp(-z), rtol=0, atol=3e-6)

@@ -1,0 +1,247 @@
+"""FP32 CUDA path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (relative L2): traces <= 1e-4, g_eps_r and g_sigma <= 1e-3, misfit <= 1e-3.
+Cases span several tiles with ragged edge tiles, several time-block depths, several shots
+and sources, a CPML with kappa_max > 1, perfect-conductor cells, and the full-size
+32-shot 540x290 workload in the launch configuration the benchmark times (sampled).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2506_20513_gb300 import _lib, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TRACE_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20513_gb300 import build as B
+    B.build_library()
+    return torch.device("cuda", 0)
+
+
+def t32(a, dev):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+
+
+def wavelets(wl, nsrc=1):
+    w = O.ricker(wl.f0, wl.grid.dt, wl.grid.nt)
+    return np.ascontiguousarray(np.broadcast_to(w, (wl.nshots, nsrc, wl.grid.nt)))
+
+
+def gpu_gradient(wl, dev, obs, tiling=None, wav=None):
+    from paper_2506_20513_gb300 import FDTD, Tiling
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev, tiling=Tiling(*tiling) if tiling else None)
+    wav = wavelets(wl, wl.src.shape[1]) if wav is None else wav
+    J, ge, gs, tr = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev),
+                                           t32(wav, dev), t32(obs, dev), return_traces=True)
+    fd.status()
+    out = float(J.item()), ge.cpu().numpy(), gs.cpu().numpy(), tr.cpu().numpy()
+    fd.close()
+    return out
+
+
+def check_case(wl, dev, tiling=None, nsrc=1):
+    wav = wavelets(wl, nsrc)
+    obs = O.forward(wl.grid, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+    J, ge, gs, tr = gpu_gradient(wl, dev, obs, tiling, wav)
+    J64, ge64, gs64, tr64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, wav,
+                                                  wl.rec, obs, nthreads=4, return_traces=True)
+    assert rel(tr, tr64) <= TRACE_TOL
+    assert abs(J - J64) <= GRAD_TOL * J64
+    assert rel(ge, ge64) <= GRAD_TOL
+    assert rel(gs, gs64) <= GRAD_TOL
+    return J64
+
+
+def test_single_shot_disc(dev):
+    """100x100 (+10 CPML) disc model, one 200 MHz shot, 20 receivers, nt 600."""
+    wl = W.single_shot_disc()
+    check_case(wl, dev)
+
+
+@pytest.mark.parametrize("seed,tiling,kappa,pec", [
+    (1, None, 1.0, False),
+    (2, (8, 6, 3), 2.0, True),
+    (3, (13, 7, 4), 1.0, True),
+    (4, (10, 10, 1), 2.0, False),
+    (5, (64, 40, 8), 1.0, False),   # one tile covers the grid, K = 8
+    (6, (30, 9, 6), 1.0, False),
+])
+def test_small_random(dev, seed, tiling, kappa, pec):
+    wl = W.small_random(seed, nxp=46, nyp=27, npml=6, nt=150, nshots=3, nrec=9,
+                        kappa_max=kappa, with_pec=pec)
+    check_case(wl, dev, tiling)
+
+
+def test_multiple_sources_per_shot(dev):
+    wl = W.small_random(9, nxp=40, nyp=30, npml=5, nt=120, nshots=2, nrec=6)
+    rng = np.random.default_rng(0)
+    src = np.zeros((2, 3, 2), dtype=np.int32)
+    src[:, :, 0] = wl.grid.npml + rng.integers(1, 39, size=(2, 3))
+    src[:, :, 1] = wl.grid.npml + rng.integers(1, 29, size=(2, 3))
+    src[1, 2] = src[1, 1]  # two sources in one cell add up
+    wl.src = src
+    check_case(wl, dev, nsrc=3)
+
+
+def test_adjoint_of_arbitrary_cotangent(dev):
+    """gf_adjoint driven by a random trace cotangent equals the oracle's transpose."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(12, nxp=50, nyp=33, npml=7, nt=140, nshots=2, nrec=8, kappa_max=2.0)
+    g = wl.grid
+    wav = wavelets(wl)
+    r = np.random.default_rng(5).standard_normal((wl.nshots, g.nt, wl.nrec))
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    tr = fd.forward(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(wav, dev))
+    ge, gs = fd.adjoint(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(r, dev))
+    fd.status()
+    ge64 = np.zeros((g.ny, g.nx))
+    gs64 = np.zeros((g.ny, g.nx))
+    for s in range(wl.nshots):
+        fw = O.forward_shot(g, wl.eps_true, wl.sig_true, wl.src[s], wav[s], wl.rec[s], history=True)
+        assert rel(tr[s].cpu().numpy(), fw["traces"]) <= TRACE_TOL
+        a = O.adjoint_shot(g, wl.eps_true, wl.sig_true, wl.src[s], wl.rec[s], r[s], fw["ez_hist"])
+        ge64 += a["g_eps_r"]
+        gs64 += a["g_sigma"]
+    assert rel(ge.cpu().numpy(), ge64) <= GRAD_TOL
+    assert rel(gs.cpu().numpy(), gs64) <= GRAD_TOL
+
+
+def test_autograd_function_matches_misfit_and_gradient(dev):
+    from paper_2506_20513_gb300 import FDTD, FDTDFunction
+    wl = W.small_random(14, nxp=36, nyp=24, npml=5, nt=100, nshots=2, nrec=5)
+    wav = t32(wavelets(wl), dev)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    obs = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), wav)
+    e = t32(wl.eps_init, dev).requires_grad_()
+    s = t32(wl.sig_init, dev).requires_grad_()
+    d = FDTDFunction.apply(e, s, fd, wav)
+    loss = 0.5 * ((d - obs) ** 2).sum()
+    loss.backward()
+    J, ge, gs = fd.misfit_and_gradient(e.detach(), s.detach(), wav, obs)
+    fd.status()
+    assert abs(loss.item() - J.item()) <= 1e-5 * J.item()
+    assert rel(e.grad.cpu().numpy(), ge.cpu().numpy()) <= 1e-5
+    assert rel(s.grad.cpu().numpy(), gs.cpu().numpy()) <= 1e-5
+
+
+def test_illumination(dev):
+    """illum = sum over shots and n = 1..nt of Ez^n squared."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(15, nxp=30, nyp=22, npml=4, nt=90, nshots=2, nrec=4)
+    g = wl.grid
+    wav = wavelets(wl)
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    _, ill = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(wav, dev),
+                              illumination=True)
+    ref = np.zeros((g.ny, g.nx))
+    for s in range(wl.nshots):
+        h = O.forward_shot(g, wl.eps_true, wl.sig_true, wl.src[s], wav[s], wl.rec[s],
+                           history=True)["ez_hist"]
+        ref += (h[1:] ** 2).sum(axis=0)
+    assert rel(ill.cpu().numpy(), ref) <= 1e-4
+
+
+def test_single_step_and_short_runs(dev):
+    """nt = 1: the only trace sample is Ez^0 = 0 and the gradient vanishes; nt = 2 is
+    ragged against every time-block depth."""
+    from paper_2506_20513_gb300 import FDTD
+    for nt in (1, 2, 5):
+        wl = W.small_random(16, nxp=20, nyp=12, npml=3, nt=nt, nshots=1, nrec=3)
+        wav = np.ones((1, 1, nt))
+        fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+        obs = np.random.default_rng(nt).standard_normal((1, nt, 3))
+        J, ge, gs, tr = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev),
+                                               t32(wav, dev), t32(obs, dev), return_traces=True)
+        fd.status()
+        J64, ge64, gs64, tr64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src,
+                                                      wav, wl.rec, obs, return_traces=True)
+        assert np.all(tr[:, 0].cpu().numpy() == 0)
+        np.testing.assert_allclose(tr.cpu().numpy(), tr64, rtol=1e-4, atol=1e-6 * np.abs(tr64).max() + 1e-30)
+        assert abs(J.item() - J64) <= 1e-5 * J64
+        if nt == 1:
+            assert not ge.abs().max().item() and not gs.abs().max().item()
+        else:
+            assert rel(ge.cpu().numpy(), ge64) <= GRAD_TOL
+
+
+def test_invalid_model_is_reported(dev):
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(18, nxp=20, nyp=12, npml=3, nt=10, nshots=1, nrec=2)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    e = t32(wl.eps_true, dev)
+    e[5, 5] = 0.5
+    fd.forward_model(e, t32(wl.sig_true, dev), t32(np.ones(10), dev))
+    with pytest.raises(_lib.GfError) as ex:
+        fd.status()
+    assert ex.value.code == _lib.GF_EINVAL
+    fd.status()  # cleared after reading
+
+
+def test_adjoint_without_forward_is_rejected(dev):
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(19, nxp=20, nyp=12, npml=3, nt=10, nshots=1, nrec=2)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    with pytest.raises(_lib.GfError) as ex:
+        fd.adjoint(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(np.zeros((1, 10, 2)), dev))
+    assert ex.value.code == _lib.GF_ESTATE
+
+
+def test_host_tensors_end_to_end(dev):
+    """CPU tensors in, CPU results out (the end-to-end path the benchmark times)."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(20, nxp=30, nyp=20, npml=4, nt=80, nshots=2, nrec=4)
+    wav = wavelets(wl)
+    obs = O.forward(wl.grid, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    c = lambda a: torch.tensor(a, dtype=torch.float32).pin_memory()
+    J, ge, gs = fd.misfit_and_gradient(c(wl.eps_init), c(wl.sig_init), c(wav), c(obs))
+    assert not ge.is_cuda
+    J64, ge64, gs64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, wav,
+                                            wl.rec, obs)
+    assert rel(ge.numpy(), ge64) <= GRAD_TOL and rel(gs.numpy(), gs64) <= GRAD_TOL
+
+
+def test_full_size_multishot_sampled(dev):
+    """540x290 grid, 32 shots, nt 2000, 100 receivers, in the benchmark's launch
+    configuration: all 32 shots run on the GPU; the oracle recomputes the traces of two
+    sampled shots and the exact gradient of a two-shot subset at the same full size."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.multishot_layered()
+    g = wl.grid
+    wav = wavelets(wl)
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    tr = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(wav, dev)).cpu().numpy()
+    fd.status()
+    fd.close()
+    picks = [0, 17]
+    tr64 = O.forward(g, wl.eps_true, wl.sig_true, wl.src[picks], wav[picks], wl.rec[picks],
+                     nthreads=2)
+    for k, s in enumerate(picks):
+        assert rel(tr[s], tr64[k]) <= TRACE_TOL
+    sub = [0, 31]
+    wl2 = W.Workload(wl.name, g, wl.f0, wl.src[sub], wl.rec[sub], wl.eps_true, wl.sig_true,
+                     wl.eps_init, wl.sig_init)
+    obs = np.stack([tr64[0], O.forward(g, wl.eps_true, wl.sig_true, wl.src[[31]], wav[[31]],
+                                       wl.rec[[31]])[0]])
+    J, ge, gs, _ = gpu_gradient(wl2, dev, obs)
+    J64, ge64, gs64 = O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl2.src, wav[sub],
+                                            wl2.rec, obs, nthreads=2)
+    assert abs(J - J64) <= GRAD_TOL * J64
+    assert rel(ge, ge64) <= GRAD_TOL
+    assert rel(gs, gs64) <= GRAD_TOL
