@@ -32,12 +32,23 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdtd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+# A test may point the wrapper at a deliberately broken build of this same source (the
+# mutation test plants mistakes in a copy of fdtd_oracle.c to show the pins catch them).
+_OVERRIDE = os.environ.get("GPRFWI_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
+def build(force: bool = False, src: str = _SRC, out: str | None = None) -> str:
     """Compile ``fdtd_oracle.c`` with gcc into ``oracle/_build/liboracle.so``."""
+    if _OVERRIDE and out is None:
+        return _OVERRIDE
+    if out is not None:
+        tmp = out + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-o", tmp, src,
+                        "-lm"], check=True)
+        os.replace(tmp, out)
+        return out
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
