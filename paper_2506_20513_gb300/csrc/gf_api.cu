@@ -57,6 +57,16 @@ struct gf_ctx {
 
 namespace {
 
+// Message of the last gf_create failure on this thread (there is no context to hold it).
+thread_local char g_create_err[512] = "no error";
+
+void create_fail(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_create_err, sizeof(g_create_err), fmt, ap);
+    va_end(ap);
+}
+
 int fail(gf_ctx* c, int code, const char* fmt, ...) {
     if (c) {
         va_list ap;
@@ -333,40 +343,58 @@ extern "C" {
 
 const char* gf_version(void) { return "gprfwi-gb300 0.1 (sm_103a)"; }
 
-const char* gf_last_error(const gf_ctx* ctx) {
-    return ctx ? ctx->err : "no context (gf_create failed before allocating one)";
-}
+const char* gf_last_error(const gf_ctx* ctx) { return ctx ? ctx->err : g_create_err; }
 
 int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq, int device) {
     if (!out) return GF_EINVAL;
     *out = nullptr;
-    if (!grid || !acq || !acq->src_ij || !acq->rec_ij) return GF_EINVAL;
+    if (!grid || !acq || !acq->src_ij || !acq->rec_ij) {
+        create_fail("gf_create: NULL grid, acquisition or geometry pointer");
+        return GF_EINVAL;
+    }
     const gf_grid_desc& g = *grid;
     if (g.nx < 3 || g.ny < 3 || g.nt < 1 || g.npml < 0 || 2 * g.npml > g.nx - 2 ||
         2 * g.npml > g.ny - 2 || !(g.dx > 0) || !(g.dy > 0) || !(g.dt > 0) || g.pml_order < 0 ||
-        !(g.pml_kappa_max >= 1.0) || !(g.pml_alpha_max >= 0.0) || !(g.pml_eps_ref > 0.0))
+        !(g.pml_kappa_max >= 1.0) || !(g.pml_alpha_max >= 0.0) || !(g.pml_eps_ref > 0.0)) {
+        create_fail("gf_create: invalid grid description");
         return GF_EINVAL;
-    if ((long long)g.nx * g.ny > (1LL << 31) - 1) return GF_EINVAL;
+    }
+    if ((long long)g.nx * g.ny > (1LL << 31) - 1) {
+        create_fail("gf_create: grid too large");
+        return GF_EINVAL;
+    }
     // Eq. cfl with the vacuum speed of light (eps_r >= 1 everywhere).
     const double dtmax = 1.0 / (kC0 * sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy)));
-    if (g.dt > dtmax) return GF_ECFL;
-    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1)
+    if (g.dt > dtmax) {
+        create_fail("gf_create: dt = %g s exceeds the CFL bound %g s", g.dt, dtmax);
+        return GF_ECFL;
+    }
+    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1) {
+        create_fail("gf_create: need nshots >= 1, 1 <= nsrc <= %d, nrec >= 1", gf::kMaxSrc);
         return GF_EINVAL;
+    }
     auto inside = [&](const int32_t* ij) {
         return ij[0] >= 1 && ij[0] <= g.nx - 2 && ij[1] >= 1 && ij[1] <= g.ny - 2;
     };
     std::vector<int> src((size_t)acq->nshots * acq->nsrc), rec((size_t)acq->nshots * acq->nrec);
     for (size_t k = 0; k < src.size(); ++k) {
-        if (!inside(acq->src_ij + 2 * k)) return GF_EINVAL;
+        if (!inside(acq->src_ij + 2 * k)) {
+            create_fail("gf_create: source %zu outside 1..nx-2 x 1..ny-2", k);
+            return GF_EINVAL;
+        }
         src[k] = acq->src_ij[2 * k + 1] * g.nx + acq->src_ij[2 * k];
     }
     for (size_t k = 0; k < rec.size(); ++k) {
-        if (!inside(acq->rec_ij + 2 * k)) return GF_EINVAL;
+        if (!inside(acq->rec_ij + 2 * k)) {
+            create_fail("gf_create: receiver %zu outside 1..nx-2 x 1..ny-2", k);
+            return GF_EINVAL;
+        }
         rec[k] = acq->rec_ij[2 * k + 1] * g.nx + acq->rec_ij[2 * k];
     }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
+        create_fail("gf_create: CUDA device %d not available (%d devices)", device, ndev);
         return GF_ECUDA;
     }
     DeviceGuard guard(device);
@@ -379,7 +407,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->N = (long long)g.nx * g.ny;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    c->smem_optin = (size_t)optin;
+    c->smem_optin = (size_t)optin - gf::tile_static_smem_bytes();
     const int stride = std::max(g.nx, g.ny);
     std::vector<float> prof(12 * (size_t)stride, 0.f);
     axis_profiles(g, g.nx, g.dx, prof.data(), stride);
@@ -393,12 +421,10 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
         e = cudaMemcpy(c->d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_rec, rec.data(), rec.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        size_t mx = std::max(gf::fwd_tile_smem_bytes(1, 1, 1), (size_t)optin);
-        e = gf::configure_tile_kernels(mx, mx);
-    }
+    if (e == cudaSuccess) e = gf::configure_tile_kernels((size_t)optin);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        create_fail("gf_create: CUDA setup failed: %s", cudaGetErrorString(e));
         gf_destroy(c);
         return GF_ECUDA;
     }
@@ -407,6 +433,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
     if (check_tiling(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
+        create_fail("gf_create: %s", c->err);
         gf_destroy(c);
         return GF_EINVAL;
     }

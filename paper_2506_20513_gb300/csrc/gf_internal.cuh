@@ -54,7 +54,8 @@ cudaError_t launch_fwd_tile(const TileParams& p, int tiles, cudaStream_t st);
 cudaError_t launch_adj_tile(const TileParams& p, int tiles, cudaStream_t st);
 size_t fwd_tile_smem_bytes(int tile_w, int tile_h, int K);
 size_t adj_tile_smem_bytes(int tile_w, int tile_h, int K);
-cudaError_t configure_tile_kernels(size_t max_fwd, size_t max_adj);
+cudaError_t configure_tile_kernels(size_t optin);
+size_t tile_static_smem_bytes();
 
 cudaError_t launch_check_model(const float* eps_r, const float* sigma, long long N, int* status,
                                cudaStream_t st);

@@ -406,23 +406,27 @@ size_t adj_tile_smem_bytes(int tile_w, int tile_h, int K) {
     return sizeof(float) * (13 * EW * EH + 6 * (EW + EH) + 3 * (size_t)tile_w * tile_h);
 }
 
-cudaError_t configure_tile_kernels(size_t max_fwd, size_t max_adj) {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(fwd_tile_kernel<true, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_fwd)))
-        return e;
-    if ((e = cudaFuncSetAttribute(fwd_tile_kernel<true, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_fwd)))
-        return e;
-    if ((e = cudaFuncSetAttribute(fwd_tile_kernel<false, true>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_fwd)))
-        return e;
-    if ((e = cudaFuncSetAttribute(fwd_tile_kernel<false, false>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_fwd)))
-        return e;
-    return cudaFuncSetAttribute(adj_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)max_adj);
+// Allow each kernel the largest dynamic shared memory that fits beside its static shared
+// memory within the per-block opt-in limit `optin`.
+template <class Kern>
+static cudaError_t allow_smem(Kern k, size_t optin) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(optin - a.sharedSizeBytes));
 }
+
+cudaError_t configure_tile_kernels(size_t optin) {
+    cudaError_t e;
+    if ((e = allow_smem(fwd_tile_kernel<true, true>, optin))) return e;
+    if ((e = allow_smem(fwd_tile_kernel<true, false>, optin))) return e;
+    if ((e = allow_smem(fwd_tile_kernel<false, true>, optin))) return e;
+    if ((e = allow_smem(fwd_tile_kernel<false, false>, optin))) return e;
+    return allow_smem(adj_tile_kernel, optin);
+}
+
+size_t tile_static_smem_bytes() { return sizeof(int) * kMaxSrc; }
 
 cudaError_t launch_fwd_tile(const TileParams& p, int tiles, cudaStream_t st) {
     const dim3 grid(tiles, p.nshots), block(kTX, kTY);
