@@ -79,7 +79,7 @@ def test_single_shot_disc(dev):
     (2, (8, 6, 3), 2.0, True),
     (3, (13, 7, 4), 1.0, True),
     (4, (10, 10, 1), 2.0, False),
-    (5, (64, 40, 8), 1.0, False),   # one tile covers the grid, K = 8
+    (5, (58, 39, 4), 1.0, False),   # one tile covers the whole grid
     (6, (30, 9, 6), 1.0, False),
 ])
 def test_small_random(dev, seed, tiling, kappa, pec):
@@ -191,6 +191,16 @@ def test_invalid_model_is_reported(dev):
         fd.status()
     assert ex.value.code == _lib.GF_EINVAL
     fd.status()  # cleared after reading
+
+
+def test_oversized_tiling_is_rejected(dev):
+    """A tile whose shared-memory footprint cannot fit is refused, not run."""
+    from paper_2506_20513_gb300 import FDTD, Tiling
+    wl = W.small_random(22, nxp=20, nyp=12, npml=3, nt=10, nshots=1, nrec=2)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    with pytest.raises(_lib.GfError) as ex:
+        fd.set_tiling(Tiling(4096, 4096, 8))
+    assert ex.value.code == _lib.GF_EINVAL
 
 
 def test_adjoint_without_forward_is_rejected(dev):
