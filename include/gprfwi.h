@@ -106,8 +106,11 @@ int gf_workspace_size(const gf_ctx* ctx, int store_mode, int forward_only, size_
  * with cudaMalloc on first use (freed by gf_destroy).  ws == NULL reverts to that. */
 int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
 
-/* Time-blocking options: tile interior width/height in cells and time steps per launch
- * (0 = keep the current value).  Rejects shapes whose shared-memory footprint does not fit. */
+/* Time-blocking options: tile interior width/height in cells and time steps per launch K.
+ * The staged tile (interior + K cells of halo on each side) is at most 64 x 64 cells; K = 0
+ * keeps the current K, a tile size of 0 selects the largest that fits (64 - 2K).  Default:
+ * 48 x 48 interior, K = 8.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
+ * not fit or when more than 512 receivers of one shot would fall in one staged tile. */
 int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
 
 /* forward_model(eps_r, sigma, sources, receivers) -> traces (Algorithm 1 for all shots).

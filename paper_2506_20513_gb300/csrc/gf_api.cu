@@ -45,7 +45,8 @@ struct gf_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
-    int tile_w = 56, tile_h = 24, K = 4;
+    int tile_w = 48, tile_h = 48, K = 8;
+    std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     size_t smem_optin = 0;
     long long launches = 0;
     bool profiling = false;
@@ -243,6 +244,8 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.ch = (float)(c->g.dt / kMu0);
     p.src_scale = (float)(1.0 / (c->g.dx * c->g.dy));
     p.geps = (float)(kEps0 / c->g.dt);
+    p.rdx = (float)(1.0 / c->g.dx);
+    p.rdy = (float)(1.0 / c->g.dy);
     p.px = c->px;
     p.py = c->py;
     p.src_cell = c->d_src;
@@ -327,13 +330,45 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     return GF_OK;
 }
 
+// Largest number of one shot's receivers inside one CTA's staged window (interior plus the
+// K-cell halo) for the given tiling; the kernels list at most gf::kMaxCtaRec per CTA.
+int max_receivers_per_window(const gf_ctx* c, int tw, int th, int K) {
+    const int nx = c->g.nx, ny = c->g.ny;
+    const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th;
+    std::vector<int> count((size_t)ntx * nty);
+    int worst = 0;
+    for (int s = 0; s < c->nshots; ++s) {
+        std::fill(count.begin(), count.end(), 0);
+        for (int r = 0; r < c->nrec; ++r) {
+            const int cell = c->h_rec[(size_t)s * c->nrec + r];
+            const int i = cell % nx, j = cell / nx;
+            // tiles t whose window [t*tw - K, t*tw - K + tw + 2K) contains i
+            const int tx0 = std::max(0, (i - tw - K) / tw), tx1 = std::min(ntx - 1, (i + K) / tw);
+            const int ty0 = std::max(0, (j - th - K) / th), ty1 = std::min(nty - 1, (j + K) / th);
+            for (int ty = ty0; ty <= ty1; ++ty)
+                for (int tx = tx0; tx <= tx1; ++tx)
+                    if (i >= tx * tw - K && i < tx * tw + tw + K && j >= ty * th - K &&
+                        j < ty * th + th + K)
+                        worst = std::max(worst, ++count[(size_t)ty * ntx + tx]);
+        }
+    }
+    return worst;
+}
+
 int check_tiling(gf_ctx* c, int tw, int th, int K) {
-    if (tw < 1 || th < 1 || K < 1 || K > 64)
-        return fail(c, GF_EINVAL, "tile %dx%d, K=%d out of range", tw, th, K);
-    const size_t f = gf::fwd_tile_smem_bytes(tw, th, K), a = gf::adj_tile_smem_bytes(tw, th, K);
-    if (std::max(f, a) > c->smem_optin)
-        return fail(c, GF_EINVAL, "tile %dx%d with K=%d needs %zu bytes of shared memory (> %zu)",
-                    tw, th, K, std::max(f, a), c->smem_optin);
+    const int E = gf::max_tile_extent();
+    if (K < 1 || tw < 1 || th < 1 || tw + 2 * K > E || th + 2 * K > E)
+        return fail(c, GF_EINVAL,
+                    "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d per side",
+                    tw, th, K, E);
+    const size_t need = std::max(gf::fwd_tile_smem_bytes(), gf::adj_tile_smem_bytes());
+    if (need > c->smem_optin)
+        return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)", need,
+                    c->smem_optin);
+    const int worst = max_receivers_per_window(c, tw, th, K);
+    if (worst > gf::kMaxCtaRec)
+        return fail(c, GF_EINVAL, "%d receivers of one shot fall in one tile window (max %d); "
+                    "use a smaller tile", worst, gf::kMaxCtaRec);
     return GF_OK;
 }
 
@@ -405,6 +440,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->nrec = acq->nrec;
     c->device = device;
     c->N = (long long)g.nx * g.ny;
+    c->h_rec = rec;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)optin - gf::tile_static_smem_bytes();
@@ -479,8 +515,9 @@ int gf_set_workspace(gf_ctx* c, void* ws, size_t bytes) {
 
 int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     if (!c) return GF_EINVAL;
-    const int tw = tile_w > 0 ? tile_w : c->tile_w, th = tile_h > 0 ? tile_h : c->tile_h;
+    const int E = gf::max_tile_extent();
     const int k = K > 0 ? K : c->K;
+    const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : E - 2 * k;
     int rc = check_tiling(c, tw, th, k);
     if (rc) return rc;
     c->tile_w = tw;

@@ -6,9 +6,9 @@
 
 namespace gf {
 
-constexpr int kMaxSrc = 8;       // sources per shot
-constexpr int kThreads = 256;    // threads per tile CTA
-constexpr int kNumFields = 7;    // Ez, Hx, Hy, psiEx, psiEy, psiHx, psiHy (or their adjoints)
+constexpr int kMaxSrc = 8;        // sources per shot
+constexpr int kMaxCtaRec = 512;   // receivers listed per CTA (checked on the host)
+constexpr int kNumFields = 7;     // Ez, Hx, Hy, psiEx, psiEy, psiHx, psiHy (or their adjoints)
 
 // Device-status bits (OR-ed into the workspace status word by kernels).
 constexpr int kStatusBadModel = 1;   // eps_r < 1, sigma < 0 or non-finite model value
@@ -30,6 +30,7 @@ struct TileParams {
     float ch;            // dt / mu0
     float src_scale;     // 1 / (dx dy)
     float geps;          // eps0 / dt (zero-lag eps_r gradient scale)
+    float rdx, rdy;      // 1 / dx, 1 / dy
     AxisProfile px, py;
     const float* eps_r;
     const float* sigma;
@@ -52,8 +53,9 @@ struct TileParams {
 // Host-side launchers (one per kernel family).
 cudaError_t launch_fwd_tile(const TileParams& p, int tiles, cudaStream_t st);
 cudaError_t launch_adj_tile(const TileParams& p, int tiles, cudaStream_t st);
-size_t fwd_tile_smem_bytes(int tile_w, int tile_h, int K);
-size_t adj_tile_smem_bytes(int tile_w, int tile_h, int K);
+int max_tile_extent();              // staged tile (interior + 2K halo) limit per side
+size_t fwd_tile_smem_bytes();
+size_t adj_tile_smem_bytes();
 cudaError_t configure_tile_kernels(size_t optin);
 size_t tile_static_smem_bytes();
 
