@@ -273,7 +273,6 @@ def ours(args):
     value = cells / (ms / 1e3) / 1e9
 
     # roofline of the dominant tile kernel (its own launches, CUDA events on its stream)
-    K = tiling.steps if tiling and tiling.steps else 4
     dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
     tot_ms, cnt = prof[dom]
     nt = g.nt
@@ -331,7 +330,7 @@ def ours(args):
                        "shots_per_gpu": wl.nshots, "nt": g.nt, "nrec": wl.nrec,
                        "cell_updates_per_step": wl.cell_updates() * world,
                        "s_per_gradient": ms / args.steps / 1e3,
-                       "tiling": args.tile or "default 56,24,4",
+                       "tiling": args.tile or "default 48,48,8",
                        "l2": "inputs larger than L2: each step streams the "
                              f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
                              "history through HBM",

@@ -79,7 +79,7 @@ def test_single_shot_disc(dev):
     (2, (8, 6, 3), 2.0, True),
     (3, (13, 7, 4), 1.0, True),
     (4, (10, 10, 1), 2.0, False),
-    (5, (58, 39, 4), 1.0, False),   # one tile covers the whole grid
+    (5, (58, 39, 3), 1.0, False),   # one tile covers the whole grid
     (6, (30, 9, 6), 1.0, False),
 ])
 def test_small_random(dev, seed, tiling, kappa, pec):
