@@ -110,8 +110,16 @@ int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
  * The staged tile (interior + K cells of halo on each side) is at most 64 x 64 cells; K = 0
  * keeps the current K, a tile size of 0 selects the largest that fits (64 - 2K).  Default:
  * 48 x 48 interior, K = 8.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
- * not fit or when more than 512 receivers of one shot would fall in one staged tile. */
+ * not fit. */
 int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
+
+/* Tile-kernel variant: 0 = four rows per thread (1024-thread CTAs, default), 1 = eight rows
+ * per thread (512-thread CTAs).  Both compute the same result. */
+int gf_set_variant(gf_ctx* ctx, int variant);
+
+/* Current tiling and variant (for autotuners). */
+int gf_get_tiling(const gf_ctx* ctx, int* tile_w, int* tile_h, int* steps_per_launch,
+                  int* variant);
 
 /* forward_model(eps_r, sigma, sources, receivers) -> traces (Algorithm 1 for all shots).
  * traces: [nshots][nt][nrec] written.  illum: optional [ny][nx], receives the illumination

@@ -32,7 +32,7 @@ ERROR_NAMES = {
 # Every entry point declared in include/gprfwi.h.
 EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
-    "gf_set_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
+    "gf_set_tiling", "gf_set_variant", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_profile",
     "gf_profile_read",
 )
@@ -88,6 +88,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_workspace_size": (i, [vp, i, i, P(sz)]),
             "gf_set_workspace": (i, [vp, vp, sz]),
             "gf_set_tiling": (i, [vp, i, i, i]),
+            "gf_set_variant": (i, [vp, i]),
+            "gf_get_tiling": (i, [vp, P(i), P(i), P(i), P(i)]),
             "gf_forward_model": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "gf_forward": (i, [vp, vp, vp, vp, vp, vp, i, vp]),
             "gf_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),

@@ -45,8 +45,10 @@ struct gf_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
-    int tile_w = 48, tile_h = 48, K = 8;
+    int tile_w = 48, tile_h = 48, K = 8, variant = 0;
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
+    int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
+    int* d_tile_rec_idx = nullptr;
     size_t smem_optin = 0;
     long long launches = 0;
     bool profiling = false;
@@ -254,12 +256,12 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.tile_w = c->tile_w;
     p.tile_h = c->tile_h;
     p.tiles_x = (c->g.nx + c->tile_w - 1) / c->tile_w;
+    p.ntiles = p.tiles_x * ((c->g.ny + c->tile_h - 1) / c->tile_h);
+    p.tile_rec_off = c->d_tile_rec_off;
+    p.tile_rec_idx = c->d_tile_rec_idx;
     return p;
 }
 
-int tiles_of(const gf_ctx* c) {
-    return ((c->g.nx + c->tile_w - 1) / c->tile_w) * ((c->g.ny + c->tile_h - 1) / c->tile_h);
-}
 
 int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
                 float* traces, float* illum, bool store, cudaStream_t st) {
@@ -279,14 +281,13 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear state");
     if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, field, st), "clear illumination");
     GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_check_model(eps_r, sigma, c->N, p.status, st); }), "check_model");
-    const int tiles = tiles_of(c);
     int cur = 0;
     for (int n0 = 0; n0 < c->g.nt; n0 += c->K) {
         p.n0 = n0;
         p.K = std::min(c->K, c->g.nt - n0);
         p.st_in = st_buf[cur];
         p.st_out = st_buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, tiles, st); }), "fwd_tile");
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
         cur ^= 1;
     }
     if (illum)
@@ -308,7 +309,6 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     float* st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
     GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear adjoint state");
     GF_CUDA(c, cudaMemsetAsync(p.grad, 0, 2 * field, st), "clear gradients");
-    const int tiles = tiles_of(c);
     int cur = 0;
     for (int n1 = c->g.nt - 1; n1 >= 0; n1 -= c->K) {
         const int k = std::min(c->K, n1 + 1);
@@ -316,7 +316,7 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         p.K = k;
         p.st_in = st_buf[cur];
         p.st_out = st_buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, tiles, st); }), "adj_tile");
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
         cur ^= 1;
     }
     if (g_eps_r)
@@ -330,45 +330,61 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     return GF_OK;
 }
 
-// Largest number of one shot's receivers inside one CTA's staged window (interior plus the
-// K-cell halo) for the given tiling; the kernels list at most gf::kMaxCtaRec per CTA.
-int max_receivers_per_window(const gf_ctx* c, int tw, int th, int K) {
+// Receivers of every (shot, tile) staged window (interior plus a K-cell halo) as a CSR list
+// in receiver-index order, uploaded for the tile kernels; rebuilt whenever the tiling changes.
+int build_receiver_lists(gf_ctx* c, int tw, int th, int K) {
     const int nx = c->g.nx, ny = c->g.ny;
-    const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th;
-    std::vector<int> count((size_t)ntx * nty);
-    int worst = 0;
-    for (int s = 0; s < c->nshots; ++s) {
-        std::fill(count.begin(), count.end(), 0);
+    const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th, nt_ = ntx * nty;
+    std::vector<std::vector<int>> lists((size_t)c->nshots * nt_);
+    for (int s = 0; s < c->nshots; ++s)
         for (int r = 0; r < c->nrec; ++r) {
             const int cell = c->h_rec[(size_t)s * c->nrec + r];
             const int i = cell % nx, j = cell / nx;
-            // tiles t whose window [t*tw - K, t*tw - K + tw + 2K) contains i
-            const int tx0 = std::max(0, (i - tw - K) / tw), tx1 = std::min(ntx - 1, (i + K) / tw);
-            const int ty0 = std::max(0, (j - th - K) / th), ty1 = std::min(nty - 1, (j + K) / th);
+            const int tx0 = std::max(0, (i - K) / tw - 1), tx1 = std::min(ntx - 1, (i + K) / tw);
+            const int ty0 = std::max(0, (j - K) / th - 1), ty1 = std::min(nty - 1, (j + K) / th);
             for (int ty = ty0; ty <= ty1; ++ty)
                 for (int tx = tx0; tx <= tx1; ++tx)
                     if (i >= tx * tw - K && i < tx * tw + tw + K && j >= ty * th - K &&
                         j < ty * th + th + K)
-                        worst = std::max(worst, ++count[(size_t)ty * ntx + tx]);
+                        lists[(size_t)s * nt_ + ty * ntx + tx].push_back(r);
         }
+    std::vector<int> off(lists.size() + 1, 0), idx;
+    for (size_t k = 0; k < lists.size(); ++k) {
+        off[k + 1] = off[k] + (int)lists[k].size();
+        idx.insert(idx.end(), lists[k].begin(), lists[k].end());
     }
-    return worst;
+    if (idx.empty()) idx.push_back(0);
+    int *d_off = nullptr, *d_idx = nullptr;
+    cudaError_t e = cudaMalloc(&d_off, off.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d_idx, idx.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d_off);
+        cudaFree(d_idx);
+        return cuda_fail(c, e, "receiver lists");
+    }
+    cudaFree(c->d_tile_rec_off);
+    cudaFree(c->d_tile_rec_idx);
+    c->d_tile_rec_off = d_off;
+    c->d_tile_rec_idx = d_idx;
+    return GF_OK;
 }
 
-int check_tiling(gf_ctx* c, int tw, int th, int K) {
+int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
     const int E = gf::max_tile_extent();
     if (K < 1 || tw < 1 || th < 1 || tw + 2 * K > E || th + 2 * K > E)
         return fail(c, GF_EINVAL,
                     "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d per side",
                     tw, th, K, E);
-    const size_t need = std::max(gf::fwd_tile_smem_bytes(), gf::adj_tile_smem_bytes());
-    if (need > c->smem_optin)
-        return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)", need,
-                    c->smem_optin);
-    const int worst = max_receivers_per_window(c, tw, th, K);
-    if (worst > gf::kMaxCtaRec)
-        return fail(c, GF_EINVAL, "%d receivers of one shot fall in one tile window (max %d); "
-                    "use a smaller tile", worst, gf::kMaxCtaRec);
+    if (variant < 0 || variant >= gf::num_tile_variants())
+        return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
+    if (gf::tile_smem_bytes(variant) > c->smem_optin)
+        return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)",
+                    gf::tile_smem_bytes(variant), c->smem_optin);
     return GF_OK;
 }
 
@@ -443,7 +459,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->h_rec = rec;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    c->smem_optin = (size_t)optin - gf::tile_static_smem_bytes();
+    c->smem_optin = (size_t)optin;
     const int stride = std::max(g.nx, g.ny);
     std::vector<float> prof(12 * (size_t)stride, 0.f);
     axis_profiles(g, g.nx, g.dx, prof.data(), stride);
@@ -468,7 +484,8 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     const size_t S = stride;
     c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
-    if (check_tiling(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
+    if (check_tiling(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK ||
+        build_receiver_lists(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
         create_fail("gf_create: %s", c->err);
         gf_destroy(c);
         return GF_EINVAL;
@@ -486,6 +503,8 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_prof);
     cudaFree(c->d_src);
     cudaFree(c->d_rec);
+    cudaFree(c->d_tile_rec_off);
+    cudaFree(c->d_tile_rec_idx);
     delete c;
 }
 
@@ -518,11 +537,31 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     const int E = gf::max_tile_extent();
     const int k = K > 0 ? K : c->K;
     const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : E - 2 * k;
-    int rc = check_tiling(c, tw, th, k);
+    int rc = check_tiling(c, tw, th, k, c->variant);
+    if (rc) return rc;
+    DeviceGuard guard(c->device);
+    rc = build_receiver_lists(c, tw, th, k);
     if (rc) return rc;
     c->tile_w = tw;
     c->tile_h = th;
     c->K = k;
+    return GF_OK;
+}
+
+int gf_set_variant(gf_ctx* c, int variant) {
+    if (!c) return GF_EINVAL;
+    int rc = check_tiling(c, c->tile_w, c->tile_h, c->K, variant);
+    if (rc) return rc;
+    c->variant = variant;
+    return GF_OK;
+}
+
+int gf_get_tiling(const gf_ctx* c, int* tile_w, int* tile_h, int* K, int* variant) {
+    if (!c || !tile_w || !tile_h || !K || !variant) return GF_EINVAL;
+    *tile_w = c->tile_w;
+    *tile_h = c->tile_h;
+    *K = c->K;
+    *variant = c->variant;
     return GF_OK;
 }
 

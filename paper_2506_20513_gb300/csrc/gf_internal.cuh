@@ -7,7 +7,6 @@
 namespace gf {
 
 constexpr int kMaxSrc = 8;        // sources per shot
-constexpr int kMaxCtaRec = 512;   // receivers listed per CTA (checked on the host)
 constexpr int kNumFields = 7;     // Ez, Hx, Hy, psiEx, psiEy, psiHx, psiHy (or their adjoints)
 
 // Device-status bits (OR-ed into the workspace status word by kernels).
@@ -46,18 +45,22 @@ struct TileParams {
     float* grad;            // adjoint: [2][nshots][N] accumulated
     int n0, K;              // first time step of the launch, steps in the launch
     int tile_w, tile_h;     // interior tile size; the staged tile has a K-cell halo
-    int tiles_x;
+    int tiles_x, ntiles;
+    // receivers of each (shot, tile) staged window, host-built CSR: entries
+    // tile_rec_idx[off[s*ntiles+t] .. off[s*ntiles+t+1]) are receiver indices in index order
+    const int* tile_rec_off;
+    const int* tile_rec_idx;
     int* status;
 };
 
 // Host-side launchers (one per kernel family).
-cudaError_t launch_fwd_tile(const TileParams& p, int tiles, cudaStream_t st);
-cudaError_t launch_adj_tile(const TileParams& p, int tiles, cudaStream_t st);
+// Tile-kernel variants: 0 = 4 rows per thread (1024 threads), 1 = 8 rows (512 threads).
+cudaError_t launch_fwd_tile(const TileParams& p, int variant, cudaStream_t st);
+cudaError_t launch_adj_tile(const TileParams& p, int variant, cudaStream_t st);
 int max_tile_extent();              // staged tile (interior + 2K halo) limit per side
-size_t fwd_tile_smem_bytes();
-size_t adj_tile_smem_bytes();
+int num_tile_variants();
+size_t tile_smem_bytes(int variant);
 cudaError_t configure_tile_kernels(size_t optin);
-size_t tile_static_smem_bytes();
 
 cudaError_t launch_check_model(const float* eps_r, const float* sigma, long long N, int* status,
                                cudaStream_t st);

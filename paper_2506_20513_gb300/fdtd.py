@@ -50,9 +50,12 @@ def _dev_f32(t: torch.Tensor, shape, name: str, device: torch.device) -> torch.T
 
 @dataclass
 class Tiling:
+    """Interior tile size and time steps per launch (0 = library default / largest that
+    fits) and the tile-kernel variant (None = keep)."""
     tile_w: int = 0
     tile_h: int = 0
     steps: int = 0
+    variant: int | None = None
 
 
 class FDTD:
@@ -103,7 +106,14 @@ class FDTD:
             pass
 
     def set_tiling(self, t: Tiling):
+        if t.variant is not None:
+            _lib.check(self.lib, self.ctx, self.lib.gf_set_variant(self.ctx, t.variant))
         _lib.check(self.lib, self.ctx, self.lib.gf_set_tiling(self.ctx, t.tile_w, t.tile_h, t.steps))
+
+    def tiling(self) -> Tiling:
+        v = [ctypes.c_int() for _ in range(4)]
+        _lib.check(self.lib, self.ctx, self.lib.gf_get_tiling(self.ctx, *[ctypes.byref(x) for x in v]))
+        return Tiling(*[x.value for x in v])
 
     def workspace_bytes(self, forward_only: bool = False) -> int:
         n = ctypes.c_size_t()

@@ -74,6 +74,7 @@ def test_single_shot_disc(dev):
     check_case(wl, dev)
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("seed,tiling,kappa,pec", [
     (1, None, 1.0, False),
     (2, (8, 6, 3), 2.0, True),
@@ -82,10 +83,19 @@ def test_single_shot_disc(dev):
     (5, (58, 39, 3), 1.0, False),   # one tile covers the whole grid
     (6, (30, 9, 6), 1.0, False),
 ])
-def test_small_random(dev, seed, tiling, kappa, pec):
+def test_small_random(dev, seed, tiling, kappa, pec, variant):
     wl = W.small_random(seed, nxp=46, nyp=27, npml=6, nt=150, nshots=3, nrec=9,
                         kappa_max=kappa, with_pec=pec)
-    check_case(wl, dev, tiling)
+    check_case(wl, dev, (tiling or (0, 0, 0)) + (variant,))
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("npml,tiling", [(0, (16, 16, 4)), (3, (20, 18, 5)), (8, (40, 40, 12))])
+def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
+    """Large grids with thin (or no) CPML: most tiles take the body without CPML memories."""
+    wl = W.small_random(30 + npml, nxp=110, nyp=84, npml=npml, nt=280, nshots=2, nrec=8,
+                        with_pec=True)
+    check_case(wl, dev, tiling + (variant,))
 
 
 def test_multiple_sources_per_shot(dev):
@@ -176,8 +186,10 @@ def test_single_step_and_short_runs(dev):
         assert abs(J.item() - J64) <= 1e-5 * J64
         if nt == 1:
             assert not ge.abs().max().item() and not gs.abs().max().item()
-        else:
-            assert rel(ge.cpu().numpy(), ge64) <= GRAD_TOL
+        # for nt = 2 the exact gradient vanishes (Ez^1 is nonzero only at the source)
+        for a, b in ((ge, ge64), (gs, gs64)):
+            a = a.cpu().numpy()
+            np.testing.assert_allclose(a, b, rtol=GRAD_TOL, atol=GRAD_TOL * np.abs(b).max() + 1e-30)
 
 
 def test_invalid_model_is_reported(dev):
