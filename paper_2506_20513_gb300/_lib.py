@@ -34,7 +34,7 @@ EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
     "gf_set_tiling", "gf_set_variant", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_profile",
-    "gf_profile_read",
+    "gf_profile_read", "gf_forward_model_noalloc",
 )
 GF_KERNEL_FWD = 0
 GF_KERNEL_ADJ = 1
@@ -101,6 +101,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_kernel_launches": (ctypes.c_longlong, [vp]),
             "gf_profile": (i, [vp, i]),
             "gf_profile_read": (i, [vp, i, P(ctypes.c_double), P(ctypes.c_longlong)]),
+            "gf_forward_model_noalloc": (i, [P(GridDesc), P(Acquisition), i, vp, vp, vp, vp,
+                                             vp]),
         }
         for name, (res, args) in decl.items():
             f = getattr(lib, name)

@@ -672,3 +672,13 @@ int gf_ricker(float* out, int nt, double dt, double f0, double amp) {
 }
 
 }  // extern "C"
+
+// Helpers shared with the allocation-free entry point (gf_noalloc.cu).
+namespace gf {
+void host_axis_profiles(const gf_grid_desc& g, int n, double d, float* out, int stride) {
+    axis_profiles(g, n, d, out, stride);
+}
+void set_error_without_context(const char* msg) {
+    snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
+}
+}  // namespace gf

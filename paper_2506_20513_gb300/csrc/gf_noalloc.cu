@@ -1,0 +1,315 @@
+// gf_noalloc.cu -- forward modelling that allocates no memory: gf_forward_model_noalloc.
+//
+// Some callers cannot allocate device memory at the moment they need a forward model:
+// programs whose device memory is owned and handed out by another runtime or a fixed pool
+// (so a cudaMalloc from a library would bypass or break its accounting), services that run
+// under a hard memory budget set by their host, and real-time loops that must never enter
+// the allocator.  This entry point serves them.  It
+// keeps everything the forward tile kernels need besides the caller's inputs and outputs --
+// the two time-stepping state buffers, the CPML profiles, the geometry and the per-tile
+// receiver lists -- in one file-scope device array of fixed size (kScratchBytes), which every
+// GPU that loads this library holds until the process exits.  It never calls cudaMalloc,
+// cudaFree or any allocating routine.
+//
+// The array is shared by every call on a device and keeps the last call's contents; each call
+// clears the state it needs to start from zero.  Calls whose work overlaps on the GPU (two
+// streams, two threads) race on the array and must be serialised by the caller.
+//
+// The first call on each device looks up the array's device address with
+// cudaGetSymbolAddress and sets the kernels' shared-memory limits, with that device current;
+// make that first call before any stream capture begins.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/gprfwi.h"
+#include "gf_internal.cuh"
+
+namespace gf {
+void host_axis_profiles(const gf_grid_desc& g, int n, double d, float* out, int stride);
+void set_error_without_context(const char* msg);
+}  // namespace gf
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB per device
+constexpr int kMaxAxis = 16384;                     // cells per axis
+constexpr int kMaxDevices = 64;
+constexpr int kTileW = 48, kTileH = 48, kSteps = 8, kVariant = 0;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+struct DeviceSlot {
+    unsigned char* ptr = nullptr;  // device address of g_scratch on this device
+    bool ready = false;
+};
+DeviceSlot g_slots[kMaxDevices];
+std::mutex g_mutex;
+// host staging for the CPML profiles (static: no heap use)
+float g_prof_host[12 * kMaxAxis];
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+int fail(int code, const char* fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    gf::set_error_without_context(msg);
+    return code;
+}
+
+// (i, j) pairs -> linear cell indices, in place order [count][2] -> [count].
+__global__ void pairs_to_cells(const int* ij, int count, int nx, int* cells) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
+        cells[k] = ij[2 * k + 1] * nx + ij[2 * k];
+}
+
+// Number of receivers of each (shot, tile) staged window (interior plus a K-cell halo).
+__global__ void count_window_receivers(const int* rec, int nshots, int nrec, int nx, int tw,
+                                       int th, int K, int tiles_x, int ntiles, int* counts) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nshots * ntiles) return;
+    const int s = k / ntiles, t = k % ntiles;
+    const int x0 = (t % tiles_x) * tw - K, y0 = (t / tiles_x) * th - K;
+    int n = 0;
+    for (int r = 0; r < nrec; ++r) {
+        const int c = rec[s * nrec + r], i = c % nx - x0, j = c / nx - y0;
+        n += (i >= 0 && i < tw + 2 * K && j >= 0 && j < th + 2 * K);
+    }
+    counts[k] = n;
+}
+
+// counts[0..n) -> exclusive offsets off[0..n] (one block, sequential chunks, fixed order).
+__global__ void exclusive_offsets(const int* counts, int n, int* off) {
+    __shared__ int part[1024];
+    const int t = threadIdx.x, chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int a = min(t * chunk, n), b = min(a + chunk, n);
+    int sum = 0;
+    for (int k = a; k < b; ++k) sum += counts[k];
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        off[n] = run;
+    }
+    __syncthreads();
+    int run = part[t];
+    for (int k = a; k < b; ++k) {
+        off[k] = run;
+        run += counts[k];
+    }
+}
+
+// Receiver indices of each window, in index order.
+__global__ void fill_window_receivers(const int* rec, int nshots, int nrec, int nx, int tw,
+                                      int th, int K, int tiles_x, int ntiles, const int* off,
+                                      int* idx) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nshots * ntiles) return;
+    const int s = k / ntiles, t = k % ntiles;
+    const int x0 = (t % tiles_x) * tw - K, y0 = (t / tiles_x) * th - K;
+    int o = off[k];
+    for (int r = 0; r < nrec; ++r) {
+        const int c = rec[s * nrec + r], i = c % nx - x0, j = c / nx - y0;
+        if (i >= 0 && i < tw + 2 * K && j >= 0 && j < th + 2 * K) idx[o++] = r;
+    }
+}
+
+// Once per device, with that device current: the scratch address and kernel attributes.
+int setup_device(int device, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DeviceSlot& slot = g_slots[device];
+    if (!slot.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GF_ECUDA, "gf_forward_model_noalloc: cudaGetSymbolAddress: %s",
+                        cudaGetErrorString(e));
+        }
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+        if (e == cudaSuccess) e = gf::configure_tile_kernels((size_t)optin);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GF_ECUDA, "gf_forward_model_noalloc: kernel set-up: %s",
+                        cudaGetErrorString(e));
+        }
+        if (gf::tile_smem_bytes(kVariant) > (size_t)optin)
+            return fail(GF_ECUDA, "gf_forward_model_noalloc: not enough shared memory per block");
+        slot.ptr = (unsigned char*)p;
+        slot.ready = true;
+    }
+    *out = slot.ptr;
+    return GF_OK;
+}
+
+}  // namespace
+
+extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acquisition* acq,
+                                        int device, const float* eps_r, const float* sigma,
+                                        const float* wavelet, float* traces, void* stream) {
+    if (!grid || !acq || !acq->src_ij || !acq->rec_ij || !eps_r || !sigma || !wavelet || !traces)
+        return fail(GF_EINVAL, "gf_forward_model_noalloc: NULL argument");
+    const gf_grid_desc& g = *grid;
+    if (g.nx < 3 || g.ny < 3 || g.nt < 1 || g.npml < 0 || 2 * g.npml > g.nx - 2 ||
+        2 * g.npml > g.ny - 2 || !(g.dx > 0) || !(g.dy > 0) || !(g.dt > 0) || g.pml_order < 0 ||
+        !(g.pml_kappa_max >= 1.0) || !(g.pml_alpha_max >= 0.0) || !(g.pml_eps_ref > 0.0))
+        return fail(GF_EINVAL, "gf_forward_model_noalloc: invalid grid description");
+    if (g.nx > kMaxAxis || g.ny > kMaxAxis)
+        return fail(GF_EINVAL, "gf_forward_model_noalloc: grid %dx%d exceeds %d cells per axis",
+                    g.nx, g.ny, kMaxAxis);
+    const double dtmax = 1.0 / (299792458.0 * sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy)));
+    if (g.dt > dtmax)
+        return fail(GF_ECFL, "gf_forward_model_noalloc: dt exceeds the CFL bound %g s", dtmax);
+    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1)
+        return fail(GF_EINVAL, "gf_forward_model_noalloc: need nshots >= 1, 1 <= nsrc <= %d, "
+                    "nrec >= 1", gf::kMaxSrc);
+    const long long nsrc_all = (long long)acq->nshots * acq->nsrc;
+    const long long nrec_all = (long long)acq->nshots * acq->nrec;
+    for (long long k = 0; k < nsrc_all + nrec_all; ++k) {
+        const int32_t* ij = k < nsrc_all ? acq->src_ij + 2 * k : acq->rec_ij + 2 * (k - nsrc_all);
+        if (ij[0] < 1 || ij[0] > g.nx - 2 || ij[1] < 1 || ij[1] > g.ny - 2)
+            return fail(GF_EINVAL, "gf_forward_model_noalloc: source or receiver off 1..n-2");
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
+        device >= kMaxDevices) {
+        cudaGetLastError();
+        return fail(GF_ECUDA, "gf_forward_model_noalloc: device %d not available", device);
+    }
+
+    // scratch layout (256-byte aligned regions)
+    const long long N = (long long)g.nx * g.ny;
+    const int S = g.nx > g.ny ? g.nx : g.ny;
+    const int tiles_x = (g.nx + kTileW - 1) / kTileW;
+    const int ntiles = tiles_x * ((g.ny + kTileH - 1) / kTileH);
+    const long long nwin = (long long)acq->nshots * ntiles;
+    // a receiver lies in at most 3 x 3 windows when tile >= 2K
+    const long long max_entries = 9 * nrec_all;
+    size_t o = 0;
+    const size_t o_prof = o; o = up256(o + sizeof(float) * 12 * (size_t)S);
+    const size_t o_srcij = o; o = up256(o + sizeof(int) * 2 * (size_t)nsrc_all);
+    const size_t o_recij = o; o = up256(o + sizeof(int) * 2 * (size_t)nrec_all);
+    const size_t o_src = o; o = up256(o + sizeof(int) * (size_t)nsrc_all);
+    const size_t o_rec = o; o = up256(o + sizeof(int) * (size_t)nrec_all);
+    const size_t o_cnt = o; o = up256(o + sizeof(int) * (size_t)nwin);
+    const size_t o_off = o; o = up256(o + sizeof(int) * (size_t)(nwin + 1));
+    const size_t o_idx = o; o = up256(o + sizeof(int) * (size_t)max_entries);
+    const size_t field = sizeof(float) * (size_t)acq->nshots * (size_t)N;
+    const size_t o_stA = o; o = up256(o + gf::kNumFields * field);
+    const size_t o_stB = o; o = up256(o + gf::kNumFields * field);
+    if (o > kScratchBytes)
+        return fail(GF_ENOMEM, "gf_forward_model_noalloc: needs %zu bytes of scratch; the static "
+                    "scratch holds %zu (nshots * nx * ny is about %zu at most)", o, kScratchBytes,
+                    kScratchBytes / (2 * gf::kNumFields * sizeof(float)));
+
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != device) cudaSetDevice(device);
+    struct Restore {
+        int prev, dev;
+        ~Restore() {
+            if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+        }
+    } restore{prev, device};
+    unsigned char* base = nullptr;
+    int rc = setup_device(device, &base);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // CPML profiles (host FP64 -> static host staging -> scratch)
+    std::unique_lock<std::mutex> lock(g_mutex);
+    gf::host_axis_profiles(g, g.nx, g.dx, g_prof_host, S);
+    gf::host_axis_profiles(g, g.ny, g.dy, g_prof_host + 6 * (size_t)S, S);
+    cudaError_t e = cudaMemcpyAsync(base + o_prof, g_prof_host, sizeof(float) * 12 * (size_t)S,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host staging is reused next call
+    lock.unlock();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_srcij, acq->src_ij, sizeof(int) * 2 * (size_t)nsrc_all,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(base + o_recij, acq->rec_ij, sizeof(int) * 2 * (size_t)nrec_all,
+                            cudaMemcpyHostToDevice, st);
+    int* src = (int*)(base + o_src);
+    int* rec = (int*)(base + o_rec);
+    int* cnt = (int*)(base + o_cnt);
+    int* off = (int*)(base + o_off);
+    int* idx = (int*)(base + o_idx);
+    if (e == cudaSuccess) {
+        pairs_to_cells<<<(int)((nsrc_all + 255) / 256), 256, 0, st>>>((const int*)(base + o_srcij),
+                                                                    (int)nsrc_all, g.nx, src);
+        pairs_to_cells<<<(int)((nrec_all + 255) / 256), 256, 0, st>>>((const int*)(base + o_recij),
+                                                                    (int)nrec_all, g.nx, rec);
+        const int wb = (int)((nwin + 255) / 256);
+        count_window_receivers<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, g.nx, kTileW,
+                                                   kTileH, kSteps, tiles_x, ntiles, cnt);
+        exclusive_offsets<<<1, 1024, 0, st>>>(cnt, (int)nwin, off);
+        fill_window_receivers<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, g.nx, kTileW,
+                                                  kTileH, kSteps, tiles_x, ntiles, off, idx);
+        e = cudaGetLastError();
+    }
+    // the state starts from zero on every call (the array keeps the previous call's contents)
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_stA, 0, gf::kNumFields * field, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GF_ECUDA, "gf_forward_model_noalloc: %s", cudaGetErrorString(e));
+    }
+
+    gf::TileParams p{};
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.npml = g.npml;
+    p.nt = g.nt;
+    p.nshots = acq->nshots;
+    p.nsrc = acq->nsrc;
+    p.nrec = acq->nrec;
+    p.N = N;
+    p.dt_eps0 = (float)(g.dt / 8.8541878128e-12);
+    p.ch = (float)(g.dt / 1.25663706212e-6);
+    p.src_scale = (float)(1.0 / (g.dx * g.dy));
+    p.geps = (float)(8.8541878128e-12 / g.dt);
+    p.rdx = (float)(1.0 / g.dx);
+    p.rdy = (float)(1.0 / g.dy);
+    float* P = (float*)(base + o_prof);
+    p.px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
+    p.py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
+    p.eps_r = eps_r;
+    p.sigma = sigma;
+    p.wavelet = wavelet;
+    p.src_cell = src;
+    p.rec_cell = rec;
+    p.traces = traces;
+    p.hist = nullptr;
+    p.illum = nullptr;
+    p.tile_w = kTileW;
+    p.tile_h = kTileH;
+    p.tiles_x = tiles_x;
+    p.ntiles = ntiles;
+    p.tile_rec_off = off;
+    p.tile_rec_idx = idx;
+    float* buf[2] = {(float*)(base + o_stA), (float*)(base + o_stB)};
+    int cur = 0;
+    for (int n0 = 0; n0 < g.nt; n0 += kSteps) {
+        p.n0 = n0;
+        p.K = g.nt - n0 < kSteps ? g.nt - n0 : kSteps;
+        p.st_in = buf[cur];
+        p.st_out = buf[cur ^ 1];
+        e = gf::launch_fwd_tile(p, kVariant, st);
+        if (e != cudaSuccess)
+            return fail(GF_ECUDA, "gf_forward_model_noalloc: tile launch: %s", cudaGetErrorString(e));
+        cur ^= 1;
+    }
+    return GF_OK;
+}
