@@ -330,7 +330,7 @@ def ours(args):
                        "shots_per_gpu": wl.nshots, "nt": g.nt, "nrec": wl.nrec,
                        "cell_updates_per_step": wl.cell_updates() * world,
                        "s_per_gradient": ms / args.steps / 1e3,
-                       "tiling": args.tile or "default 48,48,8",
+                       "tiling": args.tile or "default 52,52,6,variant 0",
                        "l2": "inputs larger than L2: each step streams the "
                              f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
                              "history through HBM",

@@ -45,7 +45,7 @@ struct gf_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
-    int tile_w = 48, tile_h = 48, K = 8, variant = 0;
+    int tile_w = 52, tile_h = 52, K = 6, variant = 0;
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
     int* d_tile_rec_idx = nullptr;
