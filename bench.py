@@ -47,7 +47,12 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nshots", type=int, default=32)
     ap.add_argument("--nt", type=int, default=2000)
-    ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch")
+    ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch[,variant]")
+    ap.add_argument("--workload", default="multishot", choices=["multishot", "large"],
+                    help="multishot: 540x290, 32 shots, nt 2000 (default); large: 2108x1084, "
+                         "16 shots, nt 8000 with checkpointing")
+    ap.add_argument("--checkpoint", type=int, default=0,
+                    help="checkpoint every k steps instead of storing the whole wavefield")
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -59,8 +64,10 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def workload(rank: int, nshots: int, nt: int):
+def workload(rank: int, nshots: int, nt: int, kind: str = "multishot"):
     from paper_2506_20513_gb300 import workloads as W
+    if kind == "large":
+        return W.large_checkpointed(seed=4000 + rank, nshots=min(nshots, 16), nt=nt)
     return W.multishot_layered(seed=1000 + rank, nshots=nshots, nt=nt)
 
 
@@ -217,10 +224,19 @@ def ours(args):
     from paper_2506_20513_gb300 import FDTD, Tiling, _lib
     from paper_2506_20513_gb300.fdtd import ricker
 
-    wl = workload(rank, args.nshots, args.nt)
+    if args.workload == "large":
+        if args.nt == 2000:
+            args.nt = 8000
+        if args.checkpoint <= 0:
+            args.checkpoint = 100
+        # the FP64 oracle would need ~146 GB of host memory per shot for this grid
+        args.no_cpu_baseline = True
+    wl = workload(rank, args.nshots, args.nt, args.workload)
     g = wl.grid
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
     fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=tiling)
+    if args.checkpoint > 0:
+        fd.set_storage(args.checkpoint)
     t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
     eps_t, sig_t = t32(wl.eps_true), t32(wl.sig_true)
@@ -333,7 +349,12 @@ def ours(args):
                        "tiling": args.tile or "default 52,52,6,variant 0",
                        "l2": "inputs larger than L2: each step streams the "
                              f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
-                             "history through HBM",
+                             "through HBM" if not args.checkpoint else
+                             "inputs larger than L2: checkpoints and segment buffers of "
+                             f"{fd.workspace_bytes() / 1e9:.1f} GB",
+                       "storage": (f"checkpoint every {args.checkpoint} steps"
+                                   if args.checkpoint else "full wavefield"),
+                       "workspace_gb": fd.workspace_bytes() / 1e9,
                        "parallelism": f"shots x{world} (independent per GPU)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk,

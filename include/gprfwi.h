@@ -80,8 +80,11 @@ typedef struct gf_acquisition {
 
 typedef struct gf_ctx gf_ctx;
 
-/* Wavefield storage for the adjoint (the forward wavefield store of Algorithm 1, stage 7). */
-#define GF_STORE_FULL 0 /* every Ez^n of every shot kept in the workspace */
+/* Wavefield storage for the adjoint (the forward wavefield store of Algorithm 1, stage 7;
+ * checkpointing is the paper's stated future work for large models, Sec. 5). */
+#define GF_STORE_FULL 0       /* every Ez^n of every shot kept in the workspace */
+#define GF_STORE_CHECKPOINT 1 /* whole state every k steps; the adjoint recomputes each
+                                 k-step segment from its checkpoint (one extra forward) */
 
 /* Create a context on CUDA device `device`: validates the grid (CFL, Eq. cfl) and the
  * geometry, builds the CPML profiles in FP64 on the host and uploads them with the
@@ -96,8 +99,8 @@ void gf_destroy(gf_ctx* ctx);
 const char* gf_last_error(const gf_ctx* ctx);
 
 /* Bytes of device workspace that gf_misfit_and_gradient / gf_forward with saving need for
- * the given storage mode (GF_STORE_FULL: nshots * nt * nx * ny * 4 bytes of wavefield plus
- * the time-stepping state).  forward_only != 0 gives the smaller forward-only figure. */
+ * the context's storage mode (store_mode must equal it; see gf_set_storage).
+ * forward_only != 0 gives the smaller forward-only figure. */
 int gf_workspace_size(const gf_ctx* ctx, int store_mode, int forward_only, size_t* bytes);
 
 /* Hand the context a caller-owned device workspace (>= gf_workspace_size bytes, 256-byte
@@ -112,6 +115,15 @@ int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
  * 52 x 52 interior, K = 6.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
  * not fit. */
 int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
+
+/* Select how gf_forward / gf_misfit_and_gradient keep the forward wavefield for the adjoint:
+ * GF_STORE_FULL (default; k ignored) or GF_STORE_CHECKPOINT with 1 <= k <= nt.  Checkpointing
+ * needs ceil(nt/k) * 7 * nshots * nx * ny * 4 bytes of checkpoints plus (k + 1) * nshots * nx
+ * * ny * 4 bytes of segment buffer instead of nt * nshots * nx * ny * 4, for one extra
+ * forward pass.  The recomputed wavefield is bit-identical to the stored one; gradients agree
+ * with GF_STORE_FULL up to FP32 rounding (adjoint launches split at segment boundaries group
+ * the gradient sums differently).  Invalidates a stored forward. */
+int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
 /* Tile-kernel variant: 0 = four rows per thread (1024-thread CTAs, default), 1 = eight rows
  * per thread (512-thread CTAs).  Both compute the same result. */

@@ -23,6 +23,7 @@ GF_ENONFINITE = -5
 GF_ETIMEOUT = -6
 GF_ESTATE = -7
 GF_STORE_FULL = 0
+GF_STORE_CHECKPOINT = 1
 
 ERROR_NAMES = {
     GF_EINVAL: "GF_EINVAL", GF_ECFL: "GF_ECFL", GF_ENOMEM: "GF_ENOMEM", GF_ECUDA: "GF_ECUDA",
@@ -32,7 +33,7 @@ ERROR_NAMES = {
 # Every entry point declared in include/gprfwi.h.
 EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
-    "gf_set_tiling", "gf_set_variant", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
+    "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_profile",
     "gf_profile_read", "gf_forward_model_noalloc",
 )
@@ -89,6 +90,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_set_workspace": (i, [vp, vp, sz]),
             "gf_set_tiling": (i, [vp, i, i, i]),
             "gf_set_variant": (i, [vp, i]),
+            "gf_set_storage": (i, [vp, i, i]),
             "gf_get_tiling": (i, [vp, P(i), P(i), P(i), P(i)]),
             "gf_forward_model": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "gf_forward": (i, [vp, vp, vp, vp, vp, vp, i, vp]),

@@ -28,7 +28,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Offsets (bytes) of the workspace regions.
 struct Layout {
-    size_t status, partial, stA, stB, illum, traces, resid, grad, hist, total;
+    size_t status, partial, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt, seg, total;
 };
 
 }  // namespace
@@ -46,6 +46,8 @@ struct gf_ctx {
     bool ws_owned = false;
     bool have_forward = false;
     int tile_w = 52, tile_h = 52, K = 6, variant = 0;
+    int store_mode = GF_STORE_FULL, ckpt_k = 0;
+    const float* last_wavelet = nullptr;  // wavelet of the stored forward (recomputation)
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
     int* d_tile_rec_idx = nullptr;
@@ -185,6 +187,8 @@ void axis_profiles(const gf_grid_desc& g, int n, double d, float* out, int strid
     }
 }
 
+int num_checkpoints(const gf_ctx* c) { return (c->g.nt + c->ckpt_k - 1) / c->ckpt_k; }
+
 Layout layout_of(const gf_ctx* c, bool forward_only) {
     Layout L{};
     const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
@@ -197,13 +201,21 @@ Layout layout_of(const gf_ctx* c, bool forward_only) {
     L.illum = o; o = align_up(o + field);
     L.traces = o; o = align_up(o + tr);
     if (forward_only) {
-        L.resid = L.grad = L.hist = 0;
         L.total = o;
         return L;
     }
     L.resid = o; o = align_up(o + tr);
     L.grad = o; o = align_up(o + 2 * field);
-    L.hist = o; o = align_up(o + field * (size_t)c->g.nt);
+    if (c->store_mode == GF_STORE_CHECKPOINT) {
+        // checkpoints of the whole state every k steps, a (k + 1)-slot Ez segment buffer and
+        // the state buffers of the segment recomputation
+        L.stC = o; o = align_up(o + gf::kNumFields * field);
+        L.stD = o; o = align_up(o + gf::kNumFields * field);
+        L.ckpt = o; o = align_up(o + gf::kNumFields * field * (size_t)num_checkpoints(c));
+        L.seg = o; o = align_up(o + field * (size_t)(c->ckpt_k + 1));
+    } else {
+        L.hist = o; o = align_up(o + field * (size_t)c->g.nt);
+    }
     L.total = o;
     return L;
 }
@@ -259,9 +271,41 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.ntiles = p.tiles_x * ((c->g.ny + c->tile_h - 1) / c->tile_h);
     p.tile_rec_off = c->d_tile_rec_off;
     p.tile_rec_idx = c->d_tile_rec_idx;
+    p.hist_stride = c->g.nt;
+    p.hist_slot0 = 0;
     return p;
 }
 
+
+// Forward launches for steps [n_begin, n_end) in blocks of at most K steps, ping-ponging
+// between buf[cur] and buf[cur ^ 1]; returns with cur pointing at the final state.
+int forward_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
+                  int n_end, cudaStream_t st) {
+    for (int n0 = n_begin; n0 < n_end; n0 += c->K) {
+        p.n0 = n0;
+        p.K = std::min(c->K, n_end - n0);
+        p.st_in = buf[cur];
+        p.st_out = buf[cur ^ 1];
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
+        cur ^= 1;
+    }
+    return GF_OK;
+}
+
+// Adjoint launches for steps n_end - 1 down to n_begin (reverse), K steps at most each.
+int adjoint_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
+                  int n_end, cudaStream_t st) {
+    for (int n1 = n_end - 1; n1 >= n_begin; n1 -= c->K) {
+        const int k = std::min(c->K, n1 - n_begin + 1);
+        p.n0 = n1 - k + 1;
+        p.K = k;
+        p.st_in = buf[cur];
+        p.st_out = buf[cur ^ 1];
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
+        cur ^= 1;
+    }
+    return GF_OK;
+}
 
 int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
                 float* traces, float* illum, bool store, cudaStream_t st) {
@@ -274,25 +318,33 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     p.sigma = sigma;
     p.wavelet = wavelet;
     p.traces = traces ? traces : (float*)(c->ws + L.traces);
-    p.hist = store ? (float*)(c->ws + L.hist) : nullptr;
+    const bool ckpt = store && c->store_mode == GF_STORE_CHECKPOINT;
+    p.hist = store && !ckpt ? (float*)(c->ws + L.hist) : nullptr;
     p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
-    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
-    float* st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
-    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear state");
-    if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, field, st), "clear illumination");
+    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear state");
+    if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, state / gf::kNumFields, st), "clear illumination");
     GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_check_model(eps_r, sigma, c->N, p.status, st); }), "check_model");
     int cur = 0;
-    for (int n0 = 0; n0 < c->g.nt; n0 += c->K) {
-        p.n0 = n0;
-        p.K = std::min(c->K, c->g.nt - n0);
-        p.st_in = st_buf[cur];
-        p.st_out = st_buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
-        cur ^= 1;
+    if (ckpt) {
+        // the state at every k-th step is saved before the segment that starts there
+        for (int j = 0; j < num_checkpoints(c); ++j) {
+            const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
+            GF_CUDA(c, cudaMemcpyAsync(c->ws + L.ckpt + state * (size_t)j, st_buf[cur], state,
+                                       cudaMemcpyDeviceToDevice, st),
+                    "save checkpoint");
+            rc = forward_steps(c, p, st_buf, cur, n_begin, n_end, st);
+            if (rc) return rc;
+        }
+    } else {
+        rc = forward_steps(c, p, st_buf, cur, 0, c->g.nt, st);
+        if (rc) return rc;
     }
     if (illum)
         GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.illum, c->nshots, c->N, illum, p.status, st); }), "sum illum");
     c->have_forward = store;
+    c->last_wavelet = wavelet;
     return GF_OK;
 }
 
@@ -303,21 +355,48 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     p.eps_r = eps_r;
     p.sigma = sigma;
     p.resid = resid;
-    p.hist = (float*)(c->ws + L.hist);
     p.grad = (float*)(c->ws + L.grad);
     const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
-    float* st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
-    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, gf::kNumFields * field, st), "clear adjoint state");
+    const size_t state = gf::kNumFields * field;
+    float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear adjoint state");
     GF_CUDA(c, cudaMemsetAsync(p.grad, 0, 2 * field, st), "clear gradients");
     int cur = 0;
-    for (int n1 = c->g.nt - 1; n1 >= 0; n1 -= c->K) {
-        const int k = std::min(c->K, n1 + 1);
-        p.n0 = n1 - k + 1;
-        p.K = k;
-        p.st_in = st_buf[cur];
-        p.st_out = st_buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
-        cur ^= 1;
+    if (c->store_mode == GF_STORE_CHECKPOINT) {
+        // segments in reverse: restore the checkpoint, recompute the segment's Ez into the
+        // segment buffer (slot 0 = Ez at the segment start), then run its adjoint steps
+        float* seg = (float*)(c->ws + L.seg);
+        float* const fw_buf[2] = {(float*)(c->ws + L.stC), (float*)(c->ws + L.stD)};
+        gf::TileParams q = p;
+        q.wavelet = c->last_wavelet;
+        q.traces = (float*)(c->ws + L.traces);  // recomputed traces are not needed
+        q.illum = nullptr;
+        q.hist = seg;
+        q.hist_stride = c->ckpt_k + 1;
+        p.hist = seg;
+        p.hist_stride = c->ckpt_k + 1;
+        for (int j = num_checkpoints(c) - 1; j >= 0; --j) {
+            const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
+            const char* ck = c->ws + L.ckpt + state * (size_t)j;
+            GF_CUDA(c, cudaMemcpyAsync(fw_buf[0], ck, state, cudaMemcpyDeviceToDevice, st),
+                    "restore checkpoint");
+            // Ez plane of every shot -> slot 0 of its segment
+            GF_CUDA(c, cudaMemcpy2DAsync(seg, (size_t)(c->ckpt_k + 1) * c->N * sizeof(float), ck,
+                                         c->N * sizeof(float), c->N * sizeof(float),
+                                         (size_t)c->nshots, cudaMemcpyDeviceToDevice, st),
+                    "segment start");
+            q.hist_slot0 = n_begin - 1;
+            p.hist_slot0 = n_begin - 1;
+            int fcur = 0;
+            int rc = forward_steps(c, q, fw_buf, fcur, n_begin, n_end, st);
+            if (rc) return rc;
+            rc = adjoint_steps(c, p, st_buf, cur, n_begin, n_end, st);
+            if (rc) return rc;
+        }
+    } else {
+        p.hist = (float*)(c->ws + L.hist);
+        int rc = adjoint_steps(c, p, st_buf, cur, 0, c->g.nt, st);
+        if (rc) return rc;
     }
     if (g_eps_r)
         GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.grad, c->nshots, c->N, g_eps_r, p.status, st); }), "sum g_eps_r");
@@ -510,7 +589,10 @@ void gf_destroy(gf_ctx* c) {
 
 int gf_workspace_size(const gf_ctx* c, int store_mode, int forward_only, size_t* bytes) {
     if (!c || !bytes) return GF_EINVAL;
-    if (store_mode != GF_STORE_FULL) return GF_EINVAL;
+    if (store_mode != c->store_mode)
+        return fail(const_cast<gf_ctx*>(c), GF_EINVAL,
+                    "store mode %d is not the context's (%d): call gf_set_storage", store_mode,
+                    c->store_mode);
     *bytes = layout_of(c, forward_only != 0).total;
     return GF_OK;
 }
@@ -548,6 +630,25 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     return GF_OK;
 }
 
+int gf_set_storage(gf_ctx* c, int mode, int k) {
+    if (!c) return GF_EINVAL;
+    if (mode == GF_STORE_FULL) {
+        k = 0;
+    } else if (mode != GF_STORE_CHECKPOINT || k < 1 || k > c->g.nt) {
+        return fail(c, GF_EINVAL, "storage mode %d with k = %d is not valid", mode, k);
+    }
+    c->store_mode = mode;
+    c->ckpt_k = k;
+    c->have_forward = false;
+    if (c->ws && c->ws_owned && c->ws_bytes < layout_of(c, false).total) {
+        DeviceGuard guard(c->device);
+        cudaFree(c->ws);
+        c->ws = nullptr;
+        c->ws_bytes = 0;
+    }
+    return GF_OK;
+}
+
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
     int rc = check_tiling(c, c->tile_w, c->tile_h, c->K, variant);
@@ -576,7 +677,9 @@ int gf_forward_model(gf_ctx* c, const float* eps_r, const float* sigma, const fl
 int gf_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
                float* traces, float* illum, int store_mode, void* stream) {
     if (!c) return GF_EINVAL;
-    if (store_mode != GF_STORE_FULL) return fail(c, GF_EINVAL, "unknown store mode %d", store_mode);
+    if (store_mode != c->store_mode)
+        return fail(c, GF_EINVAL, "store mode %d is not the context's (%d): call gf_set_storage",
+                    store_mode, c->store_mode);
     if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
     DeviceGuard guard(c->device);
     return run_forward(c, eps_r, sigma, wavelet, traces, illum, true, (cudaStream_t)stream);

@@ -38,7 +38,10 @@ struct TileParams {
     const int* rec_cell;    // [nshots][nrec]
     const float* st_in;     // time-stepping state at the start of the launch
     float* st_out;          // state at the end of the launch (other ping-pong buffer)
-    float* hist;            // [nshots][nt][N]: slot n holds Ez^{n+1}; NULL = not stored
+    float* hist;            // wavefield store, NULL = not stored: Ez^{n+1} of shot s at
+                            // hist + (s * hist_stride + n - hist_slot0) * N
+    int hist_stride;        // slots per shot (nt for the full store, k + 1 for a segment)
+    int hist_slot0;         // step whose Ez^{n+1} is slot 0 (0, or the segment start - 1)
     float* traces;          // forward: [nshots][nt][nrec] output
     const float* resid;     // adjoint: [nshots][nt][nrec] trace cotangent
     float* illum;           // forward: [nshots][N] accumulated (NULL = skip)

@@ -247,7 +247,7 @@ __device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c,
     float* sPHy = s.psi + 3 * PLANE;
     const float chx = p.ch * p.rdx, chy = p.ch * p.rdy;
     // the history column of this thread: slot n, row r at hcol + n N + r nx
-    float* hcol = kHist ? p.hist + (long long)shot * p.nt * p.N +
+    float* hcol = kHist ? p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
                               (long long)(c.Y0 + c.ly0) * p.nx + c.gx
                         : nullptr;
     const int* rec_cells = p.rec_cell + (long long)shot * p.nrec;
@@ -408,7 +408,7 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
     float* sPHy = s.psi + 3 * PLANE;
     const float chx = p.ch * p.rdx, chy = p.ch * p.rdy;
     const int n1 = p.n0 + K - 1;
-    const float* hcol = p.hist + (long long)shot * p.nt * p.N +
+    const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
                         (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
     const int* rec_cells = p.rec_cell + (long long)shot * p.nrec;
     const float* resid_base = p.resid + (long long)shot * p.nt * p.nrec;
@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
     float aez[RY], ahx[RY], ahy[RY], ca[RY], cb[RY], ge[RY], gs[RY], e1[RY];
     unsigned ystrip, interior;
     load_state<RY>(p, c, s, sbase, aez, ahx, ahy, ca, cb, ystrip, interior);
-    const float* hcol = p.hist + (long long)shot * p.nt * p.N +
+    const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
                         (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {

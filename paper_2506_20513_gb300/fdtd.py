@@ -115,10 +115,20 @@ class FDTD:
         _lib.check(self.lib, self.ctx, self.lib.gf_get_tiling(self.ctx, *[ctypes.byref(x) for x in v]))
         return Tiling(*[x.value for x in v])
 
+    def set_storage(self, checkpoint_every: int = 0):
+        """0: keep the full forward wavefield; k > 0: checkpoint every k steps and recompute
+        each segment during the adjoint (same results, less memory, one extra forward)."""
+        mode = _lib.GF_STORE_CHECKPOINT if checkpoint_every > 0 else _lib.GF_STORE_FULL
+        _lib.check(self.lib, self.ctx, self.lib.gf_set_storage(self.ctx, mode, checkpoint_every))
+        self._store_mode = mode
+        self._ws = None
+        self._ws_full = False
+
     def workspace_bytes(self, forward_only: bool = False) -> int:
         n = ctypes.c_size_t()
         _lib.check(self.lib, self.ctx, self.lib.gf_workspace_size(
-            self.ctx, _lib.GF_STORE_FULL, int(forward_only), ctypes.byref(n)))
+            self.ctx, getattr(self, "_store_mode", _lib.GF_STORE_FULL), int(forward_only),
+            ctypes.byref(n)))
         return n.value
 
     def _workspace(self, full: bool):
@@ -211,7 +221,9 @@ class FDTD:
         self._workspace(full=True)
         tr = torch.empty(self.trace_shape, dtype=torch.float32, device=self.device)
         rc = self.lib.gf_forward(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), tr.data_ptr(),
-                                 None, _lib.GF_STORE_FULL, self._stream())
+                                 None, getattr(self, "_store_mode", _lib.GF_STORE_FULL),
+                                 self._stream())
+        self._last_wavelet = w  # the recomputation of a checkpointed adjoint reads it
         _lib.check(self.lib, self.ctx, rc)
         return tr
 

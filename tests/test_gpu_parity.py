@@ -43,9 +43,11 @@ def wavelets(wl, nsrc=1):
     return np.ascontiguousarray(np.broadcast_to(w, (wl.nshots, nsrc, wl.grid.nt)))
 
 
-def gpu_gradient(wl, dev, obs, tiling=None, wav=None):
+def gpu_gradient(wl, dev, obs, tiling=None, wav=None, checkpoint_every=0):
     from paper_2506_20513_gb300 import FDTD, Tiling
     fd = FDTD(wl.grid, wl.src, wl.rec, device=dev, tiling=Tiling(*tiling) if tiling else None)
+    if checkpoint_every:
+        fd.set_storage(checkpoint_every)
     wav = wavelets(wl, wl.src.shape[1]) if wav is None else wav
     J, ge, gs, tr = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev),
                                            t32(wav, dev), t32(obs, dev), return_traces=True)
@@ -55,10 +57,10 @@ def gpu_gradient(wl, dev, obs, tiling=None, wav=None):
     return out
 
 
-def check_case(wl, dev, tiling=None, nsrc=1):
+def check_case(wl, dev, tiling=None, nsrc=1, checkpoint_every=0):
     wav = wavelets(wl, nsrc)
     obs = O.forward(wl.grid, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
-    J, ge, gs, tr = gpu_gradient(wl, dev, obs, tiling, wav)
+    J, ge, gs, tr = gpu_gradient(wl, dev, obs, tiling, wav, checkpoint_every)
     J64, ge64, gs64, tr64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, wav,
                                                   wl.rec, obs, nthreads=4, return_traces=True)
     assert rel(tr, tr64) <= TRACE_TOL
@@ -96,6 +98,33 @@ def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
     wl = W.small_random(30 + npml, nxp=110, nyp=84, npml=npml, nt=280, nshots=2, nrec=8,
                         with_pec=True)
     check_case(wl, dev, tiling + (variant,))
+
+
+@pytest.mark.parametrize("k,tiling", [(1, (20, 14, 3, 0)), (7, (20, 14, 4, 1)), (16, None),
+                                      (150, None), (64, (44, 30, 5, 0))])
+def test_checkpointed_gradient(dev, k, tiling):
+    """Checkpoints every k steps and segment recomputation in the adjoint (k = 1, k not a
+    multiple of the time block, k = nt)."""
+    wl = W.small_random(8, nxp=46, nyp=27, npml=6, nt=150, nshots=2, nrec=7, kappa_max=2.0,
+                        with_pec=True)
+    check_case(wl, dev, tiling, checkpoint_every=k)
+
+
+def test_checkpointed_matches_full_store_at_scale(dev):
+    """540x290, 32 shots, nt 400: checkpoints every 50 steps vs the full wavefield store."""
+    wl = W.multishot_layered(nt=400)
+    wav = wavelets(wl)
+    from paper_2506_20513_gb300 import FDTD
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    obs = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(wav, dev))
+    full = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), obs)
+    fd.set_storage(50)
+    ck = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), obs)
+    fd.status()
+    assert abs(full[0].item() - ck[0].item()) <= 1e-12 * full[0].item()
+    for a, b in zip(full[1:], ck[1:]):
+        assert rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
+    fd.close()
 
 
 def test_multiple_sources_per_shot(dev):
