@@ -120,9 +120,8 @@ int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
  * GF_STORE_FULL (default; k ignored) or GF_STORE_CHECKPOINT with 1 <= k <= nt.  Checkpointing
  * needs ceil(nt/k) * 7 * nshots * nx * ny * 4 bytes of checkpoints plus (k + 1) * nshots * nx
  * * ny * 4 bytes of segment buffer instead of nt * nshots * nx * ny * 4, for one extra
- * forward pass.  The recomputed wavefield is bit-identical to the stored one; gradients agree
- * with GF_STORE_FULL up to FP32 rounding (adjoint launches split at segment boundaries group
- * the gradient sums differently).  Invalidates a stored forward. */
+ * forward pass.  Results agree with GF_STORE_FULL up to FP32 rounding (launches split at
+ * segment boundaries group some sums differently).  Invalidates a stored forward. */
 int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
 /* Tile-kernel variant: 0 = four rows per thread (1024-thread CTAs, default), 1 = eight rows

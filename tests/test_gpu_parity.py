@@ -121,7 +121,8 @@ def test_checkpointed_matches_full_store_at_scale(dev):
     fd.set_storage(50)
     ck = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), obs)
     fd.status()
-    assert abs(full[0].item() - ck[0].item()) <= 1e-12 * full[0].item()
+    # launches split at segment boundaries round differently (FP32), nothing more
+    assert abs(full[0].item() - ck[0].item()) <= 1e-6 * full[0].item()
     for a, b in zip(full[1:], ck[1:]):
         assert rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-5
     fd.close()
