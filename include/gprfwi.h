@@ -161,6 +161,24 @@ int gf_misfit_and_gradient(gf_ctx* ctx, const float* eps_r, const float* sigma,
                            const float* wavelet, const float* observed, double* misfit,
                            float* g_eps_r, float* g_sigma, float* traces, void* stream);
 
+/* Misfit only (a line-search evaluation): forward model of all shots and J = 1/2 sum (d - o)^2
+ * (Eq. objective) into *misfit (device FP64).  Nothing is kept for an adjoint. */
+int gf_misfit(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
+              const float* observed, double* misfit, void* stream);
+
+/* Total-variation term of Algorithm 3 (Sec. 3.4), read as split Bregman for
+ * min_u 1/2 |u - x|^2 + lambda TV(u), TV(u) = sum sqrt((Dx u)^2 + (Dy u)^2) with circular
+ * differences, on x = model / max|model|, from u = x, Z = D x, B = 0 (lambda = 0 changes
+ * nothing): `iters` sweeps of u = (x + mu D^T(Z - B) + mu * sum
+ * of the 4 neighbours of u) / (1 + 4 mu), Z = shrink(Du + B, lambda/mu), B += Du - Z; then
+ * grad += weight * max|grad| * (x - u) (normalised units).  One
+ * neighbour average per iteration converges for small mu (0.2 is a safe choice).
+ * model, grad: device [ny][nx]; scratch: device, gf_tv_scratch_bytes(nx, ny) bytes, owned by
+ * the caller.  Asynchronous on `stream`; errors via gf_last_error(NULL). */
+size_t gf_tv_scratch_bytes(int nx, int ny);
+int gf_tv_gradient(int nx, int ny, const float* model, float* grad, void* scratch, float lambda,
+                   float mu, int iters, float weight, void* stream);
+
 /* Synchronise `stream` and return the device status word (GF_OK or the first device-side
  * error since the last gf_status call), then clear it. */
 int gf_status(gf_ctx* ctx, void* stream);

@@ -35,7 +35,8 @@ EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
     "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_profile",
-    "gf_profile_read", "gf_forward_model_noalloc",
+    "gf_profile_read", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
+    "gf_tv_gradient",
 )
 GF_KERNEL_FWD = 0
 GF_KERNEL_ADJ = 1
@@ -103,6 +104,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_kernel_launches": (ctypes.c_longlong, [vp]),
             "gf_profile": (i, [vp, i]),
             "gf_profile_read": (i, [vp, i, P(ctypes.c_double), P(ctypes.c_longlong)]),
+            "gf_misfit": (i, [vp, vp, vp, vp, vp, vp, vp]),
+            "gf_tv_scratch_bytes": (sz, [i, i]),
+            "gf_tv_gradient": (i, [i, i, vp, vp, vp, ctypes.c_float, ctypes.c_float, i,
+                                   ctypes.c_float, vp]),
             "gf_forward_model_noalloc": (i, [P(GridDesc), P(Acquisition), i, vp, vp, vp, vp,
                                              vp]),
         }

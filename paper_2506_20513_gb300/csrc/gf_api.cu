@@ -720,6 +720,50 @@ int gf_misfit_and_gradient(gf_ctx* c, const float* eps_r, const float* sigma,
     return run_adjoint(c, eps_r, sigma, resid, g_eps_r, g_sigma, st);
 }
 
+int gf_misfit(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+              const float* observed, double* misfit, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!observed || !misfit) return fail(c, GF_EINVAL, "NULL observed or misfit pointer");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = run_forward(c, eps_r, sigma, wavelet, nullptr, nullptr, false, st);
+    if (rc) return rc;
+    const Layout L = layout_of(c, true);
+    const long long count = (long long)c->nshots * c->g.nt * c->nrec;
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                return gf::launch_residual_misfit((float*)(c->ws + L.traces), observed, nullptr,
+                                                  count, (double*)(c->ws + L.partial),
+                                                  kMisfitBlocks, (int*)(c->ws + L.status), st);
+            }),
+            "residual_misfit");
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                return gf::launch_finish_misfit((double*)(c->ws + L.partial), kMisfitBlocks, misfit, st);
+            }),
+            "finish_misfit");
+    return GF_OK;
+}
+
+size_t gf_tv_scratch_bytes(int nx, int ny) {
+    return nx > 0 && ny > 0 ? sizeof(float) * gf::tv_scratch_floats((long long)nx * ny) : 0;
+}
+
+int gf_tv_gradient(int nx, int ny, const float* model, float* grad, void* scratch, float lambda,
+                   float mu, int iters, float weight, void* stream) {
+    if (nx < 2 || ny < 2 || !model || !grad || !scratch || !(lambda >= 0.f) || !(mu > 0.f) ||
+        iters < 0 || !(weight >= 0.f)) {
+        create_fail("gf_tv_gradient: invalid argument");
+        return GF_EINVAL;
+    }
+    cudaError_t e = gf::tv_gradient(nx, ny, model, grad, (float*)scratch, lambda, mu, iters, weight,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        create_fail("gf_tv_gradient: %s", cudaGetErrorString(e));
+        return GF_ECUDA;
+    }
+    return GF_OK;
+}
+
 int gf_status(gf_ctx* c, void* stream) {
     if (!c) return GF_EINVAL;
     if (!c->ws) return GF_OK;

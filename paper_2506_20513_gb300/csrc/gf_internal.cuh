@@ -72,6 +72,9 @@ cudaError_t launch_residual_misfit(const float* traces, const float* observed, f
                                    cudaStream_t st);
 cudaError_t launch_finish_misfit(const double* partial, int nblocks, double* misfit,
                                  cudaStream_t st);
+size_t tv_scratch_floats(long long n);
+cudaError_t tv_gradient(int nx, int ny, const float* X, float* G, float* scratch, float lambda,
+                        float mu, int iters, float weight, cudaStream_t st);
 cudaError_t launch_sum_shots(const float* per_shot, int nshots, long long N, float* out,
                              int* status, cudaStream_t st);
 

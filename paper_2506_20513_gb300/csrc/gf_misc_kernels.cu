@@ -19,7 +19,8 @@ __global__ void check_model_kernel(const float* __restrict__ eps_r, const float*
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusBadModel);
 }
 
-// resid = traces - observed; per-block partial sums of resid^2 / 2 in FP64 (fixed order).
+// resid = traces - observed (skipped if resid is NULL); per-block partial sums of resid^2 / 2
+// in FP64 (fixed order).
 __global__ void residual_misfit_kernel(const float* __restrict__ traces,
                                        const float* __restrict__ observed, float* resid,
                                        long long count, double* partial, int* status) {
@@ -29,7 +30,7 @@ __global__ void residual_misfit_kernel(const float* __restrict__ traces,
     for (long long k = blockIdx.x * (long long)kRedThreads + threadIdx.x; k < count;
          k += (long long)gridDim.x * kRedThreads) {
         const float r = traces[k] - observed[k];
-        resid[k] = r;
+        if (resid) resid[k] = r;
         bad |= !isfinite(r);
         acc += 0.5 * (double)r * (double)r;
     }
