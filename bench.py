@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fwi-iters", type=int, default=3,
+                    help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
     return ap.parse_args()
 
 
@@ -328,6 +330,18 @@ def ours(args):
         e2e = {"value": cells / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # seconds per dual-parameter FWI iteration (L-BFGS with its line-search evaluations)
+    fwi = None
+    if args.fwi_iters > 0:
+        from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
+        drv = FWI(fd, lambda f0: obs, interior_mask(g, rows_below_top=4),
+                  FWIConfig(bands=((wl.f0, args.fwi_iters),)))
+        _, _, hist = drv.run(eps0, sig0)
+        fwi = {"iterations": len(hist.seconds),
+               "s_per_iteration": sum(hist.seconds) / max(1, len(hist.seconds)),
+               "evaluations_per_iteration": sum(hist.evaluations) / max(1, len(hist.evaluations)),
+               "misfit_first_last": [hist.misfit[0], hist.final_misfit] if hist.misfit else None}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         shots = cpu_sample_shots(args.cpu_shots)
@@ -355,7 +369,8 @@ def ours(args):
                        "storage": (f"checkpoint every {args.checkpoint} steps"
                                    if args.checkpoint else "full wavefield"),
                        "workspace_gb": fd.workspace_bytes() / 1e9,
-                       "parallelism": f"shots x{world} (independent per GPU)"},
+                       "parallelism": f"shots x{world} (independent per GPU)",
+                       "fwi": fwi},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk,
         }
