@@ -214,6 +214,20 @@ class FDTD:
             return tuple(out)
         return (J, ge, gs, tr) if return_traces else (J, ge, gs)
 
+    def misfit(self, eps_r, sigma, wavelet, observed, out: torch.Tensor | None = None):
+        """J = 1/2 sum (d - o)^2 only (a line-search evaluation), FP64 device scalar."""
+        e, s = self._model(eps_r, sigma)
+        w = self._wavelet(wavelet)
+        o = _dev_f32(observed, self.trace_shape, "observed", self.device)
+        self._workspace(full=False)
+        J = out if out is not None else torch.empty(1, dtype=torch.float64, device=self.device)
+        if J.dtype != torch.float64 or J.device != self.device or J.numel() < 1:
+            raise ValueError("out must be a float64 tensor on the context's device")
+        rc = self.lib.gf_misfit(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), o.data_ptr(),
+                                J.data_ptr(), self._stream())
+        _lib.check(self.lib, self.ctx, rc)
+        return J
+
     def forward(self, eps_r, sigma, wavelet):
         """Traces, keeping the wavefield for a following :meth:`adjoint`."""
         e, s = self._model(eps_r, sigma)

@@ -74,16 +74,15 @@ class FWI:
 
     # -- evaluations through the library ---------------------------------------------------
     def _misfit(self, eps, sig, wav, obs) -> float:
-        fd = self.fd
-        fd._workspace(full=False)
-        rc = fd.lib.gf_misfit(fd.ctx, eps.data_ptr(), sig.data_ptr(), wav.data_ptr(),
-                              obs.data_ptr(), self._J.data_ptr(), fd._stream())
-        _lib.check(fd.lib, fd.ctx, rc)
-        return float(self._J.item())
+        return float(self.fd.misfit(eps, sig, wav, obs, out=self._J).item())
 
     def _tv(self, model, grad):
         ny, nx = self.fd.shape
         c = self.cfg
+        for t in (model, grad):
+            if t.shape != (ny, nx) or t.dtype != torch.float32 or not t.is_contiguous() \
+                    or t.device != self.fd.device:
+                raise ValueError("TV needs contiguous float32 [ny, nx] tensors on the device")
         rc = self.fd.lib.gf_tv_gradient(nx, ny, model.data_ptr(), grad.data_ptr(),
                                         self._tv_scratch.data_ptr(), c.tv_lambda, c.tv_mu,
                                         c.tv_iters, c.tv_weight, self.fd._stream())
