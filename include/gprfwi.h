@@ -124,8 +124,10 @@ int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
  * segment boundaries group some sums differently).  Invalidates a stored forward. */
 int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
-/* Tile-kernel variant: 0 = four rows per thread (1024-thread CTAs, default), 1 = eight rows
- * per thread (512-thread CTAs).  Both compute the same result. */
+/* Kernel variant: 0 = tile kernels with four rows per thread (1024-thread CTAs, default),
+ * 1 = eight rows per thread (512-thread CTAs), 2 = barrier-free warp-march forward (64-column
+ * strips, 64-row chunks, at most 7 steps per launch; the illumination output and the adjoint
+ * use the variant-0 tile kernels).  All compute the same result up to FP32 rounding. */
 int gf_set_variant(gf_ctx* ctx, int variant);
 
 /* Current tiling and variant (for autotuners). */

@@ -51,6 +51,9 @@ struct gf_ctx {
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
     int* d_tile_rec_idx = nullptr;
+    int* d_march_rec_off = nullptr;  // the same for the warp-march strips x chunks
+    int* d_march_rec_idx = nullptr;
+    int march_h = 64;                // rows per warp-march chunk
     size_t smem_optin = 0;
     long long launches = 0;
     bool profiling = false;
@@ -281,12 +284,27 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
 // between buf[cur] and buf[cur ^ 1]; returns with cur pointing at the final state.
 int forward_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
                   int n_end, cudaStream_t st) {
+    gf::TileParams q = p;
+    int chunks = 1;
+    if (c->variant == 2) {  // warp-march geometry: 64-column strips, chunks of march_h rows
+        q.halo = c->K;
+        q.tile_w = gf::max_tile_extent() - 2 * c->K;
+        q.tile_h = c->march_h;
+        q.tiles_x = (c->g.nx + q.tile_w - 1) / q.tile_w;
+        chunks = (c->g.ny + q.tile_h - 1) / q.tile_h;
+        q.ntiles = q.tiles_x * chunks;
+        q.tile_rec_off = c->d_march_rec_off;
+        q.tile_rec_idx = c->d_march_rec_idx;
+    }
     for (int n0 = n_begin; n0 < n_end; n0 += c->K) {
-        p.n0 = n0;
-        p.K = std::min(c->K, n_end - n0);
-        p.st_in = buf[cur];
-        p.st_out = buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
+        q.n0 = n0;
+        q.K = std::min(c->K, n_end - n0);
+        q.st_in = buf[cur];
+        q.st_out = buf[cur ^ 1];
+        if (c->variant == 2 && !q.illum)
+            GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_march(q, chunks, st); }), "fwd_march");
+        else
+            GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(q, c->variant == 2 ? 0 : c->variant, st); }), "fwd_tile");
         cur ^= 1;
     }
     return GF_OK;
@@ -301,7 +319,7 @@ int adjoint_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, i
         p.K = k;
         p.st_in = buf[cur];
         p.st_out = buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant == 2 ? 0 : c->variant, st); }), "adj_tile");
         cur ^= 1;
     }
     return GF_OK;
@@ -410,8 +428,9 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
 }
 
 // Receivers of every (shot, tile) staged window (interior plus a K-cell halo) as a CSR list
-// in receiver-index order, uploaded for the tile kernels; rebuilt whenever the tiling changes.
-int build_receiver_lists(gf_ctx* c, int tw, int th, int K) {
+// in (row, receiver index) order, uploaded for the kernels; rebuilt whenever the tiling
+// changes.  Written into *off / *idx (device, owned by the context).
+int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** idx_out) {
     const int nx = c->g.nx, ny = c->g.ny;
     const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th, nt_ = ntx * nty;
     std::vector<std::vector<int>> lists((size_t)c->nshots * nt_);
@@ -429,6 +448,9 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K) {
         }
     std::vector<int> off(lists.size() + 1, 0), idx;
     for (size_t k = 0; k < lists.size(); ++k) {
+        const int* cells = c->h_rec.data() + (k / nt_) * c->nrec;
+        std::stable_sort(lists[k].begin(), lists[k].end(),
+                         [&](int a, int b) { return cells[a] / nx < cells[b] / nx; });
         off[k + 1] = off[k] + (int)lists[k].size();
         idx.insert(idx.end(), lists[k].begin(), lists[k].end());
     }
@@ -446,11 +468,20 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K) {
         cudaFree(d_idx);
         return cuda_fail(c, e, "receiver lists");
     }
-    cudaFree(c->d_tile_rec_off);
-    cudaFree(c->d_tile_rec_idx);
-    c->d_tile_rec_off = d_off;
-    c->d_tile_rec_idx = d_idx;
+    cudaFree(*off_out);
+    cudaFree(*idx_out);
+    *off_out = d_off;
+    *idx_out = d_idx;
     return GF_OK;
+}
+
+// Lists for the tile kernels and, for the march variant, for its strips x chunks.
+int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K, int variant) {
+    int rc = build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx);
+    if (rc == GF_OK && variant == 2)
+        rc = build_receiver_lists(c, gf::max_tile_extent() - 2 * K, c->march_h, K,
+                                  &c->d_march_rec_off, &c->d_march_rec_idx);
+    return rc;
 }
 
 int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
@@ -459,11 +490,15 @@ int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
         return fail(c, GF_EINVAL,
                     "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d per side",
                     tw, th, K, E);
-    if (variant < 0 || variant >= gf::num_tile_variants())
+    if (variant < 0 || variant > gf::num_tile_variants())
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
-    if (gf::tile_smem_bytes(variant) > c->smem_optin)
+    if (variant == 2 && K > gf::march_max_steps())
+        return fail(c, GF_EINVAL, "the warp-march forward takes at most %d steps per launch",
+                    gf::march_max_steps());
+    const int tv = variant == 2 ? 0 : variant;
+    if (gf::tile_smem_bytes(tv) > c->smem_optin)
         return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)",
-                    gf::tile_smem_bytes(variant), c->smem_optin);
+                    gf::tile_smem_bytes(tv), c->smem_optin);
     return GF_OK;
 }
 
@@ -563,8 +598,15 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     const size_t S = stride;
     c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
+    if (e == cudaSuccess) e = gf::configure_march_kernels((size_t)optin);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        create_fail("gf_create: CUDA setup failed: %s", cudaGetErrorString(e));
+        gf_destroy(c);
+        return GF_ECUDA;
+    }
     if (check_tiling(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK ||
-        build_receiver_lists(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
+        build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK) {
         create_fail("gf_create: %s", c->err);
         gf_destroy(c);
         return GF_EINVAL;
@@ -584,6 +626,8 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_rec);
     cudaFree(c->d_tile_rec_off);
     cudaFree(c->d_tile_rec_idx);
+    cudaFree(c->d_march_rec_off);
+    cudaFree(c->d_march_rec_idx);
     delete c;
 }
 
@@ -622,7 +666,7 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     int rc = check_tiling(c, tw, th, k, c->variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_receiver_lists(c, tw, th, k);
+    rc = build_all_receiver_lists(c, tw, th, k, c->variant);
     if (rc) return rc;
     c->tile_w = tw;
     c->tile_h = th;
@@ -652,6 +696,9 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
     int rc = check_tiling(c, c->tile_w, c->tile_h, c->K, variant);
+    if (rc) return rc;
+    DeviceGuard guard(c->device);
+    rc = build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K, variant);
     if (rc) return rc;
     c->variant = variant;
     return GF_OK;

@@ -49,6 +49,7 @@ struct TileParams {
     int n0, K;              // first time step of the launch, steps in the launch
     int tile_w, tile_h;     // interior tile size; the staged tile has a K-cell halo
     int tiles_x, ntiles;
+    int halo;               // staged halo of the warp-march kernel (>= K)
     // receivers of each (shot, tile) staged window, host-built CSR: entries
     // tile_rec_idx[off[s*ntiles+t] .. off[s*ntiles+t+1]) are receiver indices in index order
     const int* tile_rec_off;
@@ -60,6 +61,11 @@ struct TileParams {
 // Tile-kernel variants: 0 = 4 rows per thread (1024 threads), 1 = 8 rows (512 threads).
 cudaError_t launch_fwd_tile(const TileParams& p, int variant, cudaStream_t st);
 cudaError_t launch_adj_tile(const TileParams& p, int variant, cudaStream_t st);
+// Warp-march forward kernel: 64-column strips, chunks of tile_h rows, K <= march_max_steps().
+cudaError_t launch_fwd_march(const TileParams& p, int chunks, cudaStream_t st);
+cudaError_t configure_march_kernels(size_t optin);
+size_t march_smem_bytes();
+int march_max_steps();
 int max_tile_extent();              // staged tile (interior + 2K halo) limit per side
 int num_tile_variants();
 size_t tile_smem_bytes(int variant);

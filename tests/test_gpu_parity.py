@@ -76,7 +76,7 @@ def test_single_shot_disc(dev):
     check_case(wl, dev)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("seed,tiling,kappa,pec", [
     (1, None, 1.0, False),
     (2, (8, 6, 3), 2.0, True),
@@ -91,17 +91,20 @@ def test_small_random(dev, seed, tiling, kappa, pec, variant):
     check_case(wl, dev, (tiling or (0, 0, 0)) + (variant,))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("npml,tiling", [(0, (16, 16, 4)), (3, (20, 18, 5)), (8, (40, 40, 12))])
 def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
-    """Large grids with thin (or no) CPML: most tiles take the body without CPML memories."""
+    """Large grids with thin (or no) CPML: most tiles take the body without CPML memories;
+    the warp-march variant runs several strips and row chunks."""
+    if variant == 2 and tiling[2] > 7:
+        pytest.skip("the warp-march forward takes at most 7 steps per launch")
     wl = W.small_random(30 + npml, nxp=110, nyp=84, npml=npml, nt=280, nshots=2, nrec=8,
                         with_pec=True)
     check_case(wl, dev, tiling + (variant,))
 
 
 @pytest.mark.parametrize("k,tiling", [(1, (20, 14, 3, 0)), (7, (20, 14, 4, 1)), (16, None),
-                                      (150, None), (64, (44, 30, 5, 0))])
+                                      (150, None), (64, (44, 30, 5, 0)), (33, (0, 0, 5, 2))])
 def test_checkpointed_gradient(dev, k, tiling):
     """Checkpoints every k steps and segment recomputation in the adjoint (k = 1, k not a
     multiple of the time block, k = nt)."""
@@ -267,6 +270,26 @@ def test_host_tensors_end_to_end(dev):
     J64, ge64, gs64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, wav,
                                             wl.rec, obs)
     assert rel(ge.numpy(), ge64) <= GRAD_TOL and rel(gs.numpy(), gs64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("K", [4, 6, 7])
+def test_warp_march_at_scale(dev, K):
+    """540x290, 32 shots, nt 300: the warp-march forward against the tile forward (traces,
+    gradients) in many strips x row chunks."""
+    from paper_2506_20513_gb300 import FDTD, Tiling
+    wl = W.multishot_layered(nt=300)
+    wav = t32(wavelets(wl), dev)
+    e0, s0 = t32(wl.eps_init, dev), t32(wl.sig_init, dev)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    obs = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), wav)
+    ref = fd.misfit_and_gradient(e0, s0, wav, obs, return_traces=True)
+    fd.set_tiling(Tiling(0, 0, K, 2))
+    got = fd.misfit_and_gradient(e0, s0, wav, obs, return_traces=True)
+    fd.status()
+    assert abs(got[0].item() - ref[0].item()) <= 1e-5 * ref[0].item()
+    for a, b in zip(got[1:], ref[1:]):
+        assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-4
+    fd.close()
 
 
 def test_full_size_multishot_sampled(dev):
