@@ -48,7 +48,7 @@ def parse_args():
     ap.add_argument("--nshots", type=int, default=32)
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch[,variant]")
-    ap.add_argument("--workload", default="multishot", choices=["multishot", "large"],
+    ap.add_argument("--workload", default="multishot", choices=["multishot", "large", "uneven"],
                     help="multishot: 540x290, 32 shots, nt 2000 (default); large: 2108x1084, "
                          "16 shots, nt 8000 with checkpointing")
     ap.add_argument("--checkpoint", type=int, default=0,
@@ -381,10 +381,73 @@ def ours(args):
     return 0
 
 
+def uneven(args):
+    """64 independent instances of uneven size (128-768 x 128-384 cells + 20-cell CPML, nt
+    800-3000, 1-8 shots, checkpoints every 100 steps), each tuned by the autotuner, one
+    gradient each per step: one after the other vs concurrently as one replayed CUDA graph."""
+    import tempfile
+
+    import torch
+    from paper_2506_20513_gb300 import FDTD, FDTDBatch, autotune, workloads as W
+    from paper_2506_20513_gb300.fdtd import ricker
+    dev = torch.device("cuda", 0)
+    insts = W.uneven_instances(count=args.nshots if args.nshots != 32 else 64)
+    t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    cache = os.path.join(tempfile.gettempdir(), "gprfwi_autotune.txt")
+    fds, ins = [], []
+    t_tune = time.perf_counter()
+    for wl in insts:
+        g = wl.grid
+        fd = FDTD(g, wl.src, wl.rec, device=dev)
+        wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
+        e0, s0 = t32(wl.eps_init), t32(wl.sig_init)
+        autotune(fd, e0, s0, wav, cache, probe_steps=36)
+        fd.set_storage(100)
+        obs = fd.forward_model(t32(wl.eps_true), t32(wl.sig_true), wav)
+        fds.append(fd)
+        ins.append((e0, s0, wav, obs))
+    torch.cuda.synchronize(dev)
+    t_tune = time.perf_counter() - t_tune
+    batch = FDTDBatch(fds)
+    cols = [list(x) for x in zip(*ins)]
+    cells = sum(w.cell_updates() for w in insts)
+    out = {}
+    for mode in (0, 2):
+        for _ in range(max(1, args.warmup)):
+            batch.misfit_and_gradient(*cols, mode=mode)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            batch.misfit_and_gradient(*cols, mode=mode)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        out[mode] = e0.elapsed_time(e1) / args.steps
+    tilings = {}
+    for fd in fds:
+        t = fd.tiling()
+        key = f"{t.tile_w}x{t.tile_h}/K{t.steps}/v{t.variant}"
+        tilings[key] = tilings.get(key, 0) + 1
+    line = {"metric": METRIC + " (uneven-instance batch)", "value": cells / (out[2] / 1e3) / 1e9,
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out[2], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(insts)} uneven instances (128-768 x 128-384 + CPML, "
+                                   "nt 800-3000, 1-8 shots), checkpoint every 100 steps",
+                       "cell_updates_per_step": cells, "ms_sequential": out[0],
+                       "ms_graph": out[2], "speedup_graph_vs_sequential": out[0] / out[2],
+                       "autotune_s": t_tune, "tilings_chosen": tilings}}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "uneven":
+        return uneven(args)
     return ours(args)
 
 

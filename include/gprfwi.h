@@ -228,6 +228,37 @@ int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acquisition* acq
                              const float* eps_r, const float* sigma, const float* wavelet,
                              float* traces, void* stream);
 
+/* Autotuner (tile shape, time-block depth, kernel variant).  Looks up the context's shape
+ * (device name, nx, ny, npml, shots, sources, receivers) in the text cache `cache_path`
+ * (NULL = no cache); on a miss, times a forward pass over the first `probe_steps` steps (0 =
+ * 48) for each candidate (variants 0 and 1 with 3..10 steps per launch, variant 2 with 4 and
+ * 6), with CUDA events on `stream`, keeps the fastest and appends it to the cache.  Leaves
+ * the chosen tiling set on the context (read it back with gf_get_tiling).  Synchronises
+ * `stream`.  eps_r, sigma, wavelet: device inputs as for gf_forward_model. */
+int gf_autotune(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
+                const char* cache_path, int probe_steps, void* stream);
+
+/* Batches of independent instances (contexts of possibly different grids, shots and nt on
+ * one device), for many small inversions at once.  The batch owns one stream per instance;
+ * it does not own the contexts, which must outlive it. */
+typedef struct gf_batch gf_batch;
+int gf_batch_create(gf_batch** out, gf_ctx* const* ctxs, int n);
+void gf_batch_destroy(gf_batch* batch);
+const char* gf_batch_last_error(const gf_batch* batch);
+
+/* misfit_and_gradient for every instance i (arrays of n device pointers, as for
+ * gf_misfit_and_gradient; misfit: device double[n]).  mode 0: one instance after the other on
+ * `stream`; mode 1: all instances concurrently on the batch's streams, forked from and joined
+ * back into `stream`; mode 2: mode 1 captured once into a CUDA graph and replayed (a single
+ * graph launch per call) while the argument pointers and every context's configuration stay
+ * the same, re-captured otherwise.  Each context's workspace is allocated before the first
+ * fork; profiling must be off.  Asynchronous on `stream`. */
+int gf_batch_misfit_and_gradient(gf_batch* batch, const float* const* eps_r,
+                                 const float* const* sigma, const float* const* wavelet,
+                                 const float* const* observed, double* misfit,
+                                 float* const* g_eps_r, float* const* g_sigma, int mode,
+                                 void* stream);
+
 /* Library version string. */
 const char* gf_version(void);
 

@@ -36,7 +36,8 @@ EXPORTS = (
     "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_profile",
     "gf_profile_read", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
-    "gf_tv_gradient",
+    "gf_tv_gradient", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
+    "gf_batch_last_error", "gf_batch_misfit_and_gradient",
 )
 GF_KERNEL_FWD = 0
 GF_KERNEL_ADJ = 1
@@ -108,6 +109,12 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_tv_scratch_bytes": (sz, [i, i]),
             "gf_tv_gradient": (i, [i, i, vp, vp, vp, ctypes.c_float, ctypes.c_float, i,
                                    ctypes.c_float, vp]),
+            "gf_autotune": (i, [vp, vp, vp, vp, ctypes.c_char_p, i, vp]),
+            "gf_batch_create": (i, [P(vp), P(vp), i]),
+            "gf_batch_destroy": (None, [vp]),
+            "gf_batch_last_error": (ctypes.c_char_p, [vp]),
+            "gf_batch_misfit_and_gradient": (i, [vp, P(vp), P(vp), P(vp), P(vp), vp, P(vp), P(vp),
+                                                 i, vp]),
             "gf_forward_model_noalloc": (i, [P(GridDesc), P(Acquisition), i, vp, vp, vp, vp,
                                              vp]),
         }

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "../../include/gprfwi.h"
@@ -54,6 +55,7 @@ struct gf_ctx {
     int* d_march_rec_off = nullptr;  // the same for the warp-march strips x chunks
     int* d_march_rec_idx = nullptr;
     int march_h = 64;                // rows per warp-march chunk
+    long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
     long long launches = 0;
     bool profiling = false;
@@ -243,6 +245,7 @@ int ensure_workspace(gf_ctx* c, bool forward_only) {
     c->ws_bytes = L.total;
     c->ws_owned = true;
     c->have_forward = false;
+    ++c->generation;
     GF_CUDA(c, cudaMemset(c->ws + L.status, 0, sizeof(int)), "clear status");
     return GF_OK;
 }
@@ -643,6 +646,7 @@ int gf_workspace_size(const gf_ctx* c, int store_mode, int forward_only, size_t*
 
 int gf_set_workspace(gf_ctx* c, void* ws, size_t bytes) {
     if (!c) return GF_EINVAL;
+    ++c->generation;
     if (ws && ((uintptr_t)ws % kAlign)) return fail(c, GF_EINVAL, "workspace not 256-byte aligned");
     DeviceGuard guard(c->device);
     if (c->ws_owned && c->ws) cudaFree(c->ws);
@@ -660,6 +664,7 @@ int gf_set_workspace(gf_ctx* c, void* ws, size_t bytes) {
 
 int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     if (!c) return GF_EINVAL;
+    ++c->generation;
     const int E = gf::max_tile_extent();
     const int k = K > 0 ? K : c->K;
     const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : E - 2 * k;
@@ -676,6 +681,7 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
 
 int gf_set_storage(gf_ctx* c, int mode, int k) {
     if (!c) return GF_EINVAL;
+    ++c->generation;
     if (mode == GF_STORE_FULL) {
         k = 0;
     } else if (mode != GF_STORE_CHECKPOINT || k < 1 || k > c->g.nt) {
@@ -695,6 +701,7 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
 
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
+    ++c->generation;
     int rc = check_tiling(c, c->tile_w, c->tile_h, c->K, variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
@@ -876,3 +883,248 @@ void set_error_without_context(const char* msg) {
     snprintf(g_create_err, sizeof(g_create_err), "%s", msg);
 }
 }  // namespace gf
+
+// ---------------------------------------------------------------------------------------
+// Autotuner and uneven-instance batches
+// ---------------------------------------------------------------------------------------
+namespace {
+
+// Forward launches over the first `nsteps` steps only (no storage): the autotuner's probe.
+int forward_prefix(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                   int nsteps, cudaStream_t st) {
+    int rc = ensure_workspace(c, true);
+    if (rc) return rc;
+    const Layout L = layout_of(c, true);
+    gf::TileParams p = base_params(c, L);
+    p.eps_r = eps_r;
+    p.sigma = sigma;
+    p.wavelet = wavelet;
+    p.traces = (float*)(c->ws + L.traces);
+    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear state");
+    int cur = 0;
+    return forward_steps(c, p, st_buf, cur, 0, std::min(nsteps, c->g.nt), st);
+}
+
+std::string tune_key(const gf_ctx* c) {
+    cudaDeviceProp prop;
+    std::string dev = cudaGetDeviceProperties(&prop, c->device) == cudaSuccess ? prop.name : "gpu";
+    for (char& ch : dev)
+        if (ch == ' ' || ch == '|') ch = '_';
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s nx=%d ny=%d npml=%d shots=%d src=%d rec=%d", dev.c_str(),
+             c->g.nx, c->g.ny, c->g.npml, c->nshots, c->nsrc, c->nrec);
+    return buf;
+}
+
+}  // namespace
+
+struct gf_batch {
+    std::vector<gf_ctx*> ctx;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const void*> key;  // argument pointers the graph was captured with
+    std::vector<long long> gens;
+    int device = 0;
+    char err[512] = {0};
+};
+
+extern "C" {
+
+int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                const char* cache_path, int probe_steps, void* stream) {
+    if (!c || !eps_r || !sigma || !wavelet) return GF_EINVAL;
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const std::string key = tune_key(c);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char line[512];
+            int best[4] = {0, 0, 0, -1};
+            while (fgets(line, sizeof(line), f)) {
+                const char* bar = strchr(line, '|');
+                if (!bar) continue;
+                if (std::string(line, bar - line) != key + " ") continue;
+                int v[4];
+                if (sscanf(bar + 1, "%d %d %d %d", &v[0], &v[1], &v[2], &v[3]) == 4)
+                    std::copy(v, v + 4, best);
+            }
+            fclose(f);
+            if (best[3] >= 0 && gf_set_variant(c, best[3]) == GF_OK &&
+                gf_set_tiling(c, best[0], best[1], best[2]) == GF_OK)
+                return GF_OK;
+        }
+    }
+    struct Cand { int variant, K; };
+    std::vector<Cand> cands;
+    for (int v = 0; v < 2; ++v)
+        for (int K : {3, 4, 5, 6, 8, 10}) cands.push_back({v, K});
+    for (int K : {4, 6}) cands.push_back({2, K});
+    const int steps = probe_steps > 0 ? probe_steps : 48;
+    cudaEvent_t e0, e1;
+    GF_CUDA(c, cudaEventCreate(&e0), "event");
+    GF_CUDA(c, cudaEventCreate(&e1), "event");
+    const bool prof = c->profiling;
+    c->profiling = false;
+    float best_ms = 1e30f;
+    Cand best{c->variant, c->K};
+    int rc = GF_OK;
+    for (const Cand& k : cands) {
+        if (gf_set_variant(c, k.variant) != GF_OK || gf_set_tiling(c, 0, 0, k.K) != GF_OK) continue;
+        rc = forward_prefix(c, eps_r, sigma, wavelet, steps, st);  // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        rc = forward_prefix(c, eps_r, sigma, wavelet, steps, st);
+        if (rc) break;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    c->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    rc = gf_set_variant(c, best.variant);
+    if (rc == GF_OK) rc = gf_set_tiling(c, 0, 0, best.K);
+    if (rc == GF_OK && cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s | %d %d %d %d\n", key.c_str(), c->tile_w, c->tile_h, c->K, c->variant);
+            fclose(f);
+        }
+    }
+    return rc;
+}
+
+int gf_batch_create(gf_batch** out, gf_ctx* const* ctxs, int n) {
+    if (!out) return GF_EINVAL;
+    *out = nullptr;
+    if (!ctxs || n < 1) return GF_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i] || ctxs[i]->device != ctxs[0]->device) return GF_EINVAL;
+    DeviceGuard guard(ctxs[0]->device);
+    gf_batch* b = new gf_batch();
+    b->device = ctxs[0]->device;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->streams.resize(n, nullptr);
+    b->join.resize(n, nullptr);
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        gf_batch_destroy(b);
+        return GF_ECUDA;
+    }
+    *out = b;
+    return GF_OK;
+}
+
+void gf_batch_destroy(gf_batch* b) {
+    if (!b) return;
+    DeviceGuard guard(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto s : b->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+const char* gf_batch_last_error(const gf_batch* b) { return b ? b->err : "no batch"; }
+
+int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const float* const* sigma,
+                                 const float* const* wavelet, const float* const* observed,
+                                 double* misfit, float* const* g_eps_r, float* const* g_sigma,
+                                 int mode, void* stream) {
+    if (!b || !eps_r || !sigma || !wavelet || !observed || !misfit || !g_eps_r || !g_sigma ||
+        mode < 0 || mode > 2)
+        return GF_EINVAL;
+    DeviceGuard guard(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)b->ctx.size();
+    auto fail_b = [&](int code, const char* what, gf_ctx* c) {
+        snprintf(b->err, sizeof(b->err), "%s: %s", what, c ? c->err : "");
+        return code;
+    };
+    // every context needs its full workspace before streams fork (and before a capture)
+    for (int i = 0; i < n; ++i) {
+        gf_ctx* c = b->ctx[i];
+        if (c->profiling) return fail_b(GF_ESTATE, "disable profiling for batches", c);
+        int rc = ensure_workspace(c, false);
+        if (rc) return fail_b(rc, "workspace", c);
+    }
+    auto run_all = [&](bool concurrent) -> int {
+        if (concurrent) {
+            if (cudaEventRecord(b->fork, st) != cudaSuccess) return GF_ECUDA;
+        }
+        for (int i = 0; i < n; ++i) {
+            cudaStream_t si = concurrent ? b->streams[i] : st;
+            if (concurrent && cudaStreamWaitEvent(si, b->fork, 0) != cudaSuccess) return GF_ECUDA;
+            int rc = gf_misfit_and_gradient(b->ctx[i], eps_r[i], sigma[i], wavelet[i], observed[i],
+                                            misfit + i, g_eps_r[i], g_sigma[i], nullptr, si);
+            if (rc) return fail_b(rc, "instance", b->ctx[i]);
+            if (concurrent) {
+                if (cudaEventRecord(b->join[i], si) != cudaSuccess) return GF_ECUDA;
+                if (cudaStreamWaitEvent(st, b->join[i], 0) != cudaSuccess) return GF_ECUDA;
+            }
+        }
+        return GF_OK;
+    };
+    if (mode < 2) return run_all(mode == 1);
+    // graph mode: capture the concurrent schedule once, replay while nothing changed
+    std::vector<const void*> key;
+    std::vector<long long> gens;
+    for (int i = 0; i < n; ++i) {
+        key.insert(key.end(), {eps_r[i], sigma[i], wavelet[i], observed[i], misfit + i,
+                               g_eps_r[i], g_sigma[i]});
+        gens.push_back(b->ctx[i]->generation);
+    }
+    if (!b->exec || key != b->key || gens != b->gens) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_b(GF_ECUDA, "begin capture", nullptr);
+        }
+        const int rc = run_all(true);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (rc || e != cudaSuccess) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            return rc ? rc : fail_b(GF_ECUDA, "end capture", nullptr);
+        }
+        if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return fail_b(GF_ECUDA, "instantiate graph", nullptr);
+        }
+        b->graph = g;
+        b->key = key;
+        b->gens = gens;
+        // the instances' launches now live in the graph; keep their counters meaningful
+    }
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_b(GF_ECUDA, "graph launch", nullptr);
+    }
+    return GF_OK;
+}
+
+}  // extern "C"
+

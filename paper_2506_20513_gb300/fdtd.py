@@ -268,3 +268,69 @@ class FDTDFunction(torch.autograd.Function):
         eps_r, sigma = ctx.saved_tensors
         ge, gs = ctx.fdtd.adjoint(eps_r.detach(), sigma.detach(), grad_traces.float())
         return ge, gs, None, None
+
+
+def autotune(fdtd: FDTD, eps_r, sigma, wavelet, cache_path: str | None = None,
+             probe_steps: int = 0) -> Tiling:
+    """Pick the fastest tiling / kernel variant for this context's shape (cached on disk)."""
+    e, s = fdtd._model(eps_r, sigma)
+    w = fdtd._wavelet(wavelet)
+    fdtd._workspace(full=False)
+    path = cache_path.encode() if cache_path else None
+    rc = fdtd.lib.gf_autotune(fdtd.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), path,
+                              probe_steps, fdtd._stream())
+    _lib.check(fdtd.lib, fdtd.ctx, rc)
+    fdtd._ws = None  # the chosen tiling may need another workspace size
+    fdtd._ws_full = False
+    return fdtd.tiling()
+
+
+class FDTDBatch:
+    """Many independent instances (possibly different grids, shots, nt) advanced together:
+    mode 0 one after the other, 1 concurrently on one stream each, 2 as one CUDA graph."""
+
+    def __init__(self, fdtds):
+        self.fds = list(fdtds)
+        self.lib = self.fds[0].lib
+        self.device = self.fds[0].device
+        arr = (ctypes.c_void_p * len(self.fds))(*[f.ctx.value for f in self.fds])
+        b = ctypes.c_void_p()
+        _lib.check(self.lib, None, self.lib.gf_batch_create(ctypes.byref(b), arr, len(self.fds)))
+        self.batch = b
+        self.J = torch.zeros(len(self.fds), dtype=torch.float64, device=self.device)
+        self.ge = [torch.zeros(f.shape, dtype=torch.float32, device=self.device) for f in self.fds]
+        self.gs = [torch.zeros(f.shape, dtype=torch.float32, device=self.device) for f in self.fds]
+
+    def close(self):
+        if getattr(self, "batch", None):
+            self.lib.gf_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def misfit_and_gradient(self, eps_r, sigma, wavelet, observed, mode: int = 2):
+        """Lists of per-instance device tensors in; (J [n], [g_eps_r], [g_sigma]) out.  The
+        output tensors are reused by every call (a replayed graph writes the same buffers);
+        pass the same input tensors to replay without re-capturing."""
+        n = len(self.fds)
+        ins = []
+        for k, f in enumerate(self.fds):
+            e, s = f._model(eps_r[k], sigma[k])
+            w = f._wavelet(wavelet[k])
+            o = _dev_f32(observed[k], f.trace_shape, "observed", f.device)
+            f._workspace(full=True)
+            ins.append((e, s, w, o))
+        self._keep = ins  # the tensors must outlive the asynchronous (or replayed) work
+        P = lambda xs: (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        rc = self.lib.gf_batch_misfit_and_gradient(
+            self.batch, P([x[0] for x in ins]), P([x[1] for x in ins]), P([x[2] for x in ins]),
+            P([x[3] for x in ins]), self.J.data_ptr(), P(self.ge), P(self.gs), mode,
+            torch.cuda.current_stream(self.device).cuda_stream)
+        if rc != _lib.GF_OK:
+            msg = self.lib.gf_batch_last_error(self.batch)
+            raise _lib.GfError(rc, msg.decode() if msg else "")
+        return self.J, self.ge, self.gs

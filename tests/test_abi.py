@@ -82,6 +82,11 @@ def test_null_arguments_are_rejected(lib):
     assert lib.gf_status(None, None) == _lib.GF_EINVAL
     lib.gf_destroy(None)
     assert lib.gf_last_error(None)
+    assert lib.gf_batch_create(None, None, 0) == _lib.GF_EINVAL
+    assert lib.gf_autotune(None, None, None, None, None, 0, None) == _lib.GF_EINVAL
+    assert lib.gf_batch_misfit_and_gradient(None, None, None, None, None, None, None, None, 0,
+                                            None) == _lib.GF_EINVAL
+    lib.gf_batch_destroy(None)
 
 
 def test_ricker_helper_closed_form(lib):

@@ -1,0 +1,109 @@
+"""Uneven-instance batches (sequential, concurrent, CUDA graph) and the autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2506_20513_gb300 import workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20513_gb300 import build as B
+    B.build_library()
+    return torch.device("cuda", 0)
+
+
+def t32(a, dev):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+
+
+def _instances():
+    return [W.small_random(60, nxp=40, nyp=30, npml=5, nt=120, nshots=2, nrec=5),
+            W.small_random(61, nxp=70, nyp=36, npml=6, nt=173, nshots=3, nrec=7, with_pec=True),
+            W.small_random(62, nxp=52, nyp=61, npml=4, nt=95, nshots=1, nrec=4, kappa_max=2.0)]
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_batch_matches_single_instances_and_oracle(dev, mode):
+    from paper_2506_20513_gb300 import FDTD, FDTDBatch
+    wls = _instances()
+    fds, args = [], []
+    for k, wl in enumerate(wls):
+        g = wl.grid
+        fd = FDTD(g, wl.src, wl.rec, device=dev)
+        if k == 1:
+            fd.set_storage(30)  # one checkpointed instance in the batch
+        wav = np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt))
+        obs = O.forward(g, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+        args.append((t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), t32(obs, dev),
+                     wav, obs))
+        fds.append(fd)
+    singles = [fd.misfit_and_gradient(*a[:4]) for fd, a in zip(fds, args)]
+    batch = FDTDBatch(fds)
+    for rep in range(2):  # the graph is captured on the first call, replayed on the second
+        J, ge, gs = batch.misfit_and_gradient([a[0] for a in args], [a[1] for a in args],
+                                              [a[2] for a in args], [a[3] for a in args], mode)
+        torch.cuda.synchronize(dev)
+        for k, (Js, ges, gss) in enumerate(singles):
+            assert J[k].item() == Js.item()
+            assert torch.equal(ge[k], ges) and torch.equal(gs[k], gss)
+    for k, (wl, a) in enumerate(zip(wls, args)):
+        J64, ge64, gs64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, a[4],
+                                                wl.rec, a[5])
+        rel = lambda x, y: np.linalg.norm(x.cpu().numpy() - y) / np.linalg.norm(y)
+        assert rel(ge[k], ge64) <= 1e-3 and rel(gs[k], gs64) <= 1e-3
+    batch.close()
+
+
+def test_graph_replay_sees_new_input_values(dev):
+    """Replaying the captured graph with new values in the same buffers recomputes."""
+    from paper_2506_20513_gb300 import FDTD, FDTDBatch
+    wls = _instances()[:2]
+    fds = [FDTD(wl.grid, wl.src, wl.rec, device=dev) for wl in wls]
+    ins = []
+    for wl in wls:
+        g = wl.grid
+        wav = np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt))
+        obs = O.forward(g, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+        ins.append([t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), t32(obs, dev)])
+    batch = FDTDBatch(fds)
+    J1 = batch.misfit_and_gradient(*[list(x) for x in zip(*ins)], mode=2)[0].clone()
+    for x in ins:
+        x[0].mul_(1.05)  # same tensors, new values
+    J2, ge, gs = batch.misfit_and_gradient(*[list(x) for x in zip(*ins)], mode=2)
+    torch.cuda.synchronize(dev)
+    for k, fd in enumerate(fds):
+        Jr, ger, gsr = fd.misfit_and_gradient(*ins[k])
+        assert J2[k].item() == Jr.item() != J1[k].item()
+        assert torch.equal(ge[k], ger)
+    batch.close()
+
+
+def test_autotune_picks_a_valid_tiling_and_caches_it(dev, tmp_path):
+    from paper_2506_20513_gb300 import FDTD, autotune
+    wl = W.small_random(63, nxp=120, nyp=80, npml=8, nt=100, nshots=2, nrec=6)
+    g = wl.grid
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    wav = t32(np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (2, 1, g.nt)), dev)
+    cache = str(tmp_path / "tune.txt")
+    t1 = autotune(fd, t32(wl.eps_init, dev), t32(wl.sig_init, dev), wav, cache, probe_steps=24)
+    assert os.path.exists(cache) and "nx=%d" % g.nx in open(cache).read()
+    assert t1.steps >= 1 and t1.tile_w + 2 * t1.steps <= 64 and t1.variant in (0, 1, 2)
+    fd2 = FDTD(g, wl.src, wl.rec, device=dev)
+    t2 = autotune(fd2, t32(wl.eps_init, dev), t32(wl.sig_init, dev), wav, cache, probe_steps=24)
+    assert t2 == t1
+    # the tuned context still computes the right gradient
+    obs = O.forward(g, wl.eps_true, wl.sig_true, wl.src, wav.cpu().double().numpy(), wl.rec)
+    J, ge, gs = fd2.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev), wav,
+                                        t32(obs, dev))
+    J64, ge64, gs64 = O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl.src,
+                                            wav.cpu().double().numpy(), wl.rec, obs)
+    assert np.linalg.norm(ge.cpu().numpy() - ge64) <= 1e-3 * np.linalg.norm(ge64)
