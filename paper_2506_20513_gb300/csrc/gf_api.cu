@@ -925,6 +925,7 @@ struct gf_batch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
+    cudaStream_t capture = nullptr;  // graphs are captured here (the caller's may be legacy)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<const void*> key;  // argument pointers the graph was captured with
@@ -1017,6 +1018,7 @@ int gf_batch_create(gf_batch** out, gf_ctx* const* ctxs, int n) {
     b->streams.resize(n, nullptr);
     b->join.resize(n, nullptr);
     cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
         e = cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming);
@@ -1040,6 +1042,7 @@ void gf_batch_destroy(gf_batch* b) {
     for (auto e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
 }
 
@@ -1066,7 +1069,7 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
         int rc = ensure_workspace(c, false);
         if (rc) return fail_b(rc, "workspace", c);
     }
-    auto run_all = [&](bool concurrent) -> int {
+    auto run_all = [&](bool concurrent, cudaStream_t st) -> int {
         if (concurrent) {
             if (cudaEventRecord(b->fork, st) != cudaSuccess) return GF_ECUDA;
         }
@@ -1083,7 +1086,7 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
         }
         return GF_OK;
     };
-    if (mode < 2) return run_all(mode == 1);
+    if (mode < 2) return run_all(mode == 1, st);
     // graph mode: capture the concurrent schedule once, replay while nothing changed
     std::vector<const void*> key;
     std::vector<long long> gens;
@@ -1097,13 +1100,13 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
         if (b->graph) cudaGraphDestroy(b->graph);
         b->exec = nullptr;
         b->graph = nullptr;
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
             return fail_b(GF_ECUDA, "begin capture", nullptr);
         }
-        const int rc = run_all(true);
+        const int rc = run_all(true, b->capture);
         cudaGraph_t g = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        const cudaError_t e = cudaStreamEndCapture(b->capture, &g);
         if (rc || e != cudaSuccess) {
             cudaGetLastError();
             if (g) cudaGraphDestroy(g);
