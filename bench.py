@@ -73,6 +73,22 @@ def workload(rank: int, nshots: int, nt: int, kind: str = "multishot"):
     return W.multishot_layered(seed=1000 + rank, nshots=nshots, nt=nt)
 
 
+def reduce_max(x: float, device) -> float:
+    """Maximum of x over the ranks of the default process group (x itself without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(cells_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job Gcell-updates/s: every rank's work over the slowest rank's time."""
+    return cells_per_rank * world / (ms_max / 1e3) / 1e9
+
+
 def cpu_sample_shots(requested: int) -> int:
     if requested > 0:
         return requested
@@ -283,12 +299,9 @@ def ours(args):
     lib.gf_profile(ctx, 0)
     clk = clocks.stop()
     fd.status()
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dev)
     cells = wl.cell_updates() * args.steps * world
-    value = cells / (ms / 1e3) / 1e9
+    value = job_value(wl.cell_updates() * args.steps, world, ms)
 
     # roofline of the dominant tile kernel (its own launches, CUDA events on its stream)
     dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
@@ -320,11 +333,7 @@ def ours(args):
         for _ in range(args.steps):
             Jh, geh, gsh = fd.misfit_and_gradient(he, hs, hw, ho)
         barrier()
-        te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            te = float(t.item())
+        te = reduce_max(time.perf_counter() - t0, dev)
         h2d = sum(x.numel() * x.element_size() for x in (he, hs, hw, ho))
         d2h = Jh.numel() * 8 + geh.numel() * 4 + gsh.numel() * 4
         e2e = {"value": cells / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -552,8 +552,10 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
     for (int r = 0; r < RY; ++r) {
         if (!((interior >> r) & 1u)) continue;
         const long long sg = sbase + (long long)(c.Y0 + c.ly0 + r) * p.nx + c.gx;
-        p.grad[sg] += ge[r];
-        p.grad[F + sg] += gs[r];
+        // one writer per cell per launch and launches in stream order: a fire-and-forget
+        // reduction is deterministic and hides the read latency of += at the end of the CTA
+        atomicAdd(p.grad + sg, ge[r]);
+        atomicAdd(p.grad + F + sg, gs[r]);
     }
 }
 
