@@ -22,6 +22,16 @@ The flat parameter vector lists, for each convolution in the order enc0a, enc0b,
 enc(L-1)b, dec(L-2)a, dec(L-2)b, ..., dec0a, dec0b, out: the weight, then the bias.
 Backward passes below are derived by hand from those definitions; the tests pin them to
 central differences of the forward pass.
+
+Optional storage rounding (``quantize``): a function applied where a BF16 implementation
+stores operands of its products -- the network input, every weight (not the biases), every
+convolution's activated output, and the output gradient of each convolution before its
+weight- and input-gradient products (the bias gradient uses the unrounded one).  With
+``quantize=bf16`` the ReLU masks and max-pool choices are taken on the same stored values a
+BF16 implementation sees, so such an implementation can be compared tightly; the products
+themselves stay FP64.  :func:`bf16` rounds to the nearest BF16 value, ties to even (the
+format keeps the top 16 bits of an IEEE binary32 pattern: sign, 8 exponent bits, 7 fraction
+bits).
 """
 from __future__ import annotations
 
@@ -81,6 +91,18 @@ def init_params(rng, levels, base, cin, cout):
     return np.concatenate(parts)
 
 
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _same(a):
+    return a
+
+
 # -- layers (definitions) ------------------------------------------------------------------
 
 def conv3x3(x, w, b):
@@ -105,7 +127,7 @@ def conv3x3_backward(x, w, dy):
     for dh in range(3):
         for dwi in range(3):
             win = xp[:, dh:dh + H, dwi:dwi + W, :]
-            dw[:, dh, dwi, :] = np.einsum("nhwo,nhwi->oi", dy, win)
+            dw[:, dh, dwi, :] = np.tensordot(dy, win, axes=([0, 1, 2], [0, 1, 2]))
             dxp[:, dh:dh + H, dwi:dwi + W, :] += dy @ w[:, dh, dwi, :]
     return dxp[:, 1:-1, 1:-1, :], dw, dy.sum(axis=(0, 1, 2))
 
@@ -115,7 +137,7 @@ def conv1x1(x, w, b):
 
 
 def conv1x1_backward(x, w, dy):
-    return dy @ w, np.einsum("nhwo,nhwi->oi", dy, x), dy.sum(axis=(0, 1, 2))
+    return dy @ w, np.tensordot(dy, x, axes=([0, 1, 2], [0, 1, 2])), dy.sum(axis=(0, 1, 2))
 
 
 def relu(z):
@@ -154,32 +176,37 @@ def upsample2_backward(dy):
 
 # -- the network ---------------------------------------------------------------------------
 
-def forward(params, x, levels, base, cin, cout, keep=False):
+def _weights(params, levels, base, cin, cout, q):
+    return {k: (q(w), b) for k, (w, b) in unpack(params, levels, base, cin, cout).items()}
+
+
+def forward(params, x, levels, base, cin, cout, keep=False, quantize=None):
     """y [n,H,W,cout]; with ``keep`` also the intermediate activations for backward."""
-    P = unpack(params, levels, base, cin, cout)
+    q = quantize or _same
+    P = _weights(params, levels, base, cin, cout, q)
     x = np.asarray(x, dtype=np.float64)
     acts = {}
-    h = x
+    h = q(x)
     skips = []
     for l in range(levels):
         if l > 0:
             acts[f"pool{l}_in"] = h
             h = maxpool2(h)
         acts[f"enc{l}a_in"] = h
-        h = relu(conv3x3(h, *P[f"enc{l}a"]))
+        h = q(relu(conv3x3(h, *P[f"enc{l}a"])))
         acts[f"enc{l}a_out"] = h
         acts[f"enc{l}b_in"] = h
-        h = relu(conv3x3(h, *P[f"enc{l}b"]))
+        h = q(relu(conv3x3(h, *P[f"enc{l}b"])))
         acts[f"enc{l}b_out"] = h
         skips.append(h)
     for l in range(levels - 2, -1, -1):
         u = upsample2(h)
         cat = np.concatenate([u, skips[l]], axis=3)
         acts[f"dec{l}a_in"] = cat
-        h = relu(conv3x3(cat, *P[f"dec{l}a"]))
+        h = q(relu(conv3x3(cat, *P[f"dec{l}a"])))
         acts[f"dec{l}a_out"] = h
         acts[f"dec{l}b_in"] = h
-        h = relu(conv3x3(h, *P[f"dec{l}b"]))
+        h = q(relu(conv3x3(h, *P[f"dec{l}b"])))
         acts[f"dec{l}b_out"] = h
     acts["out_in"] = h
     y = conv1x1(h, *P["out"])
@@ -195,22 +222,23 @@ def loss(y, t, mask=None):
     return 0.5 * inv * float(np.sum(r * r)), inv * m * r
 
 
-def loss_and_gradient(params, x, t, mask, levels, base, cin, cout):
+def loss_and_gradient(params, x, t, mask, levels, base, cin, cout, quantize=None):
     """(L, dL/dparams flat, y)."""
-    P = unpack(params, levels, base, cin, cout)
-    y, A = forward(params, x, levels, base, cin, cout, keep=True)
+    q = quantize or _same
+    P = _weights(params, levels, base, cin, cout, q)
+    y, A = forward(params, x, levels, base, cin, cout, keep=True, quantize=quantize)
     L, dy = loss(y, t, mask)
     G = {}
-    dh, gw, gb = conv1x1_backward(A["out_in"], P["out"][0], dy)
-    G["out"] = (gw, gb)
+    dh, gw, _ = conv1x1_backward(A["out_in"], P["out"][0], q(dy))
+    G["out"] = (gw, dy.sum(axis=(0, 1, 2)))
     dskip = [None] * levels
     for l in range(0, levels - 1):
         for part in ("b", "a"):
             name = f"dec{l}{part}"
             out = A[f"{name}_out"]
             dz = dh * (out > 0)
-            dx, gw, gb = conv3x3_backward(A[f"{name}_in"], P[name][0], dz)
-            G[name] = (gw, gb)
+            dx, gw, _ = conv3x3_backward(A[f"{name}_in"], P[name][0], q(dz))
+            G[name] = (gw, dz.sum(axis=(0, 1, 2)))
             dh = dx
         c_up = dh.shape[3] - base * 2 ** l
         dskip[l] = dh[..., c_up:]
@@ -222,8 +250,8 @@ def loss_and_gradient(params, x, t, mask, levels, base, cin, cout):
             name = f"enc{l}{part}"
             out = A[f"{name}_out"]
             dz = dh * (out > 0)
-            dx, gw, gb = conv3x3_backward(A[f"{name}_in"], P[name][0], dz)
-            G[name] = (gw, gb)
+            dx, gw, _ = conv3x3_backward(A[f"{name}_in"], P[name][0], q(dz))
+            G[name] = (gw, dz.sum(axis=(0, 1, 2)))
             dh = dx
         if l > 0:
             dh = maxpool2_backward(A[f"pool{l}_in"], dh)

@@ -146,3 +146,32 @@ def test_training_reduces_loss_on_a_tiny_problem():
         L0 = L if L0 is None else L0
         p, m, v = U.adam_step(p, g, m, v, step, 3e-3)
     assert L < 0.5 * L0
+
+
+def test_bf16_rounding_matches_the_format_and_torch():
+    """Nearest BF16 value with ties to even: hand-worked bit patterns, then torch's own
+    float32 -> bfloat16 conversion on random values (a library routine)."""
+    import torch
+    e = 2.0 ** -8
+    cases = {1.0: 1.0, 1 + e: 1.0, 1 + 3 * e: 1 + 4 * e, 1 + e + 2.0 ** -20: 1 + 2 * e,
+             -(1 + 3 * e): -(1 + 4 * e), 0.0: 0.0, 3.0: 3.0}
+    for x, want in cases.items():
+        assert U.bf16(np.array([x]))[0] == want, x
+    rng = np.random.default_rng(0)
+    v = (rng.standard_normal(100000) * 10.0 ** rng.uniform(-20, 20, 100000)).astype(np.float32)
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(U.bf16(v), ref)
+    np.testing.assert_array_equal(U.bf16(U.bf16(v)), U.bf16(v))
+
+
+def test_storage_rounding_stays_near_fp64():
+    """Rounding the stored operands to BF16 moves the output by about 1e-2 of itself at most
+    (the envelope the GPU comparison with the plain FP64 oracle relies on)."""
+    rng = np.random.default_rng(8)
+    lv, b, ci, co = 3, 8, 4, 2
+    p = U.init_params(rng, lv, b, ci, co)
+    x = rng.standard_normal((2, 16, 24, ci))
+    y0 = U.forward(p, x, lv, b, ci, co)
+    y1 = U.forward(p, x, lv, b, ci, co, quantize=U.bf16)
+    r = np.linalg.norm(y1 - y0) / np.linalg.norm(y0)
+    assert 1e-4 < r < 2e-2
