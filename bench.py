@@ -36,7 +36,10 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per cell-step of one launch, from `ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
 # gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
-NCU_TRAFFIC_PER_CELL_STEP: dict = {}
+NCU_TRAFFIC_PER_CELL_STEP: dict = {
+    # profiles/adj_tile_multishot_540x290x32.md: 334.6 MB per K = 6 launch
+    "adj@0a924e17d8ee@540x290x32@default": 11.1287,
+}
 
 
 def parse_args():

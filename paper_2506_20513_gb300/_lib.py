@@ -1,4 +1,5 @@
-"""ctypes binding of ``include/gprfwi.h``: the C ABI under the same names.
+"""ctypes binding of ``include/gprfwi.h`` and ``include/gprfwi_unet.h``: the C ABI under the
+same names.
 
 Argument marshalling only.  Array arguments are integer addresses (device pointers from
 ``torch.Tensor.data_ptr()``); ``stream`` is a ``cudaStream_t`` as an integer.  Every compute
@@ -30,7 +31,7 @@ ERROR_NAMES = {
     GF_ENONFINITE: "GF_ENONFINITE", GF_ETIMEOUT: "GF_ETIMEOUT", GF_ESTATE: "GF_ESTATE",
 }
 
-# Every entry point declared in include/gprfwi.h.
+# Every entry point declared in include/gprfwi.h and include/gprfwi_unet.h.
 EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
     "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
@@ -38,6 +39,9 @@ EXPORTS = (
     "gf_profile_read", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
     "gf_tv_gradient", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
     "gf_batch_last_error", "gf_batch_misfit_and_gradient",
+    "gf_unet_param_count", "gf_unet_create", "gf_unet_destroy", "gf_unet_last_error",
+    "gf_unet_set_params", "gf_unet_get_params", "gf_unet_forward", "gf_unet_loss_and_grad",
+    "gf_unet_adam_step", "gf_unet_kernel_launches",
 )
 GF_KERNEL_FWD = 0
 GF_KERNEL_ADJ = 1
@@ -59,6 +63,11 @@ class Acquisition(ctypes.Structure):
         ("nshots", ctypes.c_int32), ("nsrc", ctypes.c_int32), ("nrec", ctypes.c_int32),
         ("src_ij", ctypes.POINTER(ctypes.c_int32)), ("rec_ij", ctypes.POINTER(ctypes.c_int32)),
     ]
+
+
+class UNetDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in
+                ("levels", "base", "cin", "cout", "height", "width", "max_batch")]
 
 
 class GfError(RuntimeError):
@@ -117,6 +126,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                                  i, vp]),
             "gf_forward_model_noalloc": (i, [P(GridDesc), P(Acquisition), i, vp, vp, vp, vp,
                                              vp]),
+            "gf_unet_param_count": (ctypes.c_longlong, [P(UNetDesc)]),
+            "gf_unet_create": (i, [P(vp), P(UNetDesc), i]),
+            "gf_unet_destroy": (None, [vp]),
+            "gf_unet_last_error": (ctypes.c_char_p, [vp]),
+            "gf_unet_set_params": (i, [vp, vp, vp]),
+            "gf_unet_get_params": (i, [vp, vp, vp]),
+            "gf_unet_forward": (i, [vp, i, vp, vp, vp]),
+            "gf_unet_loss_and_grad": (i, [vp, i, vp, vp, vp, vp, vp, vp]),
+            "gf_unet_adam_step": (i, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, vp]),
+            "gf_unet_kernel_launches": (ctypes.c_longlong, [vp]),
         }
         for name, (res, args) in decl.items():
             f = getattr(lib, name)
@@ -126,7 +146,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         return lib
 
 
-def check(lib, ctx, rc: int) -> None:
+def check(lib, ctx, rc: int, last_error=None) -> None:
     if rc != GF_OK:
-        msg = lib.gf_last_error(ctx)
+        msg = (last_error or lib.gf_last_error)(ctx)
         raise GfError(rc, msg.decode() if msg else "")

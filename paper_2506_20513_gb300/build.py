@@ -10,8 +10,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(_HERE, "csrc")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libgprfwi.so")
-SOURCES = ("gf_api.cu", "gf_tile_kernels.cu", "gf_misc_kernels.cu", "gf_noalloc.cu", "gf_tv.cu", "gf_march_kernels.cu")
-HEADERS = ("gf_internal.cuh",)
+SOURCES = ("gf_api.cu", "gf_tile_kernels.cu", "gf_misc_kernels.cu", "gf_noalloc.cu", "gf_tv.cu",
+           "gf_march_kernels.cu", "gf_nn.cu", "gf_unet.cu")
+HEADERS = ("gf_internal.cuh", "gf_nn.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "--expt-relaxed-constexpr"]
@@ -33,8 +34,9 @@ def _stale(target: str, deps) -> bool:
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    inc = os.path.join(os.path.dirname(_HERE), "include", "gprfwi.h")
-    headers = [os.path.join(CSRC, h) for h in HEADERS] + [inc]
+    inc = os.path.join(os.path.dirname(_HERE), "include")
+    headers = [os.path.join(CSRC, h) for h in HEADERS] + [
+        os.path.join(inc, h) for h in ("gprfwi.h", "gprfwi_unet.h")]
     nvcc = _nvcc()
     objs = []
     jobs = []

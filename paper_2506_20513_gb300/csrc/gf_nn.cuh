@@ -1,0 +1,69 @@
+// gf_nn.cuh -- launchers of the BF16 U-Net kernels (gf_nn.cu), used by gf_unet.cu.
+// All activations are channels-last; BF16 buffers are passed as void*.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace gf {
+namespace nn {
+
+constexpr int kMseBlocks = 304;    // blocks of the loss reduction (2 per SM)
+constexpr int kColsumRows = 512;   // rows per partial block of a bias gradient
+
+// C = op(A) op(B): op(A) [M,K] is A stored [M][lda] (ta = 0) or [K][lda] (ta = 1); op(B)
+// [K,N] is B stored [N][ldb] (tb = 1) or [K][ldb] (tb = 0).  Output (one of):
+//   Cb (BF16, ldc): act(acc + bias[c]) with act = ReLU when relu != 0;
+//   C (FP32, ldc):  alpha acc + bias[c] + beta C.
+// With split-K the partial products go to a caller buffer and are summed in order (only the
+// FP32 output, bias = 0, beta = 0, is supported then).
+struct GemmArgs {
+    int M = 0, N = 0, K = 0;
+    const __nv_bfloat16* A = nullptr;
+    int lda = 0, ta = 0;
+    const __nv_bfloat16* B = nullptr;
+    int ldb = 0, tb = 0;
+    float* C = nullptr;
+    __nv_bfloat16* Cb = nullptr;
+    int ldc = 0;
+    const float* bias = nullptr;
+    int relu = 0;
+    float alpha = 1.f, beta = 0.f;
+    // filled in by gemm()
+    int kchunk = 0, va = 0, vb = 0;
+    float* P = nullptr;
+};
+
+struct GemmPlan {
+    int bm = 128, bn = 128, splits = 1, kchunk = 32;
+};
+
+GemmPlan plan_gemm(int M, int N, int K);
+// partial: FP32 buffer of plan.splits * M * N elements when plan.splits > 1
+cudaError_t gemm(GemmArgs a, const GemmPlan& plan, float* partial, cudaStream_t st);
+
+cudaError_t im2col3(const void* x, int nb, int H, int W, int C, void* col, cudaStream_t st);
+cudaError_t flip_transpose(const void* w, int Co, int Ci, void* wt, cudaStream_t st);
+cudaError_t relu_bwd(const float* dy, const void* y, long long n, int relu, float* dz, void* dzb,
+                     cudaStream_t st);
+int colsum_chunks(long long rows);
+cudaError_t column_sum(const float* in, long long rows, int C, float* part, float* out,
+                       cudaStream_t st);
+cudaError_t maxpool2(const void* x, int nb, int H, int W, int C, void* y, cudaStream_t st);
+cudaError_t maxpool2_bwd(const void* x, const void* y, const float* dy, const float* add, int nb,
+                         int H, int W, int C, float* dx, cudaStream_t st);
+cudaError_t upsample2(const void* x, int nb, int H, int W, int C, void* y, int Cy, int coff,
+                      cudaStream_t st);
+cudaError_t upsample2_bwd(const float* dy, int nb, int H, int W, int C, int Cy, int coff,
+                          float* dx, cudaStream_t st);
+cudaError_t put_channels(const void* x, long long rows, int C, void* y, int Cy, int coff,
+                         cudaStream_t st);
+cudaError_t take_channels(const float* dy, long long rows, int Cy, int coff, int C, float* dx,
+                          cudaStream_t st);
+cudaError_t mse(const float* y, const float* t, const float* mask, long long n, int C,
+                double inv_count, float* dy, double* partial, double* loss, cudaStream_t st);
+cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1,
+                 float b2, float eps, float c1, float c2, void* wb, cudaStream_t st);
+cudaError_t to_bf16(const float* x, long long n, void* y, cudaStream_t st);
+
+}  // namespace nn
+}  // namespace gf

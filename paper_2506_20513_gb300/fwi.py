@@ -14,7 +14,12 @@ driver keeps those pieces around a limited-memory BFGS update:
   scaled so that the largest eps_r change equals ``first_step`` (relative to max eps_r);
   after each step eps_r and sigma are clamped to their physical ranges (Sec. 3.1);
 * multiscale: a sequence of bands (Ricker peak frequency, iterations); the L-BFGS memory is
-  reset at each band change.
+  reset at each band change;
+* optional learned preconditioner (:class:`.precond.LearnedPreconditioner`): each iteration
+  first tries the network's update computed from the raw gradient, the model and the
+  illumination of the band's starting model; the update is kept only if the FDTD misfit
+  decreases, otherwise the plain L-BFGS step is taken.  Accepted steps of either kind feed
+  the L-BFGS memory.
 """
 from __future__ import annotations
 
@@ -51,6 +56,7 @@ class FWIHistory:
     evaluations: list = field(default_factory=list)   # misfit evaluations per iteration
     seconds: list = field(default_factory=list)       # wall time per iteration (synchronised)
     band: list = field(default_factory=list)
+    learned: list = field(default_factory=list)       # True where the learned update was kept
 
 
 class FWI:
@@ -60,8 +66,10 @@ class FWI:
     band with Ricker peak frequency f0; ``mask`` [ny, nx] (1 = free, 0 = fixed) zeroes the
     gradient where the model must not move (the absorbing layer, the rows of the sources)."""
 
-    def __init__(self, fdtd: FDTD, observed, mask: torch.Tensor, config: FWIConfig | None = None):
+    def __init__(self, fdtd: FDTD, observed, mask: torch.Tensor, config: FWIConfig | None = None,
+                 preconditioner=None):
         self.fd = fdtd
+        self.pre = preconditioner
         self.observed = observed
         self.cfg = config or FWIConfig()
         self.mask = mask.to(device=fdtd.device, dtype=torch.float32)
@@ -88,14 +96,17 @@ class FWI:
                                         c.tv_iters, c.tv_weight, self.fd._stream())
         _lib.check(self.fd.lib, None, rc)
 
-    def gradient(self, eps, sig, wav, obs):
-        """J and the masked gradient in the variables x = (eps_r, sigma / sigma_ref)."""
+    def gradient(self, eps, sig, wav, obs, raw: bool = False):
+        """J and the masked gradient in the variables x = (eps_r, sigma / sigma_ref) (and the
+        raw model gradients with ``raw``)."""
         J, ge, gs = self.fd.misfit_and_gradient(eps, sig, wav, obs)
+        if raw:
+            ge0, gs0 = ge.clone(), gs.clone()
         if self.cfg.tv:
             self._tv(eps, ge)
             self._tv(sig, gs)
         gx = torch.cat([(ge * self.mask).reshape(-1), (gs * self.mask * self.cfg.sigma_ref).reshape(-1)])
-        return float(J.item()), gx
+        return (float(J.item()), gx, ge0, gs0) if raw else (float(J.item()), gx)
 
     # -- the iteration ---------------------------------------------------------------------
     def _split(self, x):
@@ -105,9 +116,12 @@ class FWI:
         sig = (x[n:].reshape(ny, nx) * self.cfg.sigma_ref).clamp_min(self.cfg.sigma_min).contiguous()
         return eps, sig
 
-    def run(self, eps0: torch.Tensor, sig0: torch.Tensor, callback=None):
+    def run(self, eps0: torch.Tensor, sig0: torch.Tensor, callback=None,
+            stop_misfit: float | None = None):
+        """Iterate every band; with ``stop_misfit`` stop as soon as J <= stop_misfit."""
         c = self.cfg
         hist = FWIHistory()
+        learned = self.pre is not None
         x = torch.cat([eps0.reshape(-1).double(), (sig0.reshape(-1) / c.sigma_ref).double()])
         x = x.to(self.fd.device)
         for f0, iters in c.bands:
@@ -115,12 +129,49 @@ class FWI:
             obs = self.observed(f0)
             S, Y = [], []
             eps, sig = self._split(x.float())
-            J, g = self.gradient(eps, sig, wav, obs)
+            illum = None
+            if learned:
+                _, illum = self.fd.forward_model(eps, sig, wav, illumination=True)
+                J, g, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+            else:
+                J, g = self.gradient(eps, sig, wav, obs)
             g = g.double()
             first = True
+            n = x.numel() // 2
             for it in range(iters):
+                if stop_misfit is not None and J <= stop_misfit:
+                    break
                 torch.cuda.synchronize(self.fd.device)
                 t0 = time.perf_counter()
+                if learned:
+                    de, ds = self.pre.update(ge, gs, eps, illum)
+                    d_l = torch.cat([(de * self.mask).reshape(-1).double(),
+                                     (ds * self.mask / c.sigma_ref).reshape(-1).double()])
+                    e_c, s_c = self._split((x + d_l).float())
+                    J_c = self._misfit(e_c, s_c, wav, obs)
+                    if J_c < J:
+                        x_new = torch.cat([e_c.reshape(-1).double(),
+                                           (s_c.reshape(-1) / c.sigma_ref).double()])
+                        J_next, g_new, ge, gs = self.gradient(e_c, s_c, wav, obs, raw=True)
+                        g_new = g_new.double()
+                        s_k, y_k = x_new - x, g_new - g
+                        if float(torch.dot(s_k, y_k)) > 1e-12 * float(torch.dot(s_k, s_k)) ** 0.5:
+                            S.append(s_k)
+                            Y.append(y_k)
+                            if len(S) > c.memory:
+                                S.pop(0)
+                                Y.pop(0)
+                        hist.misfit.append(J)
+                        hist.evaluations.append(2)
+                        torch.cuda.synchronize(self.fd.device)
+                        hist.seconds.append(time.perf_counter() - t0)
+                        hist.band.append(f0)
+                        hist.learned.append(True)
+                        x, g, J, eps, sig = x_new, g_new, J_next, e_c, s_c
+                        first = False
+                        if callback:
+                            callback(it, J, x)
+                        continue
                 # two-loop recursion (Nocedal & Wright, Algorithm 7.4)
                 q = g.clone()
                 alphas = []
@@ -139,13 +190,12 @@ class FWI:
                 if slope >= 0:  # not a descent direction: restart from steepest descent
                     S, Y, d, first = [], [], -g, True
                     slope = float(torch.dot(g, d))
-                n = x.numel() // 2
                 alpha = 1.0
                 if first:
                     peak = float(d[:n].abs().max())
                     if peak > 0:
                         alpha = c.first_step * float(x[:n].max()) / peak
-                evals = 0
+                evals = 1 if learned else 0
                 accepted = False
                 for _ in range(c.backtracks):
                     x_new = x + alpha * d
@@ -161,10 +211,14 @@ class FWI:
                     hist.evaluations.append(evals)
                     hist.seconds.append(time.perf_counter() - t0)
                     hist.band.append(f0)
+                    hist.learned.append(False)
                     break
                 # project onto the physical ranges, then the new gradient
                 x_new = torch.cat([eps.reshape(-1).double(), (sig.reshape(-1) / c.sigma_ref).double()])
-                J_next, g_new = self.gradient(eps, sig, wav, obs)
+                if learned:
+                    J_next, g_new, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+                else:
+                    J_next, g_new = self.gradient(eps, sig, wav, obs)
                 g_new = g_new.double()
                 s_k, y_k = x_new - x, g_new - g
                 if float(torch.dot(s_k, y_k)) > 1e-12 * float(torch.dot(s_k, s_k)) ** 0.5:
@@ -178,6 +232,7 @@ class FWI:
                 torch.cuda.synchronize(self.fd.device)
                 hist.seconds.append(time.perf_counter() - t0)
                 hist.band.append(f0)
+                hist.learned.append(False)
                 x, g, J, first = x_new, g_new, J_next, False
                 if callback:
                     callback(it, J, x)

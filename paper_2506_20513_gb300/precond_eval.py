@@ -1,0 +1,130 @@
+"""Train the learned preconditioner on seeded random models and evaluate it in FWI.
+
+    python -m paper_2506_20513_gb300.precond_eval --train 10000 --eval 100
+
+Workload: 256 x 128 physical cells (+20-cell CPML), dx 0.01 m, 400 MHz Ricker, 16 shots
+on the surface, 64 receivers, nt 1500 (the preconditioner workload generator, seeds
+``--seed`` ...).  For each training model the FDTD/adjoint kernels compute the observed data
+of the true model, the misfit gradient at the smoothed starting model and that model's
+illumination; the U-Net (4 levels, 32 base channels, 4 in / 2 out, BF16 kernels) learns the
+normalised true-minus-start update.  Evaluation on held-out seeds: plain L-BFGS for
+``--iters`` iterations gives a target misfit; the learned-preconditioned run (network
+update tried first, plain step as fallback) counts the iterations, FDTD evaluations and
+wall time it needs to reach that misfit.  Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+import torch
+
+from . import workloads as W
+from .fdtd import FDTD, ricker
+from .fwi import FWI, FWIConfig, interior_mask
+from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pairs,
+                      seeded_models, train, validation_loss)
+from .unet import UNet
+
+
+def _fwi(fd, wl, obs, f0, iters, pre=None, stop=None):
+    cfg = FWIConfig(bands=((f0, iters),))
+    mask = interior_mask(wl.grid, rows_below_top=4)
+    inv = FWI(fd, lambda f: obs, mask, cfg, preconditioner=pre)
+    e0 = torch.tensor(wl.eps_init, dtype=torch.float32, device=fd.device)
+    s0 = torch.tensor(wl.sig_init, dtype=torch.float32, device=fd.device)
+    torch.cuda.synchronize(fd.device)
+    t0 = time.perf_counter()
+    _, _, hist = inv.run(e0, s0, stop_misfit=stop)
+    torch.cuda.synchronize(fd.device)
+    return hist, time.perf_counter() - t0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--train", type=int, default=10000)
+    ap.add_argument("--val", type=int, default=200)
+    ap.add_argument("--eval", type=int, default=100)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=100000)
+    ap.add_argument("--nt", type=int, default=1500)
+    ap.add_argument("--workers", type=int, default=12, help="host processes generating models")
+    ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    args = ap.parse_args(argv)
+    dev = torch.device("cuda:0")
+    first = W.preconditioner_model(args.seed, nt=args.nt)
+    g = first.grid
+    fd = FDTD(g, first.src, first.rec, device=dev)
+    wav = torch.tensor(ricker(first.f0, g.dt, g.nt), device=dev)
+    scales = PreconditionerScales()
+    gen = lambda s: W.preconditioner_model(s, nt=args.nt)  # noqa: E731
+    H, Wd = g.ny - 2 * g.npml, g.nx - 2 * g.npml
+    seeds_train = np.arange(args.seed, args.seed + args.train)
+    seeds_val = np.arange(args.seed + args.train, args.seed + args.train + args.val)
+    seeds_eval = np.arange(args.seed + 10 ** 6, args.seed + 10 ** 6 + args.eval)
+
+    t_gen = time.perf_counter()
+    X, T, gpu_gen = generate_pairs(fd, seeded_models(seeds_train, args.nt, args.workers),
+                                   len(seeds_train), wav, scales, g.npml)
+    Xv, Tv, _ = generate_pairs(fd, seeded_models(seeds_val, args.nt, args.workers),
+                               len(seeds_val), wav, scales, g.npml)
+    t_gen = time.perf_counter() - t_gen
+
+    net = UNet(4, 32, 4, 2, H, Wd, max_batch=args.batch, device=dev)
+    net.init_params(args.seed)
+    val0 = validation_loss(net, Xv, Tv, args.batch)
+    torch.cuda.synchronize(dev)
+    t_tr = time.perf_counter()
+    losses = train(net, X, T, args.epochs, args.batch, args.lr, seed=args.seed,
+                   decay_every=max(1, args.epochs // 3))
+    torch.cuda.synchronize(dev)
+    t_tr = time.perf_counter() - t_tr
+    val1 = validation_loss(net, Xv, Tv, args.batch)
+    if args.save:
+        np.save(args.save, net.get_params().cpu().numpy())
+    pre = LearnedPreconditioner(net, g.npml, scales)
+
+    rows = []
+    for s in seeds_eval:
+        wl = gen(int(s))
+        obs = fd.forward_model(torch.tensor(wl.eps_true, dtype=torch.float32, device=dev),
+                               torch.tensor(wl.sig_true, dtype=torch.float32, device=dev), wav)
+        h_plain, t_plain = _fwi(fd, wl, obs, wl.f0, args.iters)
+        target = h_plain.final_misfit
+        h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target)
+        rows.append(dict(seed=int(s), J0=h_plain.misfit[0] if h_plain.misfit else None,
+                         J_plain=target, it_plain=len(h_plain.misfit),
+                         ev_plain=int(sum(h_plain.evaluations)), s_plain=t_plain,
+                         J_learned=h_l.final_misfit, it_learned=len(h_l.misfit),
+                         ev_learned=int(sum(h_l.evaluations)), s_learned=t_l,
+                         reached=bool(h_l.final_misfit <= target),
+                         learned_accepted=int(sum(h_l.learned))))
+    reached = [r for r in rows if r["reached"]]
+    out = {
+        "workload": f"precond_{g.nx}x{g.ny}_16shots_nt{g.nt}",
+        "train_models": args.train, "val_models": args.val, "eval_models": args.eval,
+        "epochs": args.epochs, "batch": args.batch,
+        "pair_generation_s": t_gen, "pair_generation_gpu_s": gpu_gen,
+        "training_s": t_tr, "train_loss_first_epoch": losses[0], "train_loss_last_epoch": losses[-1],
+        "val_loss_before": val0, "val_loss_after": val1,
+        "reached_fraction": len(reached) / max(len(rows), 1),
+        "median_iters_plain": float(np.median([r["it_plain"] for r in rows])),
+        "median_iters_learned": float(np.median([r["it_learned"] for r in rows])),
+        "median_evals_plain": float(np.median([r["ev_plain"] for r in rows])),
+        "median_evals_learned": float(np.median([r["ev_learned"] for r in rows])),
+        "median_s_plain": float(np.median([r["s_plain"] for r in rows])),
+        "median_s_learned": float(np.median([r["s_learned"] for r in rows])),
+        "learned_steps_accepted": int(sum(r["learned_accepted"] for r in rows)),
+        "unet_kernel_launches": net.kernel_launches,
+    }
+    print(json.dumps(out))
+    return out, rows
+
+
+if __name__ == "__main__":
+    main()

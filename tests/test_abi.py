@@ -11,7 +11,7 @@ import pytest
 from paper_2506_20513_gb300 import _lib, workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "gprfwi.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("gprfwi.h", "gprfwi_unet.h")]
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +21,7 @@ def lib():
 
 
 def header_symbols():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(gf_[a-z_]+)\s*\(", text)))
 
@@ -102,3 +102,40 @@ def test_ricker_helper_closed_form(lib):
     n = np.arange(nt) * dt - t0
     z = (math.pi * f0 * n) ** 2
     np.testing.assert_allclose(w, 3.0 * (1 - 2 * z) * np.exp(-z), rtol=0, atol=3e-6)
+
+
+def _unet_desc(**kw):
+    d = dict(levels=4, base=32, cin=4, cout=2, height=128, width=256, max_batch=16)
+    d.update(kw)
+    return _lib.UNetDesc(**d)
+
+
+def test_unet_param_count_matches_oracle(lib):
+    from oracle import unet_oracle as U
+    for lv, b, ci, co in ((4, 32, 4, 2), (3, 8, 3, 5), (1, 16, 1, 1), (6, 8, 64, 64)):
+        d = _unet_desc(levels=lv, base=b, cin=ci, cout=co, height=64, width=64, max_batch=1)
+        assert lib.gf_unet_param_count(ctypes.byref(d)) == U.param_count(lv, b, ci, co)
+
+
+@pytest.mark.parametrize("bad", [dict(levels=0), dict(levels=7), dict(base=12), dict(base=4),
+                                 dict(base=64, levels=6), dict(cin=0), dict(cout=65),
+                                 dict(height=100), dict(width=0), dict(max_batch=0),
+                                 dict(max_batch=300)])
+def test_unet_create_rejects_invalid_desc(lib, bad):
+    d = _unet_desc(**bad)
+    assert lib.gf_unet_param_count(ctypes.byref(d)) == -1
+    net = ctypes.c_void_p()
+    assert lib.gf_unet_create(ctypes.byref(net), ctypes.byref(d), 0) == _lib.GF_EINVAL
+    assert not net.value
+    assert lib.gf_unet_last_error(None)
+
+
+def test_unet_null_arguments(lib):
+    assert lib.gf_unet_create(None, None, 0) == _lib.GF_EINVAL
+    assert lib.gf_unet_param_count(None) == -1
+    assert lib.gf_unet_forward(None, 1, None, None, None) == _lib.GF_EINVAL
+    assert lib.gf_unet_loss_and_grad(None, 1, None, None, None, None, None, None) == _lib.GF_EINVAL
+    assert lib.gf_unet_adam_step(None, 1e-3, 0.9, 0.999, 1e-8, None) == _lib.GF_EINVAL
+    assert lib.gf_unet_set_params(None, None, None) == _lib.GF_EINVAL
+    assert lib.gf_unet_kernel_launches(None) == 0
+    lib.gf_unet_destroy(None)
