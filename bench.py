@@ -51,7 +51,8 @@ def parse_args():
     ap.add_argument("--nshots", type=int, default=32)
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch[,variant]")
-    ap.add_argument("--workload", default="multishot", choices=["multishot", "large", "uneven"],
+    ap.add_argument("--workload", default="multishot",
+                    choices=["multishot", "large", "uneven", "unet"],
                     help="multishot: 540x290, 32 shots, nt 2000 (default); large: 2108x1084, "
                          "16 shots, nt 8000 with checkpointing")
     ap.add_argument("--checkpoint", type=int, default=0,
@@ -454,12 +455,92 @@ def uneven(args):
     return 0
 
 
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "bf16_tflops (burst) of measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def unet(args):
+    """Training step of the learned preconditioner's U-Net (4 levels, 32 base channels,
+    4 in / 2 out, 128 x 256 images, batch 16, BF16 kernels): forward, masked MSE, backward,
+    Adam.  The roofline is the tensor-core one of its GEMM launches (algorithmic 2 M N K
+    FLOPs over their CUDA-event time) against the measured cuBLAS bf16 rate."""
+    import torch
+    from oracle import unet_oracle as U
+    from paper_2506_20513_gb300.unet import UNet
+    dev = torch.device("cuda", 0)
+    B, H, Wd = 16, 128, 256
+    net = UNet(4, 32, 4, 2, H, Wd, max_batch=B, device=dev)
+    net.init_params(1)
+    g = torch.Generator().manual_seed(1)
+    x = torch.randn(B, H, Wd, 4, generator=g).to(dev)
+    t = torch.randn(B, H, Wd, 2, generator=g).to(dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    for _ in range(max(3, args.warmup)):
+        net.train_step(x, t, lr=1e-4)
+    torch.cuda.synchronize(dev)
+    net.profile(True)
+    net.profile_read()
+    l0 = net.kernel_launches
+    clocks = ClockSampler(0)
+    clocks.start()
+    total = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        net.train_step(x, t, lr=1e-4)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        total += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    gemm_ms, gemm_n, gemm_flops = net.profile_read()
+    net.profile(False)
+    launches = net.kernel_launches - l0
+    ms = total / args.steps
+    peak, peak_kind = bf16_peak()
+    achieved = gemm_flops / (gemm_ms / 1e3) / 1e12
+    fwd = U.flops_per_sample(4, 32, 4, 2, H, Wd)
+    cpu = None
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        p = U.init_params(rng, 4, 32, 4, 2)
+        xs, ts = rng.standard_normal((1, H, Wd, 4)), rng.standard_normal((1, H, Wd, 2))
+        t0 = time.perf_counter()
+        U.loss_and_gradient(p, xs, ts, None, 4, 32, 4, 2)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one 128x256 sample, FP64 numpy forward + backward, {dt:.2f} s"}
+    line = {"metric": "U-Net training samples/s (learned preconditioner) vs tensor roofline",
+            "value": B * 1e3 / ms, "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "unet_4lvl_32ch_4to2_128x256_batch16",
+                       "fwd_gflop_per_sample": fwd / 1e9,
+                       "l2": "a 256 MB buffer is written before every timed step"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "gemm_kernel (mma.sync bf16)", "peak_source": peak_kind,
+                         "gemm_ms_per_step": gemm_ms / args.steps,
+                         "gemm_launches_per_step": gemm_n / args.steps},
+            "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "uneven":
         return uneven(args)
+    if args.workload == "unet":
+        return unet(args)
     return ours(args)
 
 

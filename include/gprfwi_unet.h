@@ -18,9 +18,10 @@
  * Tensors are channels-last FP32 device arrays: input x [n][height][width][cin], output y
  *   [n][height][width][cout], optional mask [n][height][width] with entries 0 or 1.
  * Loss: L = 1/(2 n height width cout) sum mask (y - target)^2.
- * Arithmetic: activations and weights are rounded to BF16 before every product, products
- *   accumulate in FP32, the loss in FP64; expect agreement with an FP64 evaluation to a few
- *   parts in 10^3 per layer.
+ * Arithmetic: the input, weights, stored activations and the gradients fed to products are
+ *   rounded to BF16 (nearest, ties to even); products accumulate in FP32, the loss in FP64.
+ *   Against an FP64 evaluation outputs agree to about 1e-2; parameter gradients whose sums
+ *   over all cells cancel (the first layer's weights) move by several per cent.
  * Pointers, streams, ownership and error codes follow gprfwi.h: device pointers on the
  *   network's device, owned by the caller, asynchronous on `stream` (a cudaStream_t passed as
  *   void*).  A network object is not thread-safe.
@@ -76,8 +77,26 @@ int gf_unet_loss_and_grad(gf_unet* net, int n, const float* x, const float* targ
  * the gradient of the last gf_unet_loss_and_grad; GF_ESTATE if there is none. */
 int gf_unet_adam_step(gf_unet* net, float lr, float beta1, float beta2, float eps, void* stream);
 
+/* GEMM engine: 1 (default) = tcgen05 tensor-core GEMM (TMEM accumulator) for the K-major
+ * products (forward and input-gradient convolutions), mma.sync for the weight gradients and
+ * unaligned shapes; 0 = mma.sync everywhere.  Both give the same result up to FP32 rounding. */
+int gf_unet_set_gemm(gf_unet* net, int mode);
+
+/* Synchronise `stream` and return GF_OK, or GF_ETIMEOUT if a tensor-core GEMM's bounded wait
+ * for its MMAs expired since the last call (its outputs are then invalid); clears the flag. */
+int gf_unet_status(gf_unet* net, void* stream);
+
 /* Kernels this network has launched since gf_unet_create. */
 long long gf_unet_kernel_launches(const gf_unet* net);
+
+/* enable != 0: from now on bracket every GEMM launch (convolution lowerings, with a split-K
+ * reduction counted in) with CUDA events on its stream, and count its algorithmic FLOPs
+ * 2 M N K; enable == 0 stops and drops what was recorded. */
+int gf_unet_profile(gf_unet* net, int enable);
+
+/* Synchronise on the recorded events; return the summed GEMM time (ms), the number of GEMM
+ * launches and their algorithmic FLOPs since the last read, then clear the record. */
+int gf_unet_profile_read(gf_unet* net, double* ms_total, long long* launches, double* flops);
 
 #ifdef __cplusplus
 }

@@ -40,7 +40,8 @@ constexpr int PLANE = EHM * BX;
 constexpr int kMaxK = 31;     // tile + 2K <= 64 with tile >= 2
 
 __host__ __device__ constexpr size_t smem_floats(int by) {
-    return 2 * PLANE + 2 * by * BX + 4 * PLANE + 6 * EHM + 6 * BX + (kMaxK + 1) * kMaxSrc;
+    return 2 * PLANE + 2 * by * BX + 4 * PLANE + 6 * EHM + 6 * BX + (kMaxK + 1) * kMaxSrc +
+           5 * PLANE;
 }
 
 // Shared-memory carve-up (floats).
@@ -53,6 +54,9 @@ struct Smem {
     float* yprof;    // [6][EHM] row profiles aE bE cE aH bH cH
     float* xprof;    // [6][BX] column profiles aE bE cE aH bH cH
     float* wsrc;     // [kMaxK + 1][kMaxSrc] scaled source samples of this launch
+    float* coef;     // [5][EHM][BX] adjoint: Ca, Cb, the carried Ez^{n+1} and the two
+                     // gradient accumulators of the owned cells (kept here rather than in
+                     // registers, which would spill)
 };
 
 template <int BY>
@@ -66,6 +70,7 @@ __device__ __forceinline__ Smem carve(float* sm) {
     s.yprof = s.psi + 4 * PLANE;
     s.xprof = s.yprof + 6 * EHM;
     s.wsrc = s.xprof + 6 * BX;
+    s.coef = s.wsrc + (kMaxK + 1) * kMaxSrc;
     return s;
 }
 
@@ -142,8 +147,9 @@ __device__ __forceinline__ void stage_profiles(const Smem& s, const TileParams& 
 }
 
 // Load the time-stepping state of the owned cells; CPML memories of strip cells go to
-// shared memory (zero elsewhere).  Returns the row bit masks (y strip, interior).
-template <int RY>
+// shared memory (zero elsewhere), and with kCoefSmem the update coefficients too (ca, cb are
+// then left untouched).  Returns the row bit masks (y strip, interior).
+template <int RY, bool kCoefSmem = false>
 __device__ __forceinline__ void load_state(const TileParams& p, const Cell<RY>& c, const Smem& s,
                                            long long sbase, float* f0, float* f1, float* f2,
                                            float* ca, float* cb, unsigned& ystrip,
@@ -176,7 +182,14 @@ __device__ __forceinline__ void load_state(const TileParams& p, const Cell<RY>& 
             coefficients(__ldg(p.eps_r + g), __ldg(p.sigma + g), p.dt_eps0, ring, cav, cbv);
             if (c.col_int && ly >= p.K && ly < p.K + p.tile_h) interior |= 1u << r;
         }
-        f0[r] = a; f1[r] = b; f2[r] = d; ca[r] = cav; cb[r] = cbv;
+        f0[r] = a; f1[r] = b; f2[r] = d;
+        if (kCoefSmem) {
+            s.coef[l] = cav;
+            s.coef[PLANE + l] = cbv;
+        } else {
+            ca[r] = cav;
+            cb[r] = cbv;
+        }
         if (c.tile_strip) {
             s.psi[l] = pex;
             s.psi[PLANE + l] = pey;
@@ -393,8 +406,7 @@ __global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p)
 // ---------------------------------------------------------------------------------------
 template <int RY, int BY, bool kStrip>
 __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                         float* aez, float* ahx, float* ahy, const float* ca,
-                                         const float* cb, float* ge, float* gs, float* e1,
+                                         float* aez, float* ahx, float* ahy,
                                          unsigned ystrip, unsigned interior, unsigned recmask,
                                          const int* rlist, int nrl, int shot) {
     const int ty = threadIdx.y, K = p.K;
@@ -427,11 +439,12 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int ly = c.ly0 + r, l = ly * BX + c.lx;
-            const float lam = cb[r] * aez[r];
+            const float lam = s.coef[PLANE + l] * aez[r];
             if ((interior >> r) & 1u) {
-                ge[r] -= p.geps * lam * (e1[r] - pf[r]);
-                gs[r] -= 0.5f * lam * (e1[r] + pf[r]);
-                e1[r] = pf[r];
+                const float en1 = s.coef[2 * PLANE + l];
+                s.coef[3 * PLANE + l] -= p.geps * lam * (en1 - pf[r]);
+                s.coef[4 * PLANE + l] -= 0.5f * lam * (en1 + pf[r]);
+                s.coef[2 * PLANE + l] = pf[r];
             }
             if (kStrip && (c.xs || ((ystrip >> r) & 1u))) {
                 const float ayE = s.yprof[ly], byE = s.yprof[EHM + ly], cyE = s.yprof[2 * EHM + ly];
@@ -445,7 +458,7 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
                 wy[r] = -lam * p.rdy;
             }
             sSx[l] = wx[r];
-            aez[r] *= ca[r];
+            aez[r] *= s.coef[l];
         }
         sSyT[ty * BX + c.lx] = wy[0];
     };
@@ -519,16 +532,17 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
     const long long sbase = (long long)shot * p.N;
     const int n1 = p.n0 + K - 1;
 
-    float aez[RY], ahx[RY], ahy[RY], ca[RY], cb[RY], ge[RY], gs[RY], e1[RY];
+    float aez[RY], ahx[RY], ahy[RY];
     unsigned ystrip, interior;
-    load_state<RY>(p, c, s, sbase, aez, ahx, ahy, ca, cb, ystrip, interior);
+    load_state<RY, true>(p, c, s, sbase, aez, ahx, ahy, nullptr, nullptr, ystrip, interior);
     const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
                         (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-        ge[r] = 0.f;
-        gs[r] = 0.f;
-        e1[r] = ((interior >> r) & 1u) ? __ldcs(hcol + (long long)n1 * p.N + r * p.nx) : 0.f;
+        s.coef[3 * PLANE + (c.ly0 + r) * BX + c.lx] = 0.f;
+        s.coef[4 * PLANE + (c.ly0 + r) * BX + c.lx] = 0.f;
+        s.coef[2 * PLANE + (c.ly0 + r) * BX + c.lx] =
+            ((interior >> r) & 1u) ? __ldcs(hcol + (long long)n1 * p.N + r * p.nx) : 0.f;
     }
     stage_profiles(s, p, c.X0, c.Y0, tid);
     const int tile = blockIdx.x;
@@ -540,11 +554,11 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
     __syncthreads();
 
     if (c.tile_strip)
-        adj_body<RY, BY, true>(p, c, s, aez, ahx, ahy, ca, cb, ge, gs, e1, ystrip, interior,
-                               recmask, rlist, nrl, shot);
+        adj_body<RY, BY, true>(p, c, s, aez, ahx, ahy, ystrip, interior, recmask, rlist, nrl,
+                               shot);
     else
-        adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ca, cb, ge, gs, e1, ystrip, interior,
-                                recmask, rlist, nrl, shot);
+        adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ystrip, interior, recmask, rlist, nrl,
+                                shot);
 
     store_state<RY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
     const long long F = (long long)p.nshots * p.N;
@@ -554,8 +568,9 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
         const long long sg = sbase + (long long)(c.Y0 + c.ly0 + r) * p.nx + c.gx;
         // one writer per cell per launch and launches in stream order: a fire-and-forget
         // reduction is deterministic and hides the read latency of += at the end of the CTA
-        atomicAdd(p.grad + sg, ge[r]);
-        atomicAdd(p.grad + F + sg, gs[r]);
+        const int l = (c.ly0 + r) * BX + c.lx;
+        atomicAdd(p.grad + sg, s.coef[3 * PLANE + l]);
+        atomicAdd(p.grad + F + sg, s.coef[4 * PLANE + l]);
     }
 }
 

@@ -17,8 +17,10 @@ driver keeps those pieces around a limited-memory BFGS update:
   reset at each band change;
 * optional learned preconditioner (:class:`.precond.LearnedPreconditioner`): each iteration
   first tries the network's update computed from the raw gradient, the model and the
-  illumination of the band's starting model; the update is kept only if the FDTD misfit
-  decreases, otherwise the plain L-BFGS step is taken.  Accepted steps of either kind feed
+  illumination of the band's starting model (full size, then half); the update is kept only
+  if the FDTD misfit decreases, otherwise the plain L-BFGS step is taken and the network is
+  not consulted again in that band (its prediction no longer helps there, and each try costs
+  a forward model).  Accepted steps of either kind feed
   the L-BFGS memory.
 """
 from __future__ import annotations
@@ -138,17 +140,24 @@ class FWI:
             g = g.double()
             first = True
             n = x.numel() // 2
+            use_net = learned       # the network is tried until its update is first rejected
             for it in range(iters):
                 if stop_misfit is not None and J <= stop_misfit:
                     break
                 torch.cuda.synchronize(self.fd.device)
                 t0 = time.perf_counter()
-                if learned:
+                tries = 0
+                if use_net:
                     de, ds = self.pre.update(ge, gs, eps, illum)
                     d_l = torch.cat([(de * self.mask).reshape(-1).double(),
                                      (ds * self.mask / c.sigma_ref).reshape(-1).double()])
-                    e_c, s_c = self._split((x + d_l).float())
-                    J_c = self._misfit(e_c, s_c, wav, obs)
+                    J_c = float("inf")
+                    for scale in (1.0, 0.5):
+                        e_c, s_c = self._split((x + scale * d_l).float())
+                        J_c = self._misfit(e_c, s_c, wav, obs)
+                        tries += 1
+                        if J_c < J:
+                            break
                     if J_c < J:
                         x_new = torch.cat([e_c.reshape(-1).double(),
                                            (s_c.reshape(-1) / c.sigma_ref).double()])
@@ -162,7 +171,7 @@ class FWI:
                                 S.pop(0)
                                 Y.pop(0)
                         hist.misfit.append(J)
-                        hist.evaluations.append(2)
+                        hist.evaluations.append(tries + 1)
                         torch.cuda.synchronize(self.fd.device)
                         hist.seconds.append(time.perf_counter() - t0)
                         hist.band.append(f0)
@@ -172,6 +181,7 @@ class FWI:
                         if callback:
                             callback(it, J, x)
                         continue
+                    use_net = False
                 # two-loop recursion (Nocedal & Wright, Algorithm 7.4)
                 q = g.clone()
                 alphas = []
@@ -195,7 +205,7 @@ class FWI:
                     peak = float(d[:n].abs().max())
                     if peak > 0:
                         alpha = c.first_step * float(x[:n].max()) / peak
-                evals = 1 if learned else 0
+                evals = tries
                 accepted = False
                 for _ in range(c.backtracks):
                     x_new = x + alpha * d

@@ -9,11 +9,15 @@ solutions (Sec. 1) but trains none; this module is the library's own design:
   g_sigma / max|g_sigma|, eps_r / 10, and log10 of the illumination (sum over shots and
   steps of Ez^2, normalised by its maximum and floored at 1e-6) / 6 + 1;
 * output (2 channels): (eps_true - eps_r) / eps_scale and (sigma_true - sigma) / sig_scale;
-* training pairs: seeded random models (the preconditioner workload generator), the gradient
-  of the L2 misfit at the smoothed starting model and the illumination of that model, all
-  computed by the FDTD/adjoint kernels; the pairs stay resident in device memory;
-* use in FWI: the network's update is tried first; it is kept only if the true FDTD misfit
-  decreases, otherwise the plain L-BFGS step is taken (see :class:`FWI`).
+* training pairs: seeded random models (the preconditioner workload generator); each pair is
+  taken at a model m = m0 + a (m_true - m0) between the smoothed starting model m0 and the
+  truth (a = 0 for half of the pairs, else uniform in [0, 0.8), drawn from the seed), so the
+  network also sees the gradients of later FWI iterates: the gradient of the L2 misfit at m
+  and the illumination of m, computed by the FDTD/adjoint kernels, against the remaining
+  update (1 - a)(m_true - m0); the pairs stay resident in device memory;
+* use in FWI: the network's update is tried first (full, then half size); it is kept only
+  if the true FDTD misfit decreases, otherwise the plain L-BFGS step is taken (see
+  :class:`FWI`).
 
 Feature scaling, cropping and batching are a few elementwise tensor operations (PyTorch as
 plumbing); the network runs in the library's BF16 kernels (:mod:`.unet`), the gradients in
@@ -87,11 +91,22 @@ class LearnedPreconditioner:
         return de, ds
 
 
+def pair_fractions(seeds) -> np.ndarray:
+    """The fraction a of the way from the start model to the truth at which each seed's
+    training pair is taken: 0 for half of the seeds, else uniform in [0, 0.8)."""
+    out = np.empty(len(seeds))
+    for i, s in enumerate(seeds):
+        r = np.random.default_rng([int(s), 77])
+        out[i] = 0.0 if r.random() < 0.5 else 0.8 * r.random()
+    return out
+
+
 def generate_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales, npml: int,
-                   progress=None):
+                   progress=None, fractions=None):
     """Training pairs for N models from the iterable ``models``, each (eps_true, sig_true,
-    eps_init, sig_init) as device or host [ny, nx] arrays sharing the geometry of ``fd``.
-    Returns X [N, H, W, 4] and T [N, H, W, 2] on the device (and the seconds spent)."""
+    eps_init, sig_init) as device or host [ny, nx] arrays sharing the geometry of ``fd``,
+    taken at m0 + a (m_true - m0) with a = fractions[i] (0 if not given).  Returns
+    X [N, H, W, 4] and T [N, H, W, 2] on the device (and the seconds spent)."""
     ny, nx = fd.shape
     H, W = ny - 2 * npml, nx - 2 * npml
     dev = fd.device
@@ -101,6 +116,10 @@ def generate_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales, np
     t0 = time.perf_counter()
     for i, (et, st, ei, si) in enumerate(models):
         et, st, ei, si = (torch.as_tensor(a, dtype=torch.float32).to(dev) for a in (et, st, ei, si))
+        if fractions is not None and fractions[i] > 0:
+            a = float(fractions[i])
+            ei = (ei + a * (et - ei)).contiguous()
+            si = (si + a * (st - si)).contiguous()
         obs = fd.forward_model(et, st, wavelet)
         _, illum = fd.forward_model(ei, si, wavelet, illumination=True)
         _, ge, gs = fd.misfit_and_gradient(ei, si, wavelet, obs)

@@ -25,7 +25,7 @@ from . import workloads as W
 from .fdtd import FDTD, ricker
 from .fwi import FWI, FWIConfig, interior_mask
 from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pairs,
-                      seeded_models, train, validation_loss)
+                      pair_fractions, seeded_models, train, validation_loss)
 from .unet import UNet
 
 
@@ -55,6 +55,9 @@ def main(argv=None):
     ap.add_argument("--nt", type=int, default=1500)
     ap.add_argument("--workers", type=int, default=12, help="host processes generating models")
     ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
+    ap.add_argument("--out", default=None, help="write the summary and per-model rows (JSON)")
+    ap.add_argument("--load", default=None,
+                    help="trained parameters (.npy) to evaluate instead of generating and training")
     args = ap.parse_args(argv)
     dev = torch.device("cuda:0")
     first = W.preconditioner_model(args.seed, nt=args.nt)
@@ -68,14 +71,33 @@ def main(argv=None):
     seeds_val = np.arange(args.seed + args.train, args.seed + args.train + args.val)
     seeds_eval = np.arange(args.seed + 10 ** 6, args.seed + 10 ** 6 + args.eval)
 
+    net = UNet(4, 32, 4, 2, H, Wd, max_batch=args.batch, device=dev)
+    t_gen = gpu_gen = t_tr = 0.0
+    losses = [float("nan")]
+    val0 = val1 = float("nan")
+    if args.load:
+        net.set_params(torch.from_numpy(np.load(args.load).astype(np.float32)).to(dev))
+        args.train = args.val = args.epochs = 0
+    else:
+        t_gen, gpu_gen, t_tr, losses, val0, val1 = _train(args, fd, wav, scales, g, net,
+                                                          seeds_train, seeds_val)
+        if args.save:
+            np.save(args.save, net.get_params().cpu().numpy())
+    pre = LearnedPreconditioner(net, g.npml, scales)
+    return _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr, losses,
+                     val0, val1)
+
+
+def _train(args, fd, wav, scales, g, net, seeds_train, seeds_val):
+    dev = fd.device
     t_gen = time.perf_counter()
     X, T, gpu_gen = generate_pairs(fd, seeded_models(seeds_train, args.nt, args.workers),
-                                   len(seeds_train), wav, scales, g.npml)
+                                   len(seeds_train), wav, scales, g.npml,
+                                   fractions=pair_fractions(seeds_train))
     Xv, Tv, _ = generate_pairs(fd, seeded_models(seeds_val, args.nt, args.workers),
-                               len(seeds_val), wav, scales, g.npml)
+                               len(seeds_val), wav, scales, g.npml,
+                               fractions=pair_fractions(seeds_val))
     t_gen = time.perf_counter() - t_gen
-
-    net = UNet(4, 32, 4, 2, H, Wd, max_batch=args.batch, device=dev)
     net.init_params(args.seed)
     val0 = validation_loss(net, Xv, Tv, args.batch)
     torch.cuda.synchronize(dev)
@@ -85,10 +107,12 @@ def main(argv=None):
     torch.cuda.synchronize(dev)
     t_tr = time.perf_counter() - t_tr
     val1 = validation_loss(net, Xv, Tv, args.batch)
-    if args.save:
-        np.save(args.save, net.get_params().cpu().numpy())
-    pre = LearnedPreconditioner(net, g.npml, scales)
+    return t_gen, gpu_gen, t_tr, losses, val0, val1
 
+
+def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr, losses, val0,
+              val1):
+    dev = fd.device
     rows = []
     for s in seeds_eval:
         wl = gen(int(s))
@@ -108,6 +132,7 @@ def main(argv=None):
     out = {
         "workload": f"precond_{g.nx}x{g.ny}_16shots_nt{g.nt}",
         "train_models": args.train, "val_models": args.val, "eval_models": args.eval,
+        "loaded_params": args.load,
         "epochs": args.epochs, "batch": args.batch,
         "pair_generation_s": t_gen, "pair_generation_gpu_s": gpu_gen,
         "training_s": t_tr, "train_loss_first_epoch": losses[0], "train_loss_last_epoch": losses[-1],
@@ -122,7 +147,11 @@ def main(argv=None):
         "learned_steps_accepted": int(sum(r["learned_accepted"] for r in rows)),
         "unet_kernel_launches": net.kernel_launches,
     }
+    out["train_loss_per_epoch"] = losses
     print(json.dumps(out))
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump({"summary": out, "rows": rows}, f, indent=1)
     return out, rows
 
 

@@ -148,3 +148,22 @@ class UNet:
     @property
     def kernel_launches(self) -> int:
         return int(self.lib.gf_unet_kernel_launches(self._net))
+
+    def set_gemm(self, mode: int):
+        """1: tcgen05 tensor-core GEMM for the K-major products (default); 0: mma.sync only."""
+        self._check(self.lib.gf_unet_set_gemm(self._net, int(mode)), self._net)
+
+    def status(self):
+        """Synchronise and raise if a tensor-core GEMM gave up waiting (outputs invalid)."""
+        self._check(self.lib.gf_unet_status(self._net, self._stream()), self._net)
+
+    def profile(self, enable: bool = True):
+        """Bracket every GEMM launch with CUDA events (see :meth:`profile_read`)."""
+        self._check(self.lib.gf_unet_profile(self._net, int(enable)), self._net)
+
+    def profile_read(self):
+        """(GEMM milliseconds, GEMM launches, algorithmic FLOPs) since the last read."""
+        ms, n, fl = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+        self._check(self.lib.gf_unet_profile_read(self._net, ctypes.byref(ms), ctypes.byref(n),
+                                                  ctypes.byref(fl)), self._net)
+        return ms.value, n.value, fl.value
