@@ -41,6 +41,11 @@ GemmPlan plan_gemm(int M, int N, int K);
 // partial: FP32 buffer of plan.splits * M * N elements when plan.splits > 1
 cudaError_t gemm(GemmArgs a, const GemmPlan& plan, float* partial, cudaStream_t st);
 
+// tcgen05 GEMM for K-major operands (ta = 0, tb = 1, K, lda, ldb multiples of 8, 16-byte
+// aligned pointers), no split-K; a bounded-wait expiry sets bit 0 of *status (device int).
+bool tc_gemm_supported(const GemmArgs& a);
+cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st);
+
 cudaError_t im2col3(const void* x, int nb, int H, int W, int C, void* col, cudaStream_t st);
 cudaError_t flip_transpose(const void* w, int Co, int Ci, void* wt, cudaStream_t st);
 cudaError_t relu_bwd(const float* dy, const void* y, long long n, int relu, float* dz, void* dzb,

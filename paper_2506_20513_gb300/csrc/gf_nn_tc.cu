@@ -1,0 +1,277 @@
+// gf_nn_tc.cu -- tcgen05 (5th-generation tensor core) BF16 GEMM for the U-Net's K-major
+// products: C[M,N] = A[M,K] B[N,K]^T with both operands stored K-contiguous (the forward
+// convolution col(x) W^T and the input-gradient convolution col(dz) Wt^T).
+//
+// One CTA of 128 threads computes a 128 x BN tile: the accumulator lives in tensor memory
+// (TMEM, BN FP32 columns of 128 lanes), one elected thread issues tcgen05.mma (M = 128, N = BN,
+// K = 16 per instruction) from operands staged in shared memory, and tcgen05.commit signals
+// an mbarrier per pipeline stage when the MMAs that read it are done.  Operands are staged by
+// all threads with 16-byte cp.async into the canonical K-major 128-byte-swizzled layout
+// (8-row x 128-byte atoms, 16-byte chunk c of row r at chunk c ^ (r mod 8)); a stage holds 64
+// k values (one 128-byte row per matrix row).  Every mbarrier wait is bounded: on expiry the
+// kernel records an error in the status word, skips the remaining work, waits (bounded) for
+// its own MMAs and frees its TMEM.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gf_nn.cuh"
+
+namespace gf {
+namespace nn {
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTM = 128;       // tile rows (TMEM lanes)
+constexpr int kTK = 64;        // k per stage: one 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+// true once the phase with the given parity has completed; false after kSpinLimit polls or
+// as soon as another CTA has recorded an expiry in *status
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int* status) {
+    for (unsigned i = 0; i < kSpinLimit; ++i) {
+        if ((i & 1023) == 1023 && *reinterpret_cast<const volatile int*>(status)) return false;
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// K-major, 128-byte swizzle smem matrix descriptor (tcgen05 format): start address >> 4,
+// leading byte offset 16 B (unused for swizzled K-major), stride byte offset 1024 B between
+// 8-row groups, descriptor version 1, swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M = 128.
+template <int BN>
+__device__ __forceinline__ uint32_t instr_desc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(kTM >> 4) << 24);
+}
+
+// Stage rows [row0, row0 + R) x k [k0, k0 + 64) of a K-major operand (ld elements per row)
+// into a 1024-byte-aligned swizzled buffer; rows >= rowlim and k >= K read as zero.
+template <int R>
+__device__ __forceinline__ void stage_sw128(uint32_t base, const bf16* __restrict__ X, int ld,
+                                            int row0, int rowlim, int k0, int K, int tid) {
+    for (int c = tid; c < R * 8; c += 128) {
+        const int r = c >> 3, ch = c & 7;
+        const uint32_t dst = base + r * 128 + ((ch ^ (r & 7)) << 4);
+        const int gr = row0 + r, gk = k0 + ch * 8;
+        if (gr < rowlim && gk < K)
+            cp_async16(dst, X + (long long)gr * ld + gk);
+        else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst), "r"(0) : "memory");
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    constexpr int kABytes = kTM * 128, kBBytes = BN * 128, kStageBytes = kABytes + kBBytes;
+    // 1024-byte alignment of the stage buffers (required by the 128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023) & ~1023u;
+    const uint32_t bars = base + kStages * kStageBytes;  // kStages mbarriers (8 B each)
+    const uint32_t tmem_slot = bars + 8 * kStages;       // TMEM address written by tcgen05.alloc
+    unsigned char* const slot_ptr = smem_raw + (tmem_slot - raw);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * BN;
+    // another CTA already gave up: do nothing (one read, made uniform over the CTA, before any
+    // TMEM use)
+    if (__syncthreads_or(tid == 0 ? *reinterpret_cast<const volatile int*>(status) : 0)) return;
+    const int nk = (a.K + kTK - 1) / kTK;
+    constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns: a power of two >= 32
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(bars + 8 * s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         tmem_slot),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(slot_ptr);
+
+    bool ok = true;
+    // prologue: the first kStages - 1 k-tiles
+    for (int s = 0; s < kStages - 1; ++s) {
+        if (s < nk) {
+            const uint32_t sa = base + s * kStageBytes;
+            stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, s * kTK, a.K, tid);
+            stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, s * kTK, a.K, tid);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    const uint32_t idesc = instr_desc<BN>();
+    for (int kt = 0; kt < nk && ok; ++kt) {
+        const int s = kt % kStages;
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 2) : "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sa = base + s * kStageBytes;
+#pragma unroll
+            for (int kk = 0; kk < kTK / 16; ++kk) {
+                const uint64_t ad = sw128_desc(sa + kk * 32);
+                const uint64_t bd = sw128_desc(sa + kABytes + kk * 32);
+                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                    bars + 8 * s)
+                : "memory");
+        }
+        // refill the stage that k-tile kt + kStages - 1 uses, once the MMAs of its previous
+        // k-tile (kt - 1) have read it
+        const int kn = kt + kStages - 1;
+        if (kn < nk) {
+            const int sn = kn % kStages;
+            if (kt >= 1) ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status);
+            if (ok) {
+                const uint32_t sa = base + sn * kStageBytes;
+                stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, kn * kTK, a.K, tid);
+                stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, kn * kTK, a.K, tid);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        ok = __syncthreads_and(ok);
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // the last commit covers every MMA issued before it
+    if (ok && nk > 0)
+        ok = mbar_wait(bars + 8 * ((nk - 1) % kStages), (uint32_t)(((nk - 1) / kStages) & 1), status);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+        if (tid == 0) atomicOr(status, 1);
+        // give MMAs still in flight a bounded time to finish before TMEM is freed (the poll of
+        // *status is skipped here: this CTA set it)
+        const uint32_t lb = bars + 8 * ((max(nk, 1) - 1) % kStages);
+        const uint32_t lp = (uint32_t)(((max(nk, 1) - 1) / kStages) & 1);
+        for (unsigned i = 0; i < kSpinLimit; ++i) {
+            uint32_t done;
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                " selp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(lb), "r"(lp)
+                : "memory");
+            if (done) break;
+        }
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int r = m0 + warp * 32 + lane;  // TMEM lane = tile row
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+                "%13,%14,%15}, [%16];\n"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr)
+                : "memory");
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (r < a.M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = n0 + c0 + j;
+                    if (c >= a.N) break;
+                    const float acc = __uint_as_float(v[j]);
+                    if (a.Cb) {
+                        float y = acc + (a.bias ? a.bias[c] : 0.f);
+                        if (a.relu) y = fmaxf(y, 0.f);
+                        a.Cb[(long long)r * a.ldc + c] = __float2bfloat16(y);
+                    } else {
+                        float* p = a.C + (long long)r * a.ldc + c;
+                        float y = a.alpha * acc + (a.bias ? a.bias[c] : 0.f);
+                        if (a.beta != 0.f) y += a.beta * *p;
+                        *p = y;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(kCols)
+                     : "memory");
+}
+
+template <int BN>
+constexpr size_t tc_smem_bytes() {
+    return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 8 * kStages + 16;
+}
+
+template <int BN>
+cudaError_t tc_launch(const GemmArgs& a, int* status, cudaStream_t st) {
+    static bool configured = false;  // per process; the attribute is per device function
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_nt_kernel<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc_smem_bytes<BN>());
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const dim3 grid((a.N + BN - 1) / BN, (a.M + kTM - 1) / kTM);
+    tc_gemm_nt_kernel<BN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_gemm_supported(const GemmArgs& a) {
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return a.ta == 0 && a.tb == 1 && a.K % 8 == 0 && a.lda % 8 == 0 && a.ldb % 8 == 0 &&
+           al(a.A) && al(a.B) && a.M > 0 && a.N > 0 && a.K > 0 && (a.M + kTM - 1) / kTM <= 65535;
+}
+
+cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st) {
+    if (!tc_gemm_supported(a) || !status) return cudaErrorInvalidValue;
+    if (a.N <= 32) return tc_launch<32>(a, status, st);
+    if (a.N <= 64) return tc_launch<64>(a, status, st);
+    if (a.N <= 128) return tc_launch<128>(a, status, st);
+    return tc_launch<256>(a, status, st);
+}
+
+}  // namespace nn
+}  // namespace gf

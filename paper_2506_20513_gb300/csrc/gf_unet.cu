@@ -97,9 +97,16 @@ struct gf_unet {
     long long partial_cap = 0;
     float* colpart = nullptr;
     double *lpart = nullptr, *lval = nullptr;
+    int* status = nullptr;  // device word: bit 0 = a tensor-core GEMM wait expired
+    int gemm_mode = 0;      // 1: tcgen05 for K-major products, mma.sync otherwise; 0: mma.sync
     int step = 0;
     bool have_grad = false;
     long long launches = 0;
+    // GEMM profiling: events around every GEMM launch and its algorithmic FLOPs (2 M N K)
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    std::vector<cudaEvent_t> ev_pool;
+    double prof_flops = 0.0;
     std::vector<void*> allocs;
     char err[512] = "no error";
 
@@ -221,6 +228,7 @@ int create(gf_unet* u) {
     need(u->colpart = dalloc<float>(u, colsum_max));
     need(u->lpart = dalloc<double>(u, gf::nn::kMseBlocks));
     need(u->lval = dalloc<double>(u, 1));
+    need(u->status = dalloc<int>(u, 1));
     if (!ok) {
         cudaGetLastError();
         return fail(nullptr, GF_ENOMEM, "gf_unet_create: device allocation failed");
@@ -229,6 +237,7 @@ int create(gf_unet* u) {
         cudaMemset(u->wb, 0, u->np * sizeof(bf16)) != cudaSuccess ||
         cudaMemset(u->adam_m, 0, u->np * sizeof(float)) != cudaSuccess ||
         cudaMemset(u->adam_v, 0, u->np * sizeof(float)) != cudaSuccess ||
+        cudaMemset(u->status, 0, sizeof(int)) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(nullptr, GF_ECUDA, "gf_unet_create: initialisation failed");
     return GF_OK;
@@ -238,6 +247,11 @@ void release(gf_unet* u) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(u->device);
+    for (auto& pr : u->prof_ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (cudaEvent_t e : u->ev_pool) cudaEventDestroy(e);
     for (void* p : u->allocs) cudaFree(p);
     cudaSetDevice(prev);
     delete u;
@@ -251,7 +265,25 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
     }
     if (p.splits > 1 && (long long)p.splits * a.M * a.N > u->partial_cap)
         return fail(u, GF_ECUDA, "split-K buffer too small (internal error)");
-    cudaError_t e = gf::nn::gemm(a, p, u->partial, st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (u->profiling) {
+        for (cudaEvent_t* ev : {&e0, &e1}) {
+            if (!u->ev_pool.empty()) {
+                *ev = u->ev_pool.back();
+                u->ev_pool.pop_back();
+            } else if (cudaEventCreate(ev) != cudaSuccess) {
+                return fail(u, GF_ECUDA, "cudaEventCreate failed");
+            }
+        }
+        cudaEventRecord(e0, st);
+    }
+    const bool tc = u->gemm_mode == 1 && p.splits == 1 && gf::nn::tc_gemm_supported(a);
+    cudaError_t e = tc ? gf::nn::tc_gemm(a, u->status, st) : gf::nn::gemm(a, p, u->partial, st);
+    if (u->profiling) {
+        cudaEventRecord(e1, st);
+        u->prof_ev.emplace_back(e0, e1);
+        u->prof_flops += 2.0 * a.M * a.N * (double)a.K;
+    }
     if (e != cudaSuccess) return fail(u, GF_ECUDA, "gemm: %s", cudaGetErrorString(e));
     u->launches += p.splits > 1 ? 2 : 1;
     return GF_OK;
@@ -562,5 +594,59 @@ int gf_unet_adam_step(gf_unet* u, float lr, float beta1, float beta2, float eps,
 }
 
 long long gf_unet_kernel_launches(const gf_unet* u) { return u ? u->launches : 0; }
+
+int gf_unet_set_gemm(gf_unet* u, int mode) {
+    if (!u || mode < 0 || mode > 1) return fail(u, GF_EINVAL, "gf_unet_set_gemm: mode must be 0 or 1");
+    u->gemm_mode = mode;
+    return GF_OK;
+}
+
+int gf_unet_status(gf_unet* u, void* stream) {
+    if (!u) return fail(u, GF_EINVAL, "gf_unet_status: NULL network");
+    DeviceGuard g(u->device);
+    int h = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess ||
+        cudaMemcpy(&h, u->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(u->status, 0, sizeof(int)) != cudaSuccess)
+        return fail(u, GF_ECUDA, "gf_unet_status: %s", cudaGetErrorString(cudaGetLastError()));
+    if (h) return fail(u, GF_ETIMEOUT, "a tensor-core GEMM gave up waiting for its MMAs");
+    return GF_OK;
+}
+
+int gf_unet_profile(gf_unet* u, int enable) {
+    if (!u) return fail(u, GF_EINVAL, "gf_unet_profile: NULL network");
+    u->profiling = enable != 0;
+    if (!u->profiling) {
+        for (auto& pr : u->prof_ev) {
+            u->ev_pool.push_back(pr.first);
+            u->ev_pool.push_back(pr.second);
+        }
+        u->prof_ev.clear();
+        u->prof_flops = 0.0;
+    }
+    return GF_OK;
+}
+
+int gf_unet_profile_read(gf_unet* u, double* ms_total, long long* launches, double* flops) {
+    if (!u || !ms_total || !launches || !flops)
+        return fail(u, GF_EINVAL, "gf_unet_profile_read: NULL argument");
+    DeviceGuard g(u->device);
+    double total = 0.0;
+    for (auto& pr : u->prof_ev) {
+        if (cudaEventSynchronize(pr.second) != cudaSuccess)
+            return fail(u, GF_ECUDA, "gf_unet_profile_read: event synchronize failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        total += ms;
+        u->ev_pool.push_back(pr.first);
+        u->ev_pool.push_back(pr.second);
+    }
+    *ms_total = total;
+    *launches = (long long)u->prof_ev.size();
+    *flops = u->prof_flops;
+    u->prof_ev.clear();
+    u->prof_flops = 0.0;
+    return GF_OK;
+}
 
 }  // extern "C"
