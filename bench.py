@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
 # gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 334.6 MB per K = 6 launch
-    "adj@0a924e17d8ee@540x290x32@default": 11.1287,
+    # profiles/adj_tile_multishot_540x290x32.md: 319.4 MB per K = 6 launch
+    "adj@140298ea8aea@540x290x32@default": 10.6230,
 }
 
 
@@ -60,6 +60,8 @@ def parse_args():
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--gemm", type=int, default=0, choices=[0, 1],
+                    help="U-Net workload: 0 = mma.sync GEMMs, 1 = tcgen05 for the K-major ones")
     ap.add_argument("--fwi-iters", type=int, default=3,
                     help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
     return ap.parse_args()
@@ -475,6 +477,7 @@ def unet(args):
     dev = torch.device("cuda", 0)
     B, H, Wd = 16, 128, 256
     net = UNet(4, 32, 4, 2, H, Wd, max_batch=B, device=dev)
+    net.set_gemm(args.gemm)
     net.init_params(1)
     g = torch.Generator().manual_seed(1)
     x = torch.randn(B, H, Wd, 4, generator=g).to(dev)
@@ -498,6 +501,7 @@ def unet(args):
         torch.cuda.synchronize(dev)
         total += e0.elapsed_time(e1)
     clk = clocks.stop()
+    net.status()
     gemm_ms, gemm_n, gemm_flops = net.profile_read()
     net.profile(False)
     launches = net.kernel_launches - l0
@@ -524,7 +528,9 @@ def unet(args):
                        "l2": "a 256 MB buffer is written before every timed step"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "gemm_kernel (mma.sync bf16)", "peak_source": peak_kind,
+                         "kernel": ("tc_gemm_nt_kernel (tcgen05) + gemm_kernel (mma.sync)"
+                                    if args.gemm else "gemm_kernel (mma.sync bf16)"),
+                         "peak_source": peak_kind,
                          "gemm_ms_per_step": gemm_ms / args.steps,
                          "gemm_launches_per_step": gemm_n / args.steps},
             "cpu_baseline": cpu, "e2e": None, "gpu_launches": launches, "clocks": clk}

@@ -35,9 +35,10 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def make(dev, levels, base, cin, cout, H, W, n, seed):
+def make(dev, levels, base, cin, cout, H, W, n, seed, gemm=0):
     from paper_2506_20513_gb300.unet import UNet
     net = UNet(levels, base, cin, cout, H, W, max_batch=n, device=dev)
+    net.set_gemm(gemm)
     p = net.init_params(seed).cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(seed + 1)
     x = rng.standard_normal((n, H, W, cin)).astype(np.float32)
@@ -77,28 +78,47 @@ def compare(net, p, x, t, mask, dev, levels, base, cin, cout):
     assert rel(y, y0) <= 3e-2
     assert L == pytest.approx(L0, rel=3e-2)
     check_blocks(g, g0, levels, base, cin, cout, 0.1, tol_first=0.25)
+    net.status()
     return y
 
 
+@pytest.mark.parametrize("gemm", [0, 1], ids=["mma_sync", "tcgen05"])
 @pytest.mark.parametrize("levels,base,cin,cout,H,W,n", [
     (3, 8, 4, 2, 24, 44, 2),    # ragged GEMM tiles (2112 rows), narrow channels
     (2, 16, 3, 5, 10, 14, 3),   # odd cin / cout: scalar staging paths
     (1, 8, 4, 2, 9, 7, 1),      # one level: no pooling, no decoder
 ])
-def test_unet_forward_loss_and_gradient_match_oracle(dev, levels, base, cin, cout, H, W, n):
-    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=100 + levels)
+def test_unet_forward_loss_and_gradient_match_oracle(dev, levels, base, cin, cout, H, W, n, gemm):
+    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=100 + levels, gemm=gemm)
     compare(net, p, x, t, mask, dev, levels, base, cin, cout)
 
 
-def test_unet_full_size_matches_oracle(dev):
+@pytest.mark.parametrize("gemm", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_unet_full_size_matches_oracle(dev, gemm):
     """The preconditioner's network: 4 levels, 32 base channels, 4 in / 2 out, 128 x 256."""
     levels, base, cin, cout, H, W, n = 4, 32, 4, 2, 128, 256, 2
-    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=7)
+    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=7, gemm=gemm)
     y = compare(net, p, x, t, mask, dev, levels, base, cin, cout)
     # a batch of one gives the first image's own result
     xd = torch.from_numpy(x).to(dev)
     y1 = net.forward(xd[:1].contiguous()).cpu().numpy()
     np.testing.assert_array_equal(y1, y[:1])
+
+
+def test_unet_gemm_engines_agree(dev):
+    """tcgen05 and mma.sync products of the full network: same result up to FP32 summation
+    order (which can move a stored BF16 activation by one unit in the last place)."""
+    levels, base, cin, cout, H, W, n = 4, 32, 4, 2, 128, 256, 4
+    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=9, gemm=0)
+    xd, td = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
+    y0 = net.forward(xd).clone()
+    _, g0 = net.loss_and_grad(xd, td, grads=True)
+    net.set_gemm(1)
+    y1 = net.forward(xd).clone()
+    _, g1 = net.loss_and_grad(xd, td, grads=True)
+    net.status()
+    assert rel(y1.cpu().numpy(), y0.cpu().numpy()) <= 2e-3
+    assert rel(g1.cpu().numpy(), g0.cpu().numpy()) <= 1e-2
 
 
 def test_unet_gradient_is_deterministic_and_adam_matches_oracle(dev):
