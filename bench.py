@@ -37,8 +37,8 @@ FALLBACK_HBM_GBS = 6800.0
 # dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
 # gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 319.4 MB per K = 6 launch
-    "adj@140298ea8aea@540x290x32@default": 10.6230,
+    # profiles/adj_tile_multishot_540x290x32.md: 340.4 MB per K = 7 launch
+    "adj@bb1f83f02e9c@540x290x32@default": 9.7027,
 }
 
 
@@ -375,7 +375,7 @@ def ours(args):
                        "shots_per_gpu": wl.nshots, "nt": g.nt, "nrec": wl.nrec,
                        "cell_updates_per_step": wl.cell_updates() * world,
                        "s_per_gradient": ms / args.steps / 1e3,
-                       "tiling": args.tile or "default 52,52,6,variant 0",
+                       "tiling": args.tile or "default 50,50,7,variant 0",
                        "l2": "inputs larger than L2: each step streams the "
                              f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
                              "through HBM" if not args.checkpoint else

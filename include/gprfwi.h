@@ -112,7 +112,7 @@ int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
 /* Time-blocking options: tile interior width/height in cells and time steps per launch K.
  * The staged tile (interior + K cells of halo on each side) is at most 64 x 64 cells; K = 0
  * keeps the current K, a tile size of 0 selects the largest that fits (64 - 2K).  Default:
- * 52 x 52 interior, K = 6.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
+ * 50 x 50 interior, K = 7.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
  * not fit. */
 int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
 

@@ -46,7 +46,7 @@ struct gf_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
-    int tile_w = 52, tile_h = 52, K = 6, variant = 0;
+    int tile_w = 50, tile_h = 50, K = 7, variant = 0;
     int store_mode = GF_STORE_FULL, ckpt_k = 0;
     const float* last_wavelet = nullptr;  // wavelet of the stored forward (recomputation)
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]

@@ -245,8 +245,7 @@ __device__ __forceinline__ unsigned owned_mask(const int* __restrict__ idx, int 
 // ---------------------------------------------------------------------------------------
 template <int RY, int BY, bool kStrip, bool kHist, bool kIllum>
 __device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                         float* ez, float* hx, float* hy, const float* ca,
-                                         const float* cb, float* ill, unsigned ystrip,
+                                         float* ez, float* hx, float* hy, float* ill, unsigned ystrip,
                                          unsigned interior, unsigned srcmask, const int* rlist,
                                          int nrl, int shot, int tid) {
     constexpr int NTHR = BX * BY;
@@ -334,7 +333,7 @@ __device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c,
 #pragma unroll
         for (int r = 0; r < RY; ++r) {
             const int l = (c.ly0 + r) * BX + c.lx;
-            const float v = ca[r] * ez[r] + cb[r] * q[r];
+            const float v = s.coef[l] * ez[r] + s.coef[PLANE + l] * q[r];
             ez[r] = v;
             sEz[l] = v;
             if ((interior >> r) & 1u) {
@@ -356,9 +355,9 @@ __global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p)
     c.init(p);
     const long long sbase = (long long)shot * p.N;
 
-    float ez[RY], hx[RY], hy[RY], ca[RY], cb[RY], ill[RY];
+    float ez[RY], hx[RY], hy[RY], ill[RY];
     unsigned ystrip, interior;
-    load_state<RY>(p, c, s, sbase, ez, hx, hy, ca, cb, ystrip, interior);
+    load_state<RY, true>(p, c, s, sbase, ez, hx, hy, nullptr, nullptr, ystrip, interior);
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         s.xplane[(c.ly0 + r) * BX + c.lx] = ez[r];
@@ -386,10 +385,10 @@ __global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p)
     __syncthreads();
 
     if (c.tile_strip)
-        fwd_body<RY, BY, true, kHist, kIllum>(p, c, s, ez, hx, hy, ca, cb, ill, ystrip, interior,
+        fwd_body<RY, BY, true, kHist, kIllum>(p, c, s, ez, hx, hy, ill, ystrip, interior,
                                               srcmask, rlist, nrl, shot, tid);
     else
-        fwd_body<RY, BY, false, kHist, kIllum>(p, c, s, ez, hx, hy, ca, cb, ill, ystrip, interior,
+        fwd_body<RY, BY, false, kHist, kIllum>(p, c, s, ez, hx, hy, ill, ystrip, interior,
                                                srcmask, rlist, nrl, shot, tid);
 
     store_state<RY>(p, c, s, sbase, ez, hx, hy, ystrip, interior);

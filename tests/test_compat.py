@@ -1,0 +1,69 @@
+"""The paper-shaped compute(...) entry point: geometry on the CPU (Table values of the
+cross-hole example, Sec. 4), traces and autograd gradients on the GPU against the direct
+FDTD calls."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2506_20513_gb300.compat import paper_geometry
+
+TABLE = dict(dx=0.05, dy=0.05, nx=220, ny=120, source_location=[0.5, 0.5, 0],
+             source_step=[0.25, 0, 0], receiver_location=[0.5, 5.5, 0],
+             receiver_step=[0.05, 0, 0], step=40, nsrc=1, nrx=200)
+
+
+def test_geometry_of_the_cross_hole_table():
+    src, rec = paper_geometry(**TABLE)
+    assert src.shape == (40, 1, 2) and rec.shape == (40, 200, 2)
+    np.testing.assert_array_equal(src[:, 0, 0], 10 + 5 * np.arange(40))   # 0.5 m + s 0.25 m
+    assert (src[:, 0, 1] == 10).all()
+    np.testing.assert_array_equal(rec[0, :, 0], 10 + np.arange(200))      # 0.5 m + r 0.05 m
+    assert (rec[..., 1] == 110).all()                                       # 5.5 m
+    assert (rec == rec[0]).all()                                            # same line every shot
+
+
+def test_geometry_rejects_points_outside_the_grid():
+    bad = dict(TABLE, source_step=[0.3, 0, 0])   # shot 39 at 12.2 m > 10.9 m
+    with pytest.raises(ValueError):
+        paper_geometry(**bad)
+    with pytest.raises(ValueError):
+        paper_geometry(**dict(TABLE, nsrc=2))
+
+
+@pytest.mark.gpu
+def test_compute_matches_the_library_and_differentiates():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20513_gb300 import FDTD
+    from paper_2506_20513_gb300.compat import compute
+    from paper_2506_20513_gb300.fdtd import ricker
+    from paper_2506_20513_gb300.workloads import GridSpec, default_pml
+    dev = torch.device("cuda:0")
+    nx, ny, pml, dx, dt, f0 = 60, 40, 8, 0.02, 4e-11, 4e8
+    rng = np.random.default_rng(3)
+    eps = torch.tensor(4 + 3 * rng.random((nx, ny, 1)), dtype=torch.float32, device=dev)
+    sig = torch.tensor(1e-3 + 1e-2 * rng.random((nx, ny, 1)), dtype=torch.float32, device=dev)
+    eps.requires_grad_()
+    sig.requires_grad_()
+    args = dict(device="cuda", dx=dx, ny=ny, nx=nx, nz=1, time_windows=200 * dt,
+                source=["hertzian", "z"], source_location=[0.2, 0.2, 0],
+                source_step=[0.2, 0, 0], receiver_location=[0.2, 0.6, 0],
+                receiver_step=[0.04, 0, 0], pmlthick=pml, source_amplitudes=["ricker", 2.0, f0],
+                step=3, epsilon=eps, sigma=sig, miu=1, nsrc=1, nrx=20, freq=None, dt=dt)
+    tr, t = compute(**args)
+    assert tr.shape == (3, 200, 20) and t.shape == (200,)
+    (0.5 * (tr ** 2).sum()).backward()
+    # the same run through the FDTD object, in its own layout
+    src, rec = paper_geometry(dx, dx, nx, ny, [0.2, 0.2, 0], [0.2, 0, 0], [0.2, 0.6, 0],
+                              [0.04, 0, 0], 3, 1, 20)
+    g = default_pml(GridSpec(nx=nx, ny=ny, npml=pml, nt=200, dx=dx, dy=dx, dt=dt), f0)
+    fd = FDTD(g, src, rec, device=dev)
+    wav = torch.tensor(2.0 * ricker(f0, dt, 200), device=dev)
+    e2 = eps.detach()[:, :, 0].T.contiguous()
+    s2 = sig.detach()[:, :, 0].T.contiguous()
+    tr2 = fd.forward_model(e2, s2, wav)
+    torch.testing.assert_close(tr.detach(), tr2, rtol=1e-6, atol=1e-6 * float(tr2.abs().max()))
+    zero = torch.zeros_like(tr2)
+    _, ge, gs = fd.misfit_and_gradient(e2, s2, wav, zero)
+    torch.testing.assert_close(eps.grad[:, :, 0].T, ge, rtol=1e-5, atol=1e-6 * float(ge.abs().max()))
+    torch.testing.assert_close(sig.grad[:, :, 0].T, gs, rtol=1e-5, atol=1e-6 * float(gs.abs().max()))

@@ -322,6 +322,31 @@ def test_full_size_multishot_sampled(dev):
     assert rel(gs, gs64) <= GRAD_TOL
 
 
+
+def test_directional_derivative_matches_gradient(dev):
+    """<g, dm> against central differences of J along a smooth random direction dm of both
+    parameters at once (the linearised model -> misfit map against its adjoint, FP32)."""
+    from paper_2506_20513_gb300 import FDTD
+    from scipy.ndimage import gaussian_filter
+    wl = W.small_random(31, nxp=70, nyp=50, npml=8, nt=300, nshots=3, nrec=9)
+    g = wl.grid
+    wav = t32(wavelets(wl), dev)
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    obs = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), wav)
+    e0, s0 = t32(wl.eps_init, dev), t32(wl.sig_init, dev)
+    J, ge, gs = fd.misfit_and_gradient(e0, s0, wav, obs)
+    rng = np.random.default_rng(31)
+    de = gaussian_filter(rng.standard_normal((g.ny, g.nx)), 3.0)
+    ds = gaussian_filter(rng.standard_normal((g.ny, g.nx)), 3.0)
+    de *= 0.01 * float(e0.mean()) / np.abs(de).max()
+    ds *= 0.01 * float(s0.mean()) / np.abs(ds).max()
+    pred = float((ge.double() * t32(de, dev).double()).sum() + (gs.double() * t32(ds, dev).double()).sum())
+    J1 = []
+    for h in (1.0, -1.0):
+        J1.append(float(fd.misfit(e0 + h * t32(de, dev), s0 + h * t32(ds, dev), wav, obs).item()))
+    fdv = (J1[0] - J1[1]) / 2.0
+    assert fdv == pytest.approx(pred, rel=2e-3)
+
 def test_large_grid_gradient_vs_central_differences(dev):
     """2108x1084 grid (30-cell CPML), dx 5 mm, 1 GHz, 16 shots, 400 receivers, checkpointed
     gradient (nt shortened to 1500 to bound the test time): central differences of the
