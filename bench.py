@@ -60,8 +60,9 @@ def parse_args():
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--gemm", type=int, default=0, choices=[0, 1],
-                    help="U-Net workload: 0 = mma.sync GEMMs, 1 = tcgen05 for the K-major ones")
+    ap.add_argument("--gemm", type=int, default=1, choices=[0, 1],
+                    help="U-Net workload: 1 = tcgen05 for the K-major products (implicit "
+                         "im2col), 0 = explicit im2col and mma.sync GEMMs")
     ap.add_argument("--fwi-iters", type=int, default=3,
                     help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
     return ap.parse_args()

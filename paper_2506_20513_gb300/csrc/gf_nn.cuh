@@ -28,6 +28,11 @@ struct GemmArgs {
     const float* bias = nullptr;
     int relu = 0;
     float alpha = 1.f, beta = 0.f;
+    // tcgen05 engine only: when conv_h > 0, A is not read from A/lda but gathered as the 3x3
+    // im2col of the channels-last image A [M / (conv_h conv_w)][conv_h][conv_w][conv_c]:
+    // A[m][k] = image[n, h + k / (3 conv_c) - 1, w + (k / conv_c) % 3 - 1, k % conv_c] with
+    // m = (n conv_h + h) conv_w + w, zero outside the image (conv_c a multiple of 8).
+    int conv_h = 0, conv_w = 0, conv_c = 0;
     // filled in by gemm()
     int kchunk = 0, va = 0, vb = 0;
     float* P = nullptr;
@@ -42,7 +47,8 @@ GemmPlan plan_gemm(int M, int N, int K);
 cudaError_t gemm(GemmArgs a, const GemmPlan& plan, float* partial, cudaStream_t st);
 
 // tcgen05 GEMM for K-major operands (ta = 0, tb = 1, K, lda, ldb multiples of 8, 16-byte
-// aligned pointers), no split-K; a bounded-wait expiry sets bit 0 of *status (device int).
+// aligned pointers; or A an implicit im2col, see GemmArgs::conv_h), no split-K; a
+// bounded-wait expiry sets bit 0 of *status (device int).
 bool tc_gemm_supported(const GemmArgs& a);
 cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st);
 

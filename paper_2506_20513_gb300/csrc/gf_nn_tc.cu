@@ -87,6 +87,45 @@ __device__ __forceinline__ void stage_sw128(uint32_t base, const bf16* __restric
     }
 }
 
+// Per-thread geometry of the implicit im2col A operand: thread tid stages chunk tid & 7 of
+// rows (tid >> 3) + 16 i, i = 0..7, in every stage, so the pixel of each of its rows is
+// decomposed once per CTA.
+struct ConvRows {
+    int pix[8];  // (n H + h) W + w of the row, or -1 beyond M
+    int h[8], w[8];
+};
+
+__device__ __forceinline__ void conv_rows(const GemmArgs& a, int m0, int tid, ConvRows& cr) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + (tid >> 3) + 16 * i;
+        const int w = m % a.conv_w, t = m / a.conv_w;
+        cr.pix[i] = m < a.M ? m : -1;
+        cr.h[i] = t % a.conv_h;
+        cr.w[i] = w;
+    }
+}
+
+// Stage the A tile of k [k0, k0 + 64) from the image (implicit im2col, swizzled as above).
+__device__ __forceinline__ void stage_conv_a(uint32_t base, const GemmArgs& a, const ConvRows& cr,
+                                             int k0, int tid) {
+    const int ch = tid & 7, gk = k0 + ch * 8;
+    const int tap = gk / a.conv_c, c = gk - tap * a.conv_c;
+    const int dh = tap / 3 - 1, dw = tap % 3 - 1;
+    const bool kin = gk < a.K;
+    const long long shift = (long long)dh * a.conv_w + dw;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = (tid >> 3) + 16 * i;
+        const uint32_t dst = base + r * 128 + ((ch ^ (r & 7)) << 4);
+        const int hh = cr.h[i] + dh, ww = cr.w[i] + dw;
+        if (kin && cr.pix[i] >= 0 && hh >= 0 && hh < a.conv_h && ww >= 0 && ww < a.conv_w)
+            cp_async16(dst, a.A + ((long long)cr.pix[i] + shift) * a.conv_c + c);
+        else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst), "r"(0) : "memory");
+    }
+}
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -123,11 +162,20 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(slot_ptr);
 
     bool ok = true;
+    const bool conv = a.conv_h > 0;
+    ConvRows cr;
+    if (conv) conv_rows(a, m0, tid, cr);
+    auto stage_a = [&](uint32_t sa, int k0) {
+        if (conv)
+            stage_conv_a(sa, a, cr, k0, tid);
+        else
+            stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, k0, a.K, tid);
+    };
     // prologue: the first kStages - 1 k-tiles
     for (int s = 0; s < kStages - 1; ++s) {
         if (s < nk) {
             const uint32_t sa = base + s * kStageBytes;
-            stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, s * kTK, a.K, tid);
+            stage_a(sa, s * kTK);
             stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, s * kTK, a.K, tid);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -165,7 +213,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
             if (kt >= 1) ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status);
             if (ok) {
                 const uint32_t sa = base + sn * kStageBytes;
-                stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, kn * kTK, a.K, tid);
+                stage_a(sa, kn * kTK);
                 stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, kn * kTK, a.K, tid);
             }
         }
@@ -209,7 +257,20 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (r < a.M) {
+            const bool vec = a.Cb && c0 + 16 <= a.N - n0 && (a.ldc & 7) == 0 &&
+                             ((n0 + c0) & 7) == 0 && (((uintptr_t)a.Cb) & 15) == 0;
+            if (r < a.M && vec) {
+                __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float y = __uint_as_float(v[j]) + (a.bias ? a.bias[n0 + c0 + j] : 0.f);
+                    if (a.relu) y = fmaxf(y, 0.f);
+                    o[j] = __float2bfloat16(y);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(a.Cb + (long long)r * a.ldc + n0 + c0);
+                dst[0] = reinterpret_cast<const uint4*>(o)[0];
+                dst[1] = reinterpret_cast<const uint4*>(o)[1];
+            } else if (r < a.M) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int c = n0 + c0 + j;
@@ -261,8 +322,11 @@ cudaError_t tc_launch(const GemmArgs& a, int* status, cudaStream_t st) {
 
 bool tc_gemm_supported(const GemmArgs& a) {
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-    return a.ta == 0 && a.tb == 1 && a.K % 8 == 0 && a.lda % 8 == 0 && a.ldb % 8 == 0 &&
-           al(a.A) && al(a.B) && a.M > 0 && a.N > 0 && a.K > 0 && (a.M + kTM - 1) / kTM <= 65535;
+    const bool a_ok = a.conv_h > 0 ? (a.conv_w > 0 && a.conv_c % 8 == 0 && a.K == 9 * a.conv_c &&
+                                      a.M % (a.conv_h * a.conv_w) == 0)
+                                   : a.lda % 8 == 0;
+    return a.ta == 0 && a.tb == 1 && a.K % 8 == 0 && a_ok && a.ldb % 8 == 0 && al(a.A) &&
+           al(a.B) && a.M > 0 && a.N > 0 && a.K > 0 && (a.M + kTM - 1) / kTM <= 65535;
 }
 
 cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st) {

@@ -98,7 +98,7 @@ struct gf_unet {
     float* colpart = nullptr;
     double *lpart = nullptr, *lval = nullptr;
     int* status = nullptr;  // device word: bit 0 = a tensor-core GEMM wait expired
-    int gemm_mode = 0;      // 1: tcgen05 for K-major products, mma.sync otherwise; 0: mma.sync
+    int gemm_mode = 1;      // 1: tcgen05 for K-major products, mma.sync otherwise; 0: mma.sync
     int step = 0;
     bool have_grad = false;
     long long launches = 0;
@@ -277,7 +277,14 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
         }
         cudaEventRecord(e0, st);
     }
-    const bool tc = u->gemm_mode == 1 && p.splits == 1 && gf::nn::tc_gemm_supported(a);
+    // an implicit-im2col operand (conv_h > 0) is only understood by the tcgen05 engine
+    const bool tc = (u->gemm_mode == 1 || a.conv_h > 0) && (p.splits == 1 || a.conv_h > 0) &&
+                    gf::nn::tc_gemm_supported(a);
+    if (a.conv_h > 0 && !tc) return fail(u, GF_ECUDA, "implicit im2col without tcgen05 (internal)");
+    if (tc) {
+        p.splits = 1;
+        p.kchunk = std::max(32, (a.K + 31) / 32 * 32);
+    }
     cudaError_t e = tc ? gf::nn::tc_gemm(a, u->status, st) : gf::nn::gemm(a, p, u->partial, st);
     if (u->profiling) {
         cudaEventRecord(e1, st);
@@ -290,16 +297,30 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
 }
 
 // relu(conv3x3(in) + b) -> out (BF16), n images at the conv's level
+// Fill the A operand of a 3x3 convolution GEMM over the image `in` (n images, H x W, C
+// channels): an implicit im2col read by the tcgen05 engine when it can take it, else an
+// explicit one in the col buffer.
+int conv_operand(gf_unet* u, gf::nn::GemmArgs& a, const bf16* in, int n, int H, int W, int C,
+                 cudaStream_t st) {
+    a.A = in;
+    a.lda = 9 * C;
+    a.conv_h = H;
+    a.conv_w = W;
+    a.conv_c = C;
+    if (u->gemm_mode == 1 && gf::nn::tc_gemm_supported(a)) return GF_OK;
+    a.conv_h = a.conv_w = a.conv_c = 0;
+    a.A = u->col;
+    NN_CUDA(u, gf::nn::im2col3(in, n, H, W, C, u->col, st));
+    return GF_OK;
+}
+
 int conv_forward(gf_unet* u, const Conv& c, const bf16* in, bf16* out, int n, cudaStream_t st) {
     const int H = u->H(c.level), W = u->W(c.level);
     const int rows = n * H * W;
-    NN_CUDA(u, gf::nn::im2col3(in, n, H, W, c.ci, u->col, st));
     gf::nn::GemmArgs a;
     a.M = rows;
     a.N = c.co;
     a.K = 9 * c.ci;
-    a.A = u->col;
-    a.lda = 9 * c.ci;
     a.ta = 0;
     a.B = u->wb + c.woff;
     a.ldb = 9 * c.ci;
@@ -308,6 +329,8 @@ int conv_forward(gf_unet* u, const Conv& c, const bf16* in, bf16* out, int n, cu
     a.ldc = c.co;
     a.bias = u->params + c.boff;
     a.relu = 1;
+    const int rc = conv_operand(u, a, in, n, H, W, c.ci, st);
+    if (rc) return rc;
     return run_gemm(u, a, false, st);
 }
 
@@ -378,13 +401,11 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
     int rc = run_gemm(u, a, true, st);
     if (rc || !gin) return rc;
     NN_CUDA(u, gf::nn::flip_transpose(u->wb + c.woff, c.co, c.ci, u->wt, st));
-    NN_CUDA(u, gf::nn::im2col3(u->dzb, n, H, W, c.co, u->col, st));
     gf::nn::GemmArgs b;
     b.M = rows;
     b.N = c.ci;
     b.K = 9 * c.co;
-    b.A = u->col;
-    b.lda = 9 * c.co;
+    if ((rc = conv_operand(u, b, u->dzb, n, H, W, c.co, st))) return rc;
     b.B = u->wt;
     b.ldb = 9 * c.co;
     b.tb = 1;
