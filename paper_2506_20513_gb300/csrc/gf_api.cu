@@ -963,7 +963,7 @@ int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     struct Cand { int variant, K; };
     std::vector<Cand> cands;
     for (int v = 0; v < 2; ++v)
-        for (int K : {3, 4, 5, 6, 8, 10}) cands.push_back({v, K});
+        for (int K : {3, 4, 5, 6, 7, 8, 10}) cands.push_back({v, K});
     for (int K : {4, 6}) cands.push_back({2, K});
     const int steps = probe_steps > 0 ? probe_steps : 48;
     cudaEvent_t e0, e1;
