@@ -84,6 +84,13 @@ int gf_unet_adam_step(gf_unet* net, float lr, float beta1, float beta2, float ep
  * result up to FP32 rounding. */
 int gf_unet_set_gemm(gf_unet* net, int mode);
 
+/* Failure-path hook (tests): polls > 0 limits every tensor-core GEMM pipeline wait to that
+ * many polls and makes each GEMM's final wait wait on a barrier nothing arrives at, so it
+ * expires: the GEMMs skip their epilogue (outputs invalid, GF_ETIMEOUT from
+ * gf_unet_status), drain the MMAs they committed (built-in limit) and free their TMEM; no
+ * fault, the context stays usable.  polls = 0 restores the built-in limit (2^22 polls). */
+int gf_unet_set_wait_budget(gf_unet* net, unsigned polls);
+
 /* Synchronise `stream` and return GF_OK, or GF_ETIMEOUT if a tensor-core GEMM's bounded wait
  * for its MMAs expired since the last call (its outputs are then invalid); clears the flag. */
 int gf_unet_status(gf_unet* net, void* stream);

@@ -42,7 +42,7 @@ EXPORTS = (
     "gf_unet_param_count", "gf_unet_create", "gf_unet_destroy", "gf_unet_last_error",
     "gf_unet_set_params", "gf_unet_get_params", "gf_unet_forward", "gf_unet_loss_and_grad",
     "gf_unet_adam_step", "gf_unet_kernel_launches", "gf_unet_profile", "gf_unet_profile_read",
-    "gf_unet_set_gemm", "gf_unet_status",
+    "gf_unet_set_gemm", "gf_unet_status", "gf_unet_set_wait_budget",
 )
 GF_KERNEL_FWD = 0
 GF_KERNEL_ADJ = 1
@@ -141,6 +141,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_unet_profile": (i, [vp, i]),
             "gf_unet_set_gemm": (i, [vp, i]),
             "gf_unet_status": (i, [vp, vp]),
+            "gf_unet_set_wait_budget": (i, [vp, ctypes.c_uint]),
             "gf_unet_profile_read": (i, [vp, P(ctypes.c_double), P(ctypes.c_longlong),
                                          P(ctypes.c_double)]),
         }

@@ -33,6 +33,10 @@ struct GemmArgs {
     // A[m][k] = image[n, h + k / (3 conv_c) - 1, w + (k / conv_c) % 3 - 1, k % conv_c] with
     // m = (n conv_h + h) conv_w + w, zero outside the image (conv_c a multiple of 8).
     int conv_h = 0, conv_w = 0, conv_c = 0;
+    // tcgen05 engine only, failure-path tests: wait_polls > 0 limits every pipeline mbarrier
+    // wait to that many polls and makes the final one wait on a barrier nobody arrives at, so
+    // it expires (deterministically, without faulting); 0 = the built-in limit, no injection
+    unsigned wait_polls = 0;
     // filled in by gemm()
     int kchunk = 0, va = 0, vb = 0;
     float* P = nullptr;

@@ -39,10 +39,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
 }
 
-// true once the phase with the given parity has completed; false after kSpinLimit polls or
-// as soon as another CTA has recorded an expiry in *status
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int* status) {
-    for (unsigned i = 0; i < kSpinLimit; ++i) {
+// true once the phase with the given parity has completed; false after `limit` polls or as
+// soon as another CTA has recorded an expiry in *status
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const int* status,
+                                          unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i) {
         if ((i & 1023) == 1023 && *reinterpret_cast<const volatile int*>(status)) return false;
         uint32_t done;
         asm volatile(
@@ -134,7 +135,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023) & ~1023u;
     const uint32_t bars = base + kStages * kStageBytes;  // kStages mbarriers (8 B each)
-    const uint32_t tmem_slot = bars + 8 * kStages;       // TMEM address written by tcgen05.alloc
+    const uint32_t never = bars + 8 * kStages;           // an mbarrier nobody arrives at
+    const uint32_t tmem_slot = never + 8;                // TMEM address written by tcgen05.alloc
     unsigned char* const slot_ptr = smem_raw + (tmem_slot - raw);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -147,6 +149,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(bars + 8 * s, 1);
+        mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
@@ -162,6 +165,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(slot_ptr);
 
     bool ok = true;
+    const unsigned polls = a.wait_polls ? a.wait_polls : kSpinLimit;
+    const bool inject = a.wait_polls != 0;
+    int kdone = -1;  // last k-tile whose MMAs were issued and committed
     const bool conv = a.conv_h > 0;
     ConvRows cr;
     if (conv) conv_rows(a, m0, tid, cr);
@@ -183,6 +189,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     const uint32_t idesc = instr_desc<BN>();
     for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % kStages;
+        kdone = kt;
         asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -210,7 +217,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
         const int kn = kt + kStages - 1;
         if (kn < nk) {
             const int sn = kn % kStages;
-            if (kt >= 1) ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status);
+            if (kt >= 1)
+                ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status, polls);
             if (ok) {
                 const uint32_t sa = base + sn * kStageBytes;
                 stage_a(sa, kn * kTK);
@@ -223,15 +231,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     // the last commit covers every MMA issued before it
     if (ok && nk > 0)
-        ok = mbar_wait(bars + 8 * ((nk - 1) % kStages), (uint32_t)(((nk - 1) / kStages) & 1), status);
+        ok = inject ? mbar_wait(never, 0, status, polls)
+                 : mbar_wait(bars + 8 * ((nk - 1) % kStages), (uint32_t)(((nk - 1) / kStages) & 1),
+                             status, polls);
     ok = __syncthreads_and(ok);
     if (!ok) {
         if (tid == 0) atomicOr(status, 1);
-        // give MMAs still in flight a bounded time to finish before TMEM is freed (the poll of
-        // *status is skipped here: this CTA set it)
-        const uint32_t lb = bars + 8 * ((max(nk, 1) - 1) % kStages);
-        const uint32_t lp = (uint32_t)(((max(nk, 1) - 1) / kStages) & 1);
-        for (unsigned i = 0; i < kSpinLimit; ++i) {
+        // give the MMAs this CTA committed a bounded time to finish before TMEM is freed (the
+        // poll of *status is skipped here: this CTA set it)
+        const uint32_t lb = bars + 8 * ((kdone < 0 ? 0 : kdone) % kStages);
+        const uint32_t lp = (uint32_t)(((kdone < 0 ? 0 : kdone) / kStages) & 1);
+        for (unsigned i = 0; kdone >= 0 && i < kSpinLimit; ++i) {
             uint32_t done;
             asm volatile(
                 "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -300,7 +310,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
 
 template <int BN>
 constexpr size_t tc_smem_bytes() {
-    return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 8 * kStages + 16;
+    return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 8 * kStages + 8 + 16;
 }
 
 template <int BN>

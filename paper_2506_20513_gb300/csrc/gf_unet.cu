@@ -99,6 +99,7 @@ struct gf_unet {
     double *lpart = nullptr, *lval = nullptr;
     int* status = nullptr;  // device word: bit 0 = a tensor-core GEMM wait expired
     int gemm_mode = 1;      // 1: tcgen05 for K-major products, mma.sync otherwise; 0: mma.sync
+    unsigned wait_polls = 0;  // tcgen05 wait budget (0 = built-in)
     int step = 0;
     bool have_grad = false;
     long long launches = 0;
@@ -284,6 +285,7 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
     if (tc) {
         p.splits = 1;
         p.kchunk = std::max(32, (a.K + 31) / 32 * 32);
+        a.wait_polls = u->wait_polls;
     }
     cudaError_t e = tc ? gf::nn::tc_gemm(a, u->status, st) : gf::nn::gemm(a, p, u->partial, st);
     if (u->profiling) {
@@ -619,6 +621,12 @@ long long gf_unet_kernel_launches(const gf_unet* u) { return u ? u->launches : 0
 int gf_unet_set_gemm(gf_unet* u, int mode) {
     if (!u || mode < 0 || mode > 1) return fail(u, GF_EINVAL, "gf_unet_set_gemm: mode must be 0 or 1");
     u->gemm_mode = mode;
+    return GF_OK;
+}
+
+int gf_unet_set_wait_budget(gf_unet* u, unsigned polls) {
+    if (!u) return fail(u, GF_EINVAL, "gf_unet_set_wait_budget: NULL network");
+    u->wait_polls = polls;
     return GF_OK;
 }
 

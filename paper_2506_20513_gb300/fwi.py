@@ -26,6 +26,7 @@ driver keeps those pieces around a limited-memory BFGS update:
 from __future__ import annotations
 
 import ctypes
+import json
 import time
 from dataclasses import dataclass, field
 
@@ -119,34 +120,63 @@ class FWI:
         return eps, sig
 
     def run(self, eps0: torch.Tensor, sig0: torch.Tensor, callback=None,
-            stop_misfit: float | None = None):
-        """Iterate every band; with ``stop_misfit`` stop as soon as J <= stop_misfit."""
+            stop_misfit: float | None = None, checkpoint: str | None = None,
+            checkpoint_every: int = 0, resume: str | None = None, log: str | None = None):
+        """Iterate every band; with ``stop_misfit`` stop as soon as J <= stop_misfit.
+
+        ``checkpoint`` / ``checkpoint_every``: after every that many iterations of a band, save
+        the driver state (model, gradient, misfit, L-BFGS pairs, band and iteration, the
+        learned step's state and the history so far) to that file.  ``resume``: continue from
+        such a file instead of starting at (eps0, sig0); a resumed run continues exactly as the
+        uninterrupted one would (every kernel is deterministic).  ``log``: append one JSON line
+        per iteration (band, iteration, misfit, evaluations, seconds, learned)."""
         c = self.cfg
+        dev = self.fd.device
         hist = FWIHistory()
         learned = self.pre is not None
         x = torch.cat([eps0.reshape(-1).double(), (sig0.reshape(-1) / c.sigma_ref).double()])
-        x = x.to(self.fd.device)
-        for f0, iters in c.bands:
-            wav = torch.tensor(ricker(f0, self.fd.grid.dt, self.fd.grid.nt), device=self.fd.device)
+        x = x.to(dev)
+        st = torch.load(resume, map_location=dev, weights_only=False) if resume else None
+        if st is not None:
+            for k in ("misfit", "evaluations", "seconds", "band", "learned"):
+                getattr(hist, k).extend(st["hist"][k])
+        logf = open(log, "a") if log else None
+        J = float("nan")
+        for bi, (f0, iters) in enumerate(c.bands):
+            if st is not None and bi < st["band_index"]:
+                continue
+            wav = torch.tensor(ricker(f0, self.fd.grid.dt, self.fd.grid.nt), device=dev)
             obs = self.observed(f0)
-            S, Y = [], []
-            eps, sig = self._split(x.float())
-            illum = None
-            if learned:
-                _, illum = self.fd.forward_model(eps, sig, wav, illumination=True)
-                J, g, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+            ge = gs = illum = None
+            if st is not None and bi == st["band_index"]:
+                x, g, J = st["x"].to(dev), st["g"].to(dev), st["J"]
+                S = [t.to(dev) for t in st["S"]]
+                Y = [t.to(dev) for t in st["Y"]]
+                first, use_net, it0 = st["first"], st["use_net"], st["iteration"]
+                if learned:
+                    ge, gs, illum = (st[k].to(dev) for k in ("ge", "gs", "illum"))
+                eps, sig = self._split(x.float())
+                st = None
             else:
-                J, g = self.gradient(eps, sig, wav, obs)
-            g = g.double()
-            first = True
+                S, Y = [], []
+                eps, sig = self._split(x.float())
+                if learned:
+                    _, illum = self.fd.forward_model(eps, sig, wav, illumination=True)
+                    J, g, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+                else:
+                    J, g = self.gradient(eps, sig, wav, obs)
+                g = g.double()
+                first = True
+                use_net = learned   # the network is tried until its update is first rejected
+                it0 = 0
             n = x.numel() // 2
-            use_net = learned       # the network is tried until its update is first rejected
-            for it in range(iters):
+            for it in range(it0, iters):
                 if stop_misfit is not None and J <= stop_misfit:
                     break
-                torch.cuda.synchronize(self.fd.device)
+                torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
                 tries = 0
+                kept = False
                 if use_net:
                     de, ds = self.pre.update(ge, gs, eps, illum)
                     d_l = torch.cat([(de * self.mask).reshape(-1).double(),
@@ -159,71 +189,48 @@ class FWI:
                         if J_c < J:
                             break
                     if J_c < J:
-                        x_new = torch.cat([e_c.reshape(-1).double(),
-                                           (s_c.reshape(-1) / c.sigma_ref).double()])
-                        J_next, g_new, ge, gs = self.gradient(e_c, s_c, wav, obs, raw=True)
-                        g_new = g_new.double()
-                        s_k, y_k = x_new - x, g_new - g
-                        if float(torch.dot(s_k, y_k)) > 1e-12 * float(torch.dot(s_k, s_k)) ** 0.5:
-                            S.append(s_k)
-                            Y.append(y_k)
-                            if len(S) > c.memory:
-                                S.pop(0)
-                                Y.pop(0)
-                        hist.misfit.append(J)
-                        hist.evaluations.append(tries + 1)
-                        torch.cuda.synchronize(self.fd.device)
-                        hist.seconds.append(time.perf_counter() - t0)
-                        hist.band.append(f0)
-                        hist.learned.append(True)
-                        x, g, J, eps, sig = x_new, g_new, J_next, e_c, s_c
-                        first = False
-                        if callback:
-                            callback(it, J, x)
-                        continue
-                    use_net = False
-                # two-loop recursion (Nocedal & Wright, Algorithm 7.4)
-                q = g.clone()
-                alphas = []
-                for s, y in zip(reversed(S), reversed(Y)):
-                    rho = 1.0 / torch.dot(y, s)
-                    a = rho * torch.dot(s, q)
-                    q -= a * y
-                    alphas.append((rho, a))
-                if S:
-                    q *= torch.dot(S[-1], Y[-1]) / torch.dot(Y[-1], Y[-1])
-                for (s, y), (rho, a) in zip(zip(S, Y), reversed(alphas)):
-                    b = rho * torch.dot(y, q)
-                    q += s * (a - b)
-                d = -q
-                slope = float(torch.dot(g, d))
-                if slope >= 0:  # not a descent direction: restart from steepest descent
-                    S, Y, d, first = [], [], -g, True
+                        kept = True
+                        eps, sig = e_c, s_c
+                    else:
+                        use_net = False
+                if not kept:
+                    # two-loop recursion (Nocedal & Wright, Algorithm 7.4)
+                    q = g.clone()
+                    alphas = []
+                    for s_, y_ in zip(reversed(S), reversed(Y)):
+                        rho = 1.0 / torch.dot(y_, s_)
+                        a = rho * torch.dot(s_, q)
+                        q -= a * y_
+                        alphas.append((rho, a))
+                    if S:
+                        q *= torch.dot(S[-1], Y[-1]) / torch.dot(Y[-1], Y[-1])
+                    for (s_, y_), (rho, a) in zip(zip(S, Y), reversed(alphas)):
+                        b = rho * torch.dot(y_, q)
+                        q += s_ * (a - b)
+                    d = -q
                     slope = float(torch.dot(g, d))
-                alpha = 1.0
-                if first:
-                    peak = float(d[:n].abs().max())
-                    if peak > 0:
-                        alpha = c.first_step * float(x[:n].max()) / peak
-                evals = tries
-                accepted = False
-                for _ in range(c.backtracks):
-                    x_new = x + alpha * d
-                    eps, sig = self._split(x_new.float())
-                    J_new = self._misfit(eps, sig, wav, obs)
-                    evals += 1
-                    if J_new <= J + c.armijo * alpha * slope:
-                        accepted = True
+                    if slope >= 0:  # not a descent direction: restart from steepest descent
+                        S, Y, d, first = [], [], -g, True
+                        slope = float(torch.dot(g, d))
+                    alpha = 1.0
+                    if first:
+                        peak = float(d[:n].abs().max())
+                        if peak > 0:
+                            alpha = c.first_step * float(x[:n].max()) / peak
+                    accepted = False
+                    for _ in range(c.backtracks):
+                        eps, sig = self._split((x + alpha * d).float())
+                        J_new = self._misfit(eps, sig, wav, obs)
+                        tries += 1
+                        if J_new <= J + c.armijo * alpha * slope:
+                            accepted = True
+                            break
+                        alpha *= 0.5
+                    if not accepted:
+                        self._record(hist, logf, f0, it, J, tries, time.perf_counter() - t0, False)
+                        eps, sig = self._split(x.float())
                         break
-                    alpha *= 0.5
-                if not accepted:
-                    hist.misfit.append(J)
-                    hist.evaluations.append(evals)
-                    hist.seconds.append(time.perf_counter() - t0)
-                    hist.band.append(f0)
-                    hist.learned.append(False)
-                    break
-                # project onto the physical ranges, then the new gradient
+                # the accepted model (projected onto the physical ranges), then its gradient
                 x_new = torch.cat([eps.reshape(-1).double(), (sig.reshape(-1) / c.sigma_ref).double()])
                 if learned:
                     J_next, g_new, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
@@ -237,18 +244,38 @@ class FWI:
                     if len(S) > c.memory:
                         S.pop(0)
                         Y.pop(0)
-                hist.misfit.append(J)
-                hist.evaluations.append(evals + 1)
-                torch.cuda.synchronize(self.fd.device)
-                hist.seconds.append(time.perf_counter() - t0)
-                hist.band.append(f0)
-                hist.learned.append(False)
+                torch.cuda.synchronize(dev)
+                self._record(hist, logf, f0, it, J, tries + 1, time.perf_counter() - t0, kept)
                 x, g, J, first = x_new, g_new, J_next, False
+                if checkpoint and checkpoint_every > 0 and (it + 1) % checkpoint_every == 0:
+                    state = dict(band_index=bi, iteration=it + 1, x=x.cpu(), g=g.cpu(), J=J,
+                                 S=[t.cpu() for t in S], Y=[t.cpu() for t in Y], first=first,
+                                 use_net=use_net,
+                                 hist={k: list(getattr(hist, k)) for k in
+                                       ("misfit", "evaluations", "seconds", "band", "learned")})
+                    if learned:
+                        state.update(ge=ge.cpu(), gs=gs.cpu(), illum=illum.cpu())
+                    torch.save(state, checkpoint)
                 if callback:
                     callback(it, J, x)
+        if logf:
+            logf.close()
         eps, sig = self._split(x.float())
         hist.final_misfit = J
         return eps, sig, hist
+
+    @staticmethod
+    def _record(hist, logf, f0, it, J, evals, seconds, learned):
+        hist.misfit.append(J)
+        hist.evaluations.append(evals)
+        hist.seconds.append(seconds)
+        hist.band.append(f0)
+        hist.learned.append(learned)
+        if logf:
+            logf.write(json.dumps({"band_f0": f0, "iteration": it, "misfit": J,
+                                   "evaluations": evals, "seconds": seconds,
+                                   "learned": learned}) + "\n")
+            logf.flush()
 
 
 def interior_mask(grid, rows_below_top: int = 0) -> torch.Tensor:

@@ -153,6 +153,10 @@ class UNet:
         """1: tcgen05 tensor-core GEMM for the K-major products (default); 0: mma.sync only."""
         self._check(self.lib.gf_unet_set_gemm(self._net, int(mode)), self._net)
 
+    def set_wait_budget(self, polls: int):
+        """Failure-path hook: polls per tensor-core GEMM wait (0 = built-in limit)."""
+        self._check(self.lib.gf_unet_set_wait_budget(self._net, int(polls)), self._net)
+
     def status(self):
         """Synchronise and raise if a tensor-core GEMM gave up waiting (outputs invalid)."""
         self._check(self.lib.gf_unet_status(self._net, self._stream()), self._net)

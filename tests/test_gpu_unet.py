@@ -167,3 +167,24 @@ def test_unet_training_reduces_loss(dev):
         loss = net.train_step(x, t, lr=3e-3)
         first = float(loss.item()) if first is None else first
     assert float(loss.item()) < 0.3 * first
+
+
+def test_unet_expired_wait_reports_timeout_and_recovers(dev):
+    """Make every tensor-core GEMM wait give up after one poll (a host-side budget, no fault):
+    the call completes, gf_unet_status reports GF_ETIMEOUT once, and with the normal budget
+    the next call is correct again."""
+    from paper_2506_20513_gb300 import _lib
+    levels, base, cin, cout, H, W, n = 3, 16, 4, 2, 32, 64, 2
+    net, p, x, t, mask = make(dev, levels, base, cin, cout, H, W, n, seed=12, gemm=1)
+    xd = torch.from_numpy(x).to(dev)
+    y_ref = net.forward(xd).clone()
+    net.status()
+    net.set_wait_budget(64)
+    net.forward(xd)
+    with pytest.raises(_lib.GfError) as e:
+        net.status()
+    assert e.value.code == _lib.GF_ETIMEOUT
+    net.set_wait_budget(0)
+    y = net.forward(xd)
+    net.status()
+    assert torch.equal(y, y_ref)
