@@ -529,7 +529,8 @@ def unet(args):
                        "l2": "a 256 MB buffer is written before every timed step"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": ("tc_gemm_nt_kernel (tcgen05) + gemm_kernel (mma.sync)"
+                         "kernel": ("tc_gemm_kernel (tcgen05: K-major convolutions, MN-major "
+                                    "weight gradients) + gemm_kernel (mma.sync, 1x1 and cin=4)"
                                     if args.gemm else "gemm_kernel (mma.sync bf16)"),
                          "peak_source": peak_kind,
                          "gemm_ms_per_step": gemm_ms / args.steps,

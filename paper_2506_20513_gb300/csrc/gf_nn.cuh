@@ -56,6 +56,15 @@ cudaError_t gemm(GemmArgs a, const GemmPlan& plan, float* partial, cudaStream_t 
 bool tc_gemm_supported(const GemmArgs& a);
 cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st);
 
+// tcgen05 GEMM for MN-major operands (ta = 1, tb = 0: A[K][lda] m-contiguous, B[K][ldb]
+// n-contiguous; M, N, lda, ldb multiples of 8, N <= 256; FP32 output C only, bias = 0,
+// beta = 0) with split-K: the partials (plan.splits * M * N floats in `partial`) are summed
+// in a fixed order into C[m][n] (or C[n][m] with transposed != 0, row stride ldc).
+bool tc_gemm_mn_supported(const GemmArgs& a);
+GemmPlan plan_tc_mn(int M, int N, int K);
+cudaError_t tc_gemm_mn(GemmArgs a, const GemmPlan& plan, float* partial, int transposed,
+                       int* status, cudaStream_t st);
+
 cudaError_t im2col3(const void* x, int nb, int H, int W, int C, void* col, cudaStream_t st);
 cudaError_t flip_transpose(const void* w, int Co, int Ci, void* wt, cudaStream_t st);
 cudaError_t relu_bwd(const float* dy, const void* y, long long n, int relu, float* dz, void* dzb,

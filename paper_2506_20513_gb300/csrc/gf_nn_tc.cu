@@ -11,8 +11,17 @@
 // k values (one 128-byte row per matrix row).  Every mbarrier wait is bounded: on expiry the
 // kernel records an error in the status word, skips the remaining work, waits (bounded) for
 // its own MMAs and frees its TMEM.
+//
+// The same pipeline, with both operands MN-major, computes the weight-gradient products
+// P[z][m][n] = sum over k in split z of A[k][m] B[k][n] (A, B stored with m, n contiguous):
+// each stage holds 64 k x 128 m and 64 k x BN n in the canonical MN-major 128-byte-swizzled
+// layout (64-element x 8-k atoms of 1024 B, 16-byte chunk c of k row r at chunk c ^ (r mod
+// 8), k groups 1024 B apart, MN atoms 8192 B apart); the split-K partials are summed (and
+// transposed when asked) by a reduction in a fixed order.
 #include <cuda_bf16.h>
 #include <stdint.h>
+
+#include <algorithm>
 
 #include "gf_nn.cuh"
 
@@ -65,11 +74,38 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M = 128.
-template <int BN>
+// MN-major, 128-byte swizzle descriptor: leading byte offset 8192 B between 64-element MN
+// atoms, stride byte offset 1024 B between groups of 8 k.
+__device__ __forceinline__ uint64_t mn128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(8192 >> 4) << 16) |
+           ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, N, M = 128; both operands K-major,
+// or (kMN) both MN-major.
+template <int BN, bool kMN>
 __device__ __forceinline__ uint32_t instr_desc() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(kTM >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (kMN ? (1u << 15) | (1u << 16) : 0u) |
+           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+// Stage k [k0, k0 + 64) x mn [mn0, mn0 + R) of an MN-contiguous operand (X[k][ld]) into the
+// MN-major swizzled layout; k >= ke and mn >= mnlim read as zero (mnlim a multiple of 8).
+template <int R>
+__device__ __forceinline__ void stage_mn128(uint32_t base, const bf16* __restrict__ X, int ld,
+                                            int mn0, int mnlim, int k0, int ke, int tid) {
+    constexpr int CPR = R / 8;  // 16-byte chunks per k row
+    for (int c = tid; c < kTK * CPR; c += 128) {
+        const int kr = c / CPR, mc = c % CPR;
+        const int kk = kr & 7;
+        const uint32_t dst = base + (mc >> 3) * 8192 + (kr >> 3) * 1024 + kk * 128 +
+                             (((mc & 7) ^ kk) << 4);
+        const int gk = k0 + kr, gm = mn0 + mc * 8;
+        if (gk < ke && gm < mnlim)
+            cp_async16(dst, X + (long long)gk * ld + gm);
+        else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst), "r"(0) : "memory");
+    }
 }
 
 // Stage rows [row0, row0 + R) x k [k0, k0 + 64) of a K-major operand (ld elements per row)
@@ -127,8 +163,8 @@ __device__ __forceinline__ void stage_conv_a(uint32_t base, const GemmArgs& a, c
     }
 }
 
-template <int BN>
-__global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* status) {
+template <int BN, bool kMN>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int kABytes = kTM * 128, kBBytes = BN * 128, kStageBytes = kABytes + kBBytes;
     // 1024-byte alignment of the stage buffers (required by the 128-byte swizzle atoms)
@@ -144,7 +180,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     // another CTA already gave up: do nothing (one read, made uniform over the CTA, before any
     // TMEM use)
     if (__syncthreads_or(tid == 0 ? *reinterpret_cast<const volatile int*>(status) : 0)) return;
-    const int nk = (a.K + kTK - 1) / kTK;
+    // k range of this CTA: the whole K, or split z of the MN-major products
+    const int kb = kMN ? blockIdx.z * a.kchunk : 0;
+    const int ke = kMN ? min(a.K, kb + a.kchunk) : a.K;
+    const int nk = ke > kb ? (ke - kb + kTK - 1) / kTK : 0;
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns: a power of two >= 32
 
     if (tid == 0) {
@@ -168,25 +207,27 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
     const unsigned polls = a.wait_polls ? a.wait_polls : kSpinLimit;
     const bool inject = a.wait_polls != 0;
     int kdone = -1;  // last k-tile whose MMAs were issued and committed
-    const bool conv = a.conv_h > 0;
+    const bool conv = !kMN && a.conv_h > 0;
     ConvRows cr;
     if (conv) conv_rows(a, m0, tid, cr);
-    auto stage_a = [&](uint32_t sa, int k0) {
-        if (conv)
-            stage_conv_a(sa, a, cr, k0, tid);
-        else
-            stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, k0, a.K, tid);
+    auto stage_ab = [&](uint32_t sa, int k0) {
+        if (kMN) {
+            stage_mn128<kTM>(sa, a.A, a.lda, m0, a.M, k0, ke, tid);
+            stage_mn128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, ke, tid);
+        } else {
+            if (conv)
+                stage_conv_a(sa, a, cr, k0, tid);
+            else
+                stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, k0, a.K, tid);
+            stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, a.K, tid);
+        }
     };
     // prologue: the first kStages - 1 k-tiles
     for (int s = 0; s < kStages - 1; ++s) {
-        if (s < nk) {
-            const uint32_t sa = base + s * kStageBytes;
-            stage_a(sa, s * kTK);
-            stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, s * kTK, a.K, tid);
-        }
+        if (s < nk) stage_ab(base + s * kStageBytes, kb + s * kTK);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
-    const uint32_t idesc = instr_desc<BN>();
+    const uint32_t idesc = instr_desc<BN, kMN>();
     for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % kStages;
         kdone = kt;
@@ -198,8 +239,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
             const uint32_t sa = base + s * kStageBytes;
 #pragma unroll
             for (int kk = 0; kk < kTK / 16; ++kk) {
-                const uint64_t ad = sw128_desc(sa + kk * 32);
-                const uint64_t bd = sw128_desc(sa + kABytes + kk * 32);
+                // K-major: 16 k = 32 bytes inside the swizzle row; MN-major: two k groups
+                const uint64_t ad = kMN ? mn128_desc(sa + kk * 2048) : sw128_desc(sa + kk * 32);
+                const uint64_t bd = kMN ? mn128_desc(sa + kABytes + kk * 2048)
+                                        : sw128_desc(sa + kABytes + kk * 32);
                 const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -219,11 +262,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
             const int sn = kn % kStages;
             if (kt >= 1)
                 ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status, polls);
-            if (ok) {
-                const uint32_t sa = base + sn * kStageBytes;
-                stage_a(sa, kn * kTK);
-                stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, kn * kTK, a.K, tid);
-            }
+            if (ok) stage_ab(base + sn * kStageBytes, kb + kn * kTK);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
         ok = __syncthreads_and(ok);
@@ -267,6 +306,24 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_nt_kernel(GemmArgs a, int* sta
                 : "r"(taddr)
                 : "memory");
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (kMN) {
+                // split-K partial of this CTA: P[z][r][n0 + c0 + j]
+                if (r < a.M) {
+                    float* dst = a.P + ((long long)blockIdx.z * a.M + r) * a.N + n0 + c0;
+                    if (c0 + 16 <= a.N - n0 && (a.N & 3) == 0) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            reinterpret_cast<float4*>(dst)[q] =
+                                make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + c0 + j < a.N) dst[j] = __uint_as_float(v[j]);
+                    }
+                }
+                continue;
+            }
             const bool vec = a.Cb && c0 + 16 <= a.N - n0 && (a.ldc & 7) == 0 &&
                              ((n0 + c0) & 7) == 0 && (((uintptr_t)a.Cb) & 15) == 0;
             if (r < a.M && vec) {
@@ -313,19 +370,34 @@ constexpr size_t tc_smem_bytes() {
     return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 8 * kStages + 8 + 16;
 }
 
-template <int BN>
-cudaError_t tc_launch(const GemmArgs& a, int* status, cudaStream_t st) {
+template <int BN, bool kMN>
+cudaError_t tc_launch(const GemmArgs& a, int splits, int* status, cudaStream_t st) {
     static bool configured = false;  // per process; the attribute is per device function
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gemm_nt_kernel<BN>,
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, kMN>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tc_smem_bytes<BN>());
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    const dim3 grid((a.N + BN - 1) / BN, (a.M + kTM - 1) / kTM);
-    tc_gemm_nt_kernel<BN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a, status);
+    const dim3 grid((a.N + BN - 1) / BN, (a.M + kTM - 1) / kTM, splits);
+    tc_gemm_kernel<BN, kMN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a, status);
     return cudaGetLastError();
+}
+
+// out[n * ldc + m] (transposed) or out[m * ldc + n] = alpha * sum_z P[z][m][n], z in order
+__global__ void reduce_partials_kernel(const float* __restrict__ P, int splits, int M, int N,
+                                       float alpha, int transposed, float* __restrict__ out,
+                                       int ldc) {
+    const long long total = (long long)M * N;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        // transposed: walk e in output order (n major) so the writes are coalesced
+        const long long m = transposed ? e % M : e / N, n = transposed ? e / M : e % N;
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += P[(long long)z * total + m * N + n];
+        out[transposed ? n * ldc + m : m * ldc + n] = alpha * s;
+    }
 }
 
 }  // namespace
@@ -341,10 +413,53 @@ bool tc_gemm_supported(const GemmArgs& a) {
 
 cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st) {
     if (!tc_gemm_supported(a) || !status) return cudaErrorInvalidValue;
-    if (a.N <= 32) return tc_launch<32>(a, status, st);
-    if (a.N <= 64) return tc_launch<64>(a, status, st);
-    if (a.N <= 128) return tc_launch<128>(a, status, st);
-    return tc_launch<256>(a, status, st);
+    if (a.N <= 32) return tc_launch<32, false>(a, 1, status, st);
+    if (a.N <= 64) return tc_launch<64, false>(a, 1, status, st);
+    if (a.N <= 128) return tc_launch<128, false>(a, 1, status, st);
+    return tc_launch<256, false>(a, 1, status, st);
+}
+
+bool tc_gemm_mn_supported(const GemmArgs& a) {
+    auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+    return a.ta == 1 && a.tb == 0 && a.conv_h == 0 && a.M % 8 == 0 && a.N % 8 == 0 &&
+           a.lda % 8 == 0 && a.ldb % 8 == 0 && al(a.A) && al(a.B) && a.M > 0 && a.N > 0 &&
+           a.K > 0 && a.N <= 256 && (a.M + kTM - 1) / kTM <= 65535 && a.C && !a.Cb &&
+           !a.bias && a.beta == 0.f;
+}
+
+GemmPlan plan_tc_mn(int M, int N, int K) {
+    GemmPlan p;
+    p.bm = kTM;
+    p.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+    const long long ctas = (long long)((M + kTM - 1) / kTM) * ((N + p.bn - 1) / p.bn);
+    long long s = (2 * 152 + ctas - 1) / ctas;
+    const long long smax = K / 512 > 0 ? K / 512 : 1;  // at least 512 k per split
+    if (s > smax) s = smax;
+    if (s > 65535) s = 65535;
+    if (s < 1) s = 1;
+    p.kchunk = (int)(((K + s - 1) / s + kTK - 1) / kTK * kTK);
+    p.splits = (K + p.kchunk - 1) / p.kchunk;
+    return p;
+}
+
+cudaError_t tc_gemm_mn(GemmArgs a, const GemmPlan& plan, float* partial, int transposed,
+                       int* status, cudaStream_t st) {
+    if (!tc_gemm_mn_supported(a) || !status || !partial) return cudaErrorInvalidValue;
+    a.kchunk = plan.kchunk;
+    a.P = partial;
+    cudaError_t e;
+    if (plan.bn == 64)
+        e = tc_launch<64, true>(a, plan.splits, status, st);
+    else if (plan.bn == 128)
+        e = tc_launch<128, true>(a, plan.splits, status, st);
+    else
+        e = tc_launch<256, true>(a, plan.splits, status, st);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)a.M * a.N;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 16);
+    reduce_partials_kernel<<<blocks, 256, 0, st>>>(partial, plan.splits, a.M, a.N, a.alpha,
+                                                   transposed, a.C, a.ldc);
+    return cudaGetLastError();
 }
 
 }  // namespace nn

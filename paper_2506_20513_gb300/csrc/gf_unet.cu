@@ -216,11 +216,19 @@ int create(gf_unet* u) {
         }
     }
     long long pmax = 1, colsum_max = 1;
-    for (int n = 1; n <= nb; ++n)
+    for (int n = 1; n <= nb; ++n) {
         for (const Shape& s : split_shapes(*u, n)) {
             const gf::nn::GemmPlan p = gf::nn::plan_gemm(s.M, s.N, s.K);
             if (p.splits > 1) pmax = std::max(pmax, (long long)p.splits * s.M * s.N);
         }
+        // the tcgen05 weight-gradient products run transposed: M = k^2 ci, N = co
+        for (const Conv& c : u->convs) {
+            const int rows = n * u->H(c.level) * u->W(c.level);
+            const int M = c.k * c.k * c.ci;
+            const gf::nn::GemmPlan p = gf::nn::plan_tc_mn(M, c.co, rows);
+            pmax = std::max(pmax, (long long)p.splits * M * c.co);
+        }
+    }
     for (const Conv& c : u->convs)
         colsum_max = std::max(colsum_max,
                               (long long)gf::nn::colsum_chunks((long long)rows(c.level)) * c.co);
@@ -299,6 +307,35 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
 }
 
 // relu(conv3x3(in) + b) -> out (BF16), n images at the conv's level
+// The transposed (MN-major) tcgen05 product with split-K; C receives the result transposed.
+int run_gemm_mn(gf_unet* u, gf::nn::GemmArgs a, cudaStream_t st) {
+    const gf::nn::GemmPlan p = gf::nn::plan_tc_mn(a.M, a.N, a.K);
+    if ((long long)p.splits * a.M * a.N > u->partial_cap)
+        return fail(u, GF_ECUDA, "split-K buffer too small (internal error)");
+    a.wait_polls = u->wait_polls;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (u->profiling) {
+        for (cudaEvent_t* ev : {&e0, &e1}) {
+            if (!u->ev_pool.empty()) {
+                *ev = u->ev_pool.back();
+                u->ev_pool.pop_back();
+            } else if (cudaEventCreate(ev) != cudaSuccess) {
+                return fail(u, GF_ECUDA, "cudaEventCreate failed");
+            }
+        }
+        cudaEventRecord(e0, st);
+    }
+    cudaError_t e = gf::nn::tc_gemm_mn(a, p, u->partial, 1, u->status, st);
+    if (u->profiling) {
+        cudaEventRecord(e1, st);
+        u->prof_ev.emplace_back(e0, e1);
+        u->prof_flops += 2.0 * a.M * a.N * (double)a.K;
+    }
+    if (e != cudaSuccess) return fail(u, GF_ECUDA, "tcgen05 gemm: %s", cudaGetErrorString(e));
+    u->launches += 2;
+    return GF_OK;
+}
+
 // Fill the A operand of a 3x3 convolution GEMM over the image `in` (n images, H x W, C
 // channels): an implicit im2col read by the tcgen05 engine when it can take it, else an
 // explicit one in the col buffer.
@@ -388,19 +425,39 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
     NN_CUDA(u, gf::nn::column_sum(u->dz, rows, c.co, u->colpart, u->grads + c.boff, st));
     ++u->launches;
     NN_CUDA(u, gf::nn::im2col3(in, n, H, W, c.ci, u->col, st));
-    gf::nn::GemmArgs a;
-    a.M = c.co;
-    a.N = 9 * c.ci;
-    a.K = rows;
-    a.A = u->dzb;
-    a.lda = c.co;
-    a.ta = 1;
-    a.B = u->col;
-    a.ldb = 9 * c.ci;
-    a.tb = 0;
-    a.C = u->grads + c.woff;
-    a.ldc = 9 * c.ci;
-    int rc = run_gemm(u, a, true, st);
+    int rc;
+    // weight gradient dW[co][k] = sum over cells of dz[cell][co] col[cell][k]; on the tcgen05
+    // engine as the transposed product col^T dz (M = 9 ci fills the 128 TMEM lanes) with
+    // split-K and a transposing reduction
+    gf::nn::GemmArgs t;
+    t.M = 9 * c.ci;
+    t.N = c.co;
+    t.K = rows;
+    t.A = u->col;
+    t.lda = 9 * c.ci;
+    t.ta = 1;
+    t.B = u->dzb;
+    t.ldb = c.co;
+    t.tb = 0;
+    t.C = u->grads + c.woff;
+    t.ldc = 9 * c.ci;
+    if (u->gemm_mode == 1 && gf::nn::tc_gemm_mn_supported(t)) {
+        rc = run_gemm_mn(u, t, st);
+    } else {
+        gf::nn::GemmArgs a;
+        a.M = c.co;
+        a.N = 9 * c.ci;
+        a.K = rows;
+        a.A = u->dzb;
+        a.lda = c.co;
+        a.ta = 1;
+        a.B = u->col;
+        a.ldb = 9 * c.ci;
+        a.tb = 0;
+        a.C = u->grads + c.woff;
+        a.ldc = 9 * c.ci;
+        rc = run_gemm(u, a, true, st);
+    }
     if (rc || !gin) return rc;
     NN_CUDA(u, gf::nn::flip_transpose(u->wb + c.woff, c.co, c.ci, u->wt, st));
     gf::nn::GemmArgs b;
