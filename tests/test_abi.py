@@ -139,3 +139,11 @@ def test_unet_null_arguments(lib):
     assert lib.gf_unet_set_params(None, None, None) == _lib.GF_EINVAL
     assert lib.gf_unet_kernel_launches(None) == 0
     lib.gf_unet_destroy(None)
+
+
+def test_create_rejects_empty_acquisitions(lib):
+    """No shots, no sources or no receivers: GF_EINVAL before anything touches a device."""
+    g = W.GridSpec(nx=40, ny=30, npml=5, nt=10, dx=0.01, dy=0.01, dt=0.9 * W.cfl_dt_max(0.01, 0.01))
+    assert _create(lib, g, np.zeros((0, 1, 2)), np.zeros((0, 1, 2)), nshots=0) == _lib.GF_EINVAL
+    assert _create(lib, g, [[[10, 10]]], np.zeros((1, 0, 2))) == _lib.GF_EINVAL
+    assert _create(lib, g, np.zeros((1, 0, 2)), [[[20, 12]]]) == _lib.GF_EINVAL

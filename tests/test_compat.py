@@ -67,3 +67,45 @@ def test_compute_matches_the_library_and_differentiates():
     _, ge, gs = fd.misfit_and_gradient(e2, s2, wav, zero)
     torch.testing.assert_close(eps.grad[:, :, 0].T, ge, rtol=1e-5, atol=1e-6 * float(ge.abs().max()))
     torch.testing.assert_close(sig.grad[:, :, 0].T, gs, rtol=1e-5, atol=1e-6 * float(gs.abs().max()))
+
+
+@pytest.mark.gpu
+def test_paper_demo_loop_with_adam_reduces_the_loss():
+    """The paper's demo loop (Sec. 3.1): compute(...) inside torch.optim.Adam with separate
+    learning rates for eps_r and sigma, MSE loss, gradients zeroed near the sources, values
+    clamped to physical ranges; a few epochs lower the loss."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20513_gb300.compat import compute
+    from paper_2506_20513_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    nx, ny, pml, dx, dt, f0 = 80, 50, 10, 0.02, 4e-11, 4e8
+    eps_true, sig_true = W.layered_blob_model(5, nx - 2 * pml, ny - 2 * pml, dx)
+    eps_true, sig_true = W.pad_edges(eps_true, pml), W.pad_edges(sig_true, pml)
+    eps_init = W.pad_edges(W.smooth(eps_true[pml:-pml, pml:-pml], 0.1, dx), pml)
+    to_paper = lambda a: torch.tensor(a.T[:, :, None].copy(), dtype=torch.float32, device=dev)
+    args = dict(device="cuda", dx=dx, ny=ny, nx=nx, nz=1, time_windows=300 * dt,
+                source=["hertzian", "z"], source_location=[0.25, 0.24, 0],
+                source_step=[0.2, 0, 0], receiver_location=[0.22, 0.24, 0],
+                receiver_step=[0.04, 0, 0], pmlthick=pml, source_amplitudes=["ricker", 1.0, f0],
+                step=6, miu=1, nsrc=1, nrx=30, freq=None, dt=dt)
+    with torch.no_grad():
+        observed, _ = compute(epsilon=to_paper(eps_true), sigma=to_paper(sig_true), **args)
+    epsilon = to_paper(eps_init).requires_grad_()
+    sigma = to_paper(sig_true).requires_grad_()
+    opt = torch.optim.Adam([{"params": epsilon, "lr": 0.05}, {"params": sigma, "lr": 1e-4}])
+    mse = torch.nn.MSELoss()
+    losses = []
+    for _ in range(6):
+        opt.zero_grad()
+        result, _ = compute(epsilon=epsilon, sigma=sigma, **args)
+        loss = mse(result, observed)
+        loss.backward()
+        epsilon.grad[:, :pml + 1, :] = 0
+        sigma.grad[:, :pml + 1, :] = 0
+        opt.step()
+        with torch.no_grad():
+            epsilon.clamp_(min=1.0)
+            sigma.clamp_(min=0.0)
+        losses.append(float(loss.detach()))
+    assert losses[-1] < 0.8 * losses[0]
