@@ -76,6 +76,16 @@ def test_single_shot_disc(dev):
     check_case(wl, dev)
 
 
+def test_preconditioner_workload_subset(dev):
+    """The learned preconditioner's grid (256x128 + 20-cell CPML, dx 0.01 m, 400 MHz, 64
+    receivers, nt 1500), two of its 16 shots, in the default launch configuration: traces
+    and both gradients against the FP64 oracle."""
+    import dataclasses
+    wl = W.preconditioner_model(100123, nshots=16, nt=1500)
+    wl = dataclasses.replace(wl, src=wl.src[[3, 11]], rec=wl.rec[[3, 11]])
+    check_case(wl, dev)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("seed,tiling,kappa,pec", [
     (1, None, 1.0, False),
