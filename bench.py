@@ -60,9 +60,9 @@ def parse_args():
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--gemm", type=int, default=1, choices=[0, 1],
-                    help="U-Net workload: 1 = tcgen05 for the K-major products (implicit "
-                         "im2col), 0 = explicit im2col and mma.sync GEMMs")
+    ap.add_argument("--gemm", type=int, default=1, choices=[0, 1, 2],
+                    help="U-Net workload: 1 = tcgen05 with TMA operand loads, 2 = tcgen05 with "
+                         "thread-staged operands, 0 = explicit im2col and mma.sync GEMMs")
     ap.add_argument("--fwi-iters", type=int, default=3,
                     help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
     return ap.parse_args()
@@ -529,8 +529,9 @@ def unet(args):
                        "l2": "a 256 MB buffer is written before every timed step"},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": ("tc_gemm_kernel (tcgen05: K-major convolutions, MN-major "
+                         "kernel": ("tc_gemm_kernel (tcgen05%s: K-major convolutions, MN-major "
                                     "weight gradients) + gemm_kernel (mma.sync, 1x1 and cin=4)"
+                                    % (" + TMA" if args.gemm == 1 else "")
                                     if args.gemm else "gemm_kernel (mma.sync bf16)"),
                          "peak_source": peak_kind,
                          "gemm_ms_per_step": gemm_ms / args.steps,

@@ -77,12 +77,14 @@ int gf_unet_loss_and_grad(gf_unet* net, int n, const float* x, const float* targ
  * the gradient of the last gf_unet_loss_and_grad; GF_ESTATE if there is none. */
 int gf_unet_adam_step(gf_unet* net, float lr, float beta1, float beta2, float eps, void* stream);
 
-/* GEMM engine: 1 (default) = tcgen05 tensor-core GEMMs (TMEM accumulators): the forward and
- * input-gradient convolutions as K-major products reading their im2col operand straight from
- * the activation image (no im2col pass), the weight gradients as MN-major split-K products;
- * mma.sync only for shapes these cannot take (channel counts not a multiple of 8, the 1x1
- * output layer); 0 = explicit im2col and mma.sync everywhere.  Both give the same result up to
- * FP32 rounding. */
+/* GEMM engine: 1 (default) = tcgen05 tensor-core GEMMs (TMEM accumulators) with operands
+ * loaded by TMA (128-byte-swizzled boxes, mbarrier completion): the forward and
+ * input-gradient convolutions as K-major products whose im2col operand is gathered straight
+ * from the activation image (no im2col pass), the weight gradients as MN-major split-K
+ * products; mma.sync only for shapes these cannot take (channel counts not a multiple of 8,
+ * the 1x1 output layer).  2 = the same tcgen05 products with every operand staged by the
+ * threads (cp.async).  0 = explicit im2col and mma.sync everywhere.  All give the same result
+ * up to FP32 rounding. */
 int gf_unet_set_gemm(gf_unet* net, int mode);
 
 /* Failure-path hook (tests): polls > 0 limits every tensor-core GEMM pipeline wait to that

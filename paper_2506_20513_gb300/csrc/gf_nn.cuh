@@ -37,6 +37,9 @@ struct GemmArgs {
     // wait to that many polls and makes the final one wait on a barrier nobody arrives at, so
     // it expires (deterministically, without faulting); 0 = the built-in limit, no injection
     unsigned wait_polls = 0;
+    // tcgen05 engine: load A / B with TMA (set by the launcher when it could encode the
+    // tensor maps; the implicit-im2col A is always staged by the threads)
+    int tma_a = 0, tma_b = 0;
     // filled in by gemm()
     int kchunk = 0, va = 0, vb = 0;
     float* P = nullptr;

@@ -18,8 +18,12 @@
 // layout (64-element x 8-k atoms of 1024 B, 16-byte chunk c of k row r at chunk c ^ (r mod
 // 8), k groups 1024 B apart, MN atoms 8192 B apart); the split-K partials are summed (and
 // transposed when asked) by a reduction in a fixed order.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
+
+#include <string.h>
 
 #include <algorithm>
 
@@ -46,6 +50,22 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// One 2-D TMA box (tensor map in kernel parameter space) into shared memory; completion is
+// counted in bytes on the mbarrier.  Coordinates: x innermost (elements), y outer.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 // true once the phase with the given parity has completed; false after `limit` polls or as
@@ -164,7 +184,9 @@ __device__ __forceinline__ void stage_conv_a(uint32_t base, const GemmArgs& a, c
 }
 
 template <int BN, bool kMN>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status) {
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(GemmArgs a, int* status, const __grid_constant__ CUtensorMap tma_a,
+                   const __grid_constant__ CUtensorMap tma_b) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     constexpr int kABytes = kTM * 128, kBBytes = BN * 128, kStageBytes = kABytes + kBBytes;
     // 1024-byte alignment of the stage buffers (required by the 128-byte swizzle atoms)
@@ -172,7 +194,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
     const uint32_t base = (raw + 1023) & ~1023u;
     const uint32_t bars = base + kStages * kStageBytes;  // kStages mbarriers (8 B each)
     const uint32_t never = bars + 8 * kStages;           // an mbarrier nobody arrives at
-    const uint32_t tmem_slot = never + 8;                // TMEM address written by tcgen05.alloc
+    const uint32_t full = never + 8;                     // kStages mbarriers: TMA bytes landed
+    const uint32_t tmem_slot = full + 8 * kStages;       // TMEM address written by tcgen05.alloc
     unsigned char* const slot_ptr = smem_raw + (tmem_slot - raw);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -187,7 +210,10 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
     constexpr uint32_t kCols = BN < 32 ? 32 : BN;  // TMEM columns: a power of two >= 32
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(bars + 8 * s, 1);
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(bars + 8 * s, 1);
+            mbar_init(full + 8 * s, 1);
+        }
         mbar_init(never, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -210,30 +236,58 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
     const bool conv = !kMN && a.conv_h > 0;
     ConvRows cr;
     if (conv) conv_rows(a, m0, tid, cr);
-    auto stage_ab = [&](uint32_t sa, int k0) {
+    // operands loaded by TMA (a.tma_a / a.tma_b): thread 0 announces the stage's bytes on its
+    // full barrier and issues the boxes; the other operands are staged by all threads
+    const bool ta_tma = a.tma_a != 0 && !conv, tb_tma = a.tma_b != 0;
+    const bool any_tma = ta_tma || tb_tma;
+    int lastk[kStages];  // last k-tile loaded into each stage (-1: none), uniform over the CTA
+#pragma unroll
+    for (int s = 0; s < kStages; ++s) lastk[s] = -1;
+    auto stage_ab = [&](int s, int kt) {
+        const uint32_t sa = base + s * kStageBytes;
+        const int k0 = kb + kt * kTK;
+        lastk[s] = kt;
+        if (any_tma && tid == 0) {
+            mbar_expect_tx(full + 8 * s, (ta_tma ? kABytes : 0) + (tb_tma ? kBBytes : 0));
+            if (kMN) {
+                if (ta_tma)
+                    for (int q = 0; q < kTM / 64; ++q)
+                        tma_load_2d(sa + q * 8192, &tma_a, m0 + 64 * q, k0, full + 8 * s);
+                if (tb_tma)
+                    for (int q = 0; q < BN / 64; ++q)
+                        tma_load_2d(sa + kABytes + q * 8192, &tma_b, n0 + 64 * q, k0, full + 8 * s);
+            } else {
+                if (ta_tma) tma_load_2d(sa, &tma_a, k0, m0, full + 8 * s);
+                if (tb_tma) tma_load_2d(sa + kABytes, &tma_b, k0, n0, full + 8 * s);
+            }
+        }
         if (kMN) {
-            stage_mn128<kTM>(sa, a.A, a.lda, m0, a.M, k0, ke, tid);
-            stage_mn128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, ke, tid);
+            if (!ta_tma) stage_mn128<kTM>(sa, a.A, a.lda, m0, a.M, k0, ke, tid);
+            if (!tb_tma) stage_mn128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, ke, tid);
         } else {
             if (conv)
                 stage_conv_a(sa, a, cr, k0, tid);
-            else
+            else if (!ta_tma)
                 stage_sw128<kTM>(sa, a.A, a.lda, m0, a.M, k0, a.K, tid);
-            stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, a.K, tid);
+            if (!tb_tma) stage_sw128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, a.K, tid);
         }
     };
     // prologue: the first kStages - 1 k-tiles
     for (int s = 0; s < kStages - 1; ++s) {
-        if (s < nk) stage_ab(base + s * kStageBytes, kb + s * kTK);
+        if (s < nk) stage_ab(s, s);
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     const uint32_t idesc = instr_desc<BN, kMN>();
     for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % kStages;
-        kdone = kt;
         asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 2) : "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
+        if (any_tma) ok = mbar_wait(full + 8 * s, (uint32_t)((kt / kStages) & 1), status, polls);
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        kdone = kt;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t sa = base + s * kStageBytes;
@@ -262,7 +316,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
             const int sn = kn % kStages;
             if (kt >= 1)
                 ok = mbar_wait(bars + 8 * sn, (uint32_t)(((kt - 1) / kStages) & 1), status, polls);
-            if (ok) stage_ab(base + sn * kStageBytes, kb + kn * kTK);
+            if (ok) stage_ab(sn, kn);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
         ok = __syncthreads_and(ok);
@@ -289,6 +343,21 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
                 : "r"(lb), "r"(lp)
                 : "memory");
             if (done) break;
+        }
+        // and the TMA boxes still landing in this CTA's shared memory
+        for (int s2 = 0; any_tma && s2 < kStages; ++s2) {
+            if (lastk[s2] < 0) continue;
+            const uint32_t fp = (uint32_t)((lastk[s2] / kStages) & 1);
+            for (unsigned i = 0; i < kSpinLimit; ++i) {
+                uint32_t done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                    " selp.u32 %0, 1, 0, p;\n}\n"
+                    : "=r"(done)
+                    : "r"(full + 8 * s2), "r"(fp)
+                    : "memory");
+                if (done) break;
+            }
         }
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -367,11 +436,45 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(GemmArgs a, int* status
 
 template <int BN>
 constexpr size_t tc_smem_bytes() {
-    return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 8 * kStages + 8 + 16;
+    return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 16 * kStages + 8 + 16;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link-time
+// dependency on the driver library); null when unavailable, and the threads stage instead.
+PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map of a row-major [outer][ld] array (inner extent `inner`), box
+// box_inner x box_outer, 128-byte swizzle, zero fill outside the array.
+bool make_map(CUtensorMap* m, const void* ptr, long long inner, long long outer, long long ld,
+              unsigned box_inner, unsigned box_outer) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tma_encoder();
+    if (!enc || ((uintptr_t)ptr & 15) || (ld * 2) % 16) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
 }
 
 template <int BN, bool kMN>
-cudaError_t tc_launch(const GemmArgs& a, int splits, int* status, cudaStream_t st) {
+cudaError_t tc_launch(GemmArgs a, int splits, int* status, cudaStream_t st) {
     static bool configured = false;  // per process; the attribute is per device function
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, kMN>,
@@ -380,8 +483,20 @@ cudaError_t tc_launch(const GemmArgs& a, int splits, int* status, cudaStream_t s
         if (e != cudaSuccess) return e;
         configured = true;
     }
+    CUtensorMap ma, mb;
+    memset(&ma, 0, sizeof(ma));
+    memset(&mb, 0, sizeof(mb));
+    if (a.tma_a || a.tma_b) {
+        if (kMN) {
+            a.tma_a = a.tma_a && make_map(&ma, a.A, a.M, a.K, a.lda, 64, 64);
+            a.tma_b = a.tma_b && make_map(&mb, a.B, a.N, a.K, a.ldb, 64, 64);
+        } else {
+            a.tma_a = a.tma_a && a.conv_h == 0 && make_map(&ma, a.A, a.K, a.M, a.lda, 64, kTM);
+            a.tma_b = a.tma_b && make_map(&mb, a.B, a.K, a.N, a.ldb, 64, BN);
+        }
+    }
     const dim3 grid((a.N + BN - 1) / BN, (a.M + kTM - 1) / kTM, splits);
-    tc_gemm_kernel<BN, kMN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a, status);
+    tc_gemm_kernel<BN, kMN><<<grid, 128, tc_smem_bytes<BN>(), st>>>(a, status, ma, mb);
     return cudaGetLastError();
 }
 

@@ -98,7 +98,7 @@ struct gf_unet {
     float* colpart = nullptr;
     double *lpart = nullptr, *lval = nullptr;
     int* status = nullptr;  // device word: bit 0 = a tensor-core GEMM wait expired
-    int gemm_mode = 1;      // 1: tcgen05 for K-major products, mma.sync otherwise; 0: mma.sync
+    int gemm_mode = 1;      // 1: tcgen05 + TMA; 2: tcgen05, thread-staged operands; 0: mma.sync
     unsigned wait_polls = 0;  // tcgen05 wait budget (0 = built-in)
     int step = 0;
     bool have_grad = false;
@@ -287,13 +287,14 @@ int run_gemm(gf_unet* u, gf::nn::GemmArgs a, bool allow_split, cudaStream_t st) 
         cudaEventRecord(e0, st);
     }
     // an implicit-im2col operand (conv_h > 0) is only understood by the tcgen05 engine
-    const bool tc = (u->gemm_mode == 1 || a.conv_h > 0) && (p.splits == 1 || a.conv_h > 0) &&
+    const bool tc = (u->gemm_mode >= 1 || a.conv_h > 0) && (p.splits == 1 || a.conv_h > 0) &&
                     gf::nn::tc_gemm_supported(a);
     if (a.conv_h > 0 && !tc) return fail(u, GF_ECUDA, "implicit im2col without tcgen05 (internal)");
     if (tc) {
         p.splits = 1;
         p.kchunk = std::max(32, (a.K + 31) / 32 * 32);
         a.wait_polls = u->wait_polls;
+        a.tma_a = a.tma_b = u->gemm_mode == 1;
     }
     cudaError_t e = tc ? gf::nn::tc_gemm(a, u->status, st) : gf::nn::gemm(a, p, u->partial, st);
     if (u->profiling) {
@@ -313,6 +314,7 @@ int run_gemm_mn(gf_unet* u, gf::nn::GemmArgs a, cudaStream_t st) {
     if ((long long)p.splits * a.M * a.N > u->partial_cap)
         return fail(u, GF_ECUDA, "split-K buffer too small (internal error)");
     a.wait_polls = u->wait_polls;
+    a.tma_a = a.tma_b = u->gemm_mode == 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (u->profiling) {
         for (cudaEvent_t* ev : {&e0, &e1}) {
@@ -346,7 +348,7 @@ int conv_operand(gf_unet* u, gf::nn::GemmArgs& a, const bf16* in, int n, int H, 
     a.conv_h = H;
     a.conv_w = W;
     a.conv_c = C;
-    if (u->gemm_mode == 1 && gf::nn::tc_gemm_supported(a)) return GF_OK;
+    if (u->gemm_mode >= 1 && gf::nn::tc_gemm_supported(a)) return GF_OK;
     a.conv_h = a.conv_w = a.conv_c = 0;
     a.A = u->col;
     NN_CUDA(u, gf::nn::im2col3(in, n, H, W, C, u->col, st));
@@ -441,7 +443,7 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
     t.tb = 0;
     t.C = u->grads + c.woff;
     t.ldc = 9 * c.ci;
-    if (u->gemm_mode == 1 && gf::nn::tc_gemm_mn_supported(t)) {
+    if (u->gemm_mode >= 1 && gf::nn::tc_gemm_mn_supported(t)) {
         rc = run_gemm_mn(u, t, st);
     } else {
         gf::nn::GemmArgs a;
@@ -676,7 +678,8 @@ int gf_unet_adam_step(gf_unet* u, float lr, float beta1, float beta2, float eps,
 long long gf_unet_kernel_launches(const gf_unet* u) { return u ? u->launches : 0; }
 
 int gf_unet_set_gemm(gf_unet* u, int mode) {
-    if (!u || mode < 0 || mode > 1) return fail(u, GF_EINVAL, "gf_unet_set_gemm: mode must be 0 or 1");
+    if (!u || mode < 0 || mode > 2)
+        return fail(u, GF_EINVAL, "gf_unet_set_gemm: mode must be 0, 1 or 2");
     u->gemm_mode = mode;
     return GF_OK;
 }

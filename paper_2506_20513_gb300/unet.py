@@ -150,7 +150,8 @@ class UNet:
         return int(self.lib.gf_unet_kernel_launches(self._net))
 
     def set_gemm(self, mode: int):
-        """1: tcgen05 tensor-core GEMM for the K-major products (default); 0: mma.sync only."""
+        """1: tcgen05 with TMA-loaded operands (default); 2: tcgen05 with thread-staged
+        operands; 0: mma.sync only."""
         self._check(self.lib.gf_unet_set_gemm(self._net, int(mode)), self._net)
 
     def set_wait_budget(self, polls: int):

@@ -82,7 +82,7 @@ def compare(net, p, x, t, mask, dev, levels, base, cin, cout):
     return y
 
 
-@pytest.mark.parametrize("gemm", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("gemm", [0, 1, 2], ids=["mma_sync", "tcgen05_tma", "tcgen05"])
 @pytest.mark.parametrize("levels,base,cin,cout,H,W,n", [
     (3, 8, 4, 2, 24, 44, 2),    # ragged GEMM tiles (2112 rows), narrow channels
     (2, 16, 3, 5, 10, 14, 3),   # odd cin / cout: scalar staging paths
@@ -93,7 +93,7 @@ def test_unet_forward_loss_and_gradient_match_oracle(dev, levels, base, cin, cou
     compare(net, p, x, t, mask, dev, levels, base, cin, cout)
 
 
-@pytest.mark.parametrize("gemm", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("gemm", [0, 1, 2], ids=["mma_sync", "tcgen05_tma", "tcgen05"])
 def test_unet_full_size_matches_oracle(dev, gemm):
     """The preconditioner's network: 4 levels, 32 base channels, 4 in / 2 out, 128 x 256."""
     levels, base, cin, cout, H, W, n = 4, 32, 4, 2, 128, 256, 2
@@ -113,12 +113,13 @@ def test_unet_gemm_engines_agree(dev):
     xd, td = torch.from_numpy(x).to(dev), torch.from_numpy(t).to(dev)
     y0 = net.forward(xd).clone()
     _, g0 = net.loss_and_grad(xd, td, grads=True)
-    net.set_gemm(1)
-    y1 = net.forward(xd).clone()
-    _, g1 = net.loss_and_grad(xd, td, grads=True)
-    net.status()
-    assert rel(y1.cpu().numpy(), y0.cpu().numpy()) <= 2e-3
-    assert rel(g1.cpu().numpy(), g0.cpu().numpy()) <= 1e-2
+    for mode in (1, 2):
+        net.set_gemm(mode)
+        y1 = net.forward(xd).clone()
+        _, g1 = net.loss_and_grad(xd, td, grads=True)
+        net.status()
+        assert rel(y1.cpu().numpy(), y0.cpu().numpy()) <= 2e-3
+        assert rel(g1.cpu().numpy(), g0.cpu().numpy()) <= 1e-2
 
 
 def test_unet_gradient_is_deterministic_and_adam_matches_oracle(dev):
