@@ -36,6 +36,14 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per cell-step of one launch, from `ncu --metrics
 # dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
 # gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
+# Warp instructions per cell-step of one launch (ncu InstructionStats, same keys): the
+# kernels are bound by instruction issue, so the line also reports the issue roofline.
+NCU_WARP_INST_PER_CELL_STEP: dict = {
+    # profiles/adj_tile_multishot_540x290x32.md: 218.2 M warp instructions per K = 7 launch
+    "adj@bb1f83f02e9c@540x290x32@default": 6.2198,
+}
+ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
+
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
     # profiles/adj_tile_multishot_540x290x32.md: 340.4 MB per K = 7 launch
     "adj@bb1f83f02e9c@540x290x32@default": 9.7027,
@@ -328,6 +336,18 @@ def ours(args):
             "peak_source": f"hbm_gbs of {peak_kind}",
             "avg_launch_us": avg_s * 1e6, "launches": cnt,
             "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
+    ipc = NCU_WARP_INST_PER_CELL_STEP.get(key)
+    if ipc:
+        # the bound that holds the kernel: warp instructions issued per second against the
+        # issue rate of all schedulers at the SM clock sampled during the timed region
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        inst = ipc * wl.nshots * g.ncells * per_launch_steps
+        peak_issue = torch.cuda.get_device_properties(dev).multi_processor_count * \
+            ISSUE_SLOTS_PER_SM_CLK * mhz * 1e6
+        roof["issue"] = {"achieved": inst / avg_s / 1e9, "peak": peak_issue / 1e9,
+                         "unit": "G warp-instructions/s", "frac": inst / avg_s / peak_issue,
+                         "warp_instructions_per_launch": inst,
+                         "peak_source": "SMs x 4 schedulers x sampled SM clock"}
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
