@@ -124,10 +124,13 @@ int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
  * segment boundaries group some sums differently).  Invalidates a stored forward. */
 int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
-/* Kernel variant: 0 = tile kernels with four rows per thread (1024-thread CTAs, default),
- * 1 = eight rows per thread (512-thread CTAs), 2 = barrier-free warp-march forward (64-column
- * strips, 64-row chunks, at most 7 steps per launch; the illumination output and the adjoint
- * use the variant-0 tile kernels).  All compute the same result up to FP32 rounding. */
+/* Kernel variant: 0 = tile kernels with four rows per thread (1024-thread CTAs, 64 x 64
+ * staged window, default), 1 = eight rows per thread (512-thread CTAs, 64 x 64), 2 =
+ * barrier-free warp-march forward (64-column strips, 64-row chunks, at most 7 steps per
+ * launch; the illumination output and the adjoint use the variant-0 tile kernels), 3 = four
+ * rows per thread in 512-thread CTAs on a 64 x 32 window, two CTAs per SM (tile height + 2
+ * steps <= 32; a taller current tile is shrunk to fit).  All compute the same result up to
+ * FP32 rounding. */
 int gf_set_variant(gf_ctx* ctx, int variant);
 
 /* Current tiling and variant (for autotuners). */
@@ -232,7 +235,7 @@ int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acquisition* acq
  * (device name, nx, ny, npml, shots, sources, receivers) in the text cache `cache_path`
  * (NULL = no cache); on a miss, times a forward pass over the first `probe_steps` steps (0 =
  * 48) for each candidate (variants 0 and 1 with 3..10 steps per launch, variant 2 with 4 and
- * 6), with CUDA events on `stream`, keeps the fastest and appends it to the cache.  Leaves
+ * 6, variant 3 with 3..6), with CUDA events on `stream`, keeps the fastest and appends it to the cache.  Leaves
  * the chosen tiling set on the context (read it back with gf_get_tiling).  Synchronises
  * `stream`.  eps_r, sigma, wavelet: device inputs as for gf_forward_model. */
 int gf_autotune(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,

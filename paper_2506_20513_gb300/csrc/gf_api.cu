@@ -488,13 +488,14 @@ int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K, int variant) {
 }
 
 int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
-    const int E = gf::max_tile_extent();
-    if (K < 1 || tw < 1 || th < 1 || tw + 2 * K > E || th + 2 * K > E)
-        return fail(c, GF_EINVAL,
-                    "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d per side",
-                    tw, th, K, E);
     if (variant < 0 || variant > gf::num_tile_variants())
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
+    const int E = gf::max_tile_extent(), Eh = gf::max_tile_height(variant == 2 ? 0 : variant);
+    if (K < 1 || tw < 1 || th < 1 || tw + 2 * K > E || th + 2 * K > Eh)
+        return fail(c, GF_EINVAL,
+                    "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d wide and "
+                    "<= %d high",
+                    tw, th, K, E, Eh);
     if (variant == 2 && K > gf::march_max_steps())
         return fail(c, GF_EINVAL, "the warp-march forward takes at most %d steps per launch",
                     gf::march_max_steps());
@@ -666,8 +667,9 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     if (!c) return GF_EINVAL;
     ++c->generation;
     const int E = gf::max_tile_extent();
+    const int Eh = gf::max_tile_height(c->variant == 2 ? 0 : c->variant);
     const int k = K > 0 ? K : c->K;
-    const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : E - 2 * k;
+    const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : Eh - 2 * k;
     int rc = check_tiling(c, tw, th, k, c->variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
@@ -702,11 +704,18 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
     ++c->generation;
-    int rc = check_tiling(c, c->tile_w, c->tile_h, c->K, variant);
+    if (variant < 0 || variant > gf::num_tile_variants())
+        return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
+    // a tile taller than the variant's window is shrunk to the largest that fits
+    int th = c->tile_h;
+    const int Eh = gf::max_tile_height(variant == 2 ? 0 : variant);
+    if (th + 2 * c->K > Eh) th = Eh - 2 * c->K;
+    int rc = check_tiling(c, c->tile_w, th, c->K, variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K, variant);
+    rc = build_all_receiver_lists(c, c->tile_w, th, c->K, variant);
     if (rc) return rc;
+    c->tile_h = th;
     c->variant = variant;
     return GF_OK;
 }
@@ -965,6 +974,7 @@ int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     for (int v = 0; v < 2; ++v)
         for (int K : {3, 4, 5, 6, 7, 8, 10}) cands.push_back({v, K});
     for (int K : {4, 6}) cands.push_back({2, K});
+    for (int K : {3, 4, 5, 6}) cands.push_back({3, K});
     const int steps = probe_steps > 0 ? probe_steps : 48;
     cudaEvent_t e0, e1;
     GF_CUDA(c, cudaEventCreate(&e0), "event");

@@ -66,7 +66,8 @@ cudaError_t launch_fwd_march(const TileParams& p, int chunks, cudaStream_t st);
 cudaError_t configure_march_kernels(size_t optin);
 size_t march_smem_bytes();
 int march_max_steps();
-int max_tile_extent();              // staged tile (interior + 2K halo) limit per side
+int max_tile_extent();              // staged tile (interior + 2K halo) width limit
+int max_tile_height(int variant);   // staged tile height limit of a tile-kernel variant
 int num_tile_variants();
 size_t tile_smem_bytes(int variant);
 cudaError_t configure_tile_kernels(size_t optin);

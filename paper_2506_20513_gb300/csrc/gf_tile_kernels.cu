@@ -35,13 +35,13 @@ namespace gf {
 namespace {
 
 constexpr int BX = 64;        // threads along x = staged tile width
-constexpr int EHM = 64;       // staged tile height
-constexpr int PLANE = EHM * BX;
 constexpr int kMaxK = 31;     // tile + 2K <= 64 with tile >= 2
+// The staged tile height is EHM = RY * BY (64 for variants 0 and 1, 32 for variant 3); a
+// plane of the staged window holds PLANE = EHM * BX floats.
 
-__host__ __device__ constexpr size_t smem_floats(int by) {
-    return 2 * PLANE + 2 * by * BX + 4 * PLANE + 6 * EHM + 6 * BX + (kMaxK + 1) * kMaxSrc +
-           5 * PLANE;
+__host__ __device__ constexpr size_t smem_floats(int ry, int by) {
+    return 11 * (size_t)(ry * by) * BX + 2 * by * BX + 6 * (ry * by) + 6 * BX +
+           (kMaxK + 1) * kMaxSrc;
 }
 
 // Shared-memory carve-up (floats).
@@ -59,8 +59,9 @@ struct Smem {
                      // registers, which would spill)
 };
 
-template <int BY>
+template <int RY, int BY>
 __device__ __forceinline__ Smem carve(float* sm) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     Smem s;
     s.xplane = sm;
     s.xplane2 = s.xplane + PLANE;
@@ -125,6 +126,7 @@ struct Cell {
 };
 
 // Row and column CPML profiles of the staged window (clamped to the grid).
+template <int EHM>
 __device__ __forceinline__ void stage_profiles(const Smem& s, const TileParams& p, int X0, int Y0,
                                                int tid) {
     if (tid < EHM) {
@@ -149,11 +151,12 @@ __device__ __forceinline__ void stage_profiles(const Smem& s, const TileParams& 
 // Load the time-stepping state of the owned cells; CPML memories of strip cells go to
 // shared memory (zero elsewhere), and with kCoefSmem the update coefficients too (ca, cb are
 // then left untouched).  Returns the row bit masks (y strip, interior).
-template <int RY, bool kCoefSmem = false>
+template <int RY, int BY, bool kCoefSmem = false>
 __device__ __forceinline__ void load_state(const TileParams& p, const Cell<RY>& c, const Smem& s,
                                            long long sbase, float* f0, float* f1, float* f2,
                                            float* ca, float* cb, unsigned& ystrip,
                                            unsigned& interior) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     const long long F = (long long)p.nshots * p.N;
     ystrip = 0;
     interior = 0;
@@ -200,10 +203,11 @@ __device__ __forceinline__ void load_state(const TileParams& p, const Cell<RY>& 
 }
 
 // Write the owned interior cells (fields and strip memories) to the output state.
-template <int RY>
+template <int RY, int BY>
 __device__ __forceinline__ void store_state(const TileParams& p, const Cell<RY>& c, const Smem& s,
                                             long long sbase, const float* f0, const float* f1,
                                             const float* f2, unsigned ystrip, unsigned interior) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     const long long F = (long long)p.nshots * p.N;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
@@ -248,6 +252,7 @@ __device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c,
                                          float* ez, float* hx, float* hy, float* ill, unsigned ystrip,
                                          unsigned interior, unsigned srcmask, const int* rlist,
                                          int nrl, int shot, int tid) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     constexpr int NTHR = BX * BY;
     const int ty = threadIdx.y, K = p.K;
     float* sEz = s.xplane;
@@ -346,9 +351,10 @@ __device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c,
 }
 
 template <int RY, int BY, bool kHist, bool kIllum>
-__global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p) {
+__global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) fwd_tile_kernel(const TileParams p) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     extern __shared__ float4 smem_raw[];
-    const Smem s = carve<BY>(reinterpret_cast<float*>(smem_raw));
+    const Smem s = carve<RY, BY>(reinterpret_cast<float*>(smem_raw));
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int shot = blockIdx.y, K = p.K;
     Cell<RY> c;
@@ -357,13 +363,13 @@ __global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p)
 
     float ez[RY], hx[RY], hy[RY], ill[RY];
     unsigned ystrip, interior;
-    load_state<RY, true>(p, c, s, sbase, ez, hx, hy, nullptr, nullptr, ystrip, interior);
+    load_state<RY, BY, true>(p, c, s, sbase, ez, hx, hy, nullptr, nullptr, ystrip, interior);
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         s.xplane[(c.ly0 + r) * BX + c.lx] = ez[r];
         ill[r] = 0.f;
     }
-    stage_profiles(s, p, c.X0, c.Y0, tid);
+    stage_profiles<EHM>(s, p, c.X0, c.Y0, tid);
     for (int k = tid; k < K * kMaxSrc; k += BX * BY) {
         const int st = k / kMaxSrc, src = k % kMaxSrc;
         s.wsrc[k] = src < p.nsrc
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(BX* BY, 1) fwd_tile_kernel(const TileParams p)
         fwd_body<RY, BY, false, kHist, kIllum>(p, c, s, ez, hx, hy, ill, ystrip, interior,
                                                srcmask, rlist, nrl, shot, tid);
 
-    store_state<RY>(p, c, s, sbase, ez, hx, hy, ystrip, interior);
+    store_state<RY, BY>(p, c, s, sbase, ez, hx, hy, ystrip, interior);
     if (kIllum) {
 #pragma unroll
         for (int r = 0; r < RY; ++r)
@@ -408,6 +414,7 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
                                          float* aez, float* ahx, float* ahy,
                                          unsigned ystrip, unsigned interior, unsigned recmask,
                                          const int* rlist, int nrl, int shot) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     const int ty = threadIdx.y, K = p.K;
     float* sSx = s.xplane;
     float* sTx = s.xplane2;
@@ -521,9 +528,10 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
 }
 
 template <int RY, int BY>
-__global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p) {
+__global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) adj_tile_kernel(const TileParams p) {
+    constexpr int EHM = RY * BY, PLANE = EHM * BX;
     extern __shared__ float4 smem_raw[];
-    const Smem s = carve<BY>(reinterpret_cast<float*>(smem_raw));
+    const Smem s = carve<RY, BY>(reinterpret_cast<float*>(smem_raw));
     const int tid = threadIdx.y * BX + threadIdx.x;
     const int shot = blockIdx.y, K = p.K;
     Cell<RY> c;
@@ -533,7 +541,7 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
 
     float aez[RY], ahx[RY], ahy[RY];
     unsigned ystrip, interior;
-    load_state<RY, true>(p, c, s, sbase, aez, ahx, ahy, nullptr, nullptr, ystrip, interior);
+    load_state<RY, BY, true>(p, c, s, sbase, aez, ahx, ahy, nullptr, nullptr, ystrip, interior);
     const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
                         (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
 #pragma unroll
@@ -543,7 +551,7 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
         s.coef[2 * PLANE + (c.ly0 + r) * BX + c.lx] =
             ((interior >> r) & 1u) ? __ldcs(hcol + (long long)n1 * p.N + r * p.nx) : 0.f;
     }
-    stage_profiles(s, p, c.X0, c.Y0, tid);
+    stage_profiles<EHM>(s, p, c.X0, c.Y0, tid);
     const int tile = blockIdx.x;
     const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + tile];
     const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + tile + 1] - lo);
@@ -559,7 +567,7 @@ __global__ void __launch_bounds__(BX* BY, 1) adj_tile_kernel(const TileParams p)
         adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ystrip, interior, recmask, rlist, nrl,
                                 shot);
 
-    store_state<RY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
+    store_state<RY, BY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
     const long long F = (long long)p.nshots * p.N;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
@@ -597,7 +605,7 @@ cudaError_t configure_variant(size_t optin) {
 template <int RY, int BY>
 cudaError_t launch_fwd_variant(const TileParams& p, cudaStream_t st) {
     const dim3 grid(p.ntiles, p.nshots), block(BX, BY);
-    const size_t smem = sizeof(float) * smem_floats(BY);
+    const size_t smem = sizeof(float) * smem_floats(RY, BY);
     if (p.hist && p.illum)
         fwd_tile_kernel<RY, BY, true, true><<<grid, block, smem, st>>>(p);
     else if (p.hist)
@@ -612,32 +620,42 @@ cudaError_t launch_fwd_variant(const TileParams& p, cudaStream_t st) {
 template <int RY, int BY>
 cudaError_t launch_adj_variant(const TileParams& p, cudaStream_t st) {
     const dim3 grid(p.ntiles, p.nshots), block(BX, BY);
-    adj_tile_kernel<RY, BY><<<grid, block, sizeof(float) * smem_floats(BY), st>>>(p);
+    adj_tile_kernel<RY, BY><<<grid, block, sizeof(float) * smem_floats(RY, BY), st>>>(p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 int max_tile_extent() { return BX; }
-int num_tile_variants() { return 2; }
+int max_tile_height(int variant) { return variant == 3 ? 32 : 64; }
+int num_tile_variants() { return 3; }
 
 size_t tile_smem_bytes(int variant) {
-    return sizeof(float) * smem_floats(variant == 0 ? 16 : 8);
+    return sizeof(float) * (variant == 0 ? smem_floats(4, 16)
+                            : variant == 1 ? smem_floats(8, 8)
+                                           : smem_floats(4, 8));
 }
 
 cudaError_t configure_tile_kernels(size_t optin) {
     cudaError_t e = configure_variant<4, 16>(optin);
     if (e != cudaSuccess) return e;
-    return configure_variant<8, 8>(optin);
+    if ((e = configure_variant<8, 8>(optin)) != cudaSuccess) return e;
+    return configure_variant<4, 8>(optin);
 }
 
-// Variant 0: 4 rows per thread, 1024 threads; variant 1: 8 rows per thread, 512 threads.
+// Variant 0: 4 rows per thread, 1024 threads, 64 x 64 window; variant 1: 8 rows per thread,
+// 512 threads, 64 x 64; variant 3: 4 rows per thread, 512 threads, 64 x 32 window, two CTAs
+// per SM (one CTA's barrier waits and state loads overlap the other's work).
 cudaError_t launch_fwd_tile(const TileParams& p, int variant, cudaStream_t st) {
-    return variant == 0 ? launch_fwd_variant<4, 16>(p, st) : launch_fwd_variant<8, 8>(p, st);
+    return variant == 0   ? launch_fwd_variant<4, 16>(p, st)
+           : variant == 1 ? launch_fwd_variant<8, 8>(p, st)
+                          : launch_fwd_variant<4, 8>(p, st);
 }
 
 cudaError_t launch_adj_tile(const TileParams& p, int variant, cudaStream_t st) {
-    return variant == 0 ? launch_adj_variant<4, 16>(p, st) : launch_adj_variant<8, 8>(p, st);
+    return variant == 0   ? launch_adj_variant<4, 16>(p, st)
+           : variant == 1 ? launch_adj_variant<8, 8>(p, st)
+                          : launch_adj_variant<4, 8>(p, st);
 }
 
 }  // namespace gf
