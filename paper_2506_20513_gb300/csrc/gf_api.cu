@@ -451,6 +451,9 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** 
         }
     std::vector<int> off(lists.size() + 1, 0), idx;
     for (size_t k = 0; k < lists.size(); ++k) {
+        // the tile kernels address a thread's entries with 16-bit offsets
+        if (lists[k].size() > 65535)
+            return fail(c, GF_EINVAL, "more than 65535 receivers in one staged tile window");
         const int* cells = c->h_rec.data() + (k / nt_) * c->nrec;
         std::stable_sort(lists[k].begin(), lists[k].end(),
                          [&](int a, int b) { return cells[a] / nx < cells[b] / nx; });

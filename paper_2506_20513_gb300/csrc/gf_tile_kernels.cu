@@ -228,20 +228,25 @@ __device__ __forceinline__ void store_state(const TileParams& p, const Cell<RY>&
     }
 }
 
-// Bits of this thread's rows that hold one of the listed cells (receivers of this CTA from
-// the host-built list, or the shot's sources).
+// Range [first, end) of the entries of this CTA's receiver list (host-built, sorted by row,
+// at most 65535 entries) that covers every entry on this thread's cells, packed as
+// first | end << 16 (0 when there is none).  Computed once per launch so that the per-step
+// injection visits only this range (usually one entry) rather than decoding the whole list
+// on every step: a thread that did so became the straggler of its CTA at every barrier.
 template <int RY>
-__device__ __forceinline__ unsigned owned_mask(const int* __restrict__ idx, int count,
-                                               const int* __restrict__ cells, int nx,
-                                               const Cell<RY>& c) {
-    unsigned m = 0;
+__device__ __forceinline__ unsigned owned_range(const int* __restrict__ idx, int count,
+                                                const int* __restrict__ cells, int nx,
+                                                const Cell<RY>& c) {
+    unsigned first = 0, end = 0;
     for (int e = 0; e < count; ++e) {
         const int cell = __ldg(cells + __ldg(idx + e));
         const int lx = cell % nx - c.X0, ly = cell / nx - c.Y0 - c.ly0;
-        if (lx == c.lx && ly >= 0 && ly < RY && c.lx < c.EWe && c.ly0 + ly < c.EHe)
-            m |= 1u << ly;
+        if (lx == c.lx && ly >= 0 && ly < RY && c.lx < c.EWe && c.ly0 + ly < c.EHe) {
+            if (end == 0) first = e;
+            end = e + 1;
+        }
     }
-    return m;
+    return first | end << 16;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -412,8 +417,8 @@ __global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) fwd_tile_k
 template <int RY, int BY, bool kStrip>
 __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
                                          float* aez, float* ahx, float* ahy,
-                                         unsigned ystrip, unsigned interior, unsigned recmask,
-                                         const int* rlist, int nrl, int shot) {
+                                         unsigned ystrip, unsigned interior, unsigned rrange,
+                                         const int* rlist, int shot) {
     constexpr int EHM = RY * BY, PLANE = EHM * BX;
     const int ty = threadIdx.y, K = p.K;
     float* sSx = s.xplane;
@@ -511,17 +516,15 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
             const float tu = r > 0 ? wy[r - 1] : (ty > 0 ? sTyB[(ty - 1) * BX + c.lx] : wy[0]);
             aez[r] += tl - wx[r] + tu - wy[r];
         }
-        if (recmask) {
-            for (int e = 0; e < nrl; ++e) {
-                const int ri = __ldg(rlist + e);
-                const int cell = __ldg(rec_cells + ri);
-                const int r0 = cell / p.nx - c.Y0 - c.ly0;
-                if (cell % p.nx - c.X0 != c.lx || r0 < 0 || r0 >= RY) continue;
-                const float v = __ldg(resid_base + (long long)n * p.nrec + ri);
+        for (int e = rrange & 0xffffu; e < (int)(rrange >> 16); ++e) {
+            const int ri = __ldg(rlist + e);
+            const int cell = __ldg(rec_cells + ri);
+            const int r0 = cell / p.nx - c.Y0 - c.ly0;
+            if (cell % p.nx - c.X0 != c.lx || r0 < 0 || r0 >= RY) continue;
+            const float v = __ldg(resid_base + (long long)n * p.nrec + ri);
 #pragma unroll
-                for (int r = 0; r < RY; ++r)
-                    if (r == r0 && ((recmask >> r) & 1u)) aez[r] += v;
-            }
+            for (int r = 0; r < RY; ++r)
+                if (r == r0) aez[r] += v;
         }
         if (st < K - 1) phase_a();
     }
@@ -556,16 +559,14 @@ __global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) adj_tile_k
     const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + tile];
     const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + tile + 1] - lo);
     const int* rlist = p.tile_rec_idx + lo;
-    const unsigned recmask =
-        owned_mask<RY>(rlist, nrl, p.rec_cell + (long long)shot * p.nrec, p.nx, c);
+    const unsigned rrange =
+        owned_range<RY>(rlist, nrl, p.rec_cell + (long long)shot * p.nrec, p.nx, c);
     __syncthreads();
 
     if (c.tile_strip)
-        adj_body<RY, BY, true>(p, c, s, aez, ahx, ahy, ystrip, interior, recmask, rlist, nrl,
-                               shot);
+        adj_body<RY, BY, true>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist, shot);
     else
-        adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ystrip, interior, recmask, rlist, nrl,
-                                shot);
+        adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist, shot);
 
     store_state<RY, BY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
     const long long F = (long long)p.nshots * p.N;
