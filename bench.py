@@ -39,14 +39,14 @@ FALLBACK_HBM_GBS = 6800.0
 # Warp instructions per cell-step of one launch (ncu InstructionStats, same keys): the
 # kernels are bound by instruction issue, so the line also reports the issue roofline.
 NCU_WARP_INST_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 218.2 M warp instructions per K = 7 launch
-    "adj@bb1f83f02e9c@540x290x32@default": 6.2198,
+    # profiles/adj_tile_multishot_540x290x32.md: 206.0 M warp instructions per K = 7 launch
+    "adj@1d7a6b4597d3@540x290x32@default": 5.8723,
 }
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 340.4 MB per K = 7 launch
-    "adj@bb1f83f02e9c@540x290x32@default": 9.7027,
+    # profiles/adj_tile_multishot_540x290x32.md: 340.6 MB per K = 7 launch
+    "adj@1d7a6b4597d3@540x290x32@default": 9.7088,
 }
 
 
@@ -372,6 +372,9 @@ def ours(args):
         from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
         drv = FWI(fd, lambda f0: obs, interior_mask(g, rows_below_top=4),
                   FWIConfig(bands=((wl.f0, args.fwi_iters),)))
+        # an untimed pass first: the driver's first iterations otherwise include the one-time
+        # loading of the PyTorch kernels its L-BFGS algebra uses (seconds on a fresh process)
+        drv.run(eps0, sig0)
         _, _, hist = drv.run(eps0, sig0)
         fwi = {"iterations": len(hist.seconds),
                "s_per_iteration": sum(hist.seconds) / max(1, len(hist.seconds)),
