@@ -73,7 +73,9 @@ typedef struct gf_grid_desc {
 typedef struct gf_acquisition {
     int32_t nshots;         /* >= 1 */
     int32_t nsrc;           /* sources per shot, 1..8 */
-    int32_t nrec;           /* receivers per shot, >= 1 */
+    int32_t nrec;           /* receivers per shot, >= 1; at most 65535 of them may fall in
+                               one staged tile window (GF_EINVAL from gf_create or
+                               gf_set_tiling otherwise) */
     const int32_t* src_ij;  /* [nshots][nsrc][2] cell indices (i, j), 1 <= i <= nx-2 ... */
     const int32_t* rec_ij;  /* [nshots][nrec][2] cell indices, same range (off the ring) */
 } gf_acquisition;

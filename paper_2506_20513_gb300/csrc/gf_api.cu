@@ -52,6 +52,7 @@ struct gf_ctx {
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
     int* d_tile_rec_idx = nullptr;
+    int tile_rec_max = 0;           // longest per (shot, tile) list of the current tiling
     int* d_march_rec_off = nullptr;  // the same for the warp-march strips x chunks
     int* d_march_rec_idx = nullptr;
     int march_h = 64;                // rows per warp-march chunk
@@ -279,6 +280,7 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.tile_rec_idx = c->d_tile_rec_idx;
     p.hist_stride = c->g.nt;
     p.hist_slot0 = 0;
+    p.rec_staged = (long long)c->tile_rec_max * (c->K + 1) <= gf::kRecStage;
     return p;
 }
 
@@ -433,7 +435,8 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
 // Receivers of every (shot, tile) staged window (interior plus a K-cell halo) as a CSR list
 // in (row, receiver index) order, uploaded for the kernels; rebuilt whenever the tiling
 // changes.  Written into *off / *idx (device, owned by the context).
-int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** idx_out) {
+int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** idx_out,
+                         int* max_len) {
     const int nx = c->g.nx, ny = c->g.ny;
     const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th, nt_ = ntx * nty;
     std::vector<std::vector<int>> lists((size_t)c->nshots * nt_);
@@ -460,6 +463,10 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** 
         off[k + 1] = off[k] + (int)lists[k].size();
         idx.insert(idx.end(), lists[k].begin(), lists[k].end());
     }
+    if (max_len) {
+        *max_len = 0;
+        for (const auto& l : lists) *max_len = std::max(*max_len, (int)l.size());
+    }
     if (idx.empty()) idx.push_back(0);
     int *d_off = nullptr, *d_idx = nullptr;
     cudaError_t e = cudaMalloc(&d_off, off.size() * sizeof(int));
@@ -483,10 +490,11 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** 
 
 // Lists for the tile kernels and, for the march variant, for its strips x chunks.
 int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K, int variant) {
-    int rc = build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx);
+    int rc = build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx,
+                                  &c->tile_rec_max);
     if (rc == GF_OK && variant == 2)
         rc = build_receiver_lists(c, gf::max_tile_extent() - 2 * K, c->march_h, K,
-                                  &c->d_march_rec_off, &c->d_march_rec_idx);
+                                  &c->d_march_rec_off, &c->d_march_rec_idx, nullptr);
     return rc;
 }
 

@@ -8,6 +8,9 @@ namespace gf {
 
 constexpr int kMaxSrc = 8;        // sources per shot
 constexpr int kNumFields = 7;     // Ez, Hx, Hy, psiEx, psiEy, psiHx, psiHy (or their adjoints)
+// Shared-memory words in which the adjoint tile kernel stages its tile's receiver positions
+// and the residual samples of its launch (entries x (K + 1) words must fit).
+constexpr int kRecStage = 1536;
 
 // Device-status bits (OR-ed into the workspace status word by kernels).
 constexpr int kStatusBadModel = 1;   // eps_r < 1, sigma < 0 or non-finite model value
@@ -55,6 +58,7 @@ struct TileParams {
     const int* tile_rec_off;
     const int* tile_rec_idx;
     int* status;
+    int rec_staged;         // adjoint: every tile's receiver list fits the staging area
 };
 
 // Host-side launchers (one per kernel family).

@@ -41,7 +41,7 @@ constexpr int kMaxK = 31;     // tile + 2K <= 64 with tile >= 2
 
 __host__ __device__ constexpr size_t smem_floats(int ry, int by) {
     return 11 * (size_t)(ry * by) * BX + 2 * by * BX + 6 * (ry * by) + 6 * BX +
-           (kMaxK + 1) * kMaxSrc;
+           (kMaxK + 1) * kMaxSrc + kRecStage;
 }
 
 // Shared-memory carve-up (floats).
@@ -57,6 +57,8 @@ struct Smem {
     float* coef;     // [5][EHM][BX] adjoint: Ca, Cb, the carried Ez^{n+1} and the two
                      // gradient accumulators of the owned cells (kept here rather than in
                      // registers, which would spill)
+    float* rstage;   // [kRecStage] adjoint: residual samples of the launch [entry][step] from
+                     // the start, window positions lx | ly << 8 of the entries from the end
 };
 
 template <int RY, int BY>
@@ -72,6 +74,7 @@ __device__ __forceinline__ Smem carve(float* sm) {
     s.xprof = s.yprof + 6 * EHM;
     s.wsrc = s.xprof + 6 * BX;
     s.coef = s.wsrc + (kMaxK + 1) * kMaxSrc;
+    s.rstage = s.coef + 5 * PLANE;
     return s;
 }
 
@@ -414,7 +417,7 @@ __global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) fwd_tile_k
 // ---------------------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------------------
-template <int RY, int BY, bool kStrip>
+template <int RY, int BY, bool kStrip, bool kStaged>
 __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
                                          float* aez, float* ahx, float* ahy,
                                          unsigned ystrip, unsigned interior, unsigned rrange,
@@ -517,11 +520,20 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
             aez[r] += tl - wx[r] + tu - wy[r];
         }
         for (int e = rrange & 0xffffu; e < (int)(rrange >> 16); ++e) {
-            const int ri = __ldg(rlist + e);
-            const int cell = __ldg(rec_cells + ri);
-            const int r0 = cell / p.nx - c.Y0 - c.ly0;
-            if (cell % p.nx - c.X0 != c.lx || r0 < 0 || r0 >= RY) continue;
-            const float v = __ldg(resid_base + (long long)n * p.nrec + ri);
+            int r0;
+            float v;
+            if (kStaged) {
+                const int pos = __float_as_int(s.rstage[kRecStage - 1 - e]);
+                r0 = (pos >> 8) - c.ly0;
+                if ((pos & 0xff) != c.lx || r0 < 0 || r0 >= RY) continue;
+                v = s.rstage[e * K + st];
+            } else {
+                const int ri = __ldg(rlist + e);
+                const int cell = __ldg(rec_cells + ri);
+                r0 = cell / p.nx - c.Y0 - c.ly0;
+                if (cell % p.nx - c.X0 != c.lx || r0 < 0 || r0 >= RY) continue;
+                v = __ldg(resid_base + (long long)n * p.nrec + ri);
+            }
 #pragma unroll
             for (int r = 0; r < RY; ++r)
                 if (r == r0) aez[r] += v;
@@ -530,7 +542,7 @@ __device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c,
     }
 }
 
-template <int RY, int BY>
+template <int RY, int BY, bool kStaged>
 __global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) adj_tile_kernel(const TileParams p) {
     constexpr int EHM = RY * BY, PLANE = EHM * BX;
     extern __shared__ float4 smem_raw[];
@@ -561,12 +573,29 @@ __global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) adj_tile_k
     const int* rlist = p.tile_rec_idx + lo;
     const unsigned rrange =
         owned_range<RY>(rlist, nrl, p.rec_cell + (long long)shot * p.nrec, p.nx, c);
+    if (kStaged) {
+        // the receivers' window positions and the residual samples of this launch, so that
+        // the per-step injection reads shared memory only (nrl * (K + 1) <= kRecStage)
+        const int* rc = p.rec_cell + (long long)shot * p.nrec;
+        for (int e = tid; e < nrl; e += BX * BY) {
+            const int cell = __ldg(rc + __ldg(rlist + e));
+            s.rstage[kRecStage - 1 - e] =
+                __int_as_float((cell % p.nx - c.X0) | (cell / p.nx - c.Y0) << 8);
+        }
+        const float* rb = p.resid + (long long)shot * p.nt * p.nrec;
+        for (int i = tid; i < nrl * K; i += BX * BY) {
+            const int e = i / K, st = i - e * K;
+            s.rstage[i] = __ldg(rb + (long long)(n1 - st) * p.nrec + __ldg(rlist + e));
+        }
+    }
     __syncthreads();
 
     if (c.tile_strip)
-        adj_body<RY, BY, true>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist, shot);
+        adj_body<RY, BY, true, kStaged>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist,
+                                        shot);
     else
-        adj_body<RY, BY, false>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist, shot);
+        adj_body<RY, BY, false, kStaged>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist,
+                                         shot);
 
     store_state<RY, BY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
     const long long F = (long long)p.nshots * p.N;
@@ -600,7 +629,8 @@ cudaError_t configure_variant(size_t optin) {
     if ((e = allow_smem(fwd_tile_kernel<RY, BY, true, false>, optin))) return e;
     if ((e = allow_smem(fwd_tile_kernel<RY, BY, false, true>, optin))) return e;
     if ((e = allow_smem(fwd_tile_kernel<RY, BY, false, false>, optin))) return e;
-    return allow_smem(adj_tile_kernel<RY, BY>, optin);
+    if ((e = allow_smem(adj_tile_kernel<RY, BY, true>, optin))) return e;
+    return allow_smem(adj_tile_kernel<RY, BY, false>, optin);
 }
 
 template <int RY, int BY>
@@ -621,7 +651,11 @@ cudaError_t launch_fwd_variant(const TileParams& p, cudaStream_t st) {
 template <int RY, int BY>
 cudaError_t launch_adj_variant(const TileParams& p, cudaStream_t st) {
     const dim3 grid(p.ntiles, p.nshots), block(BX, BY);
-    adj_tile_kernel<RY, BY><<<grid, block, sizeof(float) * smem_floats(RY, BY), st>>>(p);
+    const size_t smem = sizeof(float) * smem_floats(RY, BY);
+    if (p.rec_staged)
+        adj_tile_kernel<RY, BY, true><<<grid, block, smem, st>>>(p);
+    else
+        adj_tile_kernel<RY, BY, false><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -110,6 +110,15 @@ def test_small_random(dev, seed, tiling, kappa, pec, variant):
     check_case(wl, dev, (tiling or (0, 0, 0)) + (variant,))
 
 
+@pytest.mark.parametrize("nrec,tiling", [(200, (0, 0, 4)), (400, (0, 0, 4)), (400, (13, 7, 4))])
+def test_dense_receivers(dev, nrec, tiling):
+    """Hundreds of receivers scattered over the grid, duplicates included: launches whose tile
+    lists fit the adjoint's shared-memory staging of positions and residual samples (up to 200
+    entries in one list) and a launch that exceeds it and reads them from global memory."""
+    wl = W.small_random(51, nxp=46, nyp=27, npml=6, nt=150, nshots=2, nrec=nrec)
+    check_case(wl, dev, tiling + (0,))
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("npml,tiling", [(0, (16, 16, 4)), (3, (20, 18, 5)), (8, (40, 40, 12))])
 def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
