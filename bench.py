@@ -39,14 +39,14 @@ FALLBACK_HBM_GBS = 6800.0
 # Warp instructions per cell-step of one launch (ncu InstructionStats, same keys): the
 # kernels are bound by instruction issue, so the line also reports the issue roofline.
 NCU_WARP_INST_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 206.0 M warp instructions per K = 7 launch
-    "adj@1d7a6b4597d3@540x290x32@default": 5.8723,
+    # profiles/adj_tile_multishot_540x290x32.md: 199.0 M warp instructions per K = 7 launch
+    "adj@7098a186bfe3@540x290x32@default": 5.6732,
 }
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 340.6 MB per K = 7 launch
-    "adj@1d7a6b4597d3@540x290x32@default": 9.7088,
+    # profiles/adj_tile_multishot_540x290x32.md: 339.3 MB per K = 7 launch
+    "adj@7098a186bfe3@540x290x32@default": 9.6736,
 }
 
 
