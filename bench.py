@@ -348,6 +348,15 @@ def ours(args):
                          "unit": "G warp-instructions/s", "frac": inst / avg_s / peak_issue,
                          "warp_instructions_per_launch": inst,
                          "peak_source": "SMs x 4 schedulers x sampled SM clock"}
+    if not args.checkpoint:
+        # the whole step against the bytes an untiled stencil moves per cell-update (forward:
+        # fields read+written 24 B, Ca/Cb 8 B, history write 4 B; adjoint: 24 + 8 B, history
+        # read 4 B, gradient pair read+written 16 B; 44 B on average over the two)
+        naive = (36.0 + 52.0) / 2
+        eff = value / world * naive  # per GPU: Gcell/s x B = GB/s
+        roof["effective"] = {"achieved": eff, "peak": peak, "unit": "GB/s", "frac": eff / peak,
+                             "naive_bytes_per_cell_update": naive,
+                             "meaning": "Gcell-updates/s x untiled bytes per cell-update"}
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
