@@ -51,6 +51,11 @@ class FWIConfig:
     tv_weight: float = 0.1
     eps_min: float = 1.0
     sigma_min: float = 0.0
+    # learned step: scales of the network's update tried in turn (each costs one misfit
+    # evaluation); after a rejection the network is consulted again once this many L-BFGS
+    # iterations have passed (0 = not again in this band)
+    learned_scales: tuple = (1.0, 0.5)
+    learned_retry: int = 0
 
 
 @dataclass
@@ -153,6 +158,7 @@ class FWI:
                 S = [t.to(dev) for t in st["S"]]
                 Y = [t.to(dev) for t in st["Y"]]
                 first, use_net, it0 = st["first"], st["use_net"], st["iteration"]
+                retry_at = st.get("retry_at", -1)
                 if learned:
                     ge, gs, illum = (st[k].to(dev) for k in ("ge", "gs", "illum"))
                 eps, sig = self._split(x.float())
@@ -167,7 +173,8 @@ class FWI:
                     J, g = self.gradient(eps, sig, wav, obs)
                 g = g.double()
                 first = True
-                use_net = learned   # the network is tried until its update is first rejected
+                use_net = learned   # the network is tried until its update is rejected
+                retry_at = -1       # iteration at which a rejected network is tried again
                 it0 = 0
             n = x.numel() // 2
             for it in range(it0, iters):
@@ -177,12 +184,14 @@ class FWI:
                 t0 = time.perf_counter()
                 tries = 0
                 kept = False
+                if learned and not use_net and 0 <= retry_at <= it:
+                    use_net, retry_at = True, -1
                 if use_net:
                     de, ds = self.pre.update(ge, gs, eps, illum)
                     d_l = torch.cat([(de * self.mask).reshape(-1).double(),
                                      (ds * self.mask / c.sigma_ref).reshape(-1).double()])
                     J_c = float("inf")
-                    for scale in (1.0, 0.5):
+                    for scale in c.learned_scales:
                         e_c, s_c = self._split((x + scale * d_l).float())
                         J_c = self._misfit(e_c, s_c, wav, obs)
                         tries += 1
@@ -193,6 +202,8 @@ class FWI:
                         eps, sig = e_c, s_c
                     else:
                         use_net = False
+                        if c.learned_retry > 0:
+                            retry_at = it + c.learned_retry
                 if not kept:
                     # two-loop recursion (Nocedal & Wright, Algorithm 7.4)
                     q = g.clone()
@@ -250,7 +261,7 @@ class FWI:
                 if checkpoint and checkpoint_every > 0 and (it + 1) % checkpoint_every == 0:
                     state = dict(band_index=bi, iteration=it + 1, x=x.cpu(), g=g.cpu(), J=J,
                                  S=[t.cpu() for t in S], Y=[t.cpu() for t in Y], first=first,
-                                 use_net=use_net,
+                                 use_net=use_net, retry_at=retry_at,
                                  hist={k: list(getattr(hist, k)) for k in
                                        ("misfit", "evaluations", "seconds", "band", "learned")})
                     if learned:

@@ -29,8 +29,8 @@ from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pair
 from .unet import UNet
 
 
-def _fwi(fd, wl, obs, f0, iters, pre=None, stop=None):
-    cfg = FWIConfig(bands=((f0, iters),))
+def _fwi(fd, wl, obs, f0, iters, pre=None, stop=None, retry=0, scales=(1.0, 0.5)):
+    cfg = FWIConfig(bands=((f0, iters),), learned_retry=retry, learned_scales=tuple(scales))
     mask = interior_mask(wl.grid, rows_below_top=4)
     inv = FWI(fd, lambda f: obs, mask, cfg, preconditioner=pre)
     e0 = torch.tensor(wl.eps_init, dtype=torch.float32, device=fd.device)
@@ -58,6 +58,13 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="write the summary and per-model rows (JSON)")
     ap.add_argument("--load", default=None,
                     help="trained parameters (.npy) to evaluate instead of generating and training")
+    ap.add_argument("--retry", type=int, default=0,
+                    help="L-BFGS iterations after a rejected learned update before the network "
+                         "is consulted again (0 = not again)")
+    ap.add_argument("--scales", default="1,0.5", help="scales of the learned update tried in turn")
+    ap.add_argument("--plain-from", default=None,
+                    help="JSON of an earlier evaluation of the same models: reuse its plain "
+                         "L-BFGS rows (the plain runs are deterministic) instead of rerunning them")
     args = ap.parse_args(argv)
     dev = torch.device("cuda:0")
     first = W.preconditioner_model(args.seed, nt=args.nt)
@@ -114,16 +121,26 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
               val1):
     dev = fd.device
     rows = []
+    plain = {}
+    if args.plain_from:
+        with open(args.plain_from) as f:
+            plain = {r["seed"]: r for r in json.load(f)["rows"]}
     for s in seeds_eval:
         wl = gen(int(s))
         obs = fd.forward_model(torch.tensor(wl.eps_true, dtype=torch.float32, device=dev),
                                torch.tensor(wl.sig_true, dtype=torch.float32, device=dev), wav)
-        h_plain, t_plain = _fwi(fd, wl, obs, wl.f0, args.iters)
-        target = h_plain.final_misfit
-        h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target)
-        rows.append(dict(seed=int(s), J0=h_plain.misfit[0] if h_plain.misfit else None,
-                         J_plain=target, it_plain=len(h_plain.misfit),
-                         ev_plain=int(sum(h_plain.evaluations)), s_plain=t_plain,
+        if int(s) in plain:
+            p = plain[int(s)]
+        else:
+            h_plain, t_plain = _fwi(fd, wl, obs, wl.f0, args.iters)
+            p = dict(J0=h_plain.misfit[0] if h_plain.misfit else None,
+                     J_plain=h_plain.final_misfit, it_plain=len(h_plain.misfit),
+                     ev_plain=int(sum(h_plain.evaluations)), s_plain=t_plain)
+        target = p["J_plain"]
+        h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target, retry=args.retry,
+                        scales=[float(v) for v in args.scales.split(",")])
+        rows.append(dict(seed=int(s), J0=p["J0"], J_plain=target, it_plain=p["it_plain"],
+                         ev_plain=p["ev_plain"], s_plain=p["s_plain"],
                          J_learned=h_l.final_misfit, it_learned=len(h_l.misfit),
                          ev_learned=int(sum(h_l.evaluations)), s_learned=t_l,
                          reached=bool(h_l.final_misfit <= target),
@@ -132,7 +149,8 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
     out = {
         "workload": f"precond_{g.nx}x{g.ny}_16shots_nt{g.nt}",
         "train_models": args.train, "val_models": args.val, "eval_models": args.eval,
-        "loaded_params": args.load,
+        "loaded_params": args.load, "learned_retry": args.retry, "learned_scales": args.scales,
+        "plain_rows_from": args.plain_from,
         "epochs": args.epochs, "batch": args.batch,
         "pair_generation_s": t_gen, "pair_generation_gpu_s": gpu_gen,
         "training_s": t_tr, "train_loss_first_epoch": losses[0], "train_loss_last_epoch": losses[-1],
