@@ -110,11 +110,13 @@ def test_small_random(dev, seed, tiling, kappa, pec, variant):
     check_case(wl, dev, (tiling or (0, 0, 0)) + (variant,))
 
 
-@pytest.mark.parametrize("nrec,tiling", [(200, (0, 0, 4)), (400, (0, 0, 4)), (400, (13, 7, 4))])
+@pytest.mark.parametrize("nrec,tiling", [(200, (0, 0, 4)), (400, (0, 0, 4)), (400, (13, 7, 4)),
+                                         (900, (0, 0, 4))])
 def test_dense_receivers(dev, nrec, tiling):
     """Hundreds of receivers scattered over the grid, duplicates included: launches whose tile
     lists fit the adjoint's shared-memory staging of positions and residual samples (up to 200
-    entries in one list) and a launch that exceeds it and reads them from global memory."""
+    entries in one list) and launches that exceed it (400 and 900 entries at K = 4) and read
+    them from global memory."""
     wl = W.small_random(51, nxp=46, nyp=27, npml=6, nt=150, nshots=2, nrec=nrec)
     check_case(wl, dev, tiling + (0,))
 
