@@ -252,25 +252,59 @@ __global__ void relu_bwd_kernel(const float* __restrict__ dy, const bf16* __rest
     }
 }
 
-// part[b][c] = sum of in[r][c] over the rows of chunk b (rows in order)
+// part[b][c] = sum of in[r][c] over the rows of chunk b.  G thread lanes share a column (G the
+// largest power of two with G * C <= 256; wider inputs loop over columns with one lane each);
+// lane j sums the rows j, j + G, ... of the chunk in four interleaved accumulators, and the
+// lanes are combined by a tree over j in shared memory: the order is fixed, so the sum is
+// deterministic.
 __global__ void colsum_partial_kernel(const float* __restrict__ in, long long rows, int C,
                                       int rows_per_chunk, float* __restrict__ part) {
+    __shared__ float red[256];
     const long long r0 = (long long)blockIdx.x * rows_per_chunk;
     const long long r1 = min(rows, r0 + rows_per_chunk);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.f;
-        for (long long r = r0; r < r1; ++r) s += in[r * C + c];
-        part[(long long)blockIdx.x * C + c] = s;
+    int G = 1;
+    while (2 * G * C <= 256) G *= 2;
+    const int Wc = 256 / G;  // columns per pass
+    const int t = threadIdx.x;
+    for (int cb = 0; cb < C; cb += Wc) {
+        const int c = cb + t % Wc, j = t / Wc;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (c < C && j < G) {
+            long long r = r0 + j;
+            for (; r + 3 * G < r1; r += 4 * G) {
+                a0 += in[r * C + c];
+                a1 += in[(r + G) * C + c];
+                a2 += in[(r + 2 * G) * C + c];
+                a3 += in[(r + 3 * G) * C + c];
+            }
+            for (; r < r1; r += G) a0 += in[r * C + c];
+        }
+        red[t] = (a0 + a1) + (a2 + a3);
+        __syncthreads();
+        // lanes j of a column sit Wc apart: halve the lane count until one is left
+        for (int h = G / 2; h >= 1; h /= 2) {
+            if (j < h) red[t] += red[t + h * Wc];
+            __syncthreads();
+        }
+        if (j == 0 && c < C) part[(long long)blockIdx.x * C + c] = red[t];
+        __syncthreads();
     }
 }
 
+// out[c] = sum over the chunks of part[b][c]: one block per column, a fixed-order tree.
 __global__ void colsum_final_kernel(const float* __restrict__ part, int chunks, int C,
                                     float* __restrict__ out) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    __shared__ float red[256];
+    const int c = blockIdx.x, t = threadIdx.x;
     float s = 0.f;
-    for (int b = 0; b < chunks; ++b) s += part[(long long)b * C + c];
-    out[c] = s;
+    for (int b = t; b < chunks; b += 256) s += part[(long long)b * C + c];
+    red[t] = s;
+    __syncthreads();
+    for (int h = 128; h >= 1; h /= 2) {
+        if (t < h) red[t] += red[t + h];
+        __syncthreads();
+    }
+    if (t == 0) out[c] = red[0];
 }
 
 __global__ void maxpool2_kernel(const bf16* __restrict__ x, int nb, int H, int W, int C,
@@ -516,7 +550,7 @@ cudaError_t column_sum(const float* in, long long rows, int C, float* part, floa
                        cudaStream_t st) {
     const int chunks = colsum_chunks(rows);
     colsum_partial_kernel<<<chunks, 256, 0, st>>>(in, rows, C, kColsumRows, part);
-    colsum_final_kernel<<<(C + 127) / 128, 128, 0, st>>>(part, chunks, C, out);
+    colsum_final_kernel<<<C, 256, 0, st>>>(part, chunks, C, out);
     return cudaGetLastError();
 }
 
