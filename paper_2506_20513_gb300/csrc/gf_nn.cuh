@@ -31,7 +31,9 @@ struct GemmArgs {
     // tcgen05 engine only: when conv_h > 0, A is not read from A/lda but gathered as the 3x3
     // im2col of the channels-last image A [M / (conv_h conv_w)][conv_h][conv_w][conv_c]:
     // A[m][k] = image[n, h + k / (3 conv_c) - 1, w + (k / conv_c) % 3 - 1, k % conv_c] with
-    // m = (n conv_h + h) conv_w + w, zero outside the image (conv_c a multiple of 8).
+    // m = (n conv_h + h) conv_w + w, zero outside the image (conv_c a multiple of 8).  In the
+    // MN-major (weight-gradient) products the roles of m and k swap: A[k][m] is that im2col
+    // with k the cell and m = tap * conv_c + c (M = 9 conv_c).
     int conv_h = 0, conv_w = 0, conv_c = 0;
     // tcgen05 engine only, failure-path tests: wait_polls > 0 limits every pipeline mbarrier
     // wait to that many polls and makes the final one wait on a barrier nobody arrives at, so

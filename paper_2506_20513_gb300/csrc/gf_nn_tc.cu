@@ -183,6 +183,51 @@ __device__ __forceinline__ void stage_conv_a(uint32_t base, const GemmArgs& a, c
     }
 }
 
+// Stage k (cells) [k0, k0 + 64) x m [m0, m0 + 128) of the MN-major A operand of a weight
+// gradient, im2col(X)[cell][tap * C + c] = X[cell shifted by the tap][c] (zero outside the
+// image), straight from the image X [cells][C] (C % 8 == 0, so each 16-byte chunk is 8
+// channels of one tap).  Same chunk-to-thread map and swizzle as stage_mn128<128>: the
+// thread's chunk column mc = tid % 16 is fixed, its cells are tid / 16 + 8 i.
+__device__ __forceinline__ void stage_conv_mn(uint32_t base, const GemmArgs& a, int m0, int k0,
+                                              int ke, int tid) {
+    constexpr int CPR = kTM / 8;
+    const int C = a.conv_c, H = a.conv_h, W = a.conv_w;
+    const int mc = tid % CPR, gm = m0 + mc * 8;
+    const int tap = gm / C, ch = gm - tap * C;
+    const int dh = tap / 3 - 1, dw = tap % 3 - 1;
+    const bool m_in = gm < a.M;
+    // with W a multiple of 64 the stage's 64 cells lie in one image row (k0 % 64 == 0)
+    const bool one_row = W % kTK == 0;
+    int h0 = 0, w0 = 0;
+    if (one_row) {
+        const int q = k0 / W;
+        w0 = k0 - q * W;
+        h0 = q % H;
+    }
+#pragma unroll
+    for (int i = 0; i < kTK * CPR / 128; ++i) {
+        const int kr = tid / CPR + (128 / CPR) * i;
+        const int kk = kr & 7;
+        const uint32_t dst = base + (mc >> 3) * 8192 + (kr >> 3) * 1024 + kk * 128 +
+                             (((mc & 7) ^ kk) << 4);
+        const int gk = k0 + kr;
+        int h, w;
+        if (one_row) {
+            h = h0;
+            w = w0 + kr;
+        } else {
+            const int q = gk / W;
+            w = gk - q * W;
+            h = q % H;
+        }
+        const int hh = h + dh, ww = w + dw;
+        if (m_in && gk < ke && hh >= 0 && hh < H && ww >= 0 && ww < W)
+            cp_async16(dst, a.A + ((long long)gk + dh * W + dw) * C + ch);
+        else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(dst), "r"(0) : "memory");
+    }
+}
+
 template <int BN, bool kMN>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(GemmArgs a, int* status, const __grid_constant__ CUtensorMap tma_a,
@@ -233,12 +278,13 @@ __global__ void __launch_bounds__(128, 1)
     const unsigned polls = a.wait_polls ? a.wait_polls : kSpinLimit;
     const bool inject = a.wait_polls != 0;
     int kdone = -1;  // last k-tile whose MMAs were issued and committed
-    const bool conv = !kMN && a.conv_h > 0;
+    const bool conv = !kMN && a.conv_h > 0;      // implicit im2col, K-major A
+    const bool conv_mn = kMN && a.conv_h > 0;    // implicit im2col, MN-major A
     ConvRows cr;
     if (conv) conv_rows(a, m0, tid, cr);
     // operands loaded by TMA (a.tma_a / a.tma_b): thread 0 announces the stage's bytes on its
     // full barrier and issues the boxes; the other operands are staged by all threads
-    const bool ta_tma = a.tma_a != 0 && !conv, tb_tma = a.tma_b != 0;
+    const bool ta_tma = a.tma_a != 0 && !conv && !conv_mn, tb_tma = a.tma_b != 0;
     const bool any_tma = ta_tma || tb_tma;
     int lastk[kStages];  // last k-tile loaded into each stage (-1: none), uniform over the CTA
 #pragma unroll
@@ -262,7 +308,10 @@ __global__ void __launch_bounds__(128, 1)
             }
         }
         if (kMN) {
-            if (!ta_tma) stage_mn128<kTM>(sa, a.A, a.lda, m0, a.M, k0, ke, tid);
+            if (conv_mn)
+                stage_conv_mn(sa, a, m0, k0, ke, tid);
+            else if (!ta_tma)
+                stage_mn128<kTM>(sa, a.A, a.lda, m0, a.M, k0, ke, tid);
             if (!tb_tma) stage_mn128<BN>(sa + kABytes, a.B, a.ldb, n0, a.N, k0, ke, tid);
         } else {
             if (conv)
@@ -488,7 +537,7 @@ cudaError_t tc_launch(GemmArgs a, int splits, int* status, cudaStream_t st) {
     memset(&mb, 0, sizeof(mb));
     if (a.tma_a || a.tma_b) {
         if (kMN) {
-            a.tma_a = a.tma_a && make_map(&ma, a.A, a.M, a.K, a.lda, 64, 64);
+            a.tma_a = a.tma_a && a.conv_h == 0 && make_map(&ma, a.A, a.M, a.K, a.lda, 64, 64);
             a.tma_b = a.tma_b && make_map(&mb, a.B, a.N, a.K, a.ldb, 64, 64);
         } else {
             a.tma_a = a.tma_a && a.conv_h == 0 && make_map(&ma, a.A, a.K, a.M, a.lda, 64, kTM);
@@ -536,8 +585,12 @@ cudaError_t tc_gemm(const GemmArgs& a, int* status, cudaStream_t st) {
 
 bool tc_gemm_mn_supported(const GemmArgs& a) {
     auto al = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
-    return a.ta == 1 && a.tb == 0 && a.conv_h == 0 && a.M % 8 == 0 && a.N % 8 == 0 &&
-           a.lda % 8 == 0 && a.ldb % 8 == 0 && al(a.A) && al(a.B) && a.M > 0 && a.N > 0 &&
+    // A either MN-major in memory (lda) or the implicit im2col of an image [K cells][conv_c]
+    const bool a_ok = a.conv_h > 0 ? (a.conv_w > 0 && a.conv_c % 8 == 0 && a.M == 9 * a.conv_c &&
+                                      a.K % (a.conv_h * a.conv_w) == 0)
+                                   : a.lda % 8 == 0;
+    return a.ta == 1 && a.tb == 0 && a_ok && a.M % 8 == 0 && a.N % 8 == 0 &&
+           a.ldb % 8 == 0 && al(a.A) && al(a.B) && a.M > 0 && a.N > 0 &&
            a.K > 0 && a.N <= 256 && (a.M + kTM - 1) / kTM <= 65535 && a.C && !a.Cb &&
            !a.bias && a.beta == 0.f;
 }

@@ -426,23 +426,32 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
     NN_CUDA(u, gf::nn::relu_bwd(gout, out, (long long)rows * c.co, 1, u->dz, u->dzb, st));
     NN_CUDA(u, gf::nn::column_sum(u->dz, rows, c.co, u->colpart, u->grads + c.boff, st));
     ++u->launches;
-    NN_CUDA(u, gf::nn::im2col3(in, n, H, W, c.ci, u->col, st));
     int rc;
     // weight gradient dW[co][k] = sum over cells of dz[cell][co] col[cell][k]; on the tcgen05
     // engine as the transposed product col^T dz (M = 9 ci fills the 128 TMEM lanes) with
-    // split-K and a transposing reduction
+    // split-K and a transposing reduction, its A operand gathered from the image itself
+    // (implicit im2col) when ci % 8 == 0, else from an explicit im2col buffer
     gf::nn::GemmArgs t;
     t.M = 9 * c.ci;
     t.N = c.co;
     t.K = rows;
-    t.A = u->col;
+    t.A = in;
     t.lda = 9 * c.ci;
     t.ta = 1;
+    t.conv_h = H;
+    t.conv_w = W;
+    t.conv_c = c.ci;
     t.B = u->dzb;
     t.ldb = c.co;
     t.tb = 0;
     t.C = u->grads + c.woff;
     t.ldc = 9 * c.ci;
+    const bool implicit = u->gemm_mode >= 1 && gf::nn::tc_gemm_mn_supported(t);
+    if (!implicit) {
+        t.conv_h = t.conv_w = t.conv_c = 0;
+        t.A = u->col;
+        NN_CUDA(u, gf::nn::im2col3(in, n, H, W, c.ci, u->col, st));
+    }
     if (u->gemm_mode >= 1 && gf::nn::tc_gemm_mn_supported(t)) {
         rc = run_gemm_mn(u, t, st);
     } else {
