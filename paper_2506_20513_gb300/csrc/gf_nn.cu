@@ -240,15 +240,37 @@ __global__ void flip_transpose_kernel(const bf16* __restrict__ w, int Co, int Ci
     }
 }
 
-// dz = dy * (y > 0) (or dz = dy without ReLU), FP32 and BF16 copies.
+// dz = dy * (y > 0) (or dz = dy without ReLU), FP32 and BF16 copies.  V = 4 elements per
+// thread (16-byte FP32 and 8-byte BF16 accesses) when n and the pointers allow, else 1.
+template <int V>
 __global__ void relu_bwd_kernel(const float* __restrict__ dy, const bf16* __restrict__ y,
                                 long long n, int relu, float* __restrict__ dz,
                                 bf16* __restrict__ dzb) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+    const long long nv = n / V;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nv;
          e += (long long)gridDim.x * blockDim.x) {
-        const float v = (!relu || __bfloat162float(y[e]) > 0.f) ? dy[e] : 0.f;
-        if (dz) dz[e] = v;
-        dzb[e] = __float2bfloat16(v);
+        if (V == 4) {
+            const float4 d = reinterpret_cast<const float4*>(dy)[e];
+            const uint2 yy = reinterpret_cast<const uint2*>(y)[e];
+            const bf16* yb = reinterpret_cast<const bf16*>(&yy);
+            float4 v;
+            v.x = (!relu || __bfloat162float(yb[0]) > 0.f) ? d.x : 0.f;
+            v.y = (!relu || __bfloat162float(yb[1]) > 0.f) ? d.y : 0.f;
+            v.z = (!relu || __bfloat162float(yb[2]) > 0.f) ? d.z : 0.f;
+            v.w = (!relu || __bfloat162float(yb[3]) > 0.f) ? d.w : 0.f;
+            if (dz) reinterpret_cast<float4*>(dz)[e] = v;
+            uint2 ob;
+            bf16* o = reinterpret_cast<bf16*>(&ob);
+            o[0] = __float2bfloat16(v.x);
+            o[1] = __float2bfloat16(v.y);
+            o[2] = __float2bfloat16(v.z);
+            o[3] = __float2bfloat16(v.w);
+            reinterpret_cast<uint2*>(dzb)[e] = ob;
+        } else {
+            const float v = (!relu || __bfloat162float(y[e]) > 0.f) ? dy[e] : 0.f;
+            if (dz) dz[e] = v;
+            dzb[e] = __float2bfloat16(v);
+        }
     }
 }
 
@@ -307,103 +329,166 @@ __global__ void colsum_final_kernel(const float* __restrict__ part, int chunks, 
     if (t == 0) out[c] = red[0];
 }
 
+// The pooling, upsampling and channel-copy kernels walk rows of the image (blockIdx.y,
+// grid-strided) and, within a row, cells x groups of V channels (V = 8 BF16 or 4 FP32
+// channels, one 16-byte access, when every channel count and offset allows; else 1), with
+// 32-bit index arithmetic.
+
+// y[n, ho, wo, c] = max of the 2 x 2 window of x (H, W even)
+template <int V>
 __global__ void maxpool2_kernel(const bf16* __restrict__ x, int nb, int H, int W, int C,
                                 bf16* __restrict__ y) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long total = (long long)nb * Ho * Wo * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        long long r = e / C;
-        const int w = (int)(r % Wo);
-        r /= Wo;
-        const int h = (int)(r % Ho);
-        const int n = (int)(r / Ho);
-        const bf16* p = x + (((long long)n * H + 2 * h) * W + 2 * w) * C + c;
-        const float m = fmaxf(fmaxf(__bfloat162float(p[0]), __bfloat162float(p[C])),
-                              fmaxf(__bfloat162float(p[(long long)W * C]),
-                                    __bfloat162float(p[(long long)W * C + C])));
-        y[e] = __float2bfloat16(m);
+    const int Ho = H / 2, Wo = W / 2, CV = C / V, per = Wo * CV;
+    for (int row = blockIdx.y; row < nb * Ho; row += gridDim.y) {
+        const int n = row / Ho, h = row - n * Ho;
+        const bf16* x0 = x + ((long long)n * H + 2 * h) * W * C;
+        const bf16* x1 = x0 + (long long)W * C;
+        bf16* yr = y + (long long)row * Wo * C;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int w = i / CV, c = (i - w * CV) * V;
+            const int o0 = 2 * w * C + c, o1 = o0 + C;
+            bf16 a[V], b[V], d[V], e[V], m[V];
+            if (V == 8) {
+                *reinterpret_cast<uint4*>(a) = *reinterpret_cast<const uint4*>(x0 + o0);
+                *reinterpret_cast<uint4*>(b) = *reinterpret_cast<const uint4*>(x0 + o1);
+                *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(x1 + o0);
+                *reinterpret_cast<uint4*>(e) = *reinterpret_cast<const uint4*>(x1 + o1);
+            } else {
+                a[0] = x0[o0]; b[0] = x0[o1]; d[0] = x1[o0]; e[0] = x1[o1];
+            }
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                m[k] = __float2bfloat16(fmaxf(fmaxf(__bfloat162float(a[k]), __bfloat162float(b[k])),
+                                              fmaxf(__bfloat162float(d[k]), __bfloat162float(e[k]))));
+            if (V == 8)
+                *reinterpret_cast<uint4*>(yr + w * C + c) = *reinterpret_cast<const uint4*>(m);
+            else
+                yr[w * C + c] = m[0];
+        }
     }
 }
 
 // dx = (first maximal element of each window, row by row) ? dy : 0, plus addend if given
+template <int V>
 __global__ void maxpool2_bwd_kernel(const bf16* __restrict__ x, const bf16* __restrict__ y,
                                     const float* __restrict__ dy, const float* __restrict__ add,
                                     int nb, int H, int W, int C, float* __restrict__ dx) {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long total = (long long)nb * Ho * Wo * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        long long r = e / C;
-        const int w = (int)(r % Wo);
-        r /= Wo;
-        const int h = (int)(r % Ho);
-        const int n = (int)(r / Ho);
-        const float m = __bfloat162float(y[e]);
-        bool done = false;
+    const int Ho = H / 2, Wo = W / 2, CV = C / V, per = Wo * CV;
+    for (int row = blockIdx.y; row < nb * Ho; row += gridDim.y) {
+        const int n = row / Ho, h = row - n * Ho;
+        const long long r0 = ((long long)n * H + 2 * h) * W * C;  // first child row
+        const long long ro = (long long)row * Wo * C;             // pooled row
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int w = i / CV, c = (i - w * CV) * V;
+            float m[V], g[V];
+            bool done[V];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const long long i = (((long long)n * H + 2 * h + (q >> 1)) * W + 2 * w + (q & 1)) * C + c;
-            const bool hit = !done && __bfloat162float(x[i]) == m;
-            dx[i] = (hit ? dy[e] : 0.f) + (add ? add[i] : 0.f);
-            done = done || hit;
+            for (int k = 0; k < V; ++k) {
+                m[k] = __bfloat162float(y[ro + w * C + c + k]);
+                g[k] = dy[ro + w * C + c + k];
+                done[k] = false;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long long idx = r0 + (long long)(q >> 1) * W * C + (2 * w + (q & 1)) * C + c;
+                float o[V];
+#pragma unroll
+                for (int k = 0; k < V; ++k) {
+                    const bool hit = !done[k] && __bfloat162float(x[idx + k]) == m[k];
+                    o[k] = (hit ? g[k] : 0.f) + (add ? add[idx + k] : 0.f);
+                    done[k] = done[k] || hit;
+                }
+                if (V == 4)
+                    *reinterpret_cast<float4*>(dx + idx) = make_float4(o[0], o[1], o[2], o[3]);
+                else
+                    dx[idx] = o[0];
+            }
         }
     }
 }
 
 // y[n, h, w, coff + c] = x[n, h/2, w/2, c], y with Cy channels per cell
+template <int V>
 __global__ void upsample2_kernel(const bf16* __restrict__ x, int nb, int H, int W, int C,
                                  bf16* __restrict__ y, int Cy, int coff) {
-    const long long total = (long long)nb * 4 * H * W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        long long r = e / C;
-        const int w = (int)(r % (2 * W));
-        r /= 2 * W;
-        const int h = (int)(r % (2 * H));
-        const int n = (int)(r / (2 * H));
-        y[(((long long)n * 2 * H + h) * 2 * W + w) * Cy + coff + c] =
-            x[(((long long)n * H + h / 2) * W + w / 2) * C + c];
+    const int CV = C / V, per = 2 * W * CV;
+    for (int row = blockIdx.y; row < nb * 2 * H; row += gridDim.y) {
+        const int n = row / (2 * H), h = row - n * 2 * H;
+        const bf16* xr = x + ((long long)n * H + h / 2) * W * C;
+        bf16* yr = y + (long long)row * 2 * W * Cy + coff;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int w = i / CV, c = (i - w * CV) * V;
+            if (V == 8)
+                *reinterpret_cast<uint4*>(yr + w * Cy + c) =
+                    *reinterpret_cast<const uint4*>(xr + (w / 2) * C + c);
+            else
+                yr[w * Cy + c] = xr[(w / 2) * C + c];
+        }
     }
 }
 
 // dx[n, h, w, c] = sum of dy[n, 2h+a, 2w+b, coff + c] over the four children
+template <int V>
 __global__ void upsample2_bwd_kernel(const float* __restrict__ dy, int nb, int H, int W, int C,
                                      int Cy, int coff, float* __restrict__ dx) {
-    const long long total = (long long)nb * H * W * C;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(e % C);
-        long long r = e / C;
-        const int w = (int)(r % W);
-        r /= W;
-        const int h = (int)(r % H);
-        const int n = (int)(r / H);
-        const float* p = dy + (((long long)n * 2 * H + 2 * h) * 2 * W + 2 * w) * Cy + coff + c;
-        const long long rowp = 2LL * W * Cy;
-        dx[e] = (p[0] + p[Cy]) + (p[rowp] + p[rowp + Cy]);
+    const int CV = C / V, per = W * CV;
+    for (int row = blockIdx.y; row < nb * H; row += gridDim.y) {
+        const int n = row / H, h = row - n * H;
+        const float* d0 = dy + ((long long)n * 2 * H + 2 * h) * 2 * W * Cy + coff;
+        const float* d1 = d0 + 2LL * W * Cy;
+        float* o = dx + (long long)row * W * C;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int w = i / CV, c = (i - w * CV) * V;
+            const int a0 = 2 * w * Cy + c, a1 = a0 + Cy;
+            if (V == 4) {
+                const float4 p = *reinterpret_cast<const float4*>(d0 + a0);
+                const float4 q = *reinterpret_cast<const float4*>(d0 + a1);
+                const float4 r = *reinterpret_cast<const float4*>(d1 + a0);
+                const float4 t = *reinterpret_cast<const float4*>(d1 + a1);
+                *reinterpret_cast<float4*>(o + w * C + c) =
+                    make_float4((p.x + q.x) + (r.x + t.x), (p.y + q.y) + (r.y + t.y),
+                                (p.z + q.z) + (r.z + t.z), (p.w + q.w) + (r.w + t.w));
+            } else {
+                o[w * C + c] = (d0[a0] + d0[a1]) + (d1[a0] + d1[a1]);
+            }
+        }
     }
 }
 
 // y[r][coff + c] = x[r][c]  (x with C channels, y with Cy)
+template <int V>
 __global__ void put_channels_kernel(const bf16* __restrict__ x, long long rows, int C,
                                     bf16* __restrict__ y, int Cy, int coff) {
-    const long long total = rows * C;
+    const int CV = C / V;
+    const long long total = rows * CV;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        y[(e / C) * Cy + coff + e % C] = x[e];
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / CV;
+        const int c = (int)(e - r * CV) * V;
+        if (V == 8)
+            *reinterpret_cast<uint4*>(y + r * Cy + coff + c) =
+                *reinterpret_cast<const uint4*>(x + r * C + c);
+        else
+            y[r * Cy + coff + c] = x[r * C + c];
+    }
 }
 
 // dx[r][c] = dy[r][coff + c]
+template <int V>
 __global__ void take_channels_kernel(const float* __restrict__ dy, long long rows, int Cy,
                                      int coff, int C, float* __restrict__ dx) {
-    const long long total = rows * C;
+    const int CV = C / V;
+    const long long total = rows * CV;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x)
-        dx[e] = dy[(e / C) * Cy + coff + e % C];
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / CV;
+        const int c = (int)(e - r * CV) * V;
+        if (V == 4)
+            *reinterpret_cast<float4*>(dx + r * C + c) =
+                *reinterpret_cast<const float4*>(dy + r * Cy + coff + c);
+        else
+            dx[r * C + c] = dy[r * Cy + coff + c];
+    }
 }
 
 // r = mask (y - t); dy = r / count; partial[b] = sum over the block of r^2 / (2 count)
@@ -540,7 +625,13 @@ cudaError_t flip_transpose(const void* w, int Co, int Ci, void* wt, cudaStream_t
 
 cudaError_t relu_bwd(const float* dy, const void* y, long long n, int relu, float* dz, void* dzb,
                      cudaStream_t st) {
-    relu_bwd_kernel<<<grid_for(n), 256, 0, st>>>(dy, (const bf16*)y, n, relu, dz, (bf16*)dzb);
+    auto al = [](const void* p, int b) { return ((uintptr_t)p & (b - 1)) == 0; };
+    if (n % 4 == 0 && al(dy, 16) && al(y, 8) && (!dz || al(dz, 16)) && al(dzb, 8))
+        relu_bwd_kernel<4><<<grid_for(n / 4), 256, 0, st>>>(dy, (const bf16*)y, n, relu, dz,
+                                                            (bf16*)dzb);
+    else
+        relu_bwd_kernel<1><<<grid_for(n), 256, 0, st>>>(dy, (const bf16*)y, n, relu, dz,
+                                                        (bf16*)dzb);
     return cudaGetLastError();
 }
 
@@ -554,43 +645,78 @@ cudaError_t column_sum(const float* in, long long rows, int C, float* part, floa
     return cudaGetLastError();
 }
 
+// grid of the row kernels: up to 65535 rows in y (grid-strided), a row's items over x
+dim3 rows_grid(long long rows, long long per_row) {
+    const long long bx = (per_row + 255) / 256;
+    return dim3((unsigned)(bx < 1 ? 1 : (bx > 64 ? 64 : bx)),
+                (unsigned)(rows < 1 ? 1 : (rows > 65535 ? 65535 : rows)));
+}
+
 cudaError_t maxpool2(const void* x, int nb, int H, int W, int C, void* y, cudaStream_t st) {
-    maxpool2_kernel<<<grid_for((long long)nb * (H / 2) * (W / 2) * C), 256, 0, st>>>(
-        (const bf16*)x, nb, H, W, C, (bf16*)y);
+    const long long rows = (long long)nb * (H / 2);
+    if (C % 8 == 0 && aligned16(x) && aligned16(y))
+        maxpool2_kernel<8><<<rows_grid(rows, (W / 2) * (C / 8)), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)y);
+    else
+        maxpool2_kernel<1><<<rows_grid(rows, (long long)(W / 2) * C), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)y);
     return cudaGetLastError();
 }
 
 cudaError_t maxpool2_bwd(const void* x, const void* y, const float* dy, const float* add, int nb,
                          int H, int W, int C, float* dx, cudaStream_t st) {
-    maxpool2_bwd_kernel<<<grid_for((long long)nb * (H / 2) * (W / 2) * C), 256, 0, st>>>(
-        (const bf16*)x, (const bf16*)y, dy, add, nb, H, W, C, dx);
+    const long long rows = (long long)nb * (H / 2);
+    if (C % 4 == 0 && aligned16(dx))
+        maxpool2_bwd_kernel<4><<<rows_grid(rows, (W / 2) * (C / 4)), 256, 0, st>>>(
+            (const bf16*)x, (const bf16*)y, dy, add, nb, H, W, C, dx);
+    else
+        maxpool2_bwd_kernel<1><<<rows_grid(rows, (long long)(W / 2) * C), 256, 0, st>>>(
+            (const bf16*)x, (const bf16*)y, dy, add, nb, H, W, C, dx);
     return cudaGetLastError();
 }
 
 cudaError_t upsample2(const void* x, int nb, int H, int W, int C, void* y, int Cy, int coff,
                       cudaStream_t st) {
-    upsample2_kernel<<<grid_for((long long)nb * 4 * H * W * C), 256, 0, st>>>(
-        (const bf16*)x, nb, H, W, C, (bf16*)y, Cy, coff);
+    const long long rows = (long long)nb * 2 * H;
+    if (C % 8 == 0 && Cy % 8 == 0 && coff % 8 == 0 && aligned16(x) && aligned16(y))
+        upsample2_kernel<8><<<rows_grid(rows, 2LL * W * (C / 8)), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)y, Cy, coff);
+    else
+        upsample2_kernel<1><<<rows_grid(rows, 2LL * W * C), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)y, Cy, coff);
     return cudaGetLastError();
 }
 
 cudaError_t upsample2_bwd(const float* dy, int nb, int H, int W, int C, int Cy, int coff,
                           float* dx, cudaStream_t st) {
-    upsample2_bwd_kernel<<<grid_for((long long)nb * H * W * C), 256, 0, st>>>(dy, nb, H, W, C,
-                                                                             Cy, coff, dx);
+    const long long rows = (long long)nb * H;
+    if (C % 4 == 0 && Cy % 4 == 0 && coff % 4 == 0 && aligned16(dy) && aligned16(dx))
+        upsample2_bwd_kernel<4><<<rows_grid(rows, (long long)W * (C / 4)), 256, 0, st>>>(
+            dy, nb, H, W, C, Cy, coff, dx);
+    else
+        upsample2_bwd_kernel<1><<<rows_grid(rows, (long long)W * C), 256, 0, st>>>(
+            dy, nb, H, W, C, Cy, coff, dx);
     return cudaGetLastError();
 }
 
 cudaError_t put_channels(const void* x, long long rows, int C, void* y, int Cy, int coff,
                          cudaStream_t st) {
-    put_channels_kernel<<<grid_for(rows * C), 256, 0, st>>>((const bf16*)x, rows, C, (bf16*)y,
-                                                            Cy, coff);
+    if (C % 8 == 0 && Cy % 8 == 0 && coff % 8 == 0 && aligned16(x) && aligned16(y))
+        put_channels_kernel<8><<<grid_for(rows * (C / 8)), 256, 0, st>>>(
+            (const bf16*)x, rows, C, (bf16*)y, Cy, coff);
+    else
+        put_channels_kernel<1><<<grid_for(rows * C), 256, 0, st>>>((const bf16*)x, rows, C,
+                                                                   (bf16*)y, Cy, coff);
     return cudaGetLastError();
 }
 
 cudaError_t take_channels(const float* dy, long long rows, int Cy, int coff, int C, float* dx,
                           cudaStream_t st) {
-    take_channels_kernel<<<grid_for(rows * C), 256, 0, st>>>(dy, rows, Cy, coff, C, dx);
+    if (C % 4 == 0 && Cy % 4 == 0 && coff % 4 == 0 && aligned16(dy) && aligned16(dx))
+        take_channels_kernel<4><<<grid_for(rows * (C / 4)), 256, 0, st>>>(dy, rows, Cy, coff,
+                                                                          C, dx);
+    else
+        take_channels_kernel<1><<<grid_for(rows * C), 256, 0, st>>>(dy, rows, Cy, coff, C, dx);
     return cudaGetLastError();
 }
 
