@@ -196,33 +196,34 @@ __global__ void splitk_reduce_kernel(const float* __restrict__ P, int splits, in
     }
 }
 
-// col[(n,h,w)][(kh,kw,c)] = x[n, h+kh-1, w+kw-1, c] (zero outside), 8 channels per thread
-// when C % 8 == 0.
+// col[(n,h,w)][(kh,kw,c)] = x[n, h+kh-1, w+kw-1, c] (zero outside): image rows over
+// blockIdx.y (grid-strided), (cell, tap, group of V channels) within a row, V = 8 (16-byte
+// copies) when C % 8 == 0, 4 (8-byte) when C % 4 == 0, else 1; 32-bit index arithmetic.
+template <int V>
 __global__ void im2col3_kernel(const bf16* __restrict__ x, int nb, int H, int W, int C,
                                bf16* __restrict__ col) {
-    const int vec = (C % 8 == 0) ? 8 : 1;
-    const int Cv = C / vec;
-    const long long total = (long long)nb * H * W * 9 * Cv;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int cv = (int)(e % Cv);
-        long long r = e / Cv;
-        const int k = (int)(r % 9);
-        r /= 9;
-        const int w = (int)(r % W);
-        r /= W;
-        const int h = (int)(r % H);
-        const int n = (int)(r / H);
-        const int hh = h + k / 3 - 1, ww = w + k % 3 - 1;
-        const bool in = hh >= 0 && hh < H && ww >= 0 && ww < W;
-        const long long src = (((long long)n * H + hh) * W + ww) * C + cv * vec;
-        const long long dst = e * vec;
-        if (vec == 8) {
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (in) v = *reinterpret_cast<const uint4*>(x + src);
-            *reinterpret_cast<uint4*>(col + dst) = v;
-        } else {
-            col[dst] = in ? x[src] : __float2bfloat16(0.f);
+    const int CV = C / V, per = W * 9 * CV;
+    for (int row = blockIdx.y; row < nb * H; row += gridDim.y) {
+        const int n = row / H, h = row - n * H;
+        bf16* out = col + (long long)row * W * 9 * C;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+            const int w = i / (9 * CV), rem = i - w * 9 * CV;
+            const int k = rem / CV, c = (rem - k * CV) * V;
+            const int hh = h + k / 3 - 1, ww = w + k % 3 - 1;
+            const bool in = hh >= 0 && hh < H && ww >= 0 && ww < W;
+            const bf16* src = x + (((long long)n * H + hh) * W + ww) * C + c;
+            bf16* dst = out + (long long)i * V;
+            if (V == 8) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (in) v = *reinterpret_cast<const uint4*>(src);
+                *reinterpret_cast<uint4*>(dst) = v;
+            } else if (V == 4) {
+                uint2 v = make_uint2(0, 0);
+                if (in) v = *reinterpret_cast<const uint2*>(src);
+                *reinterpret_cast<uint2*>(dst) = v;
+            } else {
+                *dst = in ? *src : __float2bfloat16(0.f);
+            }
         }
     }
 }
@@ -544,6 +545,13 @@ __global__ void to_bf16_kernel(const float* __restrict__ x, long long n, bf16* _
         y[e] = __float2bfloat16(x[e]);
 }
 
+// grid of the row kernels: up to 65535 rows in y (grid-strided), a row's items over x
+dim3 rows_grid(long long rows, long long per_row) {
+    const long long bx = (per_row + 255) / 256;
+    return dim3((unsigned)(bx < 1 ? 1 : (bx > 64 ? 64 : bx)),
+                (unsigned)(rows < 1 ? 1 : (rows > 65535 ? 65535 : rows)));
+}
+
 int grid_for(long long n) {
     const long long b = (n + 255) / 256;
     return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
@@ -612,8 +620,17 @@ cudaError_t gemm(GemmArgs a, const GemmPlan& plan, float* partial, cudaStream_t 
 }
 
 cudaError_t im2col3(const void* x, int nb, int H, int W, int C, void* col, cudaStream_t st) {
-    const long long n = (long long)nb * H * W * 9 * (C % 8 == 0 ? C / 8 : C);
-    im2col3_kernel<<<grid_for(n), 256, 0, st>>>((const bf16*)x, nb, H, W, C, (bf16*)col);
+    auto al = [](const void* p, int b) { return ((uintptr_t)p & (b - 1)) == 0; };
+    const long long rows = (long long)nb * H;
+    if (C % 8 == 0 && al(x, 16) && al(col, 16))
+        im2col3_kernel<8><<<rows_grid(rows, 9LL * W * (C / 8)), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)col);
+    else if (C % 4 == 0 && al(x, 8) && al(col, 8))
+        im2col3_kernel<4><<<rows_grid(rows, 9LL * W * (C / 4)), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)col);
+    else
+        im2col3_kernel<1><<<rows_grid(rows, 9LL * W * C), 256, 0, st>>>(
+            (const bf16*)x, nb, H, W, C, (bf16*)col);
     return cudaGetLastError();
 }
 
@@ -645,12 +662,6 @@ cudaError_t column_sum(const float* in, long long rows, int C, float* part, floa
     return cudaGetLastError();
 }
 
-// grid of the row kernels: up to 65535 rows in y (grid-strided), a row's items over x
-dim3 rows_grid(long long rows, long long per_row) {
-    const long long bx = (per_row + 255) / 256;
-    return dim3((unsigned)(bx < 1 ? 1 : (bx > 64 ? 64 : bx)),
-                (unsigned)(rows < 1 ? 1 : (rows > 65535 ? 65535 : rows)));
-}
 
 cudaError_t maxpool2(const void* x, int nb, int H, int W, int C, void* y, cudaStream_t st) {
     const long long rows = (long long)nb * (H / 2);
