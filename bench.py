@@ -294,7 +294,6 @@ def ours(args):
     clocks.start()
     lib, ctx = fd.lib, fd.ctx
     launches0 = lib.gf_kernel_launches(ctx)
-    lib.gf_profile(ctx, 1)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -304,6 +303,13 @@ def ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     gpu_launches = lib.gf_kernel_launches(ctx) - launches0
+    # the same K steps again with CUDA events around every launch on its stream, for the
+    # per-kernel durations of the roofline (kept out of the timed region above: the events
+    # cost about 1.5% of the step)
+    lib.gf_profile(ctx, 1)
+    for _ in range(args.steps):
+        step()
+    barrier()
     import ctypes
     prof = {}
     for name, kind in (("fwd", _lib.GF_KERNEL_FWD), ("adj", _lib.GF_KERNEL_ADJ),
