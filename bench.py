@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -34,19 +35,19 @@ UNIT = "Gcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per cell-step of one launch, from `ncu --metrics
-# dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel source (sha1 prefix of
-# gf_tile_kernels.cu), workload and tiling; see profiles/.  A kernel source change drops it.
+# dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel code (kernel_source_tag),
+# workload and tiling; see profiles/.  A change of the kernel code drops it.
 # Warp instructions per cell-step of one launch (ncu InstructionStats, same keys): the
 # kernels are bound by instruction issue, so the line also reports the issue roofline.
 NCU_WARP_INST_PER_CELL_STEP: dict = {
     # profiles/adj_tile_multishot_540x290x32.md: 199.0 M warp instructions per K = 7 launch
-    "adj@7098a186bfe3@540x290x32@default": 5.6732,
+    "adj@1085d4c1e613@540x290x32@default": 5.6732,
 }
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
     # profiles/adj_tile_multishot_540x290x32.md: 339.3 MB per K = 7 launch
-    "adj@7098a186bfe3@540x290x32@default": 9.6736,
+    "adj@1085d4c1e613@540x290x32@default": 9.6736,
 }
 
 
@@ -225,9 +226,13 @@ def hbm_peak():
 
 
 def kernel_source_tag():
+    """sha1 prefix of gf_tile_kernels.cu without its // comments and blank lines: any change
+    of the code drops the ncu figures keyed on it, an edit of a comment does not."""
     p = os.path.join(ROOT, "paper_2506_20513_gb300", "csrc", "gf_tile_kernels.cu")
-    with open(p, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    with open(p, encoding="utf-8") as f:
+        lines = [re.sub(r"//.*$", "", line).rstrip() for line in f.read().splitlines()]
+    code = "\n".join(line for line in lines if line.strip())
+    return hashlib.sha1(code.encode()).hexdigest()[:12]
 
 
 def algorithmic_bytes_per_launch(kind: str, wl, K: int) -> float:

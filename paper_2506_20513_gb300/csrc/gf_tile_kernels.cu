@@ -3,11 +3,15 @@
 // Tiling.  One CTA (64 x BY threads) owns an interior tile of tile_w x tile_h cells of one
 // shot and advances it K time steps per launch.  The tile plus a K-cell halo (at most 64 x 64
 // cells) stays on chip for the whole launch: thread (tx, ty) owns column tx and the RY
-// consecutive rows RY*ty .. RY*ty + RY - 1 (RY * BY = 64), keeping their field values, update
-// coefficients and accumulators in registers.  Shared memory only carries what neighbours
-// need: two x-neighbour planes (Ez for the H update and Hy for the E update; the transposed
-// difference weights S and T in the adjoint), one row per thread segment for the y-neighbour
-// across segments, and the CPML memory variables of strip cells.  Each time step the valid
+// consecutive rows RY*ty .. RY*ty + RY - 1 (RY * BY = 64, or 32 for the 512-thread 64 x 32
+// variant), keeping their field values in registers.  Shared memory carries what neighbours
+// exchange: two x-neighbour planes (Ez for the H update and Hy for the E update; the
+// transposed difference weights S and T in the adjoint) and one row per thread segment for
+// the y-neighbour across segments; besides, per owned cell, the CPML memory variables of strip
+// cells and the update coefficients Ca, Cb (and in the adjoint the carried Ez^{n+1} and the
+// two gradient accumulators), which would not fit the 64-register budget of a 1024-thread
+// CTA, plus the launch's source samples and, in the adjoint, the tile's receiver positions
+// and residual samples.  Each time step the valid
 // region shrinks by one cell on every side (an H update reads Ez at +1, an E update reads H
 // at -1), so after K steps exactly the interior is valid; it is written to the other
 // ping-pong state buffer.  Halo cells are recomputed redundantly by neighbouring CTAs from
