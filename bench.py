@@ -392,7 +392,7 @@ def ours(args):
         from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
         drv = FWI(fd, lambda f0: obs, interior_mask(g, rows_below_top=4),
                   FWIConfig(bands=((wl.f0, args.fwi_iters),)))
-        # an untimed pass first: the driver's first iterations otherwise include the one-time
+        # an untimed pass first: the FWI driver's first iterations otherwise include the one-time
         # loading of the PyTorch kernels its L-BFGS algebra uses (seconds on a fresh process)
         drv.run(eps0, sig0)
         _, _, hist = drv.run(eps0, sig0)

@@ -488,8 +488,8 @@ constexpr size_t tc_smem_bytes() {
     return 1024 + (size_t)kStages * (kTM * 128 + BN * 128) + 16 * kStages + 8 + 16;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link-time
-// dependency on the driver library); null when unavailable, and the threads stage instead.
+// cuTensorMapEncodeTiled from the CUDA driver, looked up once through the runtime (no link-time
+// dependency on the CUDA driver library); null when unavailable, and the threads stage instead.
 PFN_cuTensorMapEncodeTiled_v12000 tma_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static bool looked = false;

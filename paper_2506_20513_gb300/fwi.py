@@ -130,7 +130,7 @@ class FWI:
         """Iterate every band; with ``stop_misfit`` stop as soon as J <= stop_misfit.
 
         ``checkpoint`` / ``checkpoint_every``: after every that many iterations of a band, save
-        the driver state (model, gradient, misfit, L-BFGS pairs, band and iteration, the
+        the FWI state (model, gradient, misfit, L-BFGS pairs, band and iteration, the
         learned step's state and the history so far) to that file.  ``resume``: continue from
         such a file instead of starting at (eps0, sig0); a resumed run continues exactly as the
         uninterrupted one would (every kernel is deterministic).  ``log``: append one JSON line
