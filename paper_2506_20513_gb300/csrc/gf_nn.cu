@@ -749,5 +749,47 @@ cudaError_t to_bf16(const float* x, long long n, void* y, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// y[r][c] = x[r][c] (converted) for c < C, 0 for C <= c < Cp
+template <typename T>
+__global__ void pad_channels_kernel(const T* __restrict__ x, long long rows, int C, int Cp,
+                                    bf16* __restrict__ y) {
+    const long long total = rows * Cp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / Cp;
+        const int c = (int)(e - r * Cp);
+        y[e] = c < C ? bf16(x[r * C + c]) : __float2bfloat16(0.f);
+    }
+}
+
+// y[r][c] = x[r][c] for c < C of the Cp-channel rows of x
+__global__ void unpad_channels_kernel(const float* __restrict__ x, long long rows, int Cp, int C,
+                                      float* __restrict__ y) {
+    const long long total = rows * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long r = e / C;
+        y[e] = x[r * Cp + (e - r * C)];
+    }
+}
+
+cudaError_t pad_channels(const float* x, long long rows, int C, int Cp, void* y, cudaStream_t st) {
+    pad_channels_kernel<float><<<grid_for(rows * Cp), 256, 0, st>>>(x, rows, C, Cp, (bf16*)y);
+    return cudaGetLastError();
+}
+
+cudaError_t pad_channels_bf16(const void* x, long long rows, int C, int Cp, void* y,
+                              cudaStream_t st) {
+    pad_channels_kernel<bf16><<<grid_for(rows * Cp), 256, 0, st>>>((const bf16*)x, rows, C, Cp,
+                                                                   (bf16*)y);
+    return cudaGetLastError();
+}
+
+cudaError_t unpad_channels(const float* x, long long rows, int Cp, int C, float* y,
+                           cudaStream_t st) {
+    unpad_channels_kernel<<<grid_for(rows * C), 256, 0, st>>>(x, rows, Cp, C, y);
+    return cudaGetLastError();
+}
+
 }  // namespace nn
 }  // namespace gf

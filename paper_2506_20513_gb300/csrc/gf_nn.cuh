@@ -93,6 +93,13 @@ cudaError_t mse(const float* y, const float* t, const float* mask, long long n, 
 cudaError_t adam(float* w, const float* g, float* m, float* v, long long n, float lr, float b1,
                  float b2, float eps, float c1, float c2, void* wb, cudaStream_t st);
 cudaError_t to_bf16(const float* x, long long n, void* y, cudaStream_t st);
+// Channel padding of rows of C channels to Cp >= C (zeros), FP32 or BF16 in, BF16 out, and
+// the inverse selection for FP32 rows (the first layer's padded input, weights, gradient).
+cudaError_t pad_channels(const float* x, long long rows, int C, int Cp, void* y, cudaStream_t st);
+cudaError_t pad_channels_bf16(const void* x, long long rows, int C, int Cp, void* y,
+                              cudaStream_t st);
+cudaError_t unpad_channels(const float* x, long long rows, int Cp, int C, float* y,
+                           cudaStream_t st);
 
 }  // namespace nn
 }  // namespace gf

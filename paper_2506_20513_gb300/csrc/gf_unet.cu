@@ -87,6 +87,13 @@ struct gf_unet {
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     bf16 *wb = nullptr, *wt = nullptr;
     bf16* x0 = nullptr;
+    // cin not a multiple of 8: the first convolution runs on a zero-padded copy of its input
+    // and weights with cin_p = cin rounded up to 8 channels (so that the tcgen05 engine's
+    // implicit im2col takes it), its weight gradient compacted back afterwards
+    int cin_p = 0;
+    Conv enc0p{};
+    bf16* w0p = nullptr;
+    float* gw0p = nullptr;
     std::vector<bf16*> ea, eb, pool, cat, da, db;
     float* y = nullptr;
     bf16* col = nullptr;
@@ -150,7 +157,9 @@ struct Shape {
 
 std::vector<Shape> split_shapes(const gf_unet& u, int n) {
     std::vector<Shape> s;
-    for (const Conv& c : u.convs) {
+    std::vector<Conv> all = u.convs;
+    if (u.cin_p != u.d.cin) all.push_back(u.enc0p);  // the padded first convolution
+    for (const Conv& c : all) {
         const int rows = n * u.H(c.level) * u.W(c.level);
         const int kk = c.k * c.k;
         s.push_back({c.co, kk * c.ci, rows});          // weight gradient
@@ -194,7 +203,14 @@ int create(gf_unet* u) {
     need(u->dzb = dalloc<bf16>(u, dz_max));
     need(u->g0 = dalloc<float>(u, g_max));
     need(u->g1 = dalloc<float>(u, g_max));
-    need(u->x0 = dalloc<bf16>(u, rows(0) * d.cin));
+    u->cin_p = (d.cin + 7) / 8 * 8;
+    u->enc0p = u->enc(0, 0);
+    u->enc0p.ci = u->cin_p;
+    need(u->x0 = dalloc<bf16>(u, rows(0) * u->cin_p));
+    if (u->cin_p != d.cin) {
+        need(u->w0p = dalloc<bf16>(u, (size_t)u->enc0p.co * 9 * u->cin_p));
+        need(u->gw0p = dalloc<float>(u, (size_t)u->enc0p.co * 9 * u->cin_p));
+    }
     need(u->y = dalloc<float>(u, rows(0) * d.cout));
     u->ea.assign(L, nullptr);
     u->eb.assign(L, nullptr);
@@ -222,7 +238,9 @@ int create(gf_unet* u) {
             if (p.splits > 1) pmax = std::max(pmax, (long long)p.splits * s.M * s.N);
         }
         // the tcgen05 weight-gradient products run transposed: M = k^2 ci, N = co
-        for (const Conv& c : u->convs) {
+        std::vector<Conv> all = u->convs;
+        if (u->cin_p != d.cin) all.push_back(u->enc0p);
+        for (const Conv& c : all) {
             const int rows = n * u->H(c.level) * u->W(c.level);
             const int M = c.k * c.k * c.ci;
             const gf::nn::GemmPlan p = gf::nn::plan_tc_mn(M, c.co, rows);
@@ -355,7 +373,8 @@ int conv_operand(gf_unet* u, gf::nn::GemmArgs& a, const bf16* in, int n, int H, 
     return GF_OK;
 }
 
-int conv_forward(gf_unet* u, const Conv& c, const bf16* in, bf16* out, int n, cudaStream_t st) {
+int conv_forward(gf_unet* u, const Conv& c, const bf16* in, bf16* out, int n, cudaStream_t st,
+                 const bf16* w = nullptr) {
     const int H = u->H(c.level), W = u->W(c.level);
     const int rows = n * H * W;
     gf::nn::GemmArgs a;
@@ -363,7 +382,7 @@ int conv_forward(gf_unet* u, const Conv& c, const bf16* in, bf16* out, int n, cu
     a.N = c.co;
     a.K = 9 * c.ci;
     a.ta = 0;
-    a.B = u->wb + c.woff;
+    a.B = w ? w : u->wb + c.woff;
     a.ldb = 9 * c.ci;
     a.tb = 1;
     a.Cb = out;
@@ -379,7 +398,11 @@ int forward(gf_unet* u, int n, const float* x, float* y, cudaStream_t st) {
     const gf_unet_desc& d = u->d;
     const int L = d.levels;
     const long long rows0 = (long long)n * d.height * d.width;
-    NN_CUDA(u, gf::nn::to_bf16(x, rows0 * d.cin, u->x0, st));
+    const bool pad0 = u->cin_p != d.cin;
+    if (pad0)
+        NN_CUDA(u, gf::nn::pad_channels(x, rows0, d.cin, u->cin_p, u->x0, st));
+    else
+        NN_CUDA(u, gf::nn::to_bf16(x, rows0 * d.cin, u->x0, st));
     const bf16* h = u->x0;
     int rc;
     for (int l = 0; l < L; ++l) {
@@ -388,7 +411,11 @@ int forward(gf_unet* u, int n, const float* x, float* y, cudaStream_t st) {
                                         u->pool[l], st));
             h = u->pool[l];
         }
-        if ((rc = conv_forward(u, u->enc(l, 0), h, u->ea[l], n, st))) return rc;
+        if (l == 0 && pad0)
+            rc = conv_forward(u, u->enc0p, h, u->ea[0], n, st, u->w0p);
+        else
+            rc = conv_forward(u, u->enc(l, 0), h, u->ea[l], n, st);
+        if (rc) return rc;
         if ((rc = conv_forward(u, u->enc(l, 1), u->ea[l], u->eb[l], n, st))) return rc;
         h = u->eb[l];
     }
@@ -420,7 +447,9 @@ int forward(gf_unet* u, int n, const float* x, float* y, cudaStream_t st) {
 // Backward of relu(conv(in)) for n images: gout = dL/d(output) (FP32, [rows][co]) ->
 // parameter gradients, and gin = dL/d(input) ([rows][ci]) when gin != NULL.
 int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, const float* gout,
-                  float* gin, int n, cudaStream_t st) {
+                  float* gin, int n, cudaStream_t st, float* gw = nullptr,
+                  const bf16* w = nullptr) {
+    float* const dw = gw ? gw : u->grads + c.woff;  // weight gradient [co][9 ci]
     const int H = u->H(c.level), W = u->W(c.level);
     const int rows = n * H * W;
     NN_CUDA(u, gf::nn::relu_bwd(gout, out, (long long)rows * c.co, 1, u->dz, u->dzb, st));
@@ -444,7 +473,7 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
     t.B = u->dzb;
     t.ldb = c.co;
     t.tb = 0;
-    t.C = u->grads + c.woff;
+    t.C = dw;
     t.ldc = 9 * c.ci;
     const bool implicit = u->gemm_mode >= 1 && gf::nn::tc_gemm_mn_supported(t);
     if (!implicit) {
@@ -465,12 +494,12 @@ int conv_backward(gf_unet* u, const Conv& c, const bf16* in, const bf16* out, co
         a.B = u->col;
         a.ldb = 9 * c.ci;
         a.tb = 0;
-        a.C = u->grads + c.woff;
+        a.C = dw;
         a.ldc = 9 * c.ci;
         rc = run_gemm(u, a, true, st);
     }
     if (rc || !gin) return rc;
-    NN_CUDA(u, gf::nn::flip_transpose(u->wb + c.woff, c.co, c.ci, u->wt, st));
+    NN_CUDA(u, gf::nn::flip_transpose(w ? w : u->wb + c.woff, c.co, c.ci, u->wt, st));
     gf::nn::GemmArgs b;
     b.M = rows;
     b.N = c.ci;
@@ -549,6 +578,15 @@ int loss_and_grad(gf_unet* u, int n, const float* x, const float* t, const float
         const bf16* in_a = l > 0 ? u->pool[l] : u->x0;
         if ((rc = conv_backward(u, u->enc(l, 1), u->ea[l], u->eb[l], cur, other, n, st))) return rc;
         std::swap(cur, other);
+        if (l == 0 && u->cin_p != d.cin) {
+            const Conv& c0 = u->enc(0, 0);
+            if ((rc = conv_backward(u, u->enc0p, in_a, u->ea[0], cur, nullptr, n, st, u->gw0p,
+                                    u->w0p)))
+                return rc;
+            NN_CUDA(u, gf::nn::unpad_channels(u->gw0p, 9LL * c0.co, u->cin_p, d.cin,
+                                              u->grads + c0.woff, st));
+            break;
+        }
         if ((rc = conv_backward(u, u->enc(l, 0), in_a, u->ea[l], cur, l > 0 ? other : nullptr, n,
                                 st)))
             return rc;
@@ -617,6 +655,15 @@ const char* gf_unet_last_error(const gf_unet* net) {
     return net ? net->err : gf_last_error(nullptr);
 }
 
+// The padded BF16 copy of the first layer's weights (see cin_p), from the BF16 weights.
+int refresh_padded_weights(gf_unet* u, cudaStream_t st) {
+    if (u->cin_p == u->d.cin) return GF_OK;
+    const Conv& c0 = u->enc(0, 0);
+    NN_CUDA(u, gf::nn::pad_channels_bf16(u->wb + c0.woff, 9LL * c0.co, u->d.cin, u->cin_p,
+                                         u->w0p, st));
+    return GF_OK;
+}
+
 int gf_unet_set_params(gf_unet* u, const float* params, void* stream) {
     if (!u || !params) return fail(u, GF_EINVAL, "gf_unet_set_params: NULL argument");
     DeviceGuard g(u->device);
@@ -627,6 +674,7 @@ int gf_unet_set_params(gf_unet* u, const float* params, void* stream) {
         cudaMemsetAsync(u->adam_v, 0, bytes, st) != cudaSuccess)
         return fail(u, GF_ECUDA, "gf_unet_set_params: copy failed");
     NN_CUDA(u, gf::nn::to_bf16(u->params, u->np, u->wb, st));
+    if (int rc = refresh_padded_weights(u, st)) return rc;
     u->step = 0;
     u->have_grad = false;
     return GF_OK;
@@ -681,7 +729,7 @@ int gf_unet_adam_step(gf_unet* u, float lr, float beta1, float beta2, float eps,
     const float c2 = (float)(1.0 - pow((double)beta2, (double)u->step));
     NN_CUDA(u, gf::nn::adam(u->params, u->grads, u->adam_m, u->adam_v, u->np, lr, beta1, beta2,
                             eps, c1, c2, u->wb, (cudaStream_t)stream));
-    return GF_OK;
+    return refresh_padded_weights(u, (cudaStream_t)stream);
 }
 
 long long gf_unet_kernel_launches(const gf_unet* u) { return u ? u->launches : 0; }

@@ -48,7 +48,7 @@ def main(argv=None):
     ap.add_argument("--val", type=int, default=200)
     ap.add_argument("--eval", type=int, default=100)
     ap.add_argument("--iters", type=int, default=50)
-    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=100000)
