@@ -72,7 +72,7 @@ def parse_args():
     ap.add_argument("--gemm", type=int, default=1, choices=[0, 1, 2],
                     help="U-Net workload: 1 = tcgen05 with TMA operand loads, 2 = tcgen05 with "
                          "thread-staged operands, 0 = explicit im2col and mma.sync GEMMs")
-    ap.add_argument("--fwi-iters", type=int, default=3,
+    ap.add_argument("--fwi-iters", type=int, default=10,
                     help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
     return ap.parse_args()
 

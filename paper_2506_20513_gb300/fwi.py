@@ -61,7 +61,8 @@ class FWIConfig:
 @dataclass
 class FWIHistory:
     misfit: list = field(default_factory=list)        # J at the start of each iteration
-    evaluations: list = field(default_factory=list)   # misfit evaluations per iteration
+    evaluations: list = field(default_factory=list)   # FDTD evaluations per iteration
+                                                      # (misfit-only or misfit + gradient)
     seconds: list = field(default_factory=list)       # wall time per iteration (synchronised)
     band: list = field(default_factory=list)
     learned: list = field(default_factory=list)       # True where the learned update was kept
@@ -191,9 +192,16 @@ class FWI:
                     d_l = torch.cat([(de * self.mask).reshape(-1).double(),
                                      (ds * self.mask / c.sigma_ref).reshape(-1).double()])
                     J_c = float("inf")
-                    for scale in c.learned_scales:
+                    g_net = None
+                    for si, scale in enumerate(c.learned_scales):
                         e_c, s_c = self._split((x + scale * d_l).float())
-                        J_c = self._misfit(e_c, s_c, wav, obs)
+                        if si == 0:
+                            # the full-size update with its gradient, reused when it is kept
+                            J_c, g_net, ge_net, gs_net = self.gradient(e_c, s_c, wav, obs,
+                                                                       raw=True)
+                        else:
+                            J_c = self._misfit(e_c, s_c, wav, obs)
+                            g_net = None
                         tries += 1
                         if J_c < J:
                             break
@@ -229,9 +237,20 @@ class FWI:
                         if peak > 0:
                             alpha = c.first_step * float(x[:n].max()) / peak
                     accepted = False
-                    for _ in range(c.backtracks):
+                    for bt in range(c.backtracks):
                         eps, sig = self._split((x + alpha * d).float())
-                        J_new = self._misfit(eps, sig, wav, obs)
+                        if bt == 0 and not first:
+                            # an L-BFGS step is usually accepted at alpha = 1: evaluate the first
+                            # trial with its gradient (the same J as the misfit-only forward)
+                            # and reuse both when Armijo holds; backtracking evaluates misfits
+                            if learned:
+                                J_new, g_try, ge_try, gs_try = self.gradient(eps, sig, wav, obs,
+                                                                             raw=True)
+                            else:
+                                J_new, g_try = self.gradient(eps, sig, wav, obs)
+                        else:
+                            J_new = self._misfit(eps, sig, wav, obs)
+                            g_try = None
                         tries += 1
                         if J_new <= J + c.armijo * alpha * slope:
                             accepted = True
@@ -243,10 +262,18 @@ class FWI:
                         break
                 # the accepted model (projected onto the physical ranges), then its gradient
                 x_new = torch.cat([eps.reshape(-1).double(), (sig.reshape(-1) / c.sigma_ref).double()])
-                if learned:
-                    J_next, g_new, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+                if kept and g_net is not None:
+                    J_next, g_new, ge, gs = J_c, g_net, ge_net, gs_net
+                elif not kept and g_try is not None:
+                    J_next, g_new = J_new, g_try
+                    if learned:
+                        ge, gs = ge_try, gs_try
                 else:
-                    J_next, g_new = self.gradient(eps, sig, wav, obs)
+                    if learned:
+                        J_next, g_new, ge, gs = self.gradient(eps, sig, wav, obs, raw=True)
+                    else:
+                        J_next, g_new = self.gradient(eps, sig, wav, obs)
+                    tries += 1
                 g_new = g_new.double()
                 s_k, y_k = x_new - x, g_new - g
                 if float(torch.dot(s_k, y_k)) > 1e-12 * float(torch.dot(s_k, s_k)) ** 0.5:
@@ -256,7 +283,7 @@ class FWI:
                         S.pop(0)
                         Y.pop(0)
                 torch.cuda.synchronize(dev)
-                self._record(hist, logf, f0, it, J, tries + 1, time.perf_counter() - t0, kept)
+                self._record(hist, logf, f0, it, J, tries, time.perf_counter() - t0, kept)
                 x, g, J, first = x_new, g_new, J_next, False
                 if checkpoint and checkpoint_every > 0 and (it + 1) % checkpoint_every == 0:
                     state = dict(band_index=bi, iteration=it + 1, x=x.cpu(), g=g.cpu(), J=J,
