@@ -29,7 +29,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Offsets (bytes) of the workspace regions.
 struct Layout {
-    size_t status, partial, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt, seg, total;
+    size_t status, partial, coef, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt, seg,
+        total;
 };
 
 }  // namespace
@@ -37,7 +38,9 @@ struct Layout {
 struct gf_ctx {
     gf_grid_desc g;
     int nshots, nsrc, nrec, device;
-    long long N;
+    long long N;              // nx * ny (caller arrays)
+    int pitch;                // row pitch of the internal planes (gf::row_pitch)
+    long long Np;             // pitch * ny
     float* d_prof = nullptr;  // [12][max(nx, ny)] profiles (x: 6 arrays, y: 6 arrays)
     int* d_src = nullptr;     // [nshots][nsrc]
     int* d_rec = nullptr;     // [nshots][nrec]
@@ -46,16 +49,13 @@ struct gf_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
-    int tile_w = 50, tile_h = 50, K = 7, variant = 0;
+    int tile_w = 48, tile_h = 50, K = 7, variant = 0;
     int store_mode = GF_STORE_FULL, ckpt_k = 0;
     const float* last_wavelet = nullptr;  // wavelet of the stored forward (recomputation)
     std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
     int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
     int* d_tile_rec_idx = nullptr;
     int tile_rec_max = 0;           // longest per (shot, tile) list of the current tiling
-    int* d_march_rec_off = nullptr;  // the same for the warp-march strips x chunks
-    int* d_march_rec_idx = nullptr;
-    int march_h = 64;                // rows per warp-march chunk
     long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
     long long launches = 0;
@@ -197,11 +197,12 @@ int num_checkpoints(const gf_ctx* c) { return (c->g.nt + c->ckpt_k - 1) / c->ckp
 
 Layout layout_of(const gf_ctx* c, bool forward_only) {
     Layout L{};
-    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
     const size_t tr = sizeof(float) * (size_t)c->nshots * c->g.nt * c->nrec;
     size_t o = 0;
     L.status = o; o = align_up(o + sizeof(int));
     L.partial = o; o = align_up(o + sizeof(double) * kMisfitBlocks);
+    L.coef = o; o = align_up(o + 2 * sizeof(float) * (size_t)c->Np);
     L.stA = o; o = align_up(o + gf::kNumFields * field);
     L.stB = o; o = align_up(o + gf::kNumFields * field);
     L.illum = o; o = align_up(o + field);
@@ -255,13 +256,15 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     gf::TileParams p{};
     p.nx = c->g.nx;
     p.ny = c->g.ny;
+    p.pitch = c->pitch;
     p.npml = c->g.npml;
     p.nt = c->g.nt;
     p.nshots = c->nshots;
     p.nsrc = c->nsrc;
     p.nrec = c->nrec;
-    p.N = c->N;
-    p.dt_eps0 = (float)(c->g.dt / kEps0);
+    p.Np = c->Np;
+    p.ca = (const float*)(c->ws + L.coef);
+    p.cb = p.ca + c->Np;
     p.ch = (float)(c->g.dt / kMu0);
     p.src_scale = (float)(1.0 / (c->g.dx * c->g.dy));
     p.geps = (float)(kEps0 / c->g.dt);
@@ -278,10 +281,23 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.ntiles = p.tiles_x * ((c->g.ny + c->tile_h - 1) / c->tile_h);
     p.tile_rec_off = c->d_tile_rec_off;
     p.tile_rec_idx = c->d_tile_rec_idx;
+    p.rec_max = c->tile_rec_max;
     p.hist_stride = c->g.nt;
     p.hist_slot0 = 0;
-    p.rec_staged = (long long)c->tile_rec_max * (c->K + 1) <= gf::kRecStage;
     return p;
+}
+
+// Model check and the pitched Ca / Cb planes the tile kernels read.
+int prepare_model(gf_ctx* c, const Layout& L, const float* eps_r, const float* sigma,
+                  cudaStream_t st) {
+    float* ca = (float*)(c->ws + L.coef);
+    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
+                return gf::launch_prepare_model(eps_r, sigma, c->g.nx, c->g.ny, c->pitch,
+                                                (float)(c->g.dt / kEps0), ca, ca + c->Np,
+                                                (int*)(c->ws + L.status), st);
+            }),
+            "prepare_model");
+    return GF_OK;
 }
 
 
@@ -289,27 +305,13 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
 // between buf[cur] and buf[cur ^ 1]; returns with cur pointing at the final state.
 int forward_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
                   int n_end, cudaStream_t st) {
-    gf::TileParams q = p;
-    int chunks = 1;
-    if (c->variant == 2) {  // warp-march geometry: 64-column strips, chunks of march_h rows
-        q.halo = c->K;
-        q.tile_w = gf::max_tile_extent() - 2 * c->K;
-        q.tile_h = c->march_h;
-        q.tiles_x = (c->g.nx + q.tile_w - 1) / q.tile_w;
-        chunks = (c->g.ny + q.tile_h - 1) / q.tile_h;
-        q.ntiles = q.tiles_x * chunks;
-        q.tile_rec_off = c->d_march_rec_off;
-        q.tile_rec_idx = c->d_march_rec_idx;
-    }
     for (int n0 = n_begin; n0 < n_end; n0 += c->K) {
-        q.n0 = n0;
-        q.K = std::min(c->K, n_end - n0);
-        q.st_in = buf[cur];
-        q.st_out = buf[cur ^ 1];
-        if (c->variant == 2 && !q.illum)
-            GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_march(q, chunks, st); }), "fwd_march");
-        else
-            GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(q, c->variant == 2 ? 0 : c->variant, st); }), "fwd_tile");
+        p.n0 = n0;
+        p.K = std::min(c->K, n_end - n0);
+        p.kl = gf::left_halo(c->K);
+        p.st_in = buf[cur];
+        p.st_out = buf[cur ^ 1];
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
         cur ^= 1;
     }
     return GF_OK;
@@ -322,9 +324,10 @@ int adjoint_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, i
         const int k = std::min(c->K, n1 - n_begin + 1);
         p.n0 = n1 - k + 1;
         p.K = k;
+        p.kl = gf::left_halo(c->K);
         p.st_in = buf[cur];
         p.st_out = buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant == 2 ? 0 : c->variant, st); }), "adj_tile");
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
         cur ^= 1;
     }
     return GF_OK;
@@ -337,18 +340,17 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     if (rc) return rc;
     const Layout L = layout_of(c, !store);
     gf::TileParams p = base_params(c, L);
-    p.eps_r = eps_r;
-    p.sigma = sigma;
     p.wavelet = wavelet;
     p.traces = traces ? traces : (float*)(c->ws + L.traces);
     const bool ckpt = store && c->store_mode == GF_STORE_CHECKPOINT;
     p.hist = store && !ckpt ? (float*)(c->ws + L.hist) : nullptr;
     p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
-    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
     float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
     GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear state");
     if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, state / gf::kNumFields, st), "clear illumination");
-    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_check_model(eps_r, sigma, c->N, p.status, st); }), "check_model");
+    rc = prepare_model(c, L, eps_r, sigma, st);
+    if (rc) return rc;
     int cur = 0;
     if (ckpt) {
         // the state at every k-th step is saved before the segment that starts there
@@ -365,7 +367,7 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         if (rc) return rc;
     }
     if (illum)
-        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.illum, c->nshots, c->N, illum, p.status, st); }), "sum illum");
+        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.illum, c->nshots, c->g.nx, c->g.ny, c->pitch, illum, p.status, st); }), "sum illum");
     c->have_forward = store;
     c->last_wavelet = wavelet;
     return GF_OK;
@@ -375,15 +377,16 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
                 float* g_eps_r, float* g_sigma, cudaStream_t st) {
     const Layout L = layout_of(c, false);
     gf::TileParams p = base_params(c, L);
-    p.eps_r = eps_r;
-    p.sigma = sigma;
     p.resid = resid;
     p.grad = (float*)(c->ws + L.grad);
-    const size_t field = sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    const size_t plane = sizeof(float) * (size_t)c->Np;
+    const size_t field = plane * (size_t)c->nshots;
     const size_t state = gf::kNumFields * field;
     float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
     GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear adjoint state");
     GF_CUDA(c, cudaMemsetAsync(p.grad, 0, 2 * field, st), "clear gradients");
+    int rc0 = prepare_model(c, L, eps_r, sigma, st);
+    if (rc0) return rc0;
     int cur = 0;
     if (c->store_mode == GF_STORE_CHECKPOINT) {
         // segments in reverse: restore the checkpoint, recompute the segment's Ez into the
@@ -404,8 +407,7 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
             GF_CUDA(c, cudaMemcpyAsync(fw_buf[0], ck, state, cudaMemcpyDeviceToDevice, st),
                     "restore checkpoint");
             // Ez plane of every shot -> slot 0 of its segment
-            GF_CUDA(c, cudaMemcpy2DAsync(seg, (size_t)(c->ckpt_k + 1) * c->N * sizeof(float), ck,
-                                         c->N * sizeof(float), c->N * sizeof(float),
+            GF_CUDA(c, cudaMemcpy2DAsync(seg, (size_t)(c->ckpt_k + 1) * plane, ck, plane, plane,
                                          (size_t)c->nshots, cudaMemcpyDeviceToDevice, st),
                     "segment start");
             q.hist_slot0 = n_begin - 1;
@@ -422,11 +424,11 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         if (rc) return rc;
     }
     if (g_eps_r)
-        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.grad, c->nshots, c->N, g_eps_r, p.status, st); }), "sum g_eps_r");
+        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.grad, c->nshots, c->g.nx, c->g.ny, c->pitch, g_eps_r, p.status, st); }), "sum g_eps_r");
     if (g_sigma)
         GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
-                    return gf::launch_sum_shots(p.grad + (size_t)c->nshots * c->N, c->nshots, c->N,
-                                                g_sigma, p.status, st);
+                    return gf::launch_sum_shots(p.grad + (size_t)c->nshots * c->Np, c->nshots,
+                                                c->g.nx, c->g.ny, c->pitch, g_sigma, p.status, st);
                 }),
                 "sum g_sigma");
     return GF_OK;
@@ -454,9 +456,6 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** 
         }
     std::vector<int> off(lists.size() + 1, 0), idx;
     for (size_t k = 0; k < lists.size(); ++k) {
-        // the tile kernels address a thread's entries with 16-bit offsets
-        if (lists[k].size() > 65535)
-            return fail(c, GF_EINVAL, "more than 65535 receivers in one staged tile window");
         const int* cells = c->h_rec.data() + (k / nt_) * c->nrec;
         std::stable_sort(lists[k].begin(), lists[k].end(),
                          [&](int a, int b) { return cells[a] / nx < cells[b] / nx; });
@@ -488,33 +487,34 @@ int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** 
     return GF_OK;
 }
 
-// Lists for the tile kernels and, for the march variant, for its strips x chunks.
-int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K, int variant) {
-    int rc = build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx,
-                                  &c->tile_rec_max);
-    if (rc == GF_OK && variant == 2)
-        rc = build_receiver_lists(c, gf::max_tile_extent() - 2 * K, c->march_h, K,
-                                  &c->d_march_rec_off, &c->d_march_rec_idx, nullptr);
-    return rc;
+int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K) {
+    return build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx,
+                                &c->tile_rec_max);
 }
 
+// A tiling fits a variant's staged window: left halo left_halo(K) + tile_w + K columns within
+// the window width, tile_h + 2K rows within its height; tile_w even (the window starts on an
+// even column, so that column pairs are 8-byte aligned).
 int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
-    if (variant < 0 || variant > gf::num_tile_variants())
+    if (variant < 0 || variant >= gf::num_tile_variants())
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
-    const int E = gf::max_tile_extent(), Eh = gf::max_tile_height(variant == 2 ? 0 : variant);
-    if (K < 1 || tw < 1 || th < 1 || tw + 2 * K > E || th + 2 * K > Eh)
+    const int E = gf::max_tile_extent(), Eh = gf::max_tile_height(variant);
+    if (K < 1 || K > gf::kMaxK || tw < 2 || (tw & 1) || th < 1 ||
+        gf::left_halo(K) + tw + K > E || th + 2 * K > Eh)
         return fail(c, GF_EINVAL,
-                    "tile %dx%d with %d steps per launch: need tile + 2*steps <= %d wide and "
-                    "<= %d high",
-                    tw, th, K, E, Eh);
-    if (variant == 2 && K > gf::march_max_steps())
-        return fail(c, GF_EINVAL, "the warp-march forward takes at most %d steps per launch",
-                    gf::march_max_steps());
-    const int tv = variant == 2 ? 0 : variant;
-    if (gf::tile_smem_bytes(tv) > c->smem_optin)
+                    "tile %dx%d with %d steps per launch: need an even tile width with "
+                    "%d + width + steps <= %d and height + 2*steps <= %d (steps <= %d)",
+                    tw, th, K, gf::left_halo(K), E, Eh, gf::kMaxK);
+    if (gf::tile_smem_bytes(variant) > c->smem_optin)
         return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)",
-                    gf::tile_smem_bytes(tv), c->smem_optin);
+                    gf::tile_smem_bytes(variant), c->smem_optin);
     return GF_OK;
+}
+
+// Default tile of a variant for K steps per launch: the widest even tile and the tallest one.
+void default_tile(int variant, int K, int* tw, int* th) {
+    *tw = (gf::max_tile_extent() - gf::left_halo(K) - K) & ~1;
+    *th = gf::max_tile_height(variant) - 2 * K;
 }
 
 }  // namespace
@@ -585,6 +585,8 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->nrec = acq->nrec;
     c->device = device;
     c->N = (long long)g.nx * g.ny;
+    c->pitch = gf::row_pitch(g.nx);
+    c->Np = (long long)c->pitch * g.ny;
     c->h_rec = rec;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
@@ -613,15 +615,8 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     const size_t S = stride;
     c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
-    if (e == cudaSuccess) e = gf::configure_march_kernels((size_t)optin);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        create_fail("gf_create: CUDA setup failed: %s", cudaGetErrorString(e));
-        gf_destroy(c);
-        return GF_ECUDA;
-    }
     if (check_tiling(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK ||
-        build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK) {
+        build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
         create_fail("gf_create: %s", c->err);
         gf_destroy(c);
         return GF_EINVAL;
@@ -641,8 +636,6 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_rec);
     cudaFree(c->d_tile_rec_off);
     cudaFree(c->d_tile_rec_idx);
-    cudaFree(c->d_march_rec_off);
-    cudaFree(c->d_march_rec_idx);
     delete c;
 }
 
@@ -677,14 +670,15 @@ int gf_set_workspace(gf_ctx* c, void* ws, size_t bytes) {
 int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     if (!c) return GF_EINVAL;
     ++c->generation;
-    const int E = gf::max_tile_extent();
-    const int Eh = gf::max_tile_height(c->variant == 2 ? 0 : c->variant);
     const int k = K > 0 ? K : c->K;
-    const int tw = tile_w > 0 ? tile_w : E - 2 * k, th = tile_h > 0 ? tile_h : Eh - 2 * k;
+    int tw, th;
+    default_tile(c->variant, k, &tw, &th);
+    if (tile_w > 0) tw = tile_w;
+    if (tile_h > 0) th = tile_h;
     int rc = check_tiling(c, tw, th, k, c->variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_all_receiver_lists(c, tw, th, k, c->variant);
+    rc = build_all_receiver_lists(c, tw, th, k);
     if (rc) return rc;
     c->tile_w = tw;
     c->tile_h = th;
@@ -715,16 +709,16 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
     ++c->generation;
-    if (variant < 0 || variant > gf::num_tile_variants())
+    if (variant < 0 || variant >= gf::num_tile_variants())
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
     // a tile taller than the variant's window is shrunk to the largest that fits
     int th = c->tile_h;
-    const int Eh = gf::max_tile_height(variant == 2 ? 0 : variant);
+    const int Eh = gf::max_tile_height(variant);
     if (th + 2 * c->K > Eh) th = Eh - 2 * c->K;
     int rc = check_tiling(c, c->tile_w, th, c->K, variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_all_receiver_lists(c, c->tile_w, th, c->K, variant);
+    rc = build_all_receiver_lists(c, c->tile_w, th, c->K);
     if (rc) return rc;
     c->tile_h = th;
     c->variant = variant;
@@ -916,13 +910,13 @@ int forward_prefix(gf_ctx* c, const float* eps_r, const float* sigma, const floa
     if (rc) return rc;
     const Layout L = layout_of(c, true);
     gf::TileParams p = base_params(c, L);
-    p.eps_r = eps_r;
-    p.sigma = sigma;
     p.wavelet = wavelet;
     p.traces = (float*)(c->ws + L.traces);
-    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->N;
+    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
     float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
     GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear state");
+    rc = prepare_model(c, L, eps_r, sigma, st);
+    if (rc) return rc;
     int cur = 0;
     return forward_steps(c, p, st_buf, cur, 0, std::min(nsteps, c->g.nt), st);
 }
@@ -983,9 +977,8 @@ int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     struct Cand { int variant, K; };
     std::vector<Cand> cands;
     for (int v = 0; v < 2; ++v)
-        for (int K : {3, 4, 5, 6, 7, 8, 10}) cands.push_back({v, K});
-    for (int K : {4, 6}) cands.push_back({2, K});
-    for (int K : {3, 4, 5, 6}) cands.push_back({3, K});
+        for (int K : {4, 5, 6, 7, 8, 10}) cands.push_back({v, K});
+    for (int K : {3, 4, 5, 6}) cands.push_back({2, K});
     const int steps = probe_steps > 0 ? probe_steps : 48;
     cudaEvent_t e0, e1;
     GF_CUDA(c, cudaEventCreate(&e0), "event");

@@ -1,5 +1,5 @@
-// gf_misc_kernels.cu -- small HBM-bound helpers: model validation, residual + L2 misfit
-// (Eq. objective), and the sum of per-shot gradients.
+// gf_misc_kernels.cu -- small HBM-bound helpers: model validation and update coefficients,
+// residual + L2 misfit (Eq. objective), and the sum of per-shot gradients.
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -7,14 +7,35 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// eps_r >= 1, sigma >= 0 and both finite (the physical ranges the paper clamps to, Sec. 3.1).
-__global__ void check_model_kernel(const float* __restrict__ eps_r, const float* __restrict__ sigma,
-                                   long long N, int* status) {
+// eps_r >= 1, sigma >= 0 and both finite (the physical ranges the paper clamps to, Sec. 3.1),
+// and the update coefficients of every cell of the pitched [ny][pitch] planes:
+// Ca = (1 - a)/(1 + a), Cb = (dt/eps)/(1 + a), a = sigma dt / (2 eps), EB/EA and 1/EA of the
+// Sec. 3.2 coefficient listing.  The PEC ring (outermost cells), perfect conductors
+// (sigma > 100 S/m, the listing's rule) and the row padding get Ca = Cb = 0.
+__global__ void prepare_model_kernel(const float* __restrict__ eps_r,
+                                     const float* __restrict__ sigma, int nx, int ny, int pitch,
+                                     float dt_eps0, float* __restrict__ ca, float* __restrict__ cb,
+                                     int* status) {
     int bad = 0;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
-         c += (long long)gridDim.x * blockDim.x) {
-        const float e = eps_r[c], s = sigma[c];
-        bad |= !(e >= 1.0f && s >= 0.0f && isfinite(e) && isfinite(s));
+    const long long total = (long long)pitch * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(k / pitch), x = (int)(k - (long long)y * pitch);
+        float a_ = 0.f, b_ = 0.f;
+        if (x < nx) {
+            const float e = eps_r[(long long)y * nx + x], s = sigma[(long long)y * nx + x];
+            bad |= !(e >= 1.0f && s >= 0.0f && isfinite(e) && isfinite(s));
+            const bool ring = x == 0 || y == 0 || x == nx - 1 || y == ny - 1;
+            if (!ring && !(s > 100.0f)) {
+                const float dte = dt_eps0 / e;
+                const float a = 0.5f * s * dte;
+                const float inv = 1.0f / (1.0f + a);
+                a_ = (1.0f - a) * inv;
+                b_ = dte * inv;
+            }
+        }
+        ca[k] = a_;
+        cb[k] = b_;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kStatusBadModel);
 }
@@ -57,14 +78,17 @@ __global__ void finish_misfit_kernel(const double* partial, int nblocks, double*
     if (threadIdx.x == 0) *misfit = red[0];
 }
 
-// out[c] = sum_s per_shot[s][c] in shot order (deterministic), 4 cells per thread.
-__global__ void sum_shots_kernel(const float* __restrict__ per_shot, int nshots, long long N,
-                                 float* __restrict__ out, int* status) {
+// out[y * nx + x] = sum_s per_shot[s][y * pitch + x] in shot order (deterministic).
+__global__ void sum_shots_kernel(const float* __restrict__ per_shot, int nshots, int nx, int ny,
+                                 int pitch, float* __restrict__ out, int* status) {
     int bad = 0;
+    const long long N = (long long)nx * ny, Np = (long long)pitch * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(c / nx), x = (int)(c - (long long)y * nx);
+        const long long m = (long long)y * pitch + x;
         float acc = 0.f;
-        for (int s = 0; s < nshots; ++s) acc += per_shot[(long long)s * N + c];
+        for (int s = 0; s < nshots; ++s) acc += per_shot[(long long)s * Np + m];
         out[c] = acc;
         bad |= !isfinite(acc);
     }
@@ -80,9 +104,11 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
-cudaError_t launch_check_model(const float* eps_r, const float* sigma, long long N, int* status,
-                               cudaStream_t st) {
-    check_model_kernel<<<grid_for(N, 256), 256, 0, st>>>(eps_r, sigma, N, status);
+cudaError_t launch_prepare_model(const float* eps_r, const float* sigma, int nx, int ny,
+                                 int pitch, float dt_eps0, float* ca, float* cb, int* status,
+                                 cudaStream_t st) {
+    prepare_model_kernel<<<grid_for((long long)pitch * ny, 256), 256, 0, st>>>(
+        eps_r, sigma, nx, ny, pitch, dt_eps0, ca, cb, status);
     return cudaGetLastError();
 }
 
@@ -100,9 +126,10 @@ cudaError_t launch_finish_misfit(const double* partial, int nblocks, double* mis
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum_shots(const float* per_shot, int nshots, long long N, float* out,
-                             int* status, cudaStream_t st) {
-    sum_shots_kernel<<<grid_for(N, 256), 256, 0, st>>>(per_shot, nshots, N, out, status);
+cudaError_t launch_sum_shots(const float* per_shot, int nshots, int nx, int ny, int pitch,
+                             float* out, int* status, cudaStream_t st) {
+    sum_shots_kernel<<<grid_for((long long)nx * ny, 256), 256, 0, st>>>(per_shot, nshots, nx, ny,
+                                                                       pitch, out, status);
     return cudaGetLastError();
 }
 

@@ -6,8 +6,8 @@
 // under a hard memory budget set by their host, and real-time loops that must never enter
 // the allocator.  This entry point serves them.  It
 // keeps everything the forward tile kernels need besides the caller's inputs and outputs --
-// the two time-stepping state buffers, the CPML profiles, the geometry and the per-tile
-// receiver lists -- in one file-scope device array of fixed size (kScratchBytes), which every
+// the two time-stepping state buffers, the update coefficients, the CPML profiles, the
+// geometry and the per-tile receiver lists -- in one file-scope device array of fixed size (kScratchBytes), which every
 // GPU that loads this library holds until the process exits.  It never calls cudaMalloc,
 // cudaFree or any allocating routine.
 //
@@ -190,7 +190,8 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     }
 
     // scratch layout (256-byte aligned regions)
-    const long long N = (long long)g.nx * g.ny;
+    const int pitch = gf::row_pitch(g.nx);
+    const long long Np = (long long)pitch * g.ny;
     const int S = g.nx > g.ny ? g.nx : g.ny;
     const int tiles_x = (g.nx + kTileW - 1) / kTileW;
     const int ntiles = tiles_x * ((g.ny + kTileH - 1) / kTileH);
@@ -198,6 +199,8 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     // a receiver lies in at most 3 x 3 windows when tile >= 2K
     const long long max_entries = 9 * nrec_all;
     size_t o = 0;
+    const size_t o_status = o; o = up256(o + sizeof(int));
+    const size_t o_coef = o; o = up256(o + sizeof(float) * 2 * (size_t)Np);
     const size_t o_prof = o; o = up256(o + sizeof(float) * 12 * (size_t)S);
     const size_t o_srcij = o; o = up256(o + sizeof(int) * 2 * (size_t)nsrc_all);
     const size_t o_recij = o; o = up256(o + sizeof(int) * 2 * (size_t)nrec_all);
@@ -206,7 +209,7 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     const size_t o_cnt = o; o = up256(o + sizeof(int) * (size_t)nwin);
     const size_t o_off = o; o = up256(o + sizeof(int) * (size_t)(nwin + 1));
     const size_t o_idx = o; o = up256(o + sizeof(int) * (size_t)max_entries);
-    const size_t field = sizeof(float) * (size_t)acq->nshots * (size_t)N;
+    const size_t field = sizeof(float) * (size_t)acq->nshots * (size_t)Np;
     const size_t o_stA = o; o = up256(o + gf::kNumFields * field);
     const size_t o_stB = o; o = up256(o + gf::kNumFields * field);
     if (o > kScratchBytes)
@@ -234,14 +237,16 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     gf::host_axis_profiles(g, g.ny, g.dy, g_prof_host + 6 * (size_t)S, S);
     cudaError_t e = cudaMemcpyAsync(base + o_prof, g_prof_host, sizeof(float) * 12 * (size_t)S,
                                     cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host staging is reused next call
-    lock.unlock();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + o_srcij, acq->src_ij, sizeof(int) * 2 * (size_t)nsrc_all,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + o_recij, acq->rec_ij, sizeof(int) * 2 * (size_t)nrec_all,
                             cudaMemcpyHostToDevice, st);
+    // the host staging is reused by the next call, and the caller's geometry arrays are only
+    // read during this call: every host read completes here
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    lock.unlock();
     int* src = (int*)(base + o_src);
     int* rec = (int*)(base + o_rec);
     int* cnt = (int*)(base + o_cnt);
@@ -260,8 +265,14 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
                                                   kTileH, kSteps, tiles_x, ntiles, off, idx);
         e = cudaGetLastError();
     }
-    // the state starts from zero on every call (the array keeps the previous call's contents)
+    // the state starts from zero on every call (the array keeps the previous call's contents);
+    // the update coefficients of this call's model fill the pitched planes
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_stA, 0, gf::kNumFields * field, st);
+    float* ca = (float*)(base + o_coef);
+    if (e == cudaSuccess)
+        e = gf::launch_prepare_model(eps_r, sigma, g.nx, g.ny, pitch,
+                                     (float)(g.dt / 8.8541878128e-12), ca, ca + Np,
+                                     (int*)(base + o_status), st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(GF_ECUDA, "gf_forward_model_noalloc: %s", cudaGetErrorString(e));
@@ -270,13 +281,15 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     gf::TileParams p{};
     p.nx = g.nx;
     p.ny = g.ny;
+    p.pitch = pitch;
     p.npml = g.npml;
     p.nt = g.nt;
     p.nshots = acq->nshots;
     p.nsrc = acq->nsrc;
     p.nrec = acq->nrec;
-    p.N = N;
-    p.dt_eps0 = (float)(g.dt / 8.8541878128e-12);
+    p.Np = Np;
+    p.ca = ca;
+    p.cb = ca + Np;
     p.ch = (float)(g.dt / 1.25663706212e-6);
     p.src_scale = (float)(1.0 / (g.dx * g.dy));
     p.geps = (float)(8.8541878128e-12 / g.dt);
@@ -285,8 +298,6 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     float* P = (float*)(base + o_prof);
     p.px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     p.py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
-    p.eps_r = eps_r;
-    p.sigma = sigma;
     p.wavelet = wavelet;
     p.src_cell = src;
     p.rec_cell = rec;
@@ -299,6 +310,9 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     p.ntiles = ntiles;
     p.tile_rec_off = off;
     p.tile_rec_idx = idx;
+    p.rec_max = acq->nrec;  // no window holds more than a shot's receivers
+    p.status = (int*)(base + o_status);
+    p.kl = gf::left_halo(kSteps);
     float* buf[2] = {(float*)(base + o_stA), (float*)(base + o_stB)};
     int cur = 0;
     for (int n0 = 0; n0 < g.nt; n0 += kSteps) {

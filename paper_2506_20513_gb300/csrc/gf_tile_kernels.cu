@@ -1,30 +1,35 @@
 // gf_tile_kernels.cu -- temporally blocked 2-D TM FDTD forward and adjoint kernels (sm_103a).
 //
-// Tiling.  One CTA (64 x BY threads) owns an interior tile of tile_w x tile_h cells of one
-// shot and advances it K time steps per launch.  The tile plus a K-cell halo (at most 64 x 64
-// cells) stays on chip for the whole launch: thread (tx, ty) owns column tx and the RY
-// consecutive rows RY*ty .. RY*ty + RY - 1 (RY * BY = 64, or 32 for the 512-thread 64 x 32
-// variant), keeping their field values in registers.  Shared memory carries what neighbours
-// exchange: two x-neighbour planes (Ez for the H update and Hy for the E update; the
-// transposed difference weights S and T in the adjoint) and one row per thread segment for
-// the y-neighbour across segments; besides, per owned cell, the CPML memory variables of strip
-// cells and the update coefficients Ca, Cb (and in the adjoint the carried Ez^{n+1} and the
-// two gradient accumulators), which would not fit the 64-register budget of a 1024-thread
-// CTA, plus the launch's source samples and, in the adjoint, the tile's receiver positions
-// and residual samples.  Each time step the valid
-// region shrinks by one cell on every side (an H update reads Ez at +1, an E update reads H
-// at -1), so after K steps exactly the interior is valid; it is written to the other
-// ping-pong state buffer.  Halo cells are recomputed redundantly by neighbouring CTAs from
-// identical inputs.  Sources and adjoint sources are injected into every staged copy of their
-// cell; receivers and the wavefield history are written only by the CTA owning the cell.
-// Tiles whose staged window misses every CPML strip run a specialised body without the
-// memory variables (a CTA-uniform branch).
+// Tiling.  One CTA owns an interior tile of tile_w x tile_h cells of one shot and advances it
+// K time steps per launch on a staged window of 64 x WY cells (the tile plus a halo of kl >= K
+// columns on the left, >= K on the right and K rows above and below).  The window lives in
+// registers: warp w owns the R rows w*R .. w*R + R - 1 of the window and lane l of every warp
+// owns the column pair (2l, 2l + 1), so one warp spans the window's width.  Consequences:
+//   * every global access of a thread is an 8-byte pair (state, wavefield store, update
+//     coefficients, gradients), every row of a warp one 256-byte segment;
+//   * x-neighbours come from the thread itself or from the next / previous lane by a warp
+//     shuffle: no shared memory and no barrier for the x differences;
+//   * y-neighbours come from the thread's own rows, except across warps: the top row of each
+//     warp (Ez, or the adjoint's S_y weights) and the bottom row (Hx, or T_y) are exchanged
+//     through shared memory, with two block barriers per time step.
+// Each time step the valid region shrinks by one cell on every side (an H update reads Ez at
+// +1, an E update reads H at -1; the window edges read their own values), so after K steps
+// exactly the interior is valid; it is written to the other ping-pong state buffer.  Halo
+// cells are recomputed redundantly by neighbouring CTAs from identical inputs.  Sources and
+// adjoint sources are injected into every staged copy of their cell; receivers and the
+// wavefield store are written only by the CTA owning the cell.
+//
+// CPML.  The convolutional PML memories live in shared memory (four window planes).  CTAs
+// whose live columns reach an x strip take the x-CPML form of the H and E updates in every
+// column (outside the strips its profile is a = 1/d, b = c = 0, which reduces it to the plain
+// update and keeps the memory at zero): a CTA-uniform branch, chosen once per launch.  Rows in
+// a y strip take the y-CPML form, a warp-uniform branch per row.
 //
 // Forward time step n (Algorithm 1, Sec. 3.3): record d^n = Ez^n at the receivers, update H
 // and the magnetic CPML memories from Ez^n, update Ez and the electric CPML memories from
 // H^{n+1/2} with Ez^{n+1} = Ca Ez^n + Cb Q (Eqs. 3-5 in the time-averaged loss form of the
-// Sec. 3.2 coefficient listing), inject the source into Q (Sec. 3.2 source listing), store
-// Ez^{n+1}.
+// Sec. 3.2 coefficient listing), inject the source (Sec. 3.2 source listing: Q -= w^n / (dx
+// dy), applied as Ez^{n+1} -= Cb w^n / (dx dy)), store Ez^{n+1}.
 //
 // Adjoint time step n (Algorithm 2): the exact transpose of the forward step, in reverse:
 // (A) lam = Cb * adj(Ez^{n+1}) accumulates the zero-lag gradients (Eqs. grad_eps and
@@ -32,586 +37,808 @@
 // the transposed E-step differences, and adj(Ez^n) starts as Ca adj(Ez^{n+1}); (B) adj(H)
 // receives the transposed differences of S and feeds the magnetic CPML memories, giving the
 // weights T; (C) adj(Ez^n) receives the transposed differences of T and the receiver residual
-// of step n.
+// of step n.  The stored Ez^n of the gradient is read through a shared-memory ring filled by
+// cp.async kRingLead steps ahead of its use; the ring also holds the previous step's Ez^{n+1}.
 #include "gf_internal.cuh"
 
 namespace gf {
 namespace {
 
-constexpr int BX = 64;        // threads along x = staged tile width
-constexpr int kMaxK = 31;     // tile + 2K <= 64 with tile >= 2
-// The staged tile height is EHM = RY * BY (64 for variants 0 and 1, 32 for variant 3); a
-// plane of the staged window holds PLANE = EHM * BX floats.
+constexpr int WX = 64;               // staged window width: one warp, two columns per lane
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRing = 5;             // adjoint: slots of the wavefield ring
+constexpr int kRingLead = 3;         // steps between a slot's cp.async and its use
 
-__host__ __device__ constexpr size_t smem_floats(int ry, int by) {
-    return 11 * (size_t)(ry * by) * BX + 2 * by * BX + 6 * (ry * by) + 6 * BX +
-           (kMaxK + 1) * kMaxSrc + kRecStage;
-}
-
-// Shared-memory carve-up (floats).
-struct Smem {
-    float* xplane;   // [EHM][BX] x-neighbour exchange (Ez, or S in the adjoint)
-    float* xplane2;  // [EHM][BX] (Hy, or T in the adjoint)
-    float* rowA;     // [BY][BX] one row per thread segment (bottom Hx, or top S_y)
-    float* rowB;     // [BY][BX] (adjoint: bottom T_y)
-    float* psi;      // [4][EHM][BX] CPML memories: Ex, Ey, Hx, Hy
-    float* yprof;    // [6][EHM] row profiles aE bE cE aH bH cH
-    float* xprof;    // [6][BX] column profiles aE bE cE aH bH cH
-    float* wsrc;     // [kMaxK + 1][kMaxSrc] scaled source samples of this launch
-    float* coef;     // [5][EHM][BX] adjoint: Ca, Cb, the carried Ez^{n+1} and the two
-                     // gradient accumulators of the owned cells (kept here rather than in
-                     // registers, which would spill)
-    float* rstage;   // [kRecStage] adjoint: residual samples of the launch [entry][step] from
-                     // the start, window positions lx | ly << 8 of the entries from the end
+// Shared-memory carve-up of a variant (offsets in floats; every region 16-byte aligned).
+template <int R, int NW>
+struct G {
+    static constexpr int WY = R * NW;                    // window height
+    static constexpr int NT = 32 * NW;                   // threads per CTA
+    static constexpr int PL = WY * 32;                   // float2 per window plane
+    static constexpr int oPsi = 0;                       // [4][WY][32] float2: Ex Ey Hx Hy
+    static constexpr int oTop = oPsi + 8 * PL;           // [NW][32] float2
+    static constexpr int oBot = oTop + 64 * NW;          // [NW][32] float2
+    static constexpr int oYp = oBot + 64 * NW;           // [WY][2] float4: E, H row profiles
+    static constexpr int oXp = oYp + 8 * WY;             // [6][32] float2: column profiles
+    static constexpr int oWs = oXp + 6 * WX;             // [kMaxK + 1][kMaxSrc] source samples
+    static constexpr int oSp = oWs + (kMaxK + 1) * kMaxSrc;  // [kMaxSrc] source positions
+    static constexpr int oRec = oSp + kMaxSrc;           // [kRecStage] staged receivers
+    static constexpr int oCoef = oRec + kRecStage;       // [WY][32] float4: Ca, Cb of the pair
+    static constexpr int oRing = oCoef + 4 * PL;         // adjoint: [kRing][WY][32] float2
+    static constexpr int fwd_floats = oRing;
+    static constexpr int adj_floats = oRing + kRing * 2 * PL;
 };
-
-template <int RY, int BY>
-__device__ __forceinline__ Smem carve(float* sm) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
-    Smem s;
-    s.xplane = sm;
-    s.xplane2 = s.xplane + PLANE;
-    s.rowA = s.xplane2 + PLANE;
-    s.rowB = s.rowA + BY * BX;
-    s.psi = s.rowB + BY * BX;
-    s.yprof = s.psi + 4 * PLANE;
-    s.xprof = s.yprof + 6 * EHM;
-    s.wsrc = s.xprof + 6 * BX;
-    s.coef = s.wsrc + (kMaxK + 1) * kMaxSrc;
-    s.rstage = s.coef + 5 * PLANE;
-    return s;
-}
-
-// Ca = (1 - a)/(1 + a), Cb = (dt/eps)/(1 + a), a = sigma dt / (2 eps): EB/EA and 1/EA of the
-// coefficient listing.  The PEC ring and perfect conductors (sigma > 100 S/m) get 0.
-__device__ __forceinline__ void coefficients(float er, float sg, float dt_eps0, bool fixed,
-                                             float& Ca, float& Cb) {
-    if (fixed || sg > 100.0f) {
-        Ca = 0.0f;
-        Cb = 0.0f;
-        return;
-    }
-    const float dte = dt_eps0 / er;
-    const float a = 0.5f * sg * dte;
-    const float inv = 1.0f / (1.0f + a);
-    Ca = (1.0f - a) * inv;
-    Cb = dte * inv;
-}
 
 __device__ __forceinline__ bool in_xstrip(int gx, const TileParams& p) {
-    return gx < p.npml || gx >= p.nx - p.npml - 1;
+    return p.npml > 0 && (gx < p.npml || gx >= p.nx - p.npml - 1);
 }
 __device__ __forceinline__ bool in_ystrip(int gy, const TileParams& p) {
-    return gy < p.npml || gy >= p.ny - p.npml - 1;
+    return p.npml > 0 && (gy < p.npml || gy >= p.ny - p.npml - 1);
 }
 
-// Per-thread geometry shared by both kernels.
-template <int RY>
-struct Cell {
-    int lx, ly0, gx, X0, Y0, EWe, EHe;
-    bool col_active;  // column inside the staged window and the grid
-    bool col_int;     // column inside this CTA's interior and the grid
-    bool xs;          // column inside an x CPML strip
-    bool tile_strip;  // the staged window touches a CPML strip (CTA-uniform)
-
-    __device__ __forceinline__ void init(const TileParams& p) {
-        lx = threadIdx.x;
-        ly0 = threadIdx.y * RY;
-        EWe = p.tile_w + 2 * p.K;
-        EHe = p.tile_h + 2 * p.K;
-        X0 = (blockIdx.x % p.tiles_x) * p.tile_w - p.K;
-        Y0 = (blockIdx.x / p.tiles_x) * p.tile_h - p.K;
-        gx = X0 + lx;
-        col_active = lx < EWe && gx >= 0 && gx < p.nx;
-        col_int = lx >= p.K && lx < p.K + p.tile_w && gx < p.nx;
-        xs = col_active && in_xstrip(gx, p);
-        // strips: x in [0, npml) U [nx - npml - 1, nx), same for y
-        const int xe = X0 + EWe - 1, ye = Y0 + EHe - 1;
-        tile_strip = X0 < p.npml || xe >= p.nx - p.npml - 1 || Y0 < p.npml ||
-                     ye >= p.ny - p.npml - 1;
-    }
+// Position of a thread in the staged window.
+template <int R>
+struct Pos {
+    int lane, warp, ly0;   // lane, warp, first window row of the warp
+    int X0, Y0, gx0;       // window origin (X0 even); global column of the lane's first column
+    bool lane_in;          // the lane's first column lies in the grid (the second one may be
+                           // the row padding when nx is odd: its coefficients are zero)
+    bool lane_int;         // the lane's columns are interior columns of the tile
+    bool tile_xs;          // the window's live columns reach an x CPML strip (CTA-uniform)
+    bool xs0, xs1;         // the lane's columns lie in an x strip (only set when tile_xs)
+    unsigned row_in;       // bit r: row ly0 + r lies in the grid
+    unsigned row_int;      // bit r: row ly0 + r is an interior row
+    unsigned ymask;        // bit r: row ly0 + r lies in a y CPML strip (warp-uniform)
+    bool ys;               // some row of the warp lies in a y strip: the warp takes the y-CPML
+                           // form in all its rows (warp-uniform)
 };
 
-// Row and column CPML profiles of the staged window (clamped to the grid).
-template <int EHM>
-__device__ __forceinline__ void stage_profiles(const Smem& s, const TileParams& p, int X0, int Y0,
-                                               int tid) {
-    if (tid < EHM) {
-        const int g = min(max(Y0 + tid, 0), p.ny - 1);
-        s.yprof[tid] = __ldg(p.py.aE + g);
-        s.yprof[EHM + tid] = __ldg(p.py.bE + g);
-        s.yprof[2 * EHM + tid] = __ldg(p.py.cE + g);
-        s.yprof[3 * EHM + tid] = __ldg(p.py.aH + g);
-        s.yprof[4 * EHM + tid] = __ldg(p.py.bH + g);
-        s.yprof[5 * EHM + tid] = __ldg(p.py.cH + g);
-    } else if (tid < EHM + BX) {
-        const int i = tid - EHM, g = min(max(X0 + i, 0), p.nx - 1);
-        s.xprof[i] = __ldg(p.px.aE + g);
-        s.xprof[BX + i] = __ldg(p.px.bE + g);
-        s.xprof[2 * BX + i] = __ldg(p.px.cE + g);
-        s.xprof[3 * BX + i] = __ldg(p.px.aH + g);
-        s.xprof[4 * BX + i] = __ldg(p.px.bH + g);
-        s.xprof[5 * BX + i] = __ldg(p.px.cH + g);
+template <int R>
+__device__ __forceinline__ Pos<R> position(const TileParams& p) {
+    Pos<R> w;
+    w.lane = threadIdx.x & 31;
+    w.warp = threadIdx.x >> 5;
+    w.ly0 = w.warp * R;
+    const int tx = blockIdx.x % p.tiles_x, ty = blockIdx.x / p.tiles_x;
+    w.X0 = tx * p.tile_w - p.kl;
+    w.Y0 = ty * p.tile_h - p.K;
+    w.gx0 = w.X0 + 2 * w.lane;
+    w.lane_in = w.gx0 >= 0 && w.gx0 < p.nx;
+    w.lane_int = 2 * w.lane >= p.kl && 2 * w.lane < p.kl + p.tile_w && w.gx0 < p.nx;
+    const int xa = tx * p.tile_w - p.K, xb = tx * p.tile_w + p.tile_w + p.K;  // live columns
+    w.tile_xs = p.npml > 0 && (xa < p.npml || xb - 1 >= p.nx - p.npml - 1);
+    w.xs0 = w.tile_xs && in_xstrip(w.gx0, p);
+    w.xs1 = w.tile_xs && in_xstrip(w.gx0 + 1, p);
+    w.row_in = w.row_int = w.ymask = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ly = w.ly0 + r, gy = w.Y0 + ly;
+        if (gy >= 0 && gy < p.ny) {
+            w.row_in |= 1u << r;
+            if (in_ystrip(gy, p)) w.ymask |= 1u << r;
+            if (ly >= p.K && ly < p.K + p.tile_h) w.row_int |= 1u << r;
+        }
     }
+    w.ys = w.ymask != 0;
+    return w;
 }
 
-// Load the time-stepping state of the owned cells; CPML memories of strip cells go to
-// shared memory (zero elsewhere), and with kCoefSmem the update coefficients too (ca, cb are
-// then left untouched).  Returns the row bit masks (y strip, interior).
-template <int RY, int BY, bool kCoefSmem = false>
-__device__ __forceinline__ void load_state(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                           long long sbase, float* f0, float* f1, float* f2,
-                                           float* ca, float* cb, unsigned& ystrip,
-                                           unsigned& interior) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
-    const long long F = (long long)p.nshots * p.N;
-    ystrip = 0;
-    interior = 0;
+__device__ __forceinline__ float2 ld2(const float* a) { return *reinterpret_cast<const float2*>(a); }
+__device__ __forceinline__ void st2(float* a, float2 v) { *reinterpret_cast<float2*>(a) = v; }
+
+// Value of cell (r, c) of a thread's register block (r, c run-time, warp-divergent callers).
+template <int R>
+__device__ __forceinline__ float pick(const float2 (&f)[R], int r, int c) {
+    float v = 0.f;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        const int ly = c.ly0 + r, gy = c.Y0 + ly, l = ly * BX + c.lx;
-        const bool in = c.col_active && ly < c.EHe && gy >= 0 && gy < p.ny;
-        float a = 0.f, b = 0.f, d = 0.f, cav = 0.f, cbv = 0.f;
-        float pex = 0.f, pey = 0.f, phx = 0.f, phy = 0.f;
+    for (int k = 0; k < R; ++k)
+        if (k == r) v = c ? f[k].y : f[k].x;
+    return v;
+}
+template <int R>
+__device__ __forceinline__ void add_at(float2 (&f)[R], int r, int c, float v) {
+#pragma unroll
+    for (int k = 0; k < R; ++k)
+        if (k == r) {
+            if (c) f[k].y += v;
+            else f[k].x += v;
+        }
+}
+
+// Load the owned cells' state (f0, f1, f2 = Ez, Hx, Hy or their adjoints); the update
+// coefficients go to the shared-memory plane coef (Ca, Cb of both columns as one float4),
+// the CPML memories of strip cells to the psi planes (zero elsewhere in the planes the strip
+// forms read: x planes of x-strip CTAs, y planes of every row of a y-strip warp).  Every
+// global load is issued before the first shared-memory store, so that the prologue waits
+// for one memory round trip, not one per row.
+template <int R, int NW>
+__device__ __forceinline__ void load_state(const TileParams& p, const Pos<R>& w, float* sm,
+                                           int shot, float2 (&f0)[R], float2 (&f1)[R],
+                                           float2 (&f2)[R]) {
+    using Gm = G<R, NW>;
+    const long long F = (long long)p.nshots * p.Np;
+    const long long sb = (long long)shot * p.Np;
+    const float2 z = make_float2(0.f, 0.f);
+    float2 u[R], v[R], pex[R], phy[R], pey[R], phx[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool in = w.lane_in && ((w.row_in >> r) & 1u);
+        const long long m = (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0;
+        const float* s = p.st_in + sb + m;
+        f0[r] = f1[r] = f2[r] = u[r] = v[r] = z;
+        pex[r] = phy[r] = pey[r] = phx[r] = z;
         if (in) {
-            const long long g = (long long)gy * p.nx + c.gx, sg = sbase + g;
-            a = p.st_in[sg];
-            b = p.st_in[F + sg];
-            d = p.st_in[2 * F + sg];
-            const bool ys = in_ystrip(gy, p);
-            if (ys) ystrip |= 1u << r;
-            if (c.xs) {
-                pex = p.st_in[3 * F + sg];
-                phy = p.st_in[6 * F + sg];
+            f0[r] = ld2(s);
+            f1[r] = ld2(s + F);
+            f2[r] = ld2(s + 2 * F);
+            u[r] = __ldg(reinterpret_cast<const float2*>(p.ca + m));
+            v[r] = __ldg(reinterpret_cast<const float2*>(p.cb + m));
+            if (w.xs0 || w.xs1) {
+                pex[r] = ld2(s + 3 * F);
+                phy[r] = ld2(s + 6 * F);
             }
-            if (ys) {
-                pey = p.st_in[4 * F + sg];
-                phx = p.st_in[5 * F + sg];
+            if ((w.ymask >> r) & 1u) {
+                pey[r] = ld2(s + 4 * F);
+                phx[r] = ld2(s + 5 * F);
             }
-            const bool ring = c.gx == 0 || gy == 0 || c.gx == p.nx - 1 || gy == p.ny - 1;
-            coefficients(__ldg(p.eps_r + g), __ldg(p.sigma + g), p.dt_eps0, ring, cav, cbv);
-            if (c.col_int && ly >= p.K && ly < p.K + p.tile_h) interior |= 1u << r;
         }
-        f0[r] = a; f1[r] = b; f2[r] = d;
-        if (kCoefSmem) {
-            s.coef[l] = cav;
-            s.coef[PLANE + l] = cbv;
-        } else {
-            ca[r] = cav;
-            cb[r] = cbv;
+    }
+    float2* psi = reinterpret_cast<float2*>(sm + Gm::oPsi) + w.ly0 * 32 + w.lane;
+    float4* coef = reinterpret_cast<float4*>(sm + Gm::oCoef) + w.ly0 * 32 + w.lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        coef[r * 32] = make_float4(u[r].x, v[r].x, u[r].y, v[r].y);
+        if (w.tile_xs) {
+            if (!w.xs0) pex[r].x = phy[r].x = 0.f;
+            if (!w.xs1) pex[r].y = phy[r].y = 0.f;
+            psi[r * 32] = pex[r];
+            psi[3 * Gm::PL + r * 32] = phy[r];
         }
-        if (c.tile_strip) {
-            s.psi[l] = pex;
-            s.psi[PLANE + l] = pey;
-            s.psi[2 * PLANE + l] = phx;
-            s.psi[3 * PLANE + l] = phy;
+        if (w.ys) {
+            psi[Gm::PL + r * 32] = pey[r];
+            psi[2 * Gm::PL + r * 32] = phx[r];
         }
     }
 }
 
 // Write the owned interior cells (fields and strip memories) to the output state.
-template <int RY, int BY>
-__device__ __forceinline__ void store_state(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                            long long sbase, const float* f0, const float* f1,
-                                            const float* f2, unsigned ystrip, unsigned interior) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
-    const long long F = (long long)p.nshots * p.N;
+template <int R, int NW>
+__device__ __forceinline__ void store_state(const TileParams& p, const Pos<R>& w, const float* sm,
+                                            int shot, const float2 (&f0)[R], const float2 (&f1)[R],
+                                            const float2 (&f2)[R]) {
+    using Gm = G<R, NW>;
+    const long long F = (long long)p.nshots * p.Np;
+    const long long sb = (long long)shot * p.Np;
+    const float2* psi = reinterpret_cast<const float2*>(sm + Gm::oPsi) + w.ly0 * 32 + w.lane;
+    if (!w.lane_int) return;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        if (!((interior >> r) & 1u)) continue;
-        const int ly = c.ly0 + r, l = ly * BX + c.lx;
-        const long long sg = sbase + (long long)(c.Y0 + ly) * p.nx + c.gx;
-        p.st_out[sg] = f0[r];
-        p.st_out[F + sg] = f1[r];
-        p.st_out[2 * F + sg] = f2[r];
-        if (c.xs) {
-            p.st_out[3 * F + sg] = s.psi[l];
-            p.st_out[6 * F + sg] = s.psi[3 * PLANE + l];
+    for (int r = 0; r < R; ++r) {
+        if (!((w.row_int >> r) & 1u)) continue;
+        float* s = p.st_out + sb + (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0;
+        st2(s, f0[r]);
+        st2(s + F, f1[r]);
+        st2(s + 2 * F, f2[r]);
+        if (w.xs0 || w.xs1) {
+            st2(s + 3 * F, psi[r * 32]);
+            st2(s + 6 * F, psi[3 * Gm::PL + r * 32]);
         }
-        if ((ystrip >> r) & 1u) {
-            p.st_out[4 * F + sg] = s.psi[PLANE + l];
-            p.st_out[5 * F + sg] = s.psi[2 * PLANE + l];
+        if ((w.ymask >> r) & 1u) {
+            st2(s + 4 * F, psi[Gm::PL + r * 32]);
+            st2(s + 5 * F, psi[2 * Gm::PL + r * 32]);
         }
     }
 }
 
-// Range [first, end) of the entries of this CTA's receiver list (host-built, sorted by row,
-// at most 65535 entries) that covers every entry on this thread's cells, packed as
-// first | end << 16 (0 when there is none).  Computed once per launch so that the per-step
-// injection visits only this range (usually one entry) rather than decoding the whole list
-// on every step: a thread that did so became the straggler of its CTA at every barrier.
-template <int RY>
-__device__ __forceinline__ unsigned owned_range(const int* __restrict__ idx, int count,
-                                                const int* __restrict__ cells, int nx,
-                                                const Cell<RY>& c) {
-    unsigned first = 0, end = 0;
-    for (int e = 0; e < count; ++e) {
-        const int cell = __ldg(cells + __ldg(idx + e));
-        const int lx = cell % nx - c.X0, ly = cell / nx - c.Y0 - c.ly0;
-        if (lx == c.lx && ly >= 0 && ly < RY && c.lx < c.EWe && c.ly0 + ly < c.EHe) {
-            if (end == 0) first = e;
-            end = e + 1;
+// Row and column CPML profiles of the staged window (clamped to the grid).
+template <int R, int NW>
+__device__ __forceinline__ void stage_profiles(const TileParams& p, const Pos<R>& w, float* sm) {
+    using Gm = G<R, NW>;
+    for (int i = threadIdx.x; i < Gm::WY + WX; i += Gm::NT) {
+        if (i < Gm::WY) {
+            const int g = min(max(w.Y0 + i, 0), p.ny - 1);
+            float4* yp = reinterpret_cast<float4*>(sm + Gm::oYp) + 2 * i;
+            yp[0] = make_float4(__ldg(p.py.aE + g), __ldg(p.py.bE + g), __ldg(p.py.cE + g), 0.f);
+            yp[1] = make_float4(__ldg(p.py.aH + g), __ldg(p.py.bH + g), __ldg(p.py.cH + g), 0.f);
+        } else {
+            const int c = i - Gm::WY, g = min(max(w.X0 + c, 0), p.nx - 1);
+            float* xp = sm + Gm::oXp + c;  // plane k, column c at xp[k * 64]
+            xp[0] = __ldg(p.px.aE + g);
+            xp[WX] = __ldg(p.px.bE + g);
+            xp[2 * WX] = __ldg(p.px.cE + g);
+            xp[3 * WX] = __ldg(p.px.aH + g);
+            xp[4 * WX] = __ldg(p.px.bH + g);
+            xp[5 * WX] = __ldg(p.px.cH + g);
         }
     }
-    return first | end << 16;
+}
+
+// Window receivers.  With kStaged the list is staged in shared memory: rec[e] = position
+// lx | (ly + kRowBias) << 8 | interior << 16, rec[nrl + e] = receiver index (and, in the
+// adjoint, rec[2 nrl + e K + st] = residual sample of launch step st); otherwise entries are
+// decoded from global memory when used.  The lists are built for the context's time-block
+// depth; a shorter last launch starts its window lower, so a few entries can sit above row 0
+// (they match no thread).  The bias keeps the packed rows non-negative and in list order.
+constexpr int kRowBias = 64;
+__device__ __forceinline__ int rec_position(const TileParams& p, int cell, int X0, int Y0) {
+    const int y = cell / p.nx, x = cell - y * p.nx;
+    const int lx = x - X0, ly = y - Y0;
+    const bool interior =
+        lx >= p.kl && lx < p.kl + p.tile_w && ly >= p.K && ly < p.K + p.tile_h;
+    return (lx & 0xff) | (ly + kRowBias) << 8 | (interior ? 1 << 16 : 0);
+}
+__device__ __forceinline__ int rec_row(int pos) { return ((pos >> 8) & 0xff) - kRowBias; }
+
+template <bool kStaged>
+__device__ __forceinline__ void rec_entry(const TileParams& p, const int* srec, const int* rlist,
+                                          const int* rcells, int nrl, int e, int X0, int Y0,
+                                          int& pos, int& ri) {
+    if (kStaged) {
+        pos = srec[e];
+        ri = srec[nrl + e];
+    } else {
+        ri = __ldg(rlist + e);
+        pos = rec_position(p, __ldg(rcells + ri), X0, Y0);
+    }
+}
+
+// Entries [lo, hi) of the row-sorted list on the warp's rows [ly0, ly0 + R).
+template <bool kStaged, int R>
+__device__ __forceinline__ void warp_rec_range(const TileParams& p, const Pos<R>& w,
+                                               const int* srec, const int* rlist,
+                                               const int* rcells, int nrl, int& lo, int& hi) {
+    lo = hi = 0;
+    for (int base = 0; base < nrl; base += 32) {
+        const int e = base + w.lane;
+        int ly = 1 << 20;
+        if (e < nrl) {
+            int pos, ri;
+            rec_entry<kStaged>(p, srec, rlist, rcells, nrl, e, w.X0, w.Y0, pos, ri);
+            ly = rec_row(pos);
+        }
+        lo += __popc(__ballot_sync(kFull, ly < w.ly0));
+        hi += __popc(__ballot_sync(kFull, ly < w.ly0 + R));
+    }
 }
 
 // ---------------------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------------------
-template <int RY, int BY, bool kStrip, bool kHist, bool kIllum>
-__device__ __forceinline__ void fwd_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                         float* ez, float* hx, float* hy, float* ill, unsigned ystrip,
-                                         unsigned interior, unsigned srcmask, const int* rlist,
-                                         int nrl, int shot, int tid) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
-    constexpr int NTHR = BX * BY;
-    const int ty = threadIdx.y, K = p.K;
-    float* sEz = s.xplane;
-    float* sHy = s.xplane2;
-    float* sHxB = s.rowA;
-    float* sPEx = s.psi;
-    float* sPEy = s.psi + PLANE;
-    float* sPHx = s.psi + 2 * PLANE;
-    float* sPHy = s.psi + 3 * PLANE;
-    const float chx = p.ch * p.rdx, chy = p.ch * p.rdy;
-    // the history column of this thread: slot n, row r at hcol + n N + r nx
-    float* hcol = kHist ? p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
-                              (long long)(c.Y0 + c.ly0) * p.nx + c.gx
-                        : nullptr;
-    const int* rec_cells = p.rec_cell + (long long)shot * p.nrec;
-    float* trace_base = p.traces + (long long)shot * p.nt * p.nrec;
-
-    for (int st = 0; st < K; ++st) {
-        const int n = p.n0 + st;
-        // 1. receivers of this CTA's interior: d^n = Ez^n
-        for (int e = tid; e < nrl; e += NTHR) {
-            const int ri = __ldg(rlist + e);
-            const int cell = __ldg(rec_cells + ri);
-            const int lx = cell % p.nx - c.X0, ly = cell / p.nx - c.Y0;
-            if (lx >= K && lx < K + p.tile_w && ly >= K && ly < K + p.tile_h)
-                trace_base[(long long)n * p.nrec + ri] = sEz[ly * BX + lx];
-        }
-        // 2-3. H and magnetic CPML from Ez^n
+// H update of the warp's rows from Ez^n (eb: Ez of the row below the warp), with the x-CPML
+// form in every column when XS and the y-CPML form in every row when YS (both reduce to the
+// plain update outside the strips).  No per-row branches: the rows are independent chains.
+template <int R, int NW, bool XS, bool YS>
+__device__ __forceinline__ void h_rows(const TileParams& p, float2* psi, const float2* xp,
+                                       const float4* yp, const float2 (&ez)[R], float2 eb,
+                                       float2 (&hx)[R], float2 (&hy)[R]) {
+    using Gm = G<R, NW>;
+    const float ch = p.ch, chx = p.ch * p.rdx, chy = p.ch * p.rdy;
+    float2 axH, bxH, cxH;
+    if (XS) {
+        axH = xp[3 * 32];
+        bxH = xp[4 * 32];
+        cxH = xp[5 * 32];
+    }
 #pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int ly = c.ly0 + r, l = ly * BX + c.lx;
-            const float e = ez[r];
-            const float er = sEz[c.lx < BX - 1 ? l + 1 : l];
-            const float ed = r < RY - 1 ? ez[r + 1] : (ly + 1 < EHM ? sEz[l + BX] : e);
-            const float dxE = er - e, dyE = ed - e;
-            if (kStrip && (c.xs || ((ystrip >> r) & 1u))) {
-                const float ayH = s.yprof[3 * EHM + ly], byH = s.yprof[4 * EHM + ly],
-                            cyH = s.yprof[5 * EHM + ly];
-                const float phx = byH * sPHx[l] + cyH * dyE;
-                sPHx[l] = phx;
-                hx[r] -= p.ch * (ayH * dyE + phx);
-                const float phy = s.xprof[4 * BX + c.lx] * sPHy[l] + s.xprof[5 * BX + c.lx] * dxE;
-                sPHy[l] = phy;
-                hy[r] += p.ch * (s.xprof[3 * BX + c.lx] * dxE + phy);
-            } else {
-                hx[r] -= chy * dyE;
-                hy[r] += chx * dxE;
-            }
-            sHy[l] = hy[r];
+    for (int r = 0; r < R; ++r) {
+        const float2 e = ez[r];
+        const float2 ed = r < R - 1 ? ez[r + 1] : eb;
+        const float er = __shfl_down_sync(kFull, e.x, 1);
+        const float dx0 = e.y - e.x, dx1 = er - e.y;
+        const float dy0 = ed.x - e.x, dy1 = ed.y - e.y;
+        if (XS) {
+            float2 ph = psi[3 * Gm::PL + r * 32];
+            ph.x = fmaf(bxH.x, ph.x, cxH.x * dx0);
+            ph.y = fmaf(bxH.y, ph.y, cxH.y * dx1);
+            psi[3 * Gm::PL + r * 32] = ph;
+            hy[r].x = fmaf(ch, fmaf(axH.x, dx0, ph.x), hy[r].x);
+            hy[r].y = fmaf(ch, fmaf(axH.y, dx1, ph.y), hy[r].y);
+        } else {
+            hy[r].x = fmaf(chx, dx0, hy[r].x);
+            hy[r].y = fmaf(chx, dx1, hy[r].y);
         }
-        sHxB[ty * BX + c.lx] = hx[RY - 1];
-        __syncthreads();
-        // 4-6. E, electric CPML and the source term, giving Ez^{n+1}
-        float q[RY];
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int ly = c.ly0 + r, l = ly * BX + c.lx;
-            const float hl = sHy[c.lx > 0 ? l - 1 : l];
-            const float hu = r > 0 ? hx[r - 1] : (ty > 0 ? sHxB[(ty - 1) * BX + c.lx] : hx[0]);
-            const float dxH = hy[r] - hl, dyH = hx[r] - hu;
-            if (kStrip && (c.xs || ((ystrip >> r) & 1u))) {
-                const float ayE = s.yprof[ly], byE = s.yprof[EHM + ly], cyE = s.yprof[2 * EHM + ly];
-                const float pex = s.xprof[BX + c.lx] * sPEx[l] + s.xprof[2 * BX + c.lx] * dxH;
-                sPEx[l] = pex;
-                const float pey = byE * sPEy[l] + cyE * dyH;
-                sPEy[l] = pey;
-                q[r] = s.xprof[c.lx] * dxH + pex - (ayE * dyH + pey);
-            } else {
-                q[r] = p.rdx * dxH - p.rdy * dyH;
-            }
+        if (YS) {
+            const float4 pr = yp[2 * r + 1];
+            float2 ph = psi[2 * Gm::PL + r * 32];
+            ph.x = fmaf(pr.y, ph.x, pr.z * dy0);
+            ph.y = fmaf(pr.y, ph.y, pr.z * dy1);
+            psi[2 * Gm::PL + r * 32] = ph;
+            hx[r].x = fmaf(-ch, fmaf(pr.x, dy0, ph.x), hx[r].x);
+            hx[r].y = fmaf(-ch, fmaf(pr.x, dy1, ph.y), hx[r].y);
+        } else {
+            hx[r].x = fmaf(-chy, dy0, hx[r].x);
+            hx[r].y = fmaf(-chy, dy1, hx[r].y);
         }
-        if (srcmask) {
-            for (int k = 0; k < p.nsrc; ++k) {
-                const int cell = __ldg(p.src_cell + shot * p.nsrc + k);
-                const int lx = cell % p.nx - c.X0, r0 = cell / p.nx - c.Y0 - c.ly0;
-                if (lx != c.lx) continue;
-#pragma unroll
-                for (int r = 0; r < RY; ++r)
-                    if (r == r0 && ((srcmask >> r) & 1u)) q[r] -= s.wsrc[st * kMaxSrc + k];
-            }
-        }
-        float* hrow = kHist ? hcol + (long long)n * p.N : nullptr;
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int l = (c.ly0 + r) * BX + c.lx;
-            const float v = s.coef[l] * ez[r] + s.coef[PLANE + l] * q[r];
-            ez[r] = v;
-            sEz[l] = v;
-            if ((interior >> r) & 1u) {
-                if (kHist) __stcs(hrow + r * p.nx, v);
-                if (kIllum) ill[r] += v * v;
-            }
-        }
-        __syncthreads();
     }
 }
 
-template <int RY, int BY, bool kHist, bool kIllum>
-__global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) fwd_tile_kernel(const TileParams p) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
+// E update of the warp's rows from H^{n+1/2} (ha: Hx of the row above the warp):
+// Ez^{n+1} = Ca Ez^n + Cb Q.
+template <int R, int NW, bool XS, bool YS>
+__device__ __forceinline__ void e_rows(const TileParams& p, float2* psi, const float2* xp,
+                                       const float4* yp, const float4* coef, float2 (&ez)[R],
+                                       const float2 (&hx)[R], const float2 (&hy)[R], float2 ha) {
+    using Gm = G<R, NW>;
+    const float rdx = p.rdx, rdy = p.rdy;
+    float2 axE, bxE, cxE;
+    if (XS) {
+        axE = xp[0];
+        bxE = xp[32];
+        cxE = xp[2 * 32];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float2 h = hy[r];
+        const float hl = __shfl_up_sync(kFull, h.y, 1);
+        const float2 hu = r > 0 ? hx[r - 1] : ha;
+        const float dx0 = h.x - hl, dx1 = h.y - h.x;
+        const float dy0 = hx[r].x - hu.x, dy1 = hx[r].y - hu.y;
+        float q0, q1;
+        if (XS) {
+            float2 pe = psi[r * 32];
+            pe.x = fmaf(bxE.x, pe.x, cxE.x * dx0);
+            pe.y = fmaf(bxE.y, pe.y, cxE.y * dx1);
+            psi[r * 32] = pe;
+            q0 = fmaf(axE.x, dx0, pe.x);
+            q1 = fmaf(axE.y, dx1, pe.y);
+        } else {
+            q0 = rdx * dx0;
+            q1 = rdx * dx1;
+        }
+        if (YS) {
+            const float4 pr = yp[2 * r];
+            float2 pe = psi[Gm::PL + r * 32];
+            pe.x = fmaf(pr.y, pe.x, pr.z * dy0);
+            pe.y = fmaf(pr.y, pe.y, pr.z * dy1);
+            psi[Gm::PL + r * 32] = pe;
+            q0 -= fmaf(pr.x, dy0, pe.x);
+            q1 -= fmaf(pr.x, dy1, pe.y);
+        } else {
+            q0 = fmaf(-rdy, dy0, q0);
+            q1 = fmaf(-rdy, dy1, q1);
+        }
+        const float4 c = coef[r * 32];
+        ez[r].x = fmaf(c.x, ez[r].x, c.y * q0);
+        ez[r].y = fmaf(c.z, ez[r].y, c.w * q1);
+    }
+}
+
+template <int R, int NW, bool XS, bool kHist, bool kIllum, bool kStaged>
+__device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, float* sm,
+                                          float2 (&ez)[R], float2 (&hx)[R], float2 (&hy)[R],
+                                          float2 (&ill)[R], int rlo, int rhi, int nrl,
+                                          const int* rlist, bool srcany, int shot) {
+    using Gm = G<R, NW>;
+    float2* top = reinterpret_cast<float2*>(sm + Gm::oTop);
+    float2* bot = reinterpret_cast<float2*>(sm + Gm::oBot);
+    float2* psi = reinterpret_cast<float2*>(sm + Gm::oPsi) + w.ly0 * 32 + w.lane;
+    const float2* xp = reinterpret_cast<const float2*>(sm + Gm::oXp) + w.lane;
+    const float4* yp = reinterpret_cast<const float4*>(sm + Gm::oYp) + 2 * w.ly0;
+    const float4* coef = reinterpret_cast<const float4*>(sm + Gm::oCoef) + w.ly0 * 32 + w.lane;
+    const int* srec = reinterpret_cast<const int*>(sm + Gm::oRec);
+    const int* srcpos = reinterpret_cast<const int*>(sm + Gm::oSp);
+    const float* wsrc = sm + Gm::oWs;
+    const int* rcells = p.rec_cell + (long long)shot * p.nrec;
+    float* tr = p.traces + (long long)shot * p.nt * p.nrec;
+    // the wavefield store of the owned cells: row r of step n at hp + n Np + r pitch
+    float* hp = kHist ? p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.Np +
+                            (long long)(w.Y0 + w.ly0) * p.pitch + w.gx0
+                      : nullptr;
+    bool own[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) own[r] = w.lane_int && ((w.row_int >> r) & 1u);
+    const float2* below = top + (w.warp + 1) * 32 + w.lane;
+    const float2* above = bot + (w.warp - 1) * 32 + w.lane;
+
+    for (int st = 0; st < p.K; ++st) {
+        const int n = p.n0 + st;
+        // 1. receivers in this CTA's interior: d^n = Ez^n (loop bounds are warp-uniform)
+        for (int e = rlo; e < rhi; ++e) {
+            int pos, ri;
+            rec_entry<kStaged>(p, srec, rlist, rcells, nrl, e, w.X0, w.Y0, pos, ri);
+            if (((pos & 0xff) >> 1) == w.lane && (pos >> 16))
+                tr[(long long)n * p.nrec + ri] = pick<R>(ez, rec_row(pos) - w.ly0, pos & 1);
+        }
+        top[w.warp * 32 + w.lane] = ez[0];
+        __syncthreads();
+        const float2 eb = w.warp < NW - 1 ? *below : ez[R - 1];
+        // 2-3. H and magnetic CPML from Ez^n
+        if (w.ys)
+            h_rows<R, NW, XS, true>(p, psi, xp, yp, ez, eb, hx, hy);
+        else
+            h_rows<R, NW, XS, false>(p, psi, xp, yp, ez, eb, hx, hy);
+        bot[w.warp * 32 + w.lane] = hx[R - 1];
+        __syncthreads();
+        const float2 ha = w.warp > 0 ? *above : hx[0];
+        // 4-5. E and electric CPML from H^{n+1/2}, giving Ez^{n+1}
+        if (w.ys)
+            e_rows<R, NW, XS, true>(p, psi, xp, yp, coef, ez, hx, hy, ha);
+        else
+            e_rows<R, NW, XS, false>(p, psi, xp, yp, coef, ez, hx, hy, ha);
+        // 6. sources: Ez^{n+1} -= Cb w^n / (dx dy) in every staged copy
+        if (srcany) {
+            for (int k = 0; k < p.nsrc; ++k) {
+                const int pos = srcpos[k];
+                const int r = (pos >> 8) - w.ly0, c = pos & 1;
+                if (pos >= 0 && ((pos & 0xff) >> 1) == w.lane && r >= 0 && r < R) {
+                    const float4 cc = coef[r * 32];
+                    add_at<R>(ez, r, c, -(c ? cc.w : cc.y) * wsrc[st * kMaxSrc + k]);
+                }
+            }
+        }
+        // 7. wavefield store and illumination of the owned cells
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (kHist && own[r])
+                __stcs(reinterpret_cast<float2*>(hp + (long long)n * p.Np + (long long)r * p.pitch),
+                       ez[r]);
+            if (kIllum) {
+                ill[r].x = fmaf(ez[r].x, ez[r].x, ill[r].x);
+                ill[r].y = fmaf(ez[r].y, ez[r].y, ill[r].y);
+            }
+        }
+    }
+}
+
+template <int R, int NW, bool kHist, bool kIllum, bool kStaged>
+__global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1) fwd_tile_kernel(const TileParams p) {
+    using Gm = G<R, NW>;
     extern __shared__ float4 smem_raw[];
-    const Smem s = carve<RY, BY>(reinterpret_cast<float*>(smem_raw));
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    const int shot = blockIdx.y, K = p.K;
-    Cell<RY> c;
-    c.init(p);
-    const long long sbase = (long long)shot * p.N;
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    const Pos<R> w = position<R>(p);
+    const int shot = blockIdx.y, K = p.K, tid = threadIdx.x;
 
-    float ez[RY], hx[RY], hy[RY], ill[RY];
-    unsigned ystrip, interior;
-    load_state<RY, BY, true>(p, c, s, sbase, ez, hx, hy, nullptr, nullptr, ystrip, interior);
+    float2 ez[R], hx[R], hy[R], ill[R];
+    load_state<R, NW>(p, w, sm, shot, ez, hx, hy);
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        s.xplane[(c.ly0 + r) * BX + c.lx] = ez[r];
-        ill[r] = 0.f;
+    for (int r = 0; r < R; ++r) ill[r] = make_float2(0.f, 0.f);
+    stage_profiles<R, NW>(p, w, sm);
+    float* wsrc = sm + Gm::oWs;
+    int* srcpos = reinterpret_cast<int*>(sm + Gm::oSp);
+    for (int k = tid; k < K * kMaxSrc; k += Gm::NT) {
+        const int st = k / kMaxSrc, src = k - st * kMaxSrc;
+        wsrc[k] = src < p.nsrc ? p.src_scale * __ldg(p.wavelet + ((long long)shot * p.nsrc + src) *
+                                                                     p.nt + p.n0 + st)
+                               : 0.f;
     }
-    stage_profiles<EHM>(s, p, c.X0, c.Y0, tid);
-    for (int k = tid; k < K * kMaxSrc; k += BX * BY) {
-        const int st = k / kMaxSrc, src = k % kMaxSrc;
-        s.wsrc[k] = src < p.nsrc
-                        ? p.src_scale * __ldg(p.wavelet + ((long long)shot * p.nsrc + src) * p.nt + p.n0 + st)
-                        : 0.f;
+    if (tid < kMaxSrc) {
+        int pos = -1;
+        if (tid < p.nsrc) {
+            const int cell = __ldg(p.src_cell + shot * p.nsrc + tid);
+            const int y = cell / p.nx, x = cell - y * p.nx, lx = x - w.X0, ly = y - w.Y0;
+            if (lx >= 0 && lx < WX && ly >= 0 && ly < Gm::WY) pos = lx | ly << 8;
+        }
+        srcpos[tid] = pos;
     }
-    // rows of this thread holding a source (every staged copy injects)
-    unsigned srcmask = 0;
-    for (int k = 0; k < p.nsrc; ++k) {
-        const int cell = __ldg(p.src_cell + shot * p.nsrc + k);
-        const int lx = cell % p.nx - c.X0, r0 = cell / p.nx - c.Y0 - c.ly0;
-        if (lx == c.lx && r0 >= 0 && r0 < RY && c.lx < c.EWe && c.ly0 + r0 < c.EHe)
-            srcmask |= 1u << r0;
-    }
-    const int tile = blockIdx.x;
-    const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + tile];
-    const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + tile + 1] - lo);
+    const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + blockIdx.x];
+    const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + blockIdx.x + 1] - lo);
     const int* rlist = p.tile_rec_idx + lo;
+    const int* rcells = p.rec_cell + (long long)shot * p.nrec;
+    int* srec = reinterpret_cast<int*>(sm + Gm::oRec);
+    if (kStaged) {
+        for (int e = tid; e < nrl; e += Gm::NT) {
+            const int ri = __ldg(rlist + e);
+            srec[e] = rec_position(p, __ldg(rcells + ri), w.X0, w.Y0);
+            srec[nrl + e] = ri;
+        }
+    }
     __syncthreads();
+    int rlo, rhi;
+    warp_rec_range<kStaged, R>(p, w, srec, rlist, rcells, nrl, rlo, rhi);
+    bool srcany = false;
+    for (int k = 0; k < p.nsrc; ++k) {
+        const int pos = srcpos[k], r = (pos >> 8) - w.ly0;
+        srcany |= pos >= 0 && ((pos & 0xff) >> 1) == w.lane && r >= 0 && r < R;
+    }
 
-    if (c.tile_strip)
-        fwd_body<RY, BY, true, kHist, kIllum>(p, c, s, ez, hx, hy, ill, ystrip, interior,
-                                              srcmask, rlist, nrl, shot, tid);
+    if (w.tile_xs)
+        fwd_steps<R, NW, true, kHist, kIllum, kStaged>(p, w, sm, ez, hx, hy, ill, rlo, rhi, nrl,
+                                                       rlist, srcany, shot);
     else
-        fwd_body<RY, BY, false, kHist, kIllum>(p, c, s, ez, hx, hy, ill, ystrip, interior,
-                                               srcmask, rlist, nrl, shot, tid);
+        fwd_steps<R, NW, false, kHist, kIllum, kStaged>(p, w, sm, ez, hx, hy, ill, rlo, rhi, nrl,
+                                                        rlist, srcany, shot);
 
-    store_state<RY, BY>(p, c, s, sbase, ez, hx, hy, ystrip, interior);
-    if (kIllum) {
+    store_state<R, NW>(p, w, sm, shot, ez, hx, hy);
+    if (kIllum && w.lane_int) {
 #pragma unroll
-        for (int r = 0; r < RY; ++r)
-            if ((interior >> r) & 1u)
-                p.illum[sbase + (long long)(c.Y0 + c.ly0 + r) * p.nx + c.gx] += ill[r];
+        for (int r = 0; r < R; ++r) {
+            if (!((w.row_int >> r) & 1u)) continue;
+            float* a = p.illum + (long long)shot * p.Np + (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0;
+            float2 v = ld2(a);
+            v.x += ill[r].x;
+            v.y += ill[r].y;
+            st2(a, v);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------------------
-template <int RY, int BY, bool kStrip, bool kStaged>
-__device__ __forceinline__ void adj_body(const TileParams& p, const Cell<RY>& c, const Smem& s,
-                                         float* aez, float* ahx, float* ahy,
-                                         unsigned ystrip, unsigned interior, unsigned rrange,
-                                         const int* rlist, int shot) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
-    const int ty = threadIdx.y, K = p.K;
-    float* sSx = s.xplane;
-    float* sTx = s.xplane2;
-    float* sSyT = s.rowA;
-    float* sTyB = s.rowB;
-    float* sPEx = s.psi;
-    float* sPEy = s.psi + PLANE;
-    float* sPHx = s.psi + 2 * PLANE;
-    float* sPHy = s.psi + 3 * PLANE;
-    const float chx = p.ch * p.rdx, chy = p.ch * p.rdy;
-    const int n1 = p.n0 + K - 1;
-    const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
-                        (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
-    const int* rec_cells = p.rec_cell + (long long)shot * p.nrec;
-    const float* resid_base = p.resid + (long long)shot * p.nt * p.nrec;
-    float wx[RY], wy[RY], pf[RY];
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
-    // Ez^n of the owned cells (Ez^0 = 0), for the gradient of step n
-    auto load_e0 = [&](int n) {
-#pragma unroll
-        for (int r = 0; r < RY; ++r)
-            pf[r] = (n >= 1 && ((interior >> r) & 1u))
-                        ? __ldcs(hcol + (long long)(n - 1) * p.N + r * p.nx)
-                        : 0.f;
-    };
-    // A: gradient, electric CPML and the S weights; adj(Ez^n) starts as Ca adj(Ez^{n+1})
-    auto phase_a = [&]() {
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int ly = c.ly0 + r, l = ly * BX + c.lx;
-            const float lam = s.coef[PLANE + l] * aez[r];
-            if ((interior >> r) & 1u) {
-                const float en1 = s.coef[2 * PLANE + l];
-                s.coef[3 * PLANE + l] -= p.geps * lam * (en1 - pf[r]);
-                s.coef[4 * PLANE + l] -= 0.5f * lam * (en1 + pf[r]);
-                s.coef[2 * PLANE + l] = pf[r];
-            }
-            if (kStrip && (c.xs || ((ystrip >> r) & 1u))) {
-                const float ayE = s.yprof[ly], byE = s.yprof[EHM + ly], cyE = s.yprof[2 * EHM + ly];
-                const float pex = sPEx[l] + lam, pey = sPEy[l] - lam;
-                wx[r] = lam * s.xprof[c.lx] + s.xprof[2 * BX + c.lx] * pex;
-                wy[r] = -lam * ayE + cyE * pey;
-                sPEx[l] = s.xprof[BX + c.lx] * pex;
-                sPEy[l] = byE * pey;
-            } else {
-                wx[r] = lam * p.rdx;
-                wy[r] = -lam * p.rdy;
-            }
-            sSx[l] = wx[r];
-            aez[r] *= s.coef[l];
-        }
-        sSyT[ty * BX + c.lx] = wy[0];
-    };
+// cp.async of 8 bytes that reads `bytes` (8 or 0) from global memory and zero-fills the rest.
+__device__ __forceinline__ void cp_async8_zfill(void* dst_smem, const void* src, int bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(bytes)
+                 : "memory");
+}
 
-    load_e0(n1);
-    phase_a();
-    for (int st = 0; st < K; ++st) {
-        const int n = n1 - st;
-        __syncthreads();
-        if (st < K - 1) load_e0(n - 1);  // prefetch for the gradient of step n - 1
-        // B: adj(H) += transposed S differences; magnetic CPML; T weights.  Rows go upwards
-        // so that wy[r + 1] still holds S_y when row r reads it.
+// Phase A of the warp's rows: lam = Cb adj(Ez^{n+1}); zero-lag gradient sums with Ez^{n+1}
+// (ring slot `prev`) and Ez^n (ring slot `slot`); electric CPML and the S weights (wx, wy);
+// adj(Ez^n) starts as Ca adj(Ez^{n+1}).  The gradient sums carry no constant factor (applied
+// once at the end of the launch).
+template <int R, int NW, bool XS, bool YS>
+__device__ __forceinline__ void a_rows(const TileParams& p, float2* psi, const float2* xp,
+                                       const float4* yp, const float4* coef, const float2* slot,
+                                       const float2* prev, float2 (&aez)[R], float2 (&ge)[R],
+                                       float2 (&gs)[R], float2 (&wx)[R], float2 (&wy)[R]) {
+    using Gm = G<R, NW>;
+    const float rdx = p.rdx, rdy = p.rdy;
+    float2 axE, bxE, cxE;
+    if (XS) {
+        axE = xp[0];
+        bxE = xp[32];
+        cxE = xp[2 * 32];
+    }
 #pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int ly = c.ly0 + r, l = ly * BX + c.lx;
-            const float sxr = sSx[c.lx < BX - 1 ? l + 1 : l];
-            const float syd = r < RY - 1 ? wy[r + 1] : (ty < BY - 1 ? sSyT[(ty + 1) * BX + c.lx] : wy[r]);
-            const float hyv = ahy[r] + wx[r] - sxr;
-            const float hxv = ahx[r] + wy[r] - syd;
-            ahy[r] = hyv;
-            ahx[r] = hxv;
-            if (kStrip && (c.xs || ((ystrip >> r) & 1u))) {
-                const float ayH = s.yprof[3 * EHM + ly], byH = s.yprof[4 * EHM + ly],
-                            cyH = s.yprof[5 * EHM + ly];
-                const float phy = sPHy[l] + p.ch * hyv;
-                wx[r] = p.ch * hyv * s.xprof[3 * BX + c.lx] + s.xprof[5 * BX + c.lx] * phy;
-                sPHy[l] = s.xprof[4 * BX + c.lx] * phy;
-                const float phx = sPHx[l] - p.ch * hxv;
-                wy[r] = -p.ch * hxv * ayH + cyH * phx;
-                sPHx[l] = byH * phx;
-            } else {
-                wx[r] = chx * hyv;
-                wy[r] = -chy * hxv;
-            }
-            sTx[l] = wx[r];
+    for (int r = 0; r < R; ++r) {
+        const float2 pf = slot[r * 32], en1 = prev[r * 32];
+        const float4 c = coef[r * 32];
+        const float l0 = c.y * aez[r].x, l1 = c.w * aez[r].y;
+        ge[r].x = fmaf(l0, en1.x - pf.x, ge[r].x);
+        ge[r].y = fmaf(l1, en1.y - pf.y, ge[r].y);
+        gs[r].x = fmaf(l0, en1.x + pf.x, gs[r].x);
+        gs[r].y = fmaf(l1, en1.y + pf.y, gs[r].y);
+        if (XS) {
+            float2 pe = psi[r * 32];
+            pe.x += l0;
+            pe.y += l1;
+            wx[r].x = fmaf(l0, axE.x, cxE.x * pe.x);
+            wx[r].y = fmaf(l1, axE.y, cxE.y * pe.y);
+            pe.x *= bxE.x;
+            pe.y *= bxE.y;
+            psi[r * 32] = pe;
+        } else {
+            wx[r].x = l0 * rdx;
+            wx[r].y = l1 * rdx;
         }
-        sTyB[ty * BX + c.lx] = wy[RY - 1];
-        __syncthreads();
-        // C: adj(Ez^n) += transposed T differences; adjoint source of step n
-#pragma unroll
-        for (int r = 0; r < RY; ++r) {
-            const int l = (c.ly0 + r) * BX + c.lx;
-            const float tl = sTx[c.lx > 0 ? l - 1 : l];
-            const float tu = r > 0 ? wy[r - 1] : (ty > 0 ? sTyB[(ty - 1) * BX + c.lx] : wy[0]);
-            aez[r] += tl - wx[r] + tu - wy[r];
+        if (YS) {
+            const float4 pr = yp[2 * r];
+            float2 pe = psi[Gm::PL + r * 32];
+            pe.x -= l0;
+            pe.y -= l1;
+            wy[r].x = fmaf(-l0, pr.x, pr.z * pe.x);
+            wy[r].y = fmaf(-l1, pr.x, pr.z * pe.y);
+            pe.x *= pr.y;
+            pe.y *= pr.y;
+            psi[Gm::PL + r * 32] = pe;
+        } else {
+            wy[r].x = -l0 * rdy;
+            wy[r].y = -l1 * rdy;
         }
-        for (int e = rrange & 0xffffu; e < (int)(rrange >> 16); ++e) {
-            int r0;
-            float v;
-            if (kStaged) {
-                const int pos = __float_as_int(s.rstage[kRecStage - 1 - e]);
-                r0 = (pos >> 8) - c.ly0;
-                if ((pos & 0xff) != c.lx || r0 < 0 || r0 >= RY) continue;
-                v = s.rstage[e * K + st];
-            } else {
-                const int ri = __ldg(rlist + e);
-                const int cell = __ldg(rec_cells + ri);
-                r0 = cell / p.nx - c.Y0 - c.ly0;
-                if (cell % p.nx - c.X0 != c.lx || r0 < 0 || r0 >= RY) continue;
-                v = __ldg(resid_base + (long long)n * p.nrec + ri);
-            }
-#pragma unroll
-            for (int r = 0; r < RY; ++r)
-                if (r == r0) aez[r] += v;
-        }
-        if (st < K - 1) phase_a();
+        aez[r].x *= c.x;
+        aez[r].y *= c.z;
     }
 }
 
-template <int RY, int BY, bool kStaged>
-__global__ void __launch_bounds__(BX* BY, BY <= 8 && RY <= 4 ? 2 : 1) adj_tile_kernel(const TileParams p) {
-    constexpr int EHM = RY * BY, PLANE = EHM * BX;
+// Phase B: adj(H) += transposed S differences (sb_: S_y of the row below the warp); magnetic
+// CPML; the T weights replace S in wx, wy.  Rows in ascending order, so that wy[r + 1] still
+// holds S_y when row r reads it.
+template <int R, int NW, bool XS, bool YS>
+__device__ __forceinline__ void b_rows(const TileParams& p, float2* psi, const float2* xp,
+                                       const float4* yp, float2 sb_, float2 (&ahx)[R],
+                                       float2 (&ahy)[R], float2 (&wx)[R], float2 (&wy)[R]) {
+    using Gm = G<R, NW>;
+    const float ch = p.ch, chx = p.ch * p.rdx, chy = p.ch * p.rdy;
+    float2 axH, bxH, cxH;
+    if (XS) {
+        axH = xp[3 * 32];
+        bxH = xp[4 * 32];
+        cxH = xp[5 * 32];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float sxr = __shfl_down_sync(kFull, wx[r].x, 1);
+        const float2 syd = r < R - 1 ? wy[r + 1] : sb_;
+        const float hy0 = ahy[r].x + wx[r].x - wx[r].y, hy1 = ahy[r].y + wx[r].y - sxr;
+        const float hx0 = ahx[r].x + wy[r].x - syd.x, hx1 = ahx[r].y + wy[r].y - syd.y;
+        ahy[r] = make_float2(hy0, hy1);
+        ahx[r] = make_float2(hx0, hx1);
+        if (XS) {
+            float2 ph = psi[3 * Gm::PL + r * 32];
+            ph.x = fmaf(ch, hy0, ph.x);
+            ph.y = fmaf(ch, hy1, ph.y);
+            wx[r].x = fmaf(ch * hy0, axH.x, cxH.x * ph.x);
+            wx[r].y = fmaf(ch * hy1, axH.y, cxH.y * ph.y);
+            ph.x *= bxH.x;
+            ph.y *= bxH.y;
+            psi[3 * Gm::PL + r * 32] = ph;
+        } else {
+            wx[r].x = chx * hy0;
+            wx[r].y = chx * hy1;
+        }
+        if (YS) {
+            const float4 pr = yp[2 * r + 1];
+            float2 ph = psi[2 * Gm::PL + r * 32];
+            ph.x = fmaf(-ch, hx0, ph.x);
+            ph.y = fmaf(-ch, hx1, ph.y);
+            wy[r].x = fmaf(-ch * hx0, pr.x, pr.z * ph.x);
+            wy[r].y = fmaf(-ch * hx1, pr.x, pr.z * ph.y);
+            ph.x *= pr.y;
+            ph.y *= pr.y;
+            psi[2 * Gm::PL + r * 32] = ph;
+        } else {
+            wy[r].x = -chy * hx0;
+            wy[r].y = -chy * hx1;
+        }
+    }
+}
+
+// Ez^n of the owned cells for phase A number a (step n = n1 - a; a = -1 gives Ez^{n1+1}) into
+// ring slot (a + kRing) % kRing, zero when n = 0 (Ez^0 = 0); one cp.async group per a, empty
+// beyond the launch.  Cells the thread does not own are not fetched: their ring entries only
+// feed gradient sums that are never stored.  hp: the owned cells' store, Ez^{m+1} of row r at
+// hp + m Np + r pitch.
+template <int R, int NW>
+__device__ __forceinline__ void ring_fetch(const TileParams& p, float2* ring, const float* hp,
+                                           const bool (&own)[R], int n1, int a) {
+    using Gm = G<R, NW>;
+    if (a < p.K) {
+        const int n = n1 - a;
+        float2* slot = ring + ((a + kRing) % kRing) * Gm::PL;
+        const float* h = hp + (long long)(n >= 1 ? n - 1 : 0) * p.Np;
+        const int bytes = n >= 1 ? 8 : 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (own[r]) cp_async8_zfill(slot + r * 32, h + (long long)r * p.pitch, bytes);
+    }
+    cp_async_commit();
+}
+
+template <int R, int NW, bool XS, bool kStaged>
+__device__ __forceinline__ void adj_steps(const TileParams& p, const Pos<R>& w, float* sm,
+                                          float2 (&aez)[R], float2 (&ahx)[R], float2 (&ahy)[R],
+                                          float2 (&ge)[R], float2 (&gs)[R], const float* hp,
+                                          const bool (&own)[R], int rlo, int rhi, int nrl,
+                                          const int* rlist, int shot) {
+    using Gm = G<R, NW>;
+    const int K = p.K, n1 = p.n0 + K - 1;
+    float2* top = reinterpret_cast<float2*>(sm + Gm::oTop);
+    float2* bot = reinterpret_cast<float2*>(sm + Gm::oBot);
+    float2* psi = reinterpret_cast<float2*>(sm + Gm::oPsi) + w.ly0 * 32 + w.lane;
+    float2* ring = reinterpret_cast<float2*>(sm + Gm::oRing) + w.ly0 * 32 + w.lane;
+    const float2* xp = reinterpret_cast<const float2*>(sm + Gm::oXp) + w.lane;
+    const float4* yp = reinterpret_cast<const float4*>(sm + Gm::oYp) + 2 * w.ly0;
+    const float4* coef = reinterpret_cast<const float4*>(sm + Gm::oCoef) + w.ly0 * 32 + w.lane;
+    const int* srec = reinterpret_cast<const int*>(sm + Gm::oRec);
+    const int* rcells = p.rec_cell + (long long)shot * p.nrec;
+    const float* rbase = p.resid + (long long)shot * p.nt * p.nrec;
+    const float2* below = top + (w.warp + 1) * 32 + w.lane;
+    const float2* above = bot + (w.warp - 1) * 32 + w.lane;
+    float2 wx[R], wy[R];
+    auto phase_a = [&](int a) {
+        ring_fetch<R, NW>(p, ring, hp, own, n1, a + kRingLead);
+        cp_async_wait<kRingLead>();
+        const float2* slot = ring + (a % kRing) * Gm::PL;
+        const float2* prev = ring + ((a + kRing - 1) % kRing) * Gm::PL;
+        if (w.ys)
+            a_rows<R, NW, XS, true>(p, psi, xp, yp, coef, slot, prev, aez, ge, gs, wx, wy);
+        else
+            a_rows<R, NW, XS, false>(p, psi, xp, yp, coef, slot, prev, aez, ge, gs, wx, wy);
+    };
+
+    phase_a(0);
+    for (int st = 0; st < K; ++st) {
+        const int n = n1 - st;
+        top[w.warp * 32 + w.lane] = wy[0];
+        __syncthreads();
+        const float2 sb_ = w.warp < NW - 1 ? *below : wy[R - 1];
+        // B: adj(H) += transposed S differences; magnetic CPML; T weights
+        if (w.ys)
+            b_rows<R, NW, XS, true>(p, psi, xp, yp, sb_, ahx, ahy, wx, wy);
+        else
+            b_rows<R, NW, XS, false>(p, psi, xp, yp, sb_, ahx, ahy, wx, wy);
+        bot[w.warp * 32 + w.lane] = wy[R - 1];
+        __syncthreads();
+        const float2 ta = w.warp > 0 ? *above : wy[0];
+        // C: adj(Ez^n) += transposed T differences
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float tl = __shfl_up_sync(kFull, wx[r].y, 1);
+            const float2 tu = r > 0 ? wy[r - 1] : ta;
+            aez[r].x += (tl - wx[r].x) + (tu.x - wy[r].x);
+            aez[r].y += (wx[r].x - wx[r].y) + (tu.y - wy[r].y);
+        }
+        // adjoint source of step n: the residual at the receivers (every staged copy)
+        for (int e = rlo; e < rhi; ++e) {
+            int pos, ri;
+            rec_entry<kStaged>(p, srec, rlist, rcells, nrl, e, w.X0, w.Y0, pos, ri);
+            if (((pos & 0xff) >> 1) == w.lane) {
+                const float v = kStaged ? __int_as_float(srec[2 * nrl + e * K + st])
+                                        : __ldg(rbase + (long long)n * p.nrec + ri);
+                add_at<R>(aez, rec_row(pos) - w.ly0, pos & 1, v);
+            }
+        }
+        if (st < K - 1) phase_a(st + 1);
+    }
+    cp_async_wait<0>();
+}
+
+template <int R, int NW, bool kStaged>
+__global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1) adj_tile_kernel(const TileParams p) {
+    using Gm = G<R, NW>;
     extern __shared__ float4 smem_raw[];
-    const Smem s = carve<RY, BY>(reinterpret_cast<float*>(smem_raw));
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    const int shot = blockIdx.y, K = p.K;
-    Cell<RY> c;
-    c.init(p);
-    const long long sbase = (long long)shot * p.N;
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    const Pos<R> w = position<R>(p);
+    const int shot = blockIdx.y, K = p.K, tid = threadIdx.x;
     const int n1 = p.n0 + K - 1;
 
-    float aez[RY], ahx[RY], ahy[RY];
-    unsigned ystrip, interior;
-    load_state<RY, BY, true>(p, c, s, sbase, aez, ahx, ahy, nullptr, nullptr, ystrip, interior);
-    const float* hcol = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.N +
-                        (long long)(c.Y0 + c.ly0) * p.nx + c.gx;
+    float2 aez[R], ahx[R], ahy[R], ge[R], gs[R];
+    load_state<R, NW>(p, w, sm, shot, aez, ahx, ahy);
+    // the stored Ez of the owned cells: Ez^{m+1} of row r at hp + m Np + r pitch; the ring's
+    // first slots are requested before anything else of the prologue
+    const float* hp = p.hist + ((long long)shot * p.hist_stride - p.hist_slot0) * p.Np +
+                      (long long)(w.Y0 + w.ly0) * p.pitch + w.gx0;
+    bool own[R];
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        s.coef[3 * PLANE + (c.ly0 + r) * BX + c.lx] = 0.f;
-        s.coef[4 * PLANE + (c.ly0 + r) * BX + c.lx] = 0.f;
-        s.coef[2 * PLANE + (c.ly0 + r) * BX + c.lx] =
-            ((interior >> r) & 1u) ? __ldcs(hcol + (long long)n1 * p.N + r * p.nx) : 0.f;
+    for (int r = 0; r < R; ++r) {
+        own[r] = w.lane_int && ((w.row_int >> r) & 1u);
+        ge[r] = gs[r] = make_float2(0.f, 0.f);
     }
-    stage_profiles<EHM>(s, p, c.X0, c.Y0, tid);
-    const int tile = blockIdx.x;
-    const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + tile];
-    const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + tile + 1] - lo);
+    float2* ring = reinterpret_cast<float2*>(sm + Gm::oRing) + w.ly0 * 32 + w.lane;
+    for (int a = -1; a < kRingLead; ++a) ring_fetch<R, NW>(p, ring, hp, own, n1, a);
+    stage_profiles<R, NW>(p, w, sm);
+    const long long lo = p.tile_rec_off[(long long)shot * p.ntiles + blockIdx.x];
+    const int nrl = (int)(p.tile_rec_off[(long long)shot * p.ntiles + blockIdx.x + 1] - lo);
     const int* rlist = p.tile_rec_idx + lo;
-    const unsigned rrange =
-        owned_range<RY>(rlist, nrl, p.rec_cell + (long long)shot * p.nrec, p.nx, c);
+    const int* rcells = p.rec_cell + (long long)shot * p.nrec;
+    int* srec = reinterpret_cast<int*>(sm + Gm::oRec);
     if (kStaged) {
-        // the receivers' window positions and the residual samples of this launch, so that
-        // the per-step injection reads shared memory only (nrl * (K + 1) <= kRecStage)
-        const int* rc = p.rec_cell + (long long)shot * p.nrec;
-        for (int e = tid; e < nrl; e += BX * BY) {
-            const int cell = __ldg(rc + __ldg(rlist + e));
-            s.rstage[kRecStage - 1 - e] =
-                __int_as_float((cell % p.nx - c.X0) | (cell / p.nx - c.Y0) << 8);
+        // positions, indices and the residual samples of this launch, so that the per-step
+        // injection reads shared memory only (nrl * (K + 2) <= kRecStage)
+        for (int e = tid; e < nrl; e += Gm::NT) {
+            const int ri = __ldg(rlist + e);
+            srec[e] = rec_position(p, __ldg(rcells + ri), w.X0, w.Y0);
+            srec[nrl + e] = ri;
         }
         const float* rb = p.resid + (long long)shot * p.nt * p.nrec;
-        for (int i = tid; i < nrl * K; i += BX * BY) {
+        for (int i = tid; i < nrl * K; i += Gm::NT) {
             const int e = i / K, st = i - e * K;
-            s.rstage[i] = __ldg(rb + (long long)(n1 - st) * p.nrec + __ldg(rlist + e));
+            srec[2 * nrl + i] =
+                __float_as_int(__ldg(rb + (long long)(n1 - st) * p.nrec + __ldg(rlist + e)));
         }
     }
     __syncthreads();
+    int rlo, rhi;
+    warp_rec_range<kStaged, R>(p, w, srec, rlist, rcells, nrl, rlo, rhi);
 
-    if (c.tile_strip)
-        adj_body<RY, BY, true, kStaged>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist,
-                                        shot);
+    if (w.tile_xs)
+        adj_steps<R, NW, true, kStaged>(p, w, sm, aez, ahx, ahy, ge, gs, hp, own, rlo, rhi, nrl,
+                                        rlist, shot);
     else
-        adj_body<RY, BY, false, kStaged>(p, c, s, aez, ahx, ahy, ystrip, interior, rrange, rlist,
-                                         shot);
+        adj_steps<R, NW, false, kStaged>(p, w, sm, aez, ahx, ahy, ge, gs, hp, own, rlo, rhi, nrl,
+                                         rlist, shot);
 
-    store_state<RY, BY>(p, c, s, sbase, aez, ahx, ahy, ystrip, interior);
-    const long long F = (long long)p.nshots * p.N;
+    store_state<R, NW>(p, w, sm, shot, aez, ahx, ahy);
+    if (w.lane_int) {
+        const long long F = (long long)p.nshots * p.Np;
+        const float se = -p.geps;
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-        if (!((interior >> r) & 1u)) continue;
-        const long long sg = sbase + (long long)(c.Y0 + c.ly0 + r) * p.nx + c.gx;
-        // one writer per cell per launch and launches in stream order: a fire-and-forget
-        // reduction is deterministic and hides the read latency of += at the end of the CTA
-        const int l = (c.ly0 + r) * BX + c.lx;
-        atomicAdd(p.grad + sg, s.coef[3 * PLANE + l]);
-        atomicAdd(p.grad + F + sg, s.coef[4 * PLANE + l]);
+        for (int r = 0; r < R; ++r) {
+            if (!((w.row_int >> r) & 1u)) continue;
+            float* g = p.grad + (long long)shot * p.Np + (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0;
+            // one writer per cell per launch and launches in stream order: a fire-and-forget
+            // reduction is deterministic and hides the read latency of += at the end of the CTA
+            atomicAdd(reinterpret_cast<float2*>(g), make_float2(se * ge[r].x, se * ge[r].y));
+            atomicAdd(reinterpret_cast<float2*>(g + F),
+                      make_float2(-0.5f * gs[r].x, -0.5f * gs[r].y));
+        }
     }
 }
 
@@ -626,75 +853,92 @@ cudaError_t allow_smem(Kern k, size_t optin) {
                                 (int)(optin - a.sharedSizeBytes));
 }
 
-template <int RY, int BY>
+template <int R, int NW>
 cudaError_t configure_variant(size_t optin) {
     cudaError_t e;
-    if ((e = allow_smem(fwd_tile_kernel<RY, BY, true, true>, optin))) return e;
-    if ((e = allow_smem(fwd_tile_kernel<RY, BY, true, false>, optin))) return e;
-    if ((e = allow_smem(fwd_tile_kernel<RY, BY, false, true>, optin))) return e;
-    if ((e = allow_smem(fwd_tile_kernel<RY, BY, false, false>, optin))) return e;
-    if ((e = allow_smem(adj_tile_kernel<RY, BY, true>, optin))) return e;
-    return allow_smem(adj_tile_kernel<RY, BY, false>, optin);
+#define GF_ALLOW(...) \
+    if ((e = allow_smem(__VA_ARGS__, optin)) != cudaSuccess) return e
+    GF_ALLOW(fwd_tile_kernel<R, NW, true, true, true>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, true, false, true>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, false, true, true>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, false, false, true>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, true, true, false>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, true, false, false>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, false, true, false>);
+    GF_ALLOW(fwd_tile_kernel<R, NW, false, false, false>);
+    GF_ALLOW(adj_tile_kernel<R, NW, true>);
+    GF_ALLOW(adj_tile_kernel<R, NW, false>);
+#undef GF_ALLOW
+    return cudaSuccess;
 }
 
-template <int RY, int BY>
-cudaError_t launch_fwd_variant(const TileParams& p, cudaStream_t st) {
-    const dim3 grid(p.ntiles, p.nshots), block(BX, BY);
-    const size_t smem = sizeof(float) * smem_floats(RY, BY);
-    if (p.hist && p.illum)
-        fwd_tile_kernel<RY, BY, true, true><<<grid, block, smem, st>>>(p);
-    else if (p.hist)
-        fwd_tile_kernel<RY, BY, true, false><<<grid, block, smem, st>>>(p);
-    else if (p.illum)
-        fwd_tile_kernel<RY, BY, false, true><<<grid, block, smem, st>>>(p);
+template <int R, int NW, bool kHist, bool kIllum>
+cudaError_t launch_fwd_variant(const TileParams& p, bool staged, cudaStream_t st) {
+    using Gm = G<R, NW>;
+    const dim3 grid(p.ntiles, p.nshots), block(Gm::NT);
+    const size_t smem = sizeof(float) * Gm::fwd_floats;
+    if (staged)
+        fwd_tile_kernel<R, NW, kHist, kIllum, true><<<grid, block, smem, st>>>(p);
     else
-        fwd_tile_kernel<RY, BY, false, false><<<grid, block, smem, st>>>(p);
+        fwd_tile_kernel<R, NW, kHist, kIllum, false><<<grid, block, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int RY, int BY>
-cudaError_t launch_adj_variant(const TileParams& p, cudaStream_t st) {
-    const dim3 grid(p.ntiles, p.nshots), block(BX, BY);
-    const size_t smem = sizeof(float) * smem_floats(RY, BY);
-    if (p.rec_staged)
-        adj_tile_kernel<RY, BY, true><<<grid, block, smem, st>>>(p);
-    else
-        adj_tile_kernel<RY, BY, false><<<grid, block, smem, st>>>(p);
-    return cudaGetLastError();
+template <int R, int NW>
+cudaError_t launch_fwd_r(const TileParams& p, bool staged, cudaStream_t st) {
+    if (p.hist && p.illum) return launch_fwd_variant<R, NW, true, true>(p, staged, st);
+    if (p.hist) return launch_fwd_variant<R, NW, true, false>(p, staged, st);
+    if (p.illum) return launch_fwd_variant<R, NW, false, true>(p, staged, st);
+    return launch_fwd_variant<R, NW, false, false>(p, staged, st);
 }
 
+template <int R, int NW>
+cudaError_t launch_adj_r(const TileParams& p, bool staged, cudaStream_t st) {
+    using Gm = G<R, NW>;
+    const dim3 grid(p.ntiles, p.nshots), block(Gm::NT);
+    const size_t smem = sizeof(float) * Gm::adj_floats;
+    if (staged)
+        adj_tile_kernel<R, NW, true><<<grid, block, smem, st>>>(p);
+    else
+        adj_tile_kernel<R, NW, false><<<grid, block, smem, st>>>(p);
+    return cudaGetLastError();
+}
 }  // namespace
 
-int max_tile_extent() { return BX; }
-int max_tile_height(int variant) { return variant == 3 ? 32 : 64; }
+int max_tile_extent() { return WX; }
+int max_tile_height(int variant) { return variant == 1 ? G<4, 8>::WY : 64; }
 int num_tile_variants() { return 3; }
 
 size_t tile_smem_bytes(int variant) {
-    return sizeof(float) * (variant == 0 ? smem_floats(4, 16)
-                            : variant == 1 ? smem_floats(8, 8)
-                                           : smem_floats(4, 8));
+    return sizeof(float) * (variant == 0   ? G<4, 16>::adj_floats
+                            : variant == 1 ? G<4, 8>::adj_floats
+                                           : G<8, 8>::adj_floats);
 }
 
 cudaError_t configure_tile_kernels(size_t optin) {
     cudaError_t e = configure_variant<4, 16>(optin);
     if (e != cudaSuccess) return e;
-    if ((e = configure_variant<8, 8>(optin)) != cudaSuccess) return e;
-    return configure_variant<4, 8>(optin);
+    if ((e = configure_variant<4, 8>(optin)) != cudaSuccess) return e;
+    return configure_variant<8, 8>(optin);
 }
 
-// Variant 0: 4 rows per thread, 1024 threads, 64 x 64 window; variant 1: 8 rows per thread,
-// 512 threads, 64 x 64; variant 3: 4 rows per thread, 512 threads, 64 x 32 window, two CTAs
-// per SM (one CTA's barrier waits and state loads overlap the other's work).
+// Variant 0: 4 rows per thread, 512 threads, 64 x 64 window, one CTA per SM; variant 1: 4 rows
+// per thread, 256 threads, 64 x 32 window, two CTAs per SM (one CTA's loads and barrier waits
+// overlap the other's work); variant 2: 8 rows per thread, 256 threads, 64 x 64.  Receiver
+// lists are staged in shared memory when the longest one fits (forward: 2 words per entry,
+// adjoint: K + 2), else read from global memory.
 cudaError_t launch_fwd_tile(const TileParams& p, int variant, cudaStream_t st) {
-    return variant == 0   ? launch_fwd_variant<4, 16>(p, st)
-           : variant == 1 ? launch_fwd_variant<8, 8>(p, st)
-                          : launch_fwd_variant<4, 8>(p, st);
+    const bool staged = 2LL * p.rec_max <= kRecStage;
+    return variant == 0   ? launch_fwd_r<4, 16>(p, staged, st)
+           : variant == 1 ? launch_fwd_r<4, 8>(p, staged, st)
+                          : launch_fwd_r<8, 8>(p, staged, st);
 }
 
 cudaError_t launch_adj_tile(const TileParams& p, int variant, cudaStream_t st) {
-    return variant == 0   ? launch_adj_variant<4, 16>(p, st)
-           : variant == 1 ? launch_adj_variant<8, 8>(p, st)
-                          : launch_adj_variant<4, 8>(p, st);
+    const bool staged = (long long)p.rec_max * (p.K + 2) <= kRecStage;
+    return variant == 0   ? launch_adj_r<4, 16>(p, staged, st)
+           : variant == 1 ? launch_adj_r<4, 8>(p, staged, st)
+                          : launch_adj_r<8, 8>(p, staged, st);
 }
 
 }  // namespace gf

@@ -98,9 +98,12 @@ def test_autotune_picks_a_valid_tiling_and_caches_it(dev, tmp_path):
     cache = str(tmp_path / "tune.txt")
     t1 = autotune(fd, t32(wl.eps_init, dev), t32(wl.sig_init, dev), wav, cache, probe_steps=24)
     assert os.path.exists(cache) and "nx=%d" % g.nx in open(cache).read()
-    # staged window: 64 x 64 (variants 0-2) or 64 x 32 (variant 3)
-    assert t1.steps >= 1 and t1.tile_w + 2 * t1.steps <= 64 and t1.variant in (0, 1, 2, 3)
-    assert t1.tile_h + 2 * t1.steps <= (32 if t1.variant == 3 else 64)
+    # staged window: 64 x 64 (variants 0, 2) or 64 x 32 (variant 1); even tile widths behind
+    # a left halo of the steps rounded up to even
+    kl = t1.steps + (t1.steps & 1)
+    assert t1.steps >= 1 and t1.tile_w % 2 == 0 and kl + t1.tile_w + t1.steps <= 64
+    assert t1.variant in (0, 1, 2)
+    assert t1.tile_h + 2 * t1.steps <= (32 if t1.variant == 1 else 64)
     fd2 = FDTD(g, wl.src, wl.rec, device=dev)
     t2 = autotune(fd2, t32(wl.eps_init, dev), t32(wl.sig_init, dev), wav, cache, probe_steps=24)
     assert t2 == t1
