@@ -111,11 +111,13 @@ int gf_workspace_size(const gf_ctx* ctx, int store_mode, int forward_only, size_
  * with cudaMalloc on first use (freed by gf_destroy).  ws == NULL reverts to that. */
 int gf_set_workspace(gf_ctx* ctx, void* ws, size_t bytes);
 
-/* Time-blocking options: tile interior width/height in cells and time steps per launch K.
- * The staged tile (interior + K cells of halo on each side) is at most 64 x 64 cells; K = 0
- * keeps the current K, a tile size of 0 selects the largest that fits (64 - 2K).  Default:
- * 50 x 50 interior, K = 7.  Returns GF_EINVAL (and keeps the old tiling) when the shape does
- * not fit. */
+/* Time-blocking options: tile interior width/height in cells and time steps per block K.
+ * A tile is advanced K steps at a time on a staged window of 64 x 64 cells (64 x 32 for
+ * variant 1): the interior plus a left halo of K rounded up to even (to a multiple of 4 for
+ * variant 3), a right halo of at least K and K rows above and below.  The tile width must be
+ * even (a multiple of 4, and tiles at least K wide and high, for variant 3).  K = 0 keeps the
+ * current K, a tile size of 0 selects the largest that fits.  Default: 48 x 50 interior,
+ * K = 7.  Returns GF_EINVAL (and keeps the old tiling) when the shape does not fit. */
 int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
 
 /* Select how gf_forward / gf_misfit_and_gradient keep the forward wavefield for the adjoint:
@@ -126,13 +128,15 @@ int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
  * segment boundaries group some sums differently).  Invalidates a stored forward. */
 int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
-/* Kernel variant: 0 = tile kernels with four rows per thread (1024-thread CTAs, 64 x 64
- * staged window, default), 1 = eight rows per thread (512-thread CTAs, 64 x 64), 2 =
- * barrier-free warp-march forward (64-column strips, 64-row chunks, at most 7 steps per
- * launch; the illumination output and the adjoint use the variant-0 tile kernels), 3 = four
- * rows per thread in 512-thread CTAs on a 64 x 32 window, two CTAs per SM (tile height + 2
- * steps <= 32; a taller current tile is shrunk to fit).  All compute the same result up to
- * FP32 rounding. */
+/* Kernel variant.  0-2: one kernel launch per time block, one CTA per (tile, shot): 0 = four
+ * rows per thread, 512-thread CTAs, 64 x 64 window; 1 = four rows per thread, 256-thread CTAs
+ * on a 64 x 32 window, two CTAs per SM (tile height + 2 steps <= 32; a taller current tile is
+ * shrunk to fit); 2 = eight rows per thread, 256-thread CTAs, 64 x 64.  3 (default) = the
+ * persistent dataflow kernels: one cooperative launch per pass, CTAs pulling (time block,
+ * shot, tile) items with per-tile completion counters and bounded waits (GF_ETIMEOUT from
+ * gf_status when one runs out), variant 0's window, the next item's state prefetched while
+ * the current one runs (the tile width is rounded down to a multiple of 4).  All compute the
+ * same result up to FP32 rounding. */
 int gf_set_variant(gf_ctx* ctx, int variant);
 
 /* Current tiling and variant (for autotuners). */
@@ -202,6 +206,13 @@ int gf_ricker(float* out, int nt, double dt, double f0, double amp);
 
 /* Number of kernels this context has launched since gf_create (all families). */
 long long gf_kernel_launches(const gf_ctx* ctx);
+
+/* Polls of one dependency wait of the persistent kernels (variant 3) before it gives up and
+ * records GF_ETIMEOUT (default 4194304, about a second; polls >= 0).  A wait that runs out
+ * ends its CTA; the results of that call are then undefined, the next call starts afresh.
+ * Fault-injection hook for tests: a budget of 0 makes any wait that is not already satisfied
+ * run out. */
+int gf_set_wait_budget(gf_ctx* ctx, long long polls);
 
 /* enable != 0: from now on bracket every kernel launch with CUDA events on its stream (no
  * synchronisation is added); enable == 0 stops and drops what was recorded. */

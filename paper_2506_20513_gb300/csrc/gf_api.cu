@@ -29,8 +29,8 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Offsets (bytes) of the workspace regions.
 struct Layout {
-    size_t status, partial, coef, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt, seg,
-        total;
+    size_t status, partial, coef, done, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt,
+        seg, total;
 };
 
 }  // namespace
@@ -42,19 +42,29 @@ struct gf_ctx {
     int pitch;                // row pitch of the internal planes (gf::row_pitch)
     long long Np;             // pitch * ny
     float* d_prof = nullptr;  // [12][max(nx, ny)] profiles (x: 6 arrays, y: 6 arrays)
-    int* d_src = nullptr;     // [nshots][nsrc]
-    int* d_rec = nullptr;     // [nshots][nrec]
+    int2* d_src_xy = nullptr;  // [nshots][nsrc] source cells (x, y)
     gf::AxisProfile px{}, py{};
     char* ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
     bool have_forward = false;
     int tile_w = 48, tile_h = 50, K = 7, variant = 0;
+    long long wait_budget = 1LL << 22;  // polls of one dependency wait (persistent kernels)
+    // tensor maps of the tile launches: state buffer -> maps (window height of the variant)
+    struct MapEntry {
+        const float* st = nullptr;
+        const float* coef = nullptr;
+        int wy = 0;
+        gf::TileMaps m;
+    };
+    MapEntry maps[4];
+    int maps_next = 0;
     int store_mode = GF_STORE_FULL, ckpt_k = 0;
     const float* last_wavelet = nullptr;  // wavelet of the stored forward (recomputation)
-    std::vector<int> h_rec;  // host copy of the receiver cells [nshots][nrec]
-    int* d_tile_rec_off = nullptr;  // per (shot, tile) receiver lists for the current tiling
-    int* d_tile_rec_idx = nullptr;
+    std::vector<int> h_rec;  // host copies of the receiver and source cells ([nshots][nrec],
+    std::vector<int> h_src;  // [nshots][nsrc], linear j * nx + i)
+    int4* d_tile_desc = nullptr;    // per (shot, tile) descriptors for the current tiling
+    int2* d_tile_rec = nullptr;     // their receiver entries
     int tile_rec_max = 0;           // longest per (shot, tile) list of the current tiling
     long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
@@ -203,6 +213,9 @@ Layout layout_of(const gf_ctx* c, bool forward_only) {
     L.status = o; o = align_up(o + sizeof(int));
     L.partial = o; o = align_up(o + sizeof(double) * kMisfitBlocks);
     L.coef = o; o = align_up(o + 2 * sizeof(float) * (size_t)c->Np);
+    const size_t ntiles = (size_t)((c->g.nx + c->tile_w - 1) / c->tile_w) *
+                          ((c->g.ny + c->tile_h - 1) / c->tile_h);
+    L.done = o; o = align_up(o + sizeof(int) * ntiles * (size_t)c->nshots);
     L.stA = o; o = align_up(o + gf::kNumFields * field);
     L.stB = o; o = align_up(o + gf::kNumFields * field);
     L.illum = o; o = align_up(o + field);
@@ -272,16 +285,16 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.rdy = (float)(1.0 / c->g.dy);
     p.px = c->px;
     p.py = c->py;
-    p.src_cell = c->d_src;
-    p.rec_cell = c->d_rec;
+    p.src_xy = c->d_src_xy;
     p.status = (int*)(c->ws + L.status);
     p.tile_w = c->tile_w;
     p.tile_h = c->tile_h;
     p.tiles_x = (c->g.nx + c->tile_w - 1) / c->tile_w;
     p.ntiles = p.tiles_x * ((c->g.ny + c->tile_h - 1) / c->tile_h);
-    p.tile_rec_off = c->d_tile_rec_off;
-    p.tile_rec_idx = c->d_tile_rec_idx;
+    p.tile_desc = c->d_tile_desc;
+    p.tile_rec = c->d_tile_rec;
     p.rec_max = c->tile_rec_max;
+    p.kl = gf::left_halo(c->K);
     p.hist_stride = c->g.nt;
     p.hist_slot0 = 0;
     return p;
@@ -301,33 +314,77 @@ int prepare_model(gf_ctx* c, const Layout& L, const float* eps_r, const float* s
 }
 
 
-// Forward launches for steps [n_begin, n_end) in blocks of at most K steps, ping-ponging
-// between buf[cur] and buf[cur ^ 1]; returns with cur pointing at the final state.
-int forward_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
-                  int n_end, cudaStream_t st) {
+// Tensor maps for a tile launch reading state buffer `st` (cached per buffer and variant).
+const gf::TileMaps* tile_maps(gf_ctx* c, const gf::TileParams& p, const float* st) {
+    const int wy = gf::max_tile_height(c->variant);
+    for (auto& e : c->maps)
+        if (e.st == st && e.coef == p.ca && e.wy == wy) return &e.m;
+    auto& e = c->maps[c->maps_next];
+    c->maps_next = (c->maps_next + 1) % 4;
+    e.st = nullptr;
+    if (!gf::make_tile_maps(&e.m, st, p.ca, c->pitch, c->g.ny, c->nshots, wy)) return nullptr;
+    e.st = st;
+    e.coef = p.ca;
+    e.wy = wy;
+    return &e.m;
+}
+
+// Forward steps [n_begin, n_end) in blocks of at most K steps, ping-ponging between buf[cur]
+// and buf[cur ^ 1]; returns with cur pointing at the final state.  The persistent variant runs
+// the whole range in one cooperative launch, the others launch once per block.
+int forward_steps(gf_ctx* c, const Layout& L, gf::TileParams& p, float* const buf[2], int& cur,
+                  int n_begin, int n_end, cudaStream_t st) {
+    if (n_end <= n_begin) return GF_OK;
+    if (c->variant == gf::kFlowVariant) {
+        int* done = (int*)(c->ws + L.done);
+        GF_CUDA(c, cudaMemsetAsync(done, 0, sizeof(int) * (size_t)p.ntiles * c->nshots, st), "clear counters");
+        p.K = c->K;
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] {
+                    return gf::launch_flow_pass(p, buf[cur], buf[cur ^ 1], done, n_begin, n_end - 1,
+                                                c->K, c->wait_budget, false, st);
+                }),
+                "fwd_flow");
+        cur ^= ((n_end - n_begin + c->K - 1) / c->K) & 1;
+        return GF_OK;
+    }
     for (int n0 = n_begin; n0 < n_end; n0 += c->K) {
         p.n0 = n0;
         p.K = std::min(c->K, n_end - n0);
-        p.kl = gf::left_halo(c->K);
         p.st_in = buf[cur];
         p.st_out = buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, c->variant, st); }), "fwd_tile");
+        const gf::TileMaps* m = tile_maps(c, p, buf[cur]);
+        if (!m) return fail(c, GF_ECUDA, "tensor maps of the tile kernels could not be encoded");
+        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] { return gf::launch_fwd_tile(p, *m, c->variant, st); }), "fwd_tile");
         cur ^= 1;
     }
     return GF_OK;
 }
 
-// Adjoint launches for steps n_end - 1 down to n_begin (reverse), K steps at most each.
-int adjoint_steps(gf_ctx* c, gf::TileParams& p, float* const buf[2], int& cur, int n_begin,
-                  int n_end, cudaStream_t st) {
+// Adjoint steps n_end - 1 down to n_begin (reverse), K steps at most per block.
+int adjoint_steps(gf_ctx* c, const Layout& L, gf::TileParams& p, float* const buf[2], int& cur,
+                  int n_begin, int n_end, cudaStream_t st) {
+    if (n_end <= n_begin) return GF_OK;
+    if (c->variant == gf::kFlowVariant) {
+        int* done = (int*)(c->ws + L.done);
+        GF_CUDA(c, cudaMemsetAsync(done, 0, sizeof(int) * (size_t)p.ntiles * c->nshots, st), "clear counters");
+        p.K = c->K;
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] {
+                    return gf::launch_flow_pass(p, buf[cur], buf[cur ^ 1], done, n_begin, n_end - 1,
+                                                c->K, c->wait_budget, true, st);
+                }),
+                "adj_flow");
+        cur ^= ((n_end - n_begin + c->K - 1) / c->K) & 1;
+        return GF_OK;
+    }
     for (int n1 = n_end - 1; n1 >= n_begin; n1 -= c->K) {
         const int k = std::min(c->K, n1 - n_begin + 1);
         p.n0 = n1 - k + 1;
         p.K = k;
-        p.kl = gf::left_halo(c->K);
         p.st_in = buf[cur];
         p.st_out = buf[cur ^ 1];
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, c->variant, st); }), "adj_tile");
+        const gf::TileMaps* m = tile_maps(c, p, buf[cur]);
+        if (!m) return fail(c, GF_ECUDA, "tensor maps of the tile kernels could not be encoded");
+        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] { return gf::launch_adj_tile(p, *m, c->variant, st); }), "adj_tile");
         cur ^= 1;
     }
     return GF_OK;
@@ -359,11 +416,11 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
             GF_CUDA(c, cudaMemcpyAsync(c->ws + L.ckpt + state * (size_t)j, st_buf[cur], state,
                                        cudaMemcpyDeviceToDevice, st),
                     "save checkpoint");
-            rc = forward_steps(c, p, st_buf, cur, n_begin, n_end, st);
+            rc = forward_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
             if (rc) return rc;
         }
     } else {
-        rc = forward_steps(c, p, st_buf, cur, 0, c->g.nt, st);
+        rc = forward_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
         if (rc) return rc;
     }
     if (illum)
@@ -413,14 +470,14 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
             q.hist_slot0 = n_begin - 1;
             p.hist_slot0 = n_begin - 1;
             int fcur = 0;
-            int rc = forward_steps(c, q, fw_buf, fcur, n_begin, n_end, st);
+            int rc = forward_steps(c, L, q, fw_buf, fcur, n_begin, n_end, st);
             if (rc) return rc;
-            rc = adjoint_steps(c, p, st_buf, cur, n_begin, n_end, st);
+            rc = adjoint_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
             if (rc) return rc;
         }
     } else {
         p.hist = (float*)(c->ws + L.hist);
-        int rc = adjoint_steps(c, p, st_buf, cur, 0, c->g.nt, st);
+        int rc = adjoint_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
         if (rc) return rc;
     }
     if (g_eps_r)
@@ -434,87 +491,107 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     return GF_OK;
 }
 
-// Receivers of every (shot, tile) staged window (interior plus a K-cell halo) as a CSR list
-// in (row, receiver index) order, uploaded for the kernels; rebuilt whenever the tiling
-// changes.  Written into *off / *idx (device, owned by the context).
-int build_receiver_lists(gf_ctx* c, int tw, int th, int K, int** off_out, int** idx_out,
-                         int* max_len) {
+// Per (shot, tile) descriptors of the tiling (tile_w x tile_h, K steps per block) for the
+// tile kernels: the receivers of the window [tx tw - K, tx tw + tw + K) x [ty th - K,
+// ty th + th + K) as entries {receiver index, (x - tx tw + 64) | (y - ty th + 64) << 16} in
+// (row, receiver index) order, and the mask of the shot's sources in that window.  Uploaded;
+// rebuilt whenever the tiling changes.
+int build_tile_tables(gf_ctx* c, int tw, int th, int K) {
     const int nx = c->g.nx, ny = c->g.ny;
     const int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th, nt_ = ntx * nty;
     std::vector<std::vector<int>> lists((size_t)c->nshots * nt_);
-    for (int s = 0; s < c->nshots; ++s)
+    std::vector<int> masks(lists.size(), 0);
+    auto windows = [&](int i, int j, auto&& visit) {
+        const int tx0 = std::max(0, (i - K) / tw - 1), tx1 = std::min(ntx - 1, (i + K) / tw);
+        const int ty0 = std::max(0, (j - K) / th - 1), ty1 = std::min(nty - 1, (j + K) / th);
+        for (int ty = ty0; ty <= ty1; ++ty)
+            for (int tx = tx0; tx <= tx1; ++tx)
+                if (i >= tx * tw - K && i < tx * tw + tw + K && j >= ty * th - K &&
+                    j < ty * th + th + K)
+                    visit(ty * ntx + tx);
+    };
+    for (int s = 0; s < c->nshots; ++s) {
         for (int r = 0; r < c->nrec; ++r) {
             const int cell = c->h_rec[(size_t)s * c->nrec + r];
-            const int i = cell % nx, j = cell / nx;
-            const int tx0 = std::max(0, (i - K) / tw - 1), tx1 = std::min(ntx - 1, (i + K) / tw);
-            const int ty0 = std::max(0, (j - K) / th - 1), ty1 = std::min(nty - 1, (j + K) / th);
-            for (int ty = ty0; ty <= ty1; ++ty)
-                for (int tx = tx0; tx <= tx1; ++tx)
-                    if (i >= tx * tw - K && i < tx * tw + tw + K && j >= ty * th - K &&
-                        j < ty * th + th + K)
-                        lists[(size_t)s * nt_ + ty * ntx + tx].push_back(r);
+            windows(cell % nx, cell / nx, [&](int t) { lists[(size_t)s * nt_ + t].push_back(r); });
         }
-    std::vector<int> off(lists.size() + 1, 0), idx;
+        for (int k = 0; k < c->nsrc; ++k) {
+            const int cell = c->h_src[(size_t)s * c->nsrc + k];
+            windows(cell % nx, cell / nx, [&](int t) { masks[(size_t)s * nt_ + t] |= 1 << k; });
+        }
+    }
+    std::vector<int4> desc(lists.size());
+    std::vector<int2> ents;
+    int longest = 0;
     for (size_t k = 0; k < lists.size(); ++k) {
         const int* cells = c->h_rec.data() + (k / nt_) * c->nrec;
+        const int t = (int)(k % nt_), tx = t % ntx, ty = t / ntx;
         std::stable_sort(lists[k].begin(), lists[k].end(),
                          [&](int a, int b) { return cells[a] / nx < cells[b] / nx; });
-        off[k + 1] = off[k] + (int)lists[k].size();
-        idx.insert(idx.end(), lists[k].begin(), lists[k].end());
+        desc[k] = make_int4((int)ents.size(), (int)lists[k].size(), masks[k], 0);
+        for (int r : lists[k]) {
+            const int x = cells[r] % nx - tx * tw + 64, y = cells[r] / nx - ty * th + 64;
+            ents.push_back(make_int2(r, x | y << 16));
+        }
+        longest = std::max(longest, (int)lists[k].size());
     }
-    if (max_len) {
-        *max_len = 0;
-        for (const auto& l : lists) *max_len = std::max(*max_len, (int)l.size());
-    }
-    if (idx.empty()) idx.push_back(0);
-    int *d_off = nullptr, *d_idx = nullptr;
-    cudaError_t e = cudaMalloc(&d_off, off.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&d_idx, idx.size() * sizeof(int));
+    if (ents.empty()) ents.push_back(make_int2(0, 0));
+    int4* d_desc = nullptr;
+    int2* d_ents = nullptr;
+    cudaError_t e = cudaMalloc(&d_desc, desc.size() * sizeof(int4));
+    if (e == cudaSuccess) e = cudaMalloc(&d_ents, ents.size() * sizeof(int2));
     if (e == cudaSuccess)
-        e = cudaMemcpy(d_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(d_ents, ents.data(), ents.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(d_off);
-        cudaFree(d_idx);
-        return cuda_fail(c, e, "receiver lists");
+        cudaFree(d_desc);
+        cudaFree(d_ents);
+        return cuda_fail(c, e, "tile tables");
     }
-    cudaFree(*off_out);
-    cudaFree(*idx_out);
-    *off_out = d_off;
-    *idx_out = d_idx;
+    cudaFree(c->d_tile_desc);
+    cudaFree(c->d_tile_rec);
+    c->d_tile_desc = d_desc;
+    c->d_tile_rec = d_ents;
+    c->tile_rec_max = longest;
     return GF_OK;
-}
-
-int build_all_receiver_lists(gf_ctx* c, int tw, int th, int K) {
-    return build_receiver_lists(c, tw, th, K, &c->d_tile_rec_off, &c->d_tile_rec_idx,
-                                &c->tile_rec_max);
 }
 
 // A tiling fits a variant's staged window: left halo left_halo(K) + tile_w + K columns within
 // the window width, tile_h + 2K rows within its height; tile_w even (the window starts on an
-// even column, so that column pairs are 8-byte aligned).
+// even column, so that column pairs are 8-byte aligned).  The persistent variant also needs
+// tile_w a multiple of 4 (16-byte chunks), tiles at least K wide and high (a window only
+// reaches the eight neighbouring tiles) and its shared memory within the limit.
 int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
-    if (variant < 0 || variant >= gf::num_tile_variants())
+    if (variant < 0 || variant >= gf::kNumVariants)
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
-    const int E = gf::max_tile_extent(), Eh = gf::max_tile_height(variant);
-    if (K < 1 || K > gf::kMaxK || tw < 2 || (tw & 1) || th < 1 ||
-        gf::left_halo(K) + tw + K > E || th + 2 * K > Eh)
+    const bool flow = variant == gf::kFlowVariant;
+    const int E = gf::max_tile_extent(), Eh = flow ? 64 : gf::max_tile_height(variant);
+    const int kl = gf::left_halo(K);
+    if (K < 1 || K > gf::kMaxK || tw < 4 || (tw & 3) || th < 1 || kl + tw + K > E ||
+        th + 2 * K > Eh || (flow && (tw < K || th < K)))
         return fail(c, GF_EINVAL,
-                    "tile %dx%d with %d steps per launch: need an even tile width with "
-                    "%d + width + steps <= %d and height + 2*steps <= %d (steps <= %d)",
-                    tw, th, K, gf::left_halo(K), E, Eh, gf::kMaxK);
-    if (gf::tile_smem_bytes(variant) > c->smem_optin)
-        return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)",
-                    gf::tile_smem_bytes(variant), c->smem_optin);
+                    "tile %dx%d with %d steps per launch: need a tile width that is a multiple of "
+                    "4 with %d + width + steps <= %d and height + 2*steps <= %d (steps <= %d)%s",
+                    tw, th, K, kl, E, Eh, gf::kMaxK, flow ? ", width and height >= steps" : "");
+    const size_t need = flow ? gf::flow_smem_bytes(tw, th) : gf::tile_smem_bytes(variant, tw, th);
+    if (need > c->smem_optin)
+        return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)", need,
+                    c->smem_optin);
     return GF_OK;
 }
 
-// Default tile of a variant for K steps per launch: the widest even tile and the tallest one.
-void default_tile(int variant, int K, int* tw, int* th) {
-    *tw = (gf::max_tile_extent() - gf::left_halo(K) - K) & ~1;
-    *th = gf::max_tile_height(variant) - 2 * K;
+// Default tile of a variant for K steps per launch: the widest tile and the tallest one whose
+// shared memory (the adjoint's wavefield ring grows with the tile) fits.
+void default_tile(const gf_ctx* c, int variant, int K, int* tw, int* th) {
+    const bool flow = variant == gf::kFlowVariant;
+    *tw = (gf::max_tile_extent() - gf::left_halo(K) - K) & ~3;
+    *th = (flow ? 64 : gf::max_tile_height(variant)) - 2 * K;
+    auto need = [&] {
+        return flow ? gf::flow_smem_bytes(*tw, *th) : gf::tile_smem_bytes(variant, *tw, *th);
+    };
+    while (*th > K && need() > c->smem_optin) --*th;
 }
 
 }  // namespace
@@ -588,6 +665,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->pitch = gf::row_pitch(g.nx);
     c->Np = (long long)c->pitch * g.ny;
     c->h_rec = rec;
+    c->h_src = src;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)optin;
@@ -596,15 +674,15 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     axis_profiles(g, g.nx, g.dx, prof.data(), stride);
     axis_profiles(g, g.ny, g.dy, prof.data() + 6 * (size_t)stride, stride);
     cudaError_t e = cudaMalloc(&c->d_prof, prof.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_src, src.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_rec, rec.size() * sizeof(int));
+    std::vector<int2> sxy(src.size());
+    for (size_t k = 0; k < src.size(); ++k) sxy[k] = make_int2(src[k] % g.nx, src[k] / g.nx);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_src_xy, sxy.size() * sizeof(int2));
     if (e == cudaSuccess)
         e = cudaMemcpy(c->d_prof, prof.data(), prof.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_src, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(c->d_rec, rec.data(), rec.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(c->d_src_xy, sxy.data(), sxy.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = gf::configure_tile_kernels((size_t)optin);
+    if (e == cudaSuccess) e = gf::configure_flow_kernels((size_t)optin);
     if (e != cudaSuccess) {
         cudaGetLastError();
         create_fail("gf_create: CUDA setup failed: %s", cudaGetErrorString(e));
@@ -616,7 +694,7 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
     c->px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     c->py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
     if (check_tiling(c, c->tile_w, c->tile_h, c->K, c->variant) != GF_OK ||
-        build_all_receiver_lists(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
+        build_tile_tables(c, c->tile_w, c->tile_h, c->K) != GF_OK) {
         create_fail("gf_create: %s", c->err);
         gf_destroy(c);
         return GF_EINVAL;
@@ -632,10 +710,9 @@ void gf_destroy(gf_ctx* c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->ws_owned && c->ws) cudaFree(c->ws);
     cudaFree(c->d_prof);
-    cudaFree(c->d_src);
-    cudaFree(c->d_rec);
-    cudaFree(c->d_tile_rec_off);
-    cudaFree(c->d_tile_rec_idx);
+    cudaFree(c->d_src_xy);
+    cudaFree(c->d_tile_desc);
+    cudaFree(c->d_tile_rec);
     delete c;
 }
 
@@ -672,13 +749,13 @@ int gf_set_tiling(gf_ctx* c, int tile_w, int tile_h, int K) {
     ++c->generation;
     const int k = K > 0 ? K : c->K;
     int tw, th;
-    default_tile(c->variant, k, &tw, &th);
+    default_tile(c, c->variant, k, &tw, &th);
     if (tile_w > 0) tw = tile_w;
     if (tile_h > 0) th = tile_h;
     int rc = check_tiling(c, tw, th, k, c->variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_all_receiver_lists(c, tw, th, k);
+    rc = build_tile_tables(c, tw, th, k);
     if (rc) return rc;
     c->tile_w = tw;
     c->tile_h = th;
@@ -709,17 +786,19 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
 int gf_set_variant(gf_ctx* c, int variant) {
     if (!c) return GF_EINVAL;
     ++c->generation;
-    if (variant < 0 || variant >= gf::num_tile_variants())
+    if (variant < 0 || variant >= gf::kNumVariants)
         return fail(c, GF_EINVAL, "kernel variant %d does not exist", variant);
     // a tile taller than the variant's window is shrunk to the largest that fits
-    int th = c->tile_h;
-    const int Eh = gf::max_tile_height(variant);
+    const bool flow = variant == gf::kFlowVariant;
+    int th = c->tile_h, tw = c->tile_w;
+    const int Eh = flow ? 64 : gf::max_tile_height(variant);
     if (th + 2 * c->K > Eh) th = Eh - 2 * c->K;
-    int rc = check_tiling(c, c->tile_w, th, c->K, variant);
+    int rc = check_tiling(c, tw, th, c->K, variant);
     if (rc) return rc;
     DeviceGuard guard(c->device);
-    rc = build_all_receiver_lists(c, c->tile_w, th, c->K);
+    rc = build_tile_tables(c, tw, th, c->K);
     if (rc) return rc;
+    c->tile_w = tw;
     c->tile_h = th;
     c->variant = variant;
     return GF_OK;
@@ -842,11 +921,19 @@ int gf_status(gf_ctx* c, void* stream) {
     GF_CUDA(c, cudaMemset(c->ws, 0, sizeof(int)), "clear status");
     if (s & gf::kStatusBadModel)
         return fail(c, GF_EINVAL, "model has eps_r < 1, sigma < 0 or non-finite values");
+    if (s & gf::kStatusTimeout)
+        return fail(c, GF_ETIMEOUT, "a dependency wait of the persistent kernels ran out");
     if (s & gf::kStatusNonFinite) return fail(c, GF_ENONFINITE, "non-finite traces or gradients");
     return GF_OK;
 }
 
 long long gf_kernel_launches(const gf_ctx* c) { return c ? c->launches : 0; }
+
+int gf_set_wait_budget(gf_ctx* c, long long polls) {
+    if (!c || polls < 0) return GF_EINVAL;
+    c->wait_budget = polls;
+    return GF_OK;
+}
 
 int gf_profile(gf_ctx* c, int enable) {
     if (!c) return GF_EINVAL;
@@ -918,7 +1005,7 @@ int forward_prefix(gf_ctx* c, const float* eps_r, const float* sigma, const floa
     rc = prepare_model(c, L, eps_r, sigma, st);
     if (rc) return rc;
     int cur = 0;
-    return forward_steps(c, p, st_buf, cur, 0, std::min(nsteps, c->g.nt), st);
+    return forward_steps(c, L, p, st_buf, cur, 0, std::min(nsteps, c->g.nt), st);
 }
 
 std::string tune_key(const gf_ctx* c) {
@@ -976,9 +1063,10 @@ int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     }
     struct Cand { int variant, K; };
     std::vector<Cand> cands;
-    for (int v = 0; v < 2; ++v)
+    for (int v : {gf::kFlowVariant, 0})
         for (int K : {4, 5, 6, 7, 8, 10}) cands.push_back({v, K});
-    for (int K : {3, 4, 5, 6}) cands.push_back({2, K});
+    for (int K : {3, 4, 5, 6}) cands.push_back({1, K});
+    for (int K : {5, 7}) cands.push_back({2, K});
     const int steps = probe_steps > 0 ? probe_steps : 48;
     cudaEvent_t e0, e1;
     GF_CUDA(c, cudaEventCreate(&e0), "event");

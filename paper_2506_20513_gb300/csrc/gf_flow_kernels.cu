@@ -1,0 +1,437 @@
+// gf_flow_kernels.cu -- persistent dataflow kernels of the 2-D TM FDTD forward and adjoint
+// passes (sm_103a): one cooperative launch runs a whole pass (every time block of every tile
+// of every shot) instead of one launch per time block.
+//
+// Work items are (block b, shot, tile) in block-major order; CTA c takes items c, c + G,
+// c + 2G, .. (G = grid size, every CTA resident: cooperative launch).  Block b of a tile reads
+// the state after b blocks from buffer b % 2 and writes the state after b + 1 blocks to buffer
+// (b + 1) % 2, so it may start once the tile and its eight neighbours have completed b blocks:
+// their block b - 1 outputs are then written, and their block b - 1 reads of the buffer it
+// overwrites are over.  done[shot][tile] counts a tile's completed blocks (release: stores,
+// fence, barrier, fence, atomic add; acquire: load.acquire, barrier).  Since an item only waits
+// for items earlier in the order and every CTA takes its items in order, the earliest
+// unfinished item can always run: the schedule cannot deadlock.  Every wait polls at most
+// `budget` times, then records kStatusTimeout in the status word and ends the CTA; CTAs
+// waiting for it then run out of budget too, so a pass always ends.
+//
+// While a CTA computes item i it prefetches the state of its next item (16-byte cp.async
+// through L2: the data were written by other CTAs of this launch) and, once the current item
+// no longer reads them, the next item's update coefficients, so that an item starts without
+// a round trip to memory.  The time steps themselves are those of gf_tile_common.cuh.
+#include "gf_tile_common.cuh"
+
+namespace gf {
+namespace {
+
+struct FlowArgs {
+    float* buf0;          // ping-pong state buffers [kNumFields][nshots][Np]
+    float* buf1;
+    int* done;            // [nshots][ntiles] completed blocks (zero at launch)
+    int n_first, n_last;  // steps of the pass (the adjoint runs them in reverse)
+    int kb;               // steps per block
+    int nblocks;
+    long long budget;     // polls of one dependency wait
+};
+
+// One work item.
+struct Item {
+    int b, shot, tile, n0, K;
+};
+
+__device__ __forceinline__ Item decode(const TileParams& p, const FlowArgs& f, int i,
+                                       bool reverse) {
+    Item it;
+    const int ipb = p.nshots * p.ntiles;
+    it.b = i / ipb;
+    const int rem = i - it.b * ipb;
+    it.shot = rem / p.ntiles;
+    it.tile = rem - it.shot * p.ntiles;
+    if (!reverse) {
+        it.n0 = f.n_first + it.b * f.kb;
+        it.K = min(f.kb, f.n_last + 1 - it.n0);
+    } else {
+        const int n1 = f.n_last - it.b * f.kb;
+        it.n0 = max(f.n_first, n1 - f.kb + 1);
+        it.K = n1 - it.n0 + 1;
+    }
+    return it;
+}
+
+__device__ __forceinline__ int load_acquire(const int* a) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];\n" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+// Have the tile of `it` and its neighbours completed it.b blocks?  Called by all lanes of
+// warp 0: lane k < 9 watches neighbour (k % 3 - 1, k / 3 - 1), so the counters are read in
+// parallel.  poll = false: look once; poll = true: wait, at most `budget` polls (false when
+// the budget ran out).
+__device__ __forceinline__ bool warp_deps_done(const TileParams& p, const FlowArgs& f,
+                                               const Item& it, bool poll) {
+    const int lane = threadIdx.x & 31;
+    const int tx = it.tile % p.tiles_x + lane % 3 - 1, ty = it.tile / p.tiles_x + lane / 3 - 1;
+    const int nty = p.ntiles / p.tiles_x;
+    bool ok = true;
+    if (it.b > 0 && lane < 9 && tx >= 0 && tx < p.tiles_x && ty >= 0 && ty < nty) {
+        const int* a = f.done + (long long)it.shot * p.ntiles + ty * p.tiles_x + tx;
+        long long polls = 0;
+        while (load_acquire(a) < it.b) {
+            if (!poll || ++polls > f.budget) {
+                ok = false;
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    return __all_sync(kFull, ok);
+}
+
+// Blocking wait of the whole CTA for the dependencies of `it`; false (CTA-uniform) when the
+// wait gave up, after recording the timeout.
+template <int R, int NW>
+__device__ __forceinline__ bool cta_wait_deps(const TileParams& p, const FlowArgs& f,
+                                              const Item& it, float* sm) {
+    volatile int* flag = reinterpret_cast<volatile int*>(sm + G<R, NW>::oFlag);
+    if (threadIdx.x < 32) {
+        const bool ok = warp_deps_done(p, f, it, true);
+        if (threadIdx.x == 0) {
+            if (!ok) atomicOr(p.status, kStatusTimeout);
+            flag[1] = ok ? 0 : 1;
+        }
+    }
+    __syncthreads();
+    return flag[1] == 0;
+}
+
+// Warp 0 records in flag[0] whether the next item nx (if `valid`) may be prefetched now;
+// read after the next barrier.
+__device__ __forceinline__ void note_ready(const TileParams& p, const FlowArgs& f, const Item& nx,
+                                          bool valid, volatile int* flag) {
+    if (threadIdx.x < 32) {
+        const bool ok = valid && warp_deps_done(p, f, nx, false);
+        if (threadIdx.x == 0) flag[0] = ok ? 1 : 0;
+    }
+}
+
+// Publish the completion of `it` (after its stores): barrier, then one thread fences (at GPU
+// scope, cumulative over the stores the barrier ordered before it) and bumps the counter.
+template <int R, int NW>
+__device__ __forceinline__ void publish(const TileParams& p, const FlowArgs& f, const Item& it) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(f.done + (long long)it.shot * p.ntiles + it.tile, 1);
+    }
+}
+
+// Prefetch the state of item `it` (Ez, Hx, Hy or their adjoints; the whole 64 x WY window,
+// zero outside the grid) into the staging planes, 16-byte chunks shared out over the CTA
+// (window origin and row pitch are multiples of 4 floats).  One cp.async group (with the
+// coefficients when kCoef).
+template <int R, int NW>
+__device__ __forceinline__ void prefetch_state(const TileParams& p, const FlowArgs& f,
+                                               float* sm, const Item& it) {
+    using Gm = G<R, NW>;
+    const float* st = (it.b & 1) ? f.buf1 : f.buf0;
+    const long long F = (long long)p.nshots * p.Np;
+    const int tx = it.tile % p.tiles_x, ty = it.tile / p.tiles_x;
+    const int X0 = tx * p.tile_w - p.kl, Y0 = ty * p.tile_h - it.K;
+    const float* base = st + (long long)it.shot * p.Np;
+    float* stage = sm + Gm::oStage;
+    constexpr int kChunks = 3 * Gm::WY * 16;
+    for (int c = threadIdx.x; c < kChunks; c += Gm::NT) {
+        const int field = c / (Gm::WY * 16), rem = c - field * Gm::WY * 16;
+        const int row = rem >> 4, q = rem & 15;
+        const int gy = Y0 + row, gx = X0 + 4 * q;
+        const bool ok = gy >= 0 && gy < p.ny && gx >= 0 && gx < p.pitch;
+        const float* src = ok ? base + field * F + (long long)gy * p.pitch + gx : st;
+        cp_async16cg(stage + field * 2 * Gm::PL + row * WX + 4 * q, src, ok ? 16 : 0);
+    }
+}
+
+// Prefetch the update coefficients of the thread's own cells of item `it` into the two
+// planes (Ca, Cb) at coef_off, zero outside the grid.
+template <int R, int NW>
+__device__ __forceinline__ void prefetch_coef(const TileParams& p, float* sm, int coef_off,
+                                              const Item& it) {
+    const Pos<R> w = position<R>(p, it.tile, it.K);
+    float2* coef = reinterpret_cast<float2*>(sm + coef_off) + w.ly0 * 32 + w.lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool in = w.lane_in && ((w.row_in >> r) & 1u);
+        const long long m = in ? (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0 : 0;
+        cp_async8(coef + r * 32, p.ca + m, in ? 8 : 0);
+        cp_async8(coef + G<R, NW>::PL + r * 32, p.cb + m, in ? 8 : 0);
+    }
+}
+
+// The state of the thread's cells from the staging planes.
+template <int R, int NW>
+__device__ __forceinline__ void unstage_state(const Pos<R>& w, const float* sm, float2 (&f0)[R],
+                                              float2 (&f1)[R], float2 (&f2)[R]) {
+    using Gm = G<R, NW>;
+    const float2* s = reinterpret_cast<const float2*>(sm + Gm::oStage) + w.ly0 * 32 + w.lane;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        f0[r] = s[r * 32];
+        f1[r] = s[Gm::PL + r * 32];
+        f2[r] = s[2 * Gm::PL + r * 32];
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Forward pass
+// ---------------------------------------------------------------------------------------
+template <int R, int NW, bool kHist, bool kIllum, bool kStaged>
+__global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p, const FlowArgs f) {
+    using Gm = G<R, NW>;
+    extern __shared__ float4 smem_raw[];
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
+    const int total = f.nblocks * p.nshots * p.ntiles;
+    int i = blockIdx.x;
+    if (i >= total) return;
+    Item it = decode(p, f, i, false);
+    if (!cta_wait_deps<R, NW>(p, f, it, sm)) return;
+    prefetch_state<R, NW>(p, f, sm, it);
+    prefetch_coef<R, NW>(p, sm, Gm::oCoef2, it);
+    cp_async_commit();
+    for (; i < total; i += gridDim.x) {
+        const int j = i + gridDim.x;
+        const bool more = j < total;
+        const Item nx = decode(p, f, more ? j : i, false);
+        const Pos<R> w = position<R>(p, it.tile, it.K);
+        cp_async_wait<0>();
+        __syncthreads();  // item i's staged state and coefficients have landed
+        note_ready(p, f, nx, more, flag);
+        const bool strip = tile_in_strip<R>(p, w, it.K);
+        const float* st_in = (it.b & 1) ? f.buf1 : f.buf0;
+        float* st_out = (it.b & 1) ? f.buf0 : f.buf1;
+        TileLoads<R> L;
+        issue_loads<R, NW, false, false, true, true, true>(p, w, st_in, it.shot, it.tile, it.n0, it.K,
+                                                     strip, L);
+        float2 ez[R], hx[R], hy[R], ill[R];
+        unstage_state<R, NW>(w, sm, ez, hx, hy);
+        {
+            float2* c = reinterpret_cast<float2*>(sm + Gm::oCoef) + w.ly0 * 32 + w.lane;
+            const float2* c2 = reinterpret_cast<const float2*>(sm + Gm::oCoef2) + w.ly0 * 32 + w.lane;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                c[r * 32] = c2[r * 32];
+                c[Gm::PL + r * 32] = c2[Gm::PL + r * 32];
+                ill[r] = make_float2(0.f, 0.f);
+            }
+        }
+        store_loads<R, NW, false, true, true>(p, w, sm, it.K, strip, L);
+        const int nrl = L.d.y;
+        const int2* ents = stage_receivers<R, NW, kStaged, false>(p, sm, it.shot, L.d, 0, it.K);
+        __syncthreads();
+        const bool ahead = flag[0] != 0;
+        if (ahead) {  // the staging planes are free: fetch the next item during this one
+            prefetch_state<R, NW>(p, f, sm, nx);
+            prefetch_coef<R, NW>(p, sm, Gm::oCoef2, nx);
+            cp_async_commit();
+        }
+        int rlo, rhi;
+        warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl,
+                                   it.K, rlo, rhi);
+        const bool srcany = thread_has_source<R, NW>(p, w, sm);
+        if (w.tile_xs)
+            fwd_steps<R, NW, true, kHist, kIllum, kStaged>(p, w, sm, it.shot, it.n0, it.K, ez, hx,
+                                                           hy, ill, rlo, rhi, nrl, ents, srcany);
+        else
+            fwd_steps<R, NW, false, kHist, kIllum, kStaged>(p, w, sm, it.shot, it.n0, it.K, ez, hx,
+                                                            hy, ill, rlo, rhi, nrl, ents, srcany);
+        store_state<R, NW>(p, w, sm, st_out, it.shot, ez, hx, hy);
+        if (kIllum) add_illumination<R>(p, w, it.shot, ill);
+        publish<R, NW>(p, f, it);
+        if (!ahead && more) {
+            if (!cta_wait_deps<R, NW>(p, f, nx, sm)) break;
+            prefetch_state<R, NW>(p, f, sm, nx);
+            prefetch_coef<R, NW>(p, sm, Gm::oCoef2, nx);
+            cp_async_commit();
+        }
+        it = nx;
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------------
+// Adjoint pass
+// ---------------------------------------------------------------------------------------
+template <int R, int NW, bool kStaged>
+__global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p, const FlowArgs f) {
+    using Gm = G<R, NW>;
+    extern __shared__ float4 smem_raw[];
+    float* sm = reinterpret_cast<float*>(smem_raw);
+    volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
+    const int total = f.nblocks * p.nshots * p.ntiles;
+    int i = blockIdx.x;
+    if (i >= total) return;
+    Item it = decode(p, f, i, true);
+    if (!cta_wait_deps<R, NW>(p, f, it, sm)) return;
+    prefetch_state<R, NW>(p, f, sm, it);
+    prefetch_coef<R, NW>(p, sm, Gm::oCoef, it);
+    cp_async_commit();
+    for (; i < total; i += gridDim.x) {
+        const int j = i + gridDim.x;
+        const bool more = j < total;
+        const int K = it.K, n1 = it.n0 + K - 1;
+        const Pos<R> w = position<R>(p, it.tile, K);
+        cp_async_wait<0>();
+        __syncthreads();  // item i's staged state and coefficients have landed
+        // (the next item is decoded where it is needed: holding it through the time steps
+        // would cost registers)
+        note_ready(p, f, decode(p, f, more ? j : i, true), more, flag);
+        float2 aez[R], ahx[R], ahy[R], ge[R], gs[R];
+        const float* hp = p.hist + ((long long)it.shot * p.hist_stride - p.hist_slot0) * p.Np +
+                          (long long)(w.Y0 + w.ly0) * p.pitch + w.gx0;
+        bool own[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            own[r] = w.lane_int && ((w.row_int >> r) & 1u);
+            ge[r] = gs[r] = make_float2(0.f, 0.f);
+        }
+        const Ring rg = make_ring<R, NW>(p, w, sm, Gm::adj_ring_off, K);
+        for (int a = -1; a < kRingLead; ++a) ring_fetch<R>(p, rg, hp, own, n1, K, a);
+        const bool strip = tile_in_strip<R>(p, w, K);
+        const float* st_in = (it.b & 1) ? f.buf1 : f.buf0;
+        float* st_out = (it.b & 1) ? f.buf0 : f.buf1;
+        TileLoads<R> L;
+        issue_loads<R, NW, false, false, true, true, false>(p, w, st_in, it.shot, it.tile, it.n0, K,
+                                                      strip, L);
+        unstage_state<R, NW>(w, sm, aez, ahx, ahy);
+        store_loads<R, NW, false, true, false>(p, w, sm, K, strip, L);
+        const int nrl = L.d.y;
+        const int2* ents = stage_receivers<R, NW, kStaged, true>(p, sm, it.shot, L.d, n1, K);
+        __syncthreads();
+        const bool ahead = flag[0] != 0;
+        int rlo, rhi;
+        warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl,
+                                   K, rlo, rhi);
+        // after phase A 0 the staging planes are free: fetch the next item's state; after the
+        // last phase A this item no longer reads its coefficients: fetch the next item's
+        auto after_a = [&](int a) {
+            if (!more) return;
+            if (a == 0 && ahead) {
+                prefetch_state<R, NW>(p, f, sm, decode(p, f, j, true));
+                cp_async_commit();
+            }
+            if (a == K - 1) {
+                prefetch_coef<R, NW>(p, sm, Gm::oCoef, decode(p, f, j, true));
+                cp_async_commit();
+            }
+        };
+        if (w.tile_xs)
+            adj_steps<R, NW, true, kStaged>(p, w, sm, it.shot, it.n0, K, aez, ahx, ahy, ge, gs, hp,
+                                            own, rg, rlo, rhi, nrl, ents, after_a);
+        else
+            adj_steps<R, NW, false, kStaged>(p, w, sm, it.shot, it.n0, K, aez, ahx, ahy, ge, gs,
+                                             hp, own, rg, rlo, rhi, nrl, ents, after_a);
+        store_state<R, NW>(p, w, sm, st_out, it.shot, aez, ahx, ahy);
+        add_gradients<R>(p, w, it.shot, ge, gs);
+        publish<R, NW>(p, f, it);
+        if (!more) break;
+        it = decode(p, f, j, true);
+        if (!ahead) {
+            if (!cta_wait_deps<R, NW>(p, f, it, sm)) break;
+            prefetch_state<R, NW>(p, f, sm, it);
+            cp_async_commit();
+        }
+    }
+    cp_async_wait<0>();
+}
+
+template <class Kern>
+cudaError_t allow_flow_smem(Kern k, size_t optin) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, k);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(optin - a.sharedSizeBytes));
+}
+
+template <class Kern>
+cudaError_t launch_flow(Kern k, const TileParams& p, const FlowArgs& f, int threads, size_t smem,
+                        cudaStream_t st) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long total = (long long)f.nblocks * p.nshots * p.ntiles;
+    const int grid = (int)(total < (long long)sms * per_sm ? total : (long long)sms * per_sm);
+    TileParams pc = p;
+    FlowArgs fc = f;
+    void* args[] = {&pc, &fc};
+    return cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(threads), args, smem, st);
+}
+
+template <int R, int NW, bool kHist, bool kIllum>
+cudaError_t launch_fwd_flow_v(const TileParams& p, const FlowArgs& f, bool staged, cudaStream_t st) {
+    using Gm = G<R, NW>;
+    const size_t smem = sizeof(float) * Gm::fwd_flow_floats;
+    if (staged) return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, true>, p, f, Gm::NT, smem, st);
+    return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, false>, p, f, Gm::NT, smem, st);
+}
+
+}  // namespace
+
+size_t flow_smem_bytes(int tile_w, int tile_h) {
+    using Gm = G<4, 16>;
+    const size_t f = sizeof(float) * Gm::fwd_flow_floats;
+    const size_t a = sizeof(float) * (Gm::adj_ring_off + (size_t)kRing * tile_w * tile_h);
+    return f > a ? f : a;
+}
+
+cudaError_t configure_flow_kernels(size_t optin) {
+    cudaError_t e;
+#define GF_ALLOW(...) \
+    if ((e = allow_flow_smem(__VA_ARGS__, optin)) != cudaSuccess) return e
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, false>);
+    GF_ALLOW(adj_flow_kernel<4, 16, true>);
+    GF_ALLOW(adj_flow_kernel<4, 16, false>);
+#undef GF_ALLOW
+    return cudaSuccess;
+}
+
+// One cooperative launch for the forward steps [n_first, n_last] (blocks of kb steps) or, with
+// `adjoint`, the adjoint steps n_last down to n_first; the pass starts from buf0 and ends in
+// buf[nblocks % 2].  done must hold nshots * ntiles zeros.
+cudaError_t launch_flow_pass(const TileParams& p, float* buf0, float* buf1, int* done,
+                             int n_first, int n_last, int kb, long long budget, bool adjoint,
+                             cudaStream_t st) {
+    FlowArgs f;
+    f.buf0 = buf0;
+    f.buf1 = buf1;
+    f.done = done;
+    f.n_first = n_first;
+    f.n_last = n_last;
+    f.kb = kb;
+    f.nblocks = (n_last - n_first + kb) / kb;
+    f.budget = budget;
+    using Gm = G<4, 16>;
+    if (!adjoint) {
+        const bool staged = 2LL * p.rec_max <= kRecStage;
+        if (p.hist && p.illum) return launch_fwd_flow_v<4, 16, true, true>(p, f, staged, st);
+        if (p.hist) return launch_fwd_flow_v<4, 16, true, false>(p, f, staged, st);
+        if (p.illum) return launch_fwd_flow_v<4, 16, false, true>(p, f, staged, st);
+        return launch_fwd_flow_v<4, 16, false, false>(p, f, staged, st);
+    }
+    const bool staged = (long long)p.rec_max * (kb + 2) <= kRecStage;
+    const size_t smem = sizeof(float) * (Gm::adj_ring_off + (size_t)kRing * p.tile_w * p.tile_h);
+    if (staged) return launch_flow(adj_flow_kernel<4, 16, true>, p, f, Gm::NT, smem, st);
+    return launch_flow(adj_flow_kernel<4, 16, false>, p, f, Gm::NT, smem, st);
+}
+
+}  // namespace gf

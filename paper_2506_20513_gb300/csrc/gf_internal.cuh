@@ -1,5 +1,6 @@
 // gf_internal.cuh -- types shared by the host runtime and the sm_103a kernels of libgprfwi.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -12,11 +13,12 @@ constexpr int kMaxK = 31;         // time steps per tile launch
 // Shared-memory words in which a tile kernel stages its window's receiver list: positions
 // and receiver indices (2 words per entry) and, in the adjoint, the residual samples of the
 // launch (K more words per entry).  Longer lists are read from global memory.
-constexpr int kRecStage = 4096;
+constexpr int kRecStage = 2048;
 
 // Device-status bits (OR-ed into the workspace status word by kernels).
 constexpr int kStatusBadModel = 1;   // eps_r < 1, sigma < 0 or non-finite model value
 constexpr int kStatusNonFinite = 2;  // non-finite trace or gradient
+constexpr int kStatusTimeout = 4;    // a persistent kernel's dependency wait ran out
 
 // Row pitch (floats) of the library's internal [ny][pitch] planes (state, wavefield store,
 // per-shot gradients and illumination, update coefficients): nx rounded up to a multiple of
@@ -24,9 +26,10 @@ constexpr int kStatusNonFinite = 2;  // non-finite trace or gradient
 // aligned.  Caller arrays (model, gradients, illumination) stay [ny][nx].
 inline int row_pitch(int nx) { return (nx + 3) & ~3; }
 
-// Left halo of a tile launch with K steps: K rounded up to even, so that the staged window
-// starts on an even column (tile widths are even).
-inline int left_halo(int K) { return (K + 1) & ~1; }
+// Left halo of a tile launch with K steps: K rounded up to a multiple of 4, so that the staged
+// window starts on a 16-byte boundary (tile widths are multiples of 4): its rows are loaded by
+// TMA boxes or 16-byte copies.
+inline int left_halo(int K) { return (K + 3) & ~3; }
 
 // CPML profiles of one axis (FP32, uploaded once per context).  For a node at index i:
 //   a = 1 / (kappa * d), b = exp(-(sigma/kappa + alpha) dt / eps0),
@@ -49,8 +52,7 @@ struct TileParams {
     const float* ca;     // update coefficients Ca, Cb of the model, [Np] each (0 on the PEC
     const float* cb;     // ring, in perfect conductors and in the row padding)
     const float* wavelet;   // [nshots][nsrc][nt]
-    const int* src_cell;    // [nshots][nsrc] linear cell index j*nx+i
-    const int* rec_cell;    // [nshots][nrec]
+    const int2* src_xy;     // [nshots][nsrc] source cells (x, y)
     const float* st_in;     // time-stepping state at the start of the launch
     float* st_out;          // state at the end of the launch (other ping-pong buffer)
     float* hist;            // wavefield store, NULL = not stored: Ez^{n+1} of shot s at
@@ -65,25 +67,51 @@ struct TileParams {
     int tile_w, tile_h;     // interior tile size (tile_w even)
     int kl;                 // left halo of the staged window (left_halo(K)); K elsewhere
     int tiles_x, ntiles;
-    // receivers of each (shot, tile) window [tx*tile_w - K, tx*tile_w + tile_w + K) x
-    // [ty*tile_h - K, ty*tile_h + tile_h + K), host-built CSR sorted by row: entries
-    // tile_rec_idx[off[s*ntiles+t] .. off[s*ntiles+t+1]) are receiver indices
-    const int* tile_rec_off;
-    const int* tile_rec_idx;
-    int rec_max;            // longest of these lists (decides shared-memory staging)
+    // Per (shot, tile) descriptor {first entry, entries, source mask, 0} of the window
+    // [tx*tile_w - K, tx*tile_w + tile_w + K) x [ty*tile_h - K, ty*tile_h + tile_h + K) (K of
+    // the context): its receiver list tile_rec[first .. first + entries) sorted by row, each
+    // entry {receiver index, (x - tx*tile_w + 64) | (y - ty*tile_h + 64) << 16}, and bit k set
+    // when source k of the shot lies in the window.  Host-built per tiling.
+    const int4* tile_desc;  // [nshots][ntiles]
+    const int2* tile_rec;
+    int rec_max;            // longest list (decides shared-memory staging)
     int* status;
 };
 
-// Host-side launchers.  Tile-kernel variants: 0 = 4 rows per thread, 512 threads, 64 x 64
-// window; 1 = 4 rows per thread, 256 threads, 64 x 32 (two CTAs per SM); 2 = 8 rows per
-// thread, 256 threads, 64 x 64.
-cudaError_t launch_fwd_tile(const TileParams& p, int variant, cudaStream_t st);
-cudaError_t launch_adj_tile(const TileParams& p, int variant, cudaStream_t st);
+// Tensor maps of one tile launch (TMA loads of the staged window, fp32, box 64 x WY, zero
+// outside the arrays): the state buffer the launch reads ([kNumFields * nshots][ny][pitch],
+// plane z = field * nshots + shot) and the update coefficients ([2][ny][pitch]: Ca, Cb).
+struct TileMaps {
+    CUtensorMap st;
+    CUtensorMap coef;
+};
+
+// Encode a TileMaps for state buffer `st` and coefficient planes `coef` (window height wy);
+// false when the driver's encoder is unavailable or rejects the layout.
+bool make_tile_maps(TileMaps* m, const float* st, const float* coef, int pitch, int ny,
+                    int nshots, int wy);
+
+// Host-side launchers.  Kernel variants: 0 = one launch per time block, 4 rows per thread,
+// 512 threads, 64 x 64 window; 1 = the same with 256 threads and a 64 x 32 window (two CTAs
+// per SM); 2 = 8 rows per thread, 256 threads, 64 x 64; 3 = the persistent dataflow kernels
+// (one cooperative launch per pass, variant 0's window).
+constexpr int kFlowVariant = 3;
+constexpr int kNumVariants = 4;
+cudaError_t launch_fwd_tile(const TileParams& p, const TileMaps& m, int variant, cudaStream_t st);
+cudaError_t launch_adj_tile(const TileParams& p, const TileMaps& m, int variant, cudaStream_t st);
 int max_tile_extent();              // staged window width
-int max_tile_height(int variant);   // staged window height of a tile-kernel variant
-int num_tile_variants();
-size_t tile_smem_bytes(int variant);
+int max_tile_height(int variant);   // staged window height of a per-launch variant (0-2)
+size_t tile_smem_bytes(int variant, int tile_w, int tile_h);  // per-launch variants (0-2)
 cudaError_t configure_tile_kernels(size_t optin);
+// Persistent dataflow pass: forward steps [n_first, n_last] in blocks of kb steps, or the
+// adjoint steps n_last down to n_first, from buf0 to buf[nblocks % 2]; done: nshots * ntiles
+// zeroed ints; budget: polls of one dependency wait.  The tiling needs tile_w a multiple of 4,
+// kl a multiple of 4 and tile_w, tile_h >= kb.
+cudaError_t launch_flow_pass(const TileParams& p, float* buf0, float* buf1, int* done,
+                             int n_first, int n_last, int kb, long long budget, bool adjoint,
+                             cudaStream_t st);
+size_t flow_smem_bytes(int tile_w, int tile_h);
+cudaError_t configure_flow_kernels(size_t optin);
 
 // Model check (eps_r >= 1, sigma >= 0, finite) and the update coefficients Ca, Cb of every
 // cell of the pitched planes.

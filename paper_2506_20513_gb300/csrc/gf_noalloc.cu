@@ -63,34 +63,31 @@ int fail(int code, const char* fmt, ...) {
     return code;
 }
 
-// (i, j) pairs -> linear cell indices, in place order [count][2] -> [count].
-__global__ void pairs_to_cells(const int* ij, int count, int nx, int* cells) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
-        cells[k] = ij[2 * k + 1] * nx + ij[2 * k];
-}
-
-// Number of receivers of each (shot, tile) staged window (interior plus a K-cell halo).
-__global__ void count_window_receivers(const int* rec, int nshots, int nrec, int nx, int tw,
-                                       int th, int K, int tiles_x, int ntiles, int* counts) {
+// Per (shot, tile) window [tx tw - K, tx tw + tw + K) x [ty th - K, ty th + th + K): the
+// number of its receivers (desc.y) and the mask of its sources (desc.z); positions (x, y).
+__global__ void count_windows(const int2* rec, const int2* src, int nshots, int nrec, int nsrc,
+                              int tw, int th, int K, int tiles_x, int ntiles, int4* desc) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nshots * ntiles) return;
     const int s = k / ntiles, t = k % ntiles;
     const int x0 = (t % tiles_x) * tw - K, y0 = (t / tiles_x) * th - K;
-    int n = 0;
-    for (int r = 0; r < nrec; ++r) {
-        const int c = rec[s * nrec + r], i = c % nx - x0, j = c / nx - y0;
-        n += (i >= 0 && i < tw + 2 * K && j >= 0 && j < th + 2 * K);
-    }
-    counts[k] = n;
+    auto inside = [&](int2 c) {
+        return c.x >= x0 && c.x < x0 + tw + 2 * K && c.y >= y0 && c.y < y0 + th + 2 * K;
+    };
+    int n = 0, mask = 0;
+    for (int r = 0; r < nrec; ++r) n += inside(rec[s * nrec + r]);
+    for (int q = 0; q < nsrc; ++q)
+        if (inside(src[s * nsrc + q])) mask |= 1 << q;
+    desc[k] = make_int4(0, n, mask, 0);
 }
 
-// counts[0..n) -> exclusive offsets off[0..n] (one block, sequential chunks, fixed order).
-__global__ void exclusive_offsets(const int* counts, int n, int* off) {
+// desc[0..n).y -> exclusive offsets desc[k].x (one block, sequential chunks, fixed order).
+__global__ void exclusive_offsets(int4* desc, int n) {
     __shared__ int part[1024];
     const int t = threadIdx.x, chunk = (n + blockDim.x - 1) / blockDim.x;
     const int a = min(t * chunk, n), b = min(a + chunk, n);
     int sum = 0;
-    for (int k = a; k < b; ++k) sum += counts[k];
+    for (int k = a; k < b; ++k) sum += desc[k].y;
     part[t] = sum;
     __syncthreads();
     if (t == 0) {
@@ -100,28 +97,37 @@ __global__ void exclusive_offsets(const int* counts, int n, int* off) {
             part[k] = run;
             run += v;
         }
-        off[n] = run;
     }
     __syncthreads();
     int run = part[t];
     for (int k = a; k < b; ++k) {
-        off[k] = run;
-        run += counts[k];
+        desc[k].x = run;
+        run += desc[k].y;
     }
 }
 
-// Receiver indices of each window, in index order.
-__global__ void fill_window_receivers(const int* rec, int nshots, int nrec, int nx, int tw,
-                                      int th, int K, int tiles_x, int ntiles, const int* off,
-                                      int* idx) {
+// Receiver entries of each window {index, (x - tx tw + 64) | (y - ty th + 64) << 16}, sorted
+// by row (insertion sort of the window's short list, stable: index order within a row).
+__global__ void fill_windows(const int2* rec, int nshots, int nrec, int tw, int th, int K,
+                             int tiles_x, int ntiles, const int4* desc, int2* ents) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nshots * ntiles) return;
     const int s = k / ntiles, t = k % ntiles;
-    const int x0 = (t % tiles_x) * tw - K, y0 = (t / tiles_x) * th - K;
-    int o = off[k];
+    const int tx = t % tiles_x, ty = t / tiles_x;
+    const int x0 = tx * tw - K, y0 = ty * th - K;
+    int2* out = ents + desc[k].x;
+    int n = 0;
     for (int r = 0; r < nrec; ++r) {
-        const int c = rec[s * nrec + r], i = c % nx - x0, j = c / nx - y0;
-        if (i >= 0 && i < tw + 2 * K && j >= 0 && j < th + 2 * K) idx[o++] = r;
+        const int2 c = rec[s * nrec + r];
+        if (c.x >= x0 && c.x < x0 + tw + 2 * K && c.y >= y0 && c.y < y0 + th + 2 * K) {
+            const int2 e = make_int2(r, (c.x - tx * tw + 64) | (c.y - ty * th + 64) << 16);
+            int q = n++;
+            while (q > 0 && (out[q - 1].y >> 16) > (e.y >> 16)) {
+                out[q] = out[q - 1];
+                --q;
+            }
+            out[q] = e;
+        }
     }
 }
 
@@ -145,7 +151,7 @@ int setup_device(int device, unsigned char** out) {
             return fail(GF_ECUDA, "gf_forward_model_noalloc: kernel set-up: %s",
                         cudaGetErrorString(e));
         }
-        if (gf::tile_smem_bytes(kVariant) > (size_t)optin)
+        if (gf::tile_smem_bytes(kVariant, kTileW, kTileH) > (size_t)optin)
             return fail(GF_ECUDA, "gf_forward_model_noalloc: not enough shared memory per block");
         slot.ptr = (unsigned char*)p;
         slot.ready = true;
@@ -204,11 +210,8 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     const size_t o_prof = o; o = up256(o + sizeof(float) * 12 * (size_t)S);
     const size_t o_srcij = o; o = up256(o + sizeof(int) * 2 * (size_t)nsrc_all);
     const size_t o_recij = o; o = up256(o + sizeof(int) * 2 * (size_t)nrec_all);
-    const size_t o_src = o; o = up256(o + sizeof(int) * (size_t)nsrc_all);
-    const size_t o_rec = o; o = up256(o + sizeof(int) * (size_t)nrec_all);
-    const size_t o_cnt = o; o = up256(o + sizeof(int) * (size_t)nwin);
-    const size_t o_off = o; o = up256(o + sizeof(int) * (size_t)(nwin + 1));
-    const size_t o_idx = o; o = up256(o + sizeof(int) * (size_t)max_entries);
+    const size_t o_desc = o; o = up256(o + sizeof(int4) * (size_t)nwin);
+    const size_t o_ents = o; o = up256(o + sizeof(int2) * (size_t)max_entries);
     const size_t field = sizeof(float) * (size_t)acq->nshots * (size_t)Np;
     const size_t o_stA = o; o = up256(o + gf::kNumFields * field);
     const size_t o_stB = o; o = up256(o + gf::kNumFields * field);
@@ -247,22 +250,18 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     // read during this call: every host read completes here
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     lock.unlock();
-    int* src = (int*)(base + o_src);
-    int* rec = (int*)(base + o_rec);
-    int* cnt = (int*)(base + o_cnt);
-    int* off = (int*)(base + o_off);
-    int* idx = (int*)(base + o_idx);
+    // (i, j) pairs are (x, y) cells as they come
+    const int2* src = (const int2*)(base + o_srcij);
+    const int2* rec = (const int2*)(base + o_recij);
+    int4* desc = (int4*)(base + o_desc);
+    int2* ents = (int2*)(base + o_ents);
     if (e == cudaSuccess) {
-        pairs_to_cells<<<(int)((nsrc_all + 255) / 256), 256, 0, st>>>((const int*)(base + o_srcij),
-                                                                    (int)nsrc_all, g.nx, src);
-        pairs_to_cells<<<(int)((nrec_all + 255) / 256), 256, 0, st>>>((const int*)(base + o_recij),
-                                                                    (int)nrec_all, g.nx, rec);
         const int wb = (int)((nwin + 255) / 256);
-        count_window_receivers<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, g.nx, kTileW,
-                                                   kTileH, kSteps, tiles_x, ntiles, cnt);
-        exclusive_offsets<<<1, 1024, 0, st>>>(cnt, (int)nwin, off);
-        fill_window_receivers<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, g.nx, kTileW,
-                                                  kTileH, kSteps, tiles_x, ntiles, off, idx);
+        count_windows<<<wb, 256, 0, st>>>(rec, src, acq->nshots, acq->nrec, acq->nsrc, kTileW,
+                                          kTileH, kSteps, tiles_x, ntiles, desc);
+        exclusive_offsets<<<1, 1024, 0, st>>>(desc, (int)nwin);
+        fill_windows<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, kTileW, kTileH, kSteps,
+                                         tiles_x, ntiles, desc, ents);
         e = cudaGetLastError();
     }
     // the state starts from zero on every call (the array keeps the previous call's contents);
@@ -299,8 +298,7 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     p.px = {P, P + S, P + 2 * S, P + 3 * S, P + 4 * S, P + 5 * S};
     p.py = {P + 6 * S, P + 7 * S, P + 8 * S, P + 9 * S, P + 10 * S, P + 11 * S};
     p.wavelet = wavelet;
-    p.src_cell = src;
-    p.rec_cell = rec;
+    p.src_xy = src;
     p.traces = traces;
     p.hist = nullptr;
     p.illum = nullptr;
@@ -308,8 +306,8 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     p.tile_h = kTileH;
     p.tiles_x = tiles_x;
     p.ntiles = ntiles;
-    p.tile_rec_off = off;
-    p.tile_rec_idx = idx;
+    p.tile_desc = desc;
+    p.tile_rec = ents;
     p.rec_max = acq->nrec;  // no window holds more than a shot's receivers
     p.status = (int*)(base + o_status);
     p.kl = gf::left_halo(kSteps);
@@ -320,7 +318,11 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
         p.K = g.nt - n0 < kSteps ? g.nt - n0 : kSteps;
         p.st_in = buf[cur];
         p.st_out = buf[cur ^ 1];
-        e = gf::launch_fwd_tile(p, kVariant, st);
+        gf::TileMaps maps;
+        if (!gf::make_tile_maps(&maps, buf[cur], ca, pitch, g.ny, acq->nshots,
+                                gf::max_tile_height(kVariant)))
+            return fail(GF_ECUDA, "gf_forward_model_noalloc: tensor maps could not be encoded");
+        e = gf::launch_fwd_tile(p, maps, kVariant, st);
         if (e != cudaSuccess)
             return fail(GF_ECUDA, "gf_forward_model_noalloc: tile launch: %s", cudaGetErrorString(e));
         cur ^= 1;

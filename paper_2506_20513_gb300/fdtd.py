@@ -109,6 +109,9 @@ class FDTD:
         if t.variant is not None:
             _lib.check(self.lib, self.ctx, self.lib.gf_set_variant(self.ctx, t.variant))
         _lib.check(self.lib, self.ctx, self.lib.gf_set_tiling(self.ctx, t.tile_w, t.tile_h, t.steps))
+        # the workspace holds per-tile counters: its size follows the tiling
+        self._ws = None
+        self._ws_full = False
 
     def tiling(self) -> Tiling:
         v = [ctypes.c_int() for _ in range(4)]

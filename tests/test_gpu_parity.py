@@ -58,11 +58,22 @@ def gpu_gradient(wl, dev, obs, tiling=None, wav=None, checkpoint_every=0):
 
 
 def fit_variant(tiling):
-    """Variant 1 stages a 64 x 32 window: shrink the tile height to fit (tile + 2K <= 32)."""
-    if tiling and len(tiling) == 4 and tiling[3] == 1 and tiling[1] > 0:
-        tw, th, k, v = tiling
-        return (tw, max(1, min(th, 32 - 2 * k)), k, v)
-    return tiling
+    """Tile widths are multiples of 4 (windows start on 16-byte boundaries).  Variant 1 stages
+    a 64 x 32 window: shrink the tile height to fit (tile + 2K <= 32).  Variant 3 (persistent)
+    wants tiles at least K wide and high."""
+    if not tiling:
+        return tiling
+    tw, th, k = tiling[:3]
+    v = tiling[3] if len(tiling) == 4 else None
+    if tw > 0:
+        tw = max(tw - tw % 4, 4)
+        if v == 3:
+            tw = max(tw, 4 * ((k + 3) // 4))
+    if v == 1 and th > 0:
+        th = max(1, min(th, 32 - 2 * k))
+    if v == 3 and th > 0:
+        th = max(th, k)
+    return (tw, th, k) + ((v,) if v is not None else ())
 
 
 def check_case(wl, dev, tiling=None, nsrc=1, checkpoint_every=0):
@@ -95,7 +106,7 @@ def test_preconditioner_workload_subset(dev):
     check_case(wl, dev)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("seed,tiling,kappa,pec", [
     (1, None, 1.0, False),
     (2, (8, 6, 3), 2.0, True),
@@ -110,18 +121,19 @@ def test_small_random(dev, seed, tiling, kappa, pec, variant):
     check_case(wl, dev, (tiling or (0, 0, 0)) + (variant,))
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("nrec,tiling", [(200, (0, 0, 4)), (400, (0, 0, 4)), (400, (12, 7, 4)),
                                          (900, (0, 0, 4)), (900, (0, 0, 10))])
-def test_dense_receivers(dev, nrec, tiling):
+def test_dense_receivers(dev, nrec, tiling, variant):
     """Hundreds of receivers scattered over the grid, duplicates included: launches whose
     window lists fit the shared-memory staging of positions, indices and (adjoint) residual
     samples (up to 682 entries at K = 4, 341 at K = 10) and launches that exceed it (900
     entries) and decode them from global memory."""
     wl = W.small_random(51, nxp=46, nyp=27, npml=6, nt=150, nshots=2, nrec=nrec)
-    check_case(wl, dev, tiling + (0,))
+    check_case(wl, dev, tiling + (variant,))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("npml,tiling", [(0, (16, 16, 4)), (3, (20, 18, 5)), (8, (40, 40, 12))])
 def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
     """Large grids with thin (or no) CPML: most tiles take the body without CPML memories."""
@@ -131,7 +143,8 @@ def test_tiles_off_the_absorbing_strips(dev, npml, tiling, variant):
 
 
 @pytest.mark.parametrize("k,tiling", [(1, (20, 14, 3, 0)), (7, (20, 14, 4, 1)), (16, None),
-                                      (150, None), (64, (44, 30, 5, 0)), (33, (0, 0, 5, 2))])
+                                      (150, None), (64, (44, 30, 5, 0)), (33, (0, 0, 5, 2)),
+                                      (33, (20, 14, 5, 3)), (1, (0, 0, 3, 3))])
 def test_checkpointed_gradient(dev, k, tiling):
     """Checkpoints every k steps and segment recomputation in the adjoint (k = 1, k not a
     multiple of the time block, k = nt)."""
@@ -299,10 +312,11 @@ def test_host_tensors_end_to_end(dev):
     assert rel(ge.numpy(), ge64) <= GRAD_TOL and rel(gs.numpy(), gs64) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("variant,K", [(1, 4), (2, 7), (0, 10)])
+@pytest.mark.parametrize("variant,K", [(3, 7), (1, 4), (2, 7), (0, 10)])
 def test_variants_at_scale(dev, variant, K):
     """540x290, 32 shots, nt 300: other kernel variants and time-block depths against the
-    default launch configuration (traces, misfit, gradients), over many tiles and shots."""
+    default launch configuration (variant 0, K = 7): traces, misfit, gradients, over many
+    tiles and shots."""
     from paper_2506_20513_gb300 import FDTD, Tiling
     wl = W.multishot_layered(nt=300)
     wav = t32(wavelets(wl), dev)
@@ -418,4 +432,35 @@ def test_large_grid_gradient_vs_central_differences(dev):
         out[name] = (fdv, adv)
         assert np.corrcoef(fdv, adv)[0, 1] >= 0.999, name
         assert np.max(np.abs(fdv - adv) / np.abs(adv)) <= 0.05, name
+    fd.close()
+
+
+def test_dependency_wait_timeout_is_reported_and_recovered(dev):
+    """The persistent kernels' dependency waits are bounded: with a budget of zero polls a
+    wait that is not already satisfied gives up, the CTA ends and gf_status reports
+    GF_ETIMEOUT (nothing hangs, the context stays usable); with the default budget restored the
+    next call is exact again."""
+    from paper_2506_20513_gb300 import FDTD
+    # 3 x 3 tiles and 2 shots: 18 items per time block, fewer than the resident CTAs, so the
+    # items of block b + 1 are taken while their neighbours' block b is still running
+    from paper_2506_20513_gb300 import Tiling
+    wl = W.small_random(60, nxp=140, nyp=110, npml=8, nt=200, nshots=2, nrec=8)
+    g = wl.grid
+    wav = t32(wavelets(wl), dev)
+    fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=Tiling(0, 0, 7, 3))
+    obs = fd.forward_model(t32(wl.eps_true, dev), t32(wl.sig_true, dev), wav)
+    e0, s0 = t32(wl.eps_init, dev), t32(wl.sig_init, dev)
+    ref = fd.misfit_and_gradient(e0, s0, wav, obs)
+    fd.status()
+    _lib.check(fd.lib, fd.ctx, fd.lib.gf_set_wait_budget(fd.ctx, 0))
+    fd.misfit_and_gradient(e0, s0, wav, obs)
+    with pytest.raises(_lib.GfError) as ex:
+        fd.status()
+    assert ex.value.code == _lib.GF_ETIMEOUT
+    _lib.check(fd.lib, fd.ctx, fd.lib.gf_set_wait_budget(fd.ctx, 1 << 22))
+    got = fd.misfit_and_gradient(e0, s0, wav, obs)
+    fd.status()
+    assert got[0].item() == ref[0].item()
+    for a, b in zip(got[1:], ref[1:]):
+        assert torch.equal(a, b)
     fd.close()
