@@ -65,6 +65,7 @@ struct gf_ctx {
     std::vector<int> h_src;  // [nshots][nsrc], linear j * nx + i)
     int4* d_tile_desc = nullptr;    // per (shot, tile) descriptors for the current tiling
     int2* d_tile_rec = nullptr;     // their receiver entries
+    int* d_cta_order = nullptr;     // launch order of the (shot, tile) pairs
     int tile_rec_max = 0;           // longest per (shot, tile) list of the current tiling
     long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
@@ -293,6 +294,7 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.ntiles = p.tiles_x * ((c->g.ny + c->tile_h - 1) / c->tile_h);
     p.tile_desc = c->d_tile_desc;
     p.tile_rec = c->d_tile_rec;
+    p.cta_order = c->d_cta_order;
     p.rec_max = c->tile_rec_max;
     p.kl = gf::left_halo(c->K);
     p.hist_stride = c->g.nt;
@@ -536,24 +538,47 @@ int build_tile_tables(gf_ctx* c, int tw, int th, int K) {
         longest = std::max(longest, (int)lists[k].size());
     }
     if (ents.empty()) ents.push_back(make_int2(0, 0));
+    // launch order: receiver tiles, then tiles whose window (the tile and K cells around it)
+    // touches a CPML strip, then the others; shot-major within a class
+    std::vector<int> order;
+    order.reserve(lists.size());
+    const int np = c->g.npml;
+    auto strip_tile = [&](int t) {
+        const int tx = t % ntx, ty = t / ntx;
+        const int xa = tx * tw - K, xb = tx * tw + tw + K, ya = ty * th - K, yb = ty * th + th + K;
+        return np > 0 && (xa < np || xb - 1 >= nx - np - 1 || ya < np || yb - 1 >= ny - np - 1);
+    };
+    for (int cls = 0; cls < 3; ++cls)
+        for (size_t k = 0; k < lists.size(); ++k) {
+            const int t = (int)(k % nt_);
+            const int kc = !lists[k].empty() ? 0 : strip_tile(t) ? 1 : 2;
+            if (kc == cls) order.push_back((int)(k / nt_) << 16 | t);
+        }
     int4* d_desc = nullptr;
     int2* d_ents = nullptr;
+    int* d_order = nullptr;
     cudaError_t e = cudaMalloc(&d_desc, desc.size() * sizeof(int4));
     if (e == cudaSuccess) e = cudaMalloc(&d_ents, ents.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&d_order, order.size() * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMemcpy(d_desc, desc.data(), desc.size() * sizeof(int4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(d_ents, ents.data(), ents.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(d_desc);
         cudaFree(d_ents);
+        cudaFree(d_order);
         return cuda_fail(c, e, "tile tables");
     }
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
+    cudaFree(c->d_cta_order);
     c->d_tile_desc = d_desc;
     c->d_tile_rec = d_ents;
+    c->d_cta_order = d_order;
     c->tile_rec_max = longest;
     return GF_OK;
 }
@@ -575,6 +600,8 @@ int check_tiling(gf_ctx* c, int tw, int th, int K, int variant) {
                     "tile %dx%d with %d steps per launch: need a tile width that is a multiple of "
                     "4 with %d + width + steps <= %d and height + 2*steps <= %d (steps <= %d)%s",
                     tw, th, K, kl, E, Eh, gf::kMaxK, flow ? ", width and height >= steps" : "");
+    if ((long long)((c->g.nx + tw - 1) / tw) * ((c->g.ny + th - 1) / th) > 65535)
+        return fail(c, GF_EINVAL, "tile %dx%d gives more than 65535 tiles", tw, th);
     const size_t need = flow ? gf::flow_smem_bytes(tw, th) : gf::tile_smem_bytes(variant, tw, th);
     if (need > c->smem_optin)
         return fail(c, GF_EINVAL, "tile kernels need %zu bytes of shared memory (> %zu)", need,
@@ -626,8 +653,9 @@ int gf_create(gf_ctx** out, const gf_grid_desc* grid, const gf_acquisition* acq,
         create_fail("gf_create: dt = %g s exceeds the CFL bound %g s", g.dt, dtmax);
         return GF_ECFL;
     }
-    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1) {
-        create_fail("gf_create: need nshots >= 1, 1 <= nsrc <= %d, nrec >= 1", gf::kMaxSrc);
+    if (acq->nshots < 1 || acq->nshots > 65535 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc ||
+        acq->nrec < 1) {
+        create_fail("gf_create: need 1 <= nshots <= 65535, 1 <= nsrc <= %d, nrec >= 1", gf::kMaxSrc);
         return GF_EINVAL;
     }
     auto inside = [&](const int32_t* ij) {
@@ -713,6 +741,7 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_src_xy);
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
+    cudaFree(c->d_cta_order);
     delete c;
 }
 

@@ -43,9 +43,9 @@ __device__ __forceinline__ Item decode(const TileParams& p, const FlowArgs& f, i
     Item it;
     const int ipb = p.nshots * p.ntiles;
     it.b = i / ipb;
-    const int rem = i - it.b * ipb;
-    it.shot = rem / p.ntiles;
-    it.tile = rem - it.shot * p.ntiles;
+    const int code = __ldg(p.cta_order + (i - it.b * ipb));
+    it.shot = code >> 16;
+    it.tile = code & 0xffff;
     if (!reverse) {
         it.n0 = f.n_first + it.b * f.kb;
         it.K = min(f.kb, f.n_last + 1 - it.n0);
@@ -237,13 +237,15 @@ __global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p
         int rlo, rhi;
         warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl,
                                    it.K, rlo, rhi);
+        const OwnRec orc = own_receivers<kStaged, R>(
+            p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl, it.K, rlo, rhi, true);
         const bool srcany = thread_has_source<R, NW>(p, w, sm);
         if (w.tile_xs)
             fwd_steps<R, NW, true, kHist, kIllum, kStaged>(p, w, sm, it.shot, it.n0, it.K, ez, hx,
-                                                           hy, ill, rlo, rhi, nrl, ents, srcany);
+                                                           hy, ill, rlo, rhi, nrl, ents, orc, srcany);
         else
             fwd_steps<R, NW, false, kHist, kIllum, kStaged>(p, w, sm, it.shot, it.n0, it.K, ez, hx,
-                                                            hy, ill, rlo, rhi, nrl, ents, srcany);
+                                                            hy, ill, rlo, rhi, nrl, ents, orc, srcany);
         store_state<R, NW>(p, w, sm, st_out, it.shot, ez, hx, hy);
         if (kIllum) add_illumination<R>(p, w, it.shot, ill);
         publish<R, NW>(p, f, it);
@@ -311,6 +313,8 @@ __global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p
         int rlo, rhi;
         warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl,
                                    K, rlo, rhi);
+        const OwnRec orc = own_receivers<kStaged, R>(
+            p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl, K, rlo, rhi, false);
         // after phase A 0 the staging planes are free: fetch the next item's state; after the
         // last phase A this item no longer reads its coefficients: fetch the next item's
         auto after_a = [&](int a) {
@@ -326,10 +330,10 @@ __global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p
         };
         if (w.tile_xs)
             adj_steps<R, NW, true, kStaged>(p, w, sm, it.shot, it.n0, K, aez, ahx, ahy, ge, gs, hp,
-                                            own, rg, rlo, rhi, nrl, ents, after_a);
+                                            own, rg, rlo, rhi, nrl, ents, orc, after_a);
         else
             adj_steps<R, NW, false, kStaged>(p, w, sm, it.shot, it.n0, K, aez, ahx, ahy, ge, gs,
-                                             hp, own, rg, rlo, rhi, nrl, ents, after_a);
+                                             hp, own, rg, rlo, rhi, nrl, ents, orc, after_a);
         store_state<R, NW>(p, w, sm, st_out, it.shot, aez, ahx, ahy);
         add_gradients<R>(p, w, it.shot, ge, gs);
         publish<R, NW>(p, f, it);

@@ -74,6 +74,10 @@ struct TileParams {
     // when source k of the shot lies in the window.  Host-built per tiling.
     const int4* tile_desc;  // [nshots][ntiles]
     const int2* tile_rec;
+    // Launch order of the (shot, tile) pairs, shot << 16 | tile: tiles with receivers first,
+    // then tiles touching a CPML strip, then the rest (the slow ones start early, the last wave
+    // is short)
+    const int* cta_order;   // [nshots * ntiles]
     int rec_max;            // longest list (decides shared-memory staging)
     int* status;
 };

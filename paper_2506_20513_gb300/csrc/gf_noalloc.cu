@@ -131,6 +131,12 @@ __global__ void fill_windows(const int2* rec, int nshots, int nrec, int tw, int 
     }
 }
 
+// Launch order of the (shot, tile) pairs: shot << 16 | tile, in index order.
+__global__ void fill_order(int nshots, int ntiles, int* order) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nshots * ntiles) order[k] = (k / ntiles) << 16 | (k % ntiles);
+}
+
 // Once per device, with that device current: the scratch address and kernel attributes.
 int setup_device(int device, unsigned char** out) {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -178,7 +184,8 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     const double dtmax = 1.0 / (299792458.0 * sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy)));
     if (g.dt > dtmax)
         return fail(GF_ECFL, "gf_forward_model_noalloc: dt exceeds the CFL bound %g s", dtmax);
-    if (acq->nshots < 1 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc || acq->nrec < 1)
+    if (acq->nshots < 1 || acq->nshots > 65535 || acq->nsrc < 1 || acq->nsrc > gf::kMaxSrc ||
+        acq->nrec < 1)
         return fail(GF_EINVAL, "gf_forward_model_noalloc: need nshots >= 1, 1 <= nsrc <= %d, "
                     "nrec >= 1", gf::kMaxSrc);
     const long long nsrc_all = (long long)acq->nshots * acq->nsrc;
@@ -212,6 +219,7 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     const size_t o_recij = o; o = up256(o + sizeof(int) * 2 * (size_t)nrec_all);
     const size_t o_desc = o; o = up256(o + sizeof(int4) * (size_t)nwin);
     const size_t o_ents = o; o = up256(o + sizeof(int2) * (size_t)max_entries);
+    const size_t o_order = o; o = up256(o + sizeof(int) * (size_t)nwin);
     const size_t field = sizeof(float) * (size_t)acq->nshots * (size_t)Np;
     const size_t o_stA = o; o = up256(o + gf::kNumFields * field);
     const size_t o_stB = o; o = up256(o + gf::kNumFields * field);
@@ -262,6 +270,7 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
         exclusive_offsets<<<1, 1024, 0, st>>>(desc, (int)nwin);
         fill_windows<<<wb, 256, 0, st>>>(rec, acq->nshots, acq->nrec, kTileW, kTileH, kSteps,
                                          tiles_x, ntiles, desc, ents);
+        fill_order<<<wb, 256, 0, st>>>(acq->nshots, ntiles, (int*)(base + o_order));
         e = cudaGetLastError();
     }
     // the state starts from zero on every call (the array keeps the previous call's contents);
@@ -308,6 +317,7 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
     p.ntiles = ntiles;
     p.tile_desc = desc;
     p.tile_rec = ents;
+    p.cta_order = (const int*)(base + o_order);
     p.rec_max = acq->nrec;  // no window holds more than a shot's receivers
     p.status = (int*)(base + o_status);
     p.kl = gf::left_halo(kSteps);

@@ -531,6 +531,36 @@ __device__ __forceinline__ void warp_rec_range(const TileParams& p, const Pos<R>
     }
 }
 
+// The receiver entries of a thread's cells, found once per tile so that every step records
+// (or injects) them in parallel across the warp instead of one warp walking the list: at
+// most two per thread, each packed as entry << 4 | row << 1 | column (-1 = none); `walk`
+// (warp-uniform) when some lane holds more, and the warp then walks its range every step.
+struct OwnRec {
+    int e0, e1;
+    bool walk;
+};
+
+template <bool kStaged, int R>
+__device__ __forceinline__ OwnRec own_receivers(const TileParams& p, const Pos<R>& w,
+                                                const int* srec, const int2* ents, int nrl, int K,
+                                                int rlo, int rhi, bool interior_only) {
+    OwnRec o;
+    o.e0 = o.e1 = -1;
+    int n = 0;
+    for (int e = rlo; e < rhi; ++e) {
+        int pos, ri;
+        rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
+        if (((pos & 0xff) >> 1) == w.lane && (!interior_only || (pos >> 16))) {
+            const int code = e << 4 | (rec_row(pos) - w.ly0) << 1 | (pos & 1);
+            if (n == 0) o.e0 = code;
+            else if (n == 1) o.e1 = code;
+            ++n;
+        }
+    }
+    o.walk = __any_sync(kFull, n > 2);
+    return o;
+}
+
 // ---------------------------------------------------------------------------------------
 // Row updates of one warp (no per-row branches: the rows are independent chains)
 // ---------------------------------------------------------------------------------------
@@ -786,7 +816,7 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
                                           int shot, int n0, int K, float2 (&ez)[R],
                                           float2 (&hx)[R], float2 (&hy)[R], float2 (&ill)[R],
                                           int rlo, int rhi, int nrl, const int2* ents,
-                                          bool srcany) {
+                                          const OwnRec& orc, bool srcany) {
     using Gm = G<R, NW>;
     float2* top = reinterpret_cast<float2*>(sm + Gm::oTop);
     float2* bot = reinterpret_cast<float2*>(sm + Gm::oBot);
@@ -811,11 +841,23 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
     for (int st = 0; st < K; ++st) {
         const int n = n0 + st;
         // 1. receivers in this tile's interior: d^n = Ez^n (loop bounds are warp-uniform)
-        for (int e = rlo; e < rhi; ++e) {
-            int pos, ri;
-            rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
-            if (((pos & 0xff) >> 1) == w.lane && (pos >> 16))
-                tr[(long long)n * p.nrec + ri] = pick<R>(ez, rec_row(pos) - w.ly0, pos & 1);
+        if (orc.walk) {
+            for (int e = rlo; e < rhi; ++e) {
+                int pos, ri;
+                rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
+                if (((pos & 0xff) >> 1) == w.lane && (pos >> 16))
+                    tr[(long long)n * p.nrec + ri] = pick<R>(ez, rec_row(pos) - w.ly0, pos & 1);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int code = q ? orc.e1 : orc.e0;
+                if (code >= 0) {
+                    const int e = code >> 4;
+                    const int ri = kStaged ? srec[nrl + e] : __ldg(ents + e).x;
+                    tr[(long long)n * p.nrec + ri] = pick<R>(ez, (code >> 1) & 7, code & 1);
+                }
+            }
         }
         top[w.warp * 32 + w.lane] = ez[0];
         __syncthreads();
@@ -884,7 +926,7 @@ __device__ __forceinline__ void adj_steps(const TileParams& p, const Pos<R>& w, 
                                           float2 (&ahx)[R], float2 (&ahy)[R], float2 (&ge)[R],
                                           float2 (&gs)[R], const float* hp, const bool (&own)[R],
                                           const Ring& rg, int rlo, int rhi, int nrl,
-                                          const int2* ents, AfterA after_a) {
+                                          const int2* ents, const OwnRec& orc, AfterA after_a) {
     using Gm = G<R, NW>;
     const int n1 = n0 + K - 1;
     float2* top = reinterpret_cast<float2*>(sm + Gm::oTop);
@@ -933,17 +975,36 @@ __device__ __forceinline__ void adj_steps(const TileParams& p, const Pos<R>& w, 
             aez[r].y += (wx[r].x - wx[r].y) + (tu.y - wy[r].y);
         }
         // adjoint source of step n: the residual at the receivers (every staged copy)
-        for (int e = rlo; e < rhi; ++e) {
-            int pos, ri;
-            rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
-            if (((pos & 0xff) >> 1) == w.lane) {
-                const float v = kStaged ? __int_as_float(srec[2 * nrl + e * K + st])
-                                        : __ldg(rbase + (long long)n * p.nrec + ri);
-                add_at<R>(aez, rec_row(pos) - w.ly0, pos & 1, v);
+        if (orc.walk) {
+            for (int e = rlo; e < rhi; ++e) {
+                int pos, ri;
+                rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
+                if (((pos & 0xff) >> 1) == w.lane) {
+                    const float v = kStaged ? __int_as_float(srec[2 * nrl + e * K + st])
+                                            : __ldg(rbase + (long long)n * p.nrec + ri);
+                    add_at<R>(aez, rec_row(pos) - w.ly0, pos & 1, v);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int code = q ? orc.e1 : orc.e0;
+                if (code >= 0) {
+                    const int e = code >> 4;
+                    const float v = kStaged ? __int_as_float(srec[2 * nrl + e * K + st])
+                                            : __ldg(rbase + (long long)n * p.nrec + __ldg(ents + e).x);
+                    add_at<R>(aez, (code >> 1) & 7, code & 1, v);
+                }
             }
         }
         if (st < K - 1) phase_a(st + 1);
     }
+}
+
+// a[0] += x, a[1] += y as one fire-and-forget vector reduction (no value returned, so the
+// thread does not wait for it)
+__device__ __forceinline__ void red_add2(float* a, float x, float y) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};\n" ::"l"(a), "f"(x), "f"(y) : "memory");
 }
 
 // Add the tile's gradient sums (owned cells) to the per-shot accumulators: g_eps_r gets
@@ -960,8 +1021,8 @@ __device__ __forceinline__ void add_gradients(const TileParams& p, const Pos<R>&
     for (int r = 0; r < R; ++r) {
         if (!((w.row_int >> r) & 1u)) continue;
         float* g = p.grad + (long long)shot * p.Np + (long long)(w.Y0 + w.ly0 + r) * p.pitch + w.gx0;
-        atomicAdd(reinterpret_cast<float2*>(g), make_float2(se * ge[r].x, se * ge[r].y));
-        atomicAdd(reinterpret_cast<float2*>(g + F), make_float2(-0.5f * gs[r].x, -0.5f * gs[r].y));
+        red_add2(g, se * ge[r].x, se * ge[r].y);
+        red_add2(g + F, -0.5f * gs[r].x, -0.5f * gs[r].y);
     }
 }
 

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     fwd_tile_kernel(const TileParams p, const __grid_constant__ TileMaps m) {
     extern __shared__ __align__(1024) float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
-    const int shot = blockIdx.y, tile = blockIdx.x, K = p.K;
+    const int code = __ldg(p.cta_order + blockIdx.x);
+    const int shot = code >> 16, tile = code & 0xffff, K = p.K;
     const Pos<R> w = position<R>(p, tile, K);
     const bool strip = tile_in_strip<R>(p, w, K);
     const uint32_t bar = smem_u32(sm + G<R, NW>::oBar);
@@ -35,14 +36,16 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     int rlo, rhi;
     warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + G<R, NW>::oRec), ents,
                                nrl, K, rlo, rhi);
+    const OwnRec orc = own_receivers<kStaged, R>(
+        p, w, reinterpret_cast<const int*>(sm + G<R, NW>::oRec), ents, nrl, K, rlo, rhi, true);
     const bool srcany = thread_has_source<R, NW>(p, w, sm);
 
     if (w.tile_xs)
         fwd_steps<R, NW, true, kHist, kIllum, kStaged>(p, w, sm, shot, p.n0, K, L.f0, L.f1, L.f2,
-                                                       ill, rlo, rhi, nrl, ents, srcany);
+                                                       ill, rlo, rhi, nrl, ents, orc, srcany);
     else
         fwd_steps<R, NW, false, kHist, kIllum, kStaged>(p, w, sm, shot, p.n0, K, L.f0, L.f1, L.f2,
-                                                        ill, rlo, rhi, nrl, ents, srcany);
+                                                        ill, rlo, rhi, nrl, ents, orc, srcany);
 
     store_state<R, NW>(p, w, sm, p.st_out, shot, L.f0, L.f1, L.f2);
     if (kIllum) add_illumination<R>(p, w, shot, ill);
@@ -54,7 +57,8 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     using Gm = G<R, NW>;
     extern __shared__ __align__(1024) float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
-    const int shot = blockIdx.y, tile = blockIdx.x, K = p.K;
+    const int code = __ldg(p.cta_order + blockIdx.x);
+    const int shot = code >> 16, tile = code & 0xffff, K = p.K;
     const int n1 = p.n0 + K - 1;
     const Pos<R> w = position<R>(p, tile, K);
     const bool strip = tile_in_strip<R>(p, w, K);
@@ -85,14 +89,16 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     int rlo, rhi;
     warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl, K,
                                rlo, rhi);
+    const OwnRec orc = own_receivers<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec),
+                                                 ents, nrl, K, rlo, rhi, false);
 
     auto none = [](int) {};
     if (w.tile_xs)
         adj_steps<R, NW, true, kStaged>(p, w, sm, shot, p.n0, K, L.f0, L.f1, L.f2, ge, gs, hp,
-                                        own, rg, rlo, rhi, nrl, ents, none);
+                                        own, rg, rlo, rhi, nrl, ents, orc, none);
     else
         adj_steps<R, NW, false, kStaged>(p, w, sm, shot, p.n0, K, L.f0, L.f1, L.f2, ge, gs, hp,
-                                         own, rg, rlo, rhi, nrl, ents, none);
+                                         own, rg, rlo, rhi, nrl, ents, orc, none);
     cp_async_wait<0>();
 
     store_state<R, NW>(p, w, sm, p.st_out, shot, L.f0, L.f1, L.f2);
@@ -133,7 +139,7 @@ template <int R, int NW, bool kHist, bool kIllum>
 cudaError_t launch_fwd_variant(const TileParams& p, const TileMaps& m, bool staged,
                                cudaStream_t st) {
     using Gm = G<R, NW>;
-    const dim3 grid(p.ntiles, p.nshots), block(Gm::NT);
+    const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = sizeof(float) * Gm::fwd_floats;
     if (staged)
         fwd_tile_kernel<R, NW, kHist, kIllum, true><<<grid, block, smem, st>>>(p, m);
@@ -158,7 +164,7 @@ size_t adj_smem(int tile_w, int tile_h) {
 template <int R, int NW>
 cudaError_t launch_adj_r(const TileParams& p, const TileMaps& m, bool staged, cudaStream_t st) {
     using Gm = G<R, NW>;
-    const dim3 grid(p.ntiles, p.nshots), block(Gm::NT);
+    const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = adj_smem<R, NW>(p.tile_w, p.tile_h);
     if (staged)
         adj_tile_kernel<R, NW, true><<<grid, block, smem, st>>>(p, m);
