@@ -34,21 +34,18 @@ METRIC = "Gcell-updates/s (fwd+adjoint) and s per dual-param FWI iteration vs HB
 UNIT = "Gcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) per cell-step of one launch, from `ncu --metrics
-# dram__bytes_read.sum,dram__bytes_write.sum` of the same kernel code (kernel_source_tag),
-# workload and tiling; see profiles/.  A change of the kernel code drops it.
-# Warp instructions per cell-step of one launch (ncu InstructionStats, same keys): the
-# kernels are bound by instruction issue, so the line also reports the issue roofline.
-NCU_WARP_INST_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 199.0 M warp instructions per K = 7 launch
-    "adj@1085d4c1e613@540x290x32@default": 5.6732,
-}
+# Per-launch figures from one ncu capture of the tile kernels (`ncu --clock-control none -k
+# regex:<kernel> --metrics dram__bytes_read.sum,dram__bytes_write.sum,smsp__inst_executed.sum`
+# on the multishot workload with nt = 70, default tiling), divided by the launch's cell-steps.
+# Keyed on kernel_source_tag(): any change of the kernel code drops them (reported as null).
+# DRAM bytes (read + write) per cell-step:
+NCU_TRAFFIC_PER_CELL_STEP: dict = {}
+# Warp instructions per cell-step (the kernels are bound by instruction issue, so the line
+# also reports the issue roofline):
+NCU_WARP_INST_PER_CELL_STEP: dict = {}
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
-
-NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    # profiles/adj_tile_multishot_540x290x32.md: 339.3 MB per K = 7 launch
-    "adj@1085d4c1e613@540x290x32@default": 9.6736,
-}
+# the files holding the tile kernels' device code
+KERNEL_SOURCES = ("gf_tile_kernels.cu", "gf_tile_common.cuh")
 
 
 def parse_args():
@@ -72,8 +69,12 @@ def parse_args():
     ap.add_argument("--gemm", type=int, default=1, choices=[0, 1, 2],
                     help="U-Net workload: 1 = tcgen05 with TMA operand loads, 2 = tcgen05 with "
                          "thread-staged operands, 0 = explicit im2col and mma.sync GEMMs")
-    ap.add_argument("--fwi-iters", type=int, default=10,
-                    help="L-BFGS iterations timed for the s-per-FWI-iteration figure (0 = skip)")
+    ap.add_argument("--fwi-iters", type=int, default=50,
+                    help="L-BFGS iterations of the timed three-band FWI run (0 = skip)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 2108x1084, 16-shot, nt 8000 checkpointed-gradient sub-record")
+    ap.add_argument("--large-checkpoint", type=int, default=200,
+                    help="checkpoint interval of the large-grid sub-record")
     return ap.parse_args()
 
 
@@ -105,20 +106,29 @@ def job_value(cells_per_rank: int, world: int, ms_max: float) -> float:
     return cells_per_rank * world / (ms_max / 1e3) / 1e9
 
 
-def cpu_sample_shots(requested: int) -> int:
+def host_cores() -> int:
+    """Cores this process may run on (the box's nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_sample_shots(requested: int, nshots: int) -> int:
+    """Shots of the oracle sample: one OpenMP thread each, as many as there are cores and
+    shots, fewer if host memory is short (each thread keeps its shot's FP64 wavefield
+    history, about 2.6 GB on the 540x290, nt 2000 grid)."""
     if requested > 0:
-        return requested
-    cores = os.cpu_count() or 1
+        return min(requested, nshots)
     try:
         mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
     except (ValueError, OSError):
         mem_gb = 16.0
-    # the oracle keeps each shot's FP64 wavefield history (~2.5 GB here) per thread
-    return max(1, min(8, cores, int(mem_gb * 0.4 / 2.6)))
+    return max(1, min(nshots, host_cores(), int(mem_gb * 0.4 / 2.6)))
 
 
 def run_oracle_sample(wl, shots: int):
-    """Time the FP64 oracle gradient of `shots` shots (one OpenMP thread per shot)."""
+    """Time the FP64 oracle gradient of the first `shots` shots (one OpenMP thread per shot)."""
     from oracle import oracle as O
     g = wl.grid
     wav = np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (shots, 1, g.nt))
@@ -131,12 +141,21 @@ def run_oracle_sample(wl, shots: int):
     return cells / dt / 1e9, dt
 
 
+def oracle_sample_text(wl, shots: int, seconds: float) -> str:
+    g = wl.grid
+    return (f"shots 0-{shots - 1} of the {wl.nshots}-shot batch (full {g.nx}x{g.ny} grid, "
+            f"nt {g.nt}, forward + adjoint gradient), FP64 C oracle, one OpenMP thread per "
+            f"shot on {shots} of {host_cores()} host cores, {seconds:.1f} s; the rate is over "
+            f"the cells computed, so the whole batch would take "
+            f"{seconds * wl.nshots / shots:.1f} s at it")
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     wl = workload(0, args.nshots, args.nt)
-    shots = cpu_sample_shots(args.cpu_shots)
+    shots = cpu_sample_shots(args.cpu_shots, wl.nshots)
     for _ in range(args.warmup):
         run_oracle_sample(wl, shots)
     vals, times = [], []
@@ -145,8 +164,6 @@ def reference_arm(args):
         vals.append(v)
         times.append(t)
     value = 2 * wl.grid.ncells * wl.grid.nt * shots * args.steps / sum(times) / 1e9
-    sample = (f"{shots} of {wl.nshots} shots per step (full {wl.grid.nx}x{wl.grid.ny} grid, "
-              f"nt {wl.grid.nt}, forward + adjoint gradient), FP64 C oracle, one thread per shot")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -154,8 +171,9 @@ def reference_arm(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name, "grid": f"{wl.grid.nx}x{wl.grid.ny}",
                    "shots_per_step": shots, "nt": wl.grid.nt, "nrec": wl.nrec},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": shots, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": shots, "nproc": host_cores(),
+                         "kind": "oracle",
+                         "sample": oracle_sample_text(wl, shots, sum(times) / len(times))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -226,29 +244,185 @@ def hbm_peak():
 
 
 def kernel_source_tag():
-    """sha1 prefix of gf_tile_kernels.cu without its // comments and blank lines: any change
-    of the code drops the ncu figures keyed on it, an edit of a comment does not."""
-    p = os.path.join(ROOT, "paper_2506_20513_gb300", "csrc", "gf_tile_kernels.cu")
-    with open(p, encoding="utf-8") as f:
-        lines = [re.sub(r"//.*$", "", line).rstrip() for line in f.read().splitlines()]
-    code = "\n".join(line for line in lines if line.strip())
-    return hashlib.sha1(code.encode()).hexdigest()[:12]
+    """sha1 prefix of the tile kernels' device code without its // comments and blank lines:
+    any change of the code drops the ncu figures keyed on it, an edit of a comment does not."""
+    code = []
+    for name in KERNEL_SOURCES:
+        p = os.path.join(ROOT, "paper_2506_20513_gb300", "csrc", name)
+        with open(p, encoding="utf-8") as f:
+            lines = [re.sub(r"//.*$", "", line).rstrip() for line in f.read().splitlines()]
+        code.append("\n".join(line for line in lines if line.strip()))
+    return hashlib.sha1("\n\f".join(code).encode()).hexdigest()[:12]
 
 
-def algorithmic_bytes_per_launch(kind: str, wl, K: int) -> float:
+def algorithmic_bytes_per_launch(kind: str, wl, K: float, history: float = 1.0) -> float:
     """Compulsory HBM bytes of one tile-kernel launch of K steps over all cells and shots:
-    fields Ez, Hx, Hy read and written once (24 B), the model read once per cell (8 B,
-    shared by the shots), CPML memories read and written in the strips (2 arrays x 8 B),
-    plus per step: forward, the Ez history write (4 B); adjoint, the history read (4 B,
-    K + 1 slots) and the per-shot gradient pair read and written once (16 B)."""
+    fields Ez, Hx, Hy read and written once (24 B), the model read once per cell (Ca, Cb:
+    8 B, shared by the shots), CPML memories read and written in the strips (2 arrays x 8 B),
+    plus per step: forward, the Ez history write (4 B; ``history`` = the fraction of forward
+    launches that store it, 0 for a misfit-only forward, 1/2 under checkpointing where the
+    first pass keeps only the checkpoints); adjoint, the history read (4 B, K + 1 slots) and
+    the per-shot gradient pair read and written once (16 B)."""
     g = wl.grid
     N, S = g.ncells, wl.nshots
     w = 2 * g.npml + 1
     strip_cells = w * g.ny + w * g.nx
     base = S * N * 24 + 8 * N + S * strip_cells * 16
     if kind == "fwd":
-        return base + S * N * 4 * K
+        return base + history * S * N * 4 * K
     return base + S * N * (16 + 4 * (K + 1))
+
+
+def read_profile(lib, ctx) -> dict:
+    """Per launch class: (total ms, launches) from the library's CUDA-event profile."""
+    import ctypes
+    from paper_2506_20513_gb300 import _lib
+    prof = {}
+    for name, kind in (("fwd", _lib.GF_KERNEL_FWD), ("adj", _lib.GF_KERNEL_ADJ),
+                       ("aux", _lib.GF_KERNEL_AUX)):
+        tot, cnt = ctypes.c_double(), ctypes.c_longlong()
+        lib.gf_profile_read(ctx, kind, ctypes.byref(tot), ctypes.byref(cnt))
+        prof[name] = (tot.value, cnt.value)
+    return prof
+
+
+def tile_roofline(prof: dict, wl, steps: int, history_fwd: float, tiling: str, clk: dict,
+                  sms: int) -> dict:
+    """Roofline of the dominant tile kernel from its own launches' CUDA-event durations."""
+    g = wl.grid
+    dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
+    tot_ms, cnt = prof[dom]
+    # launches of K steps except a possibly shorter last one: use the mean steps per launch;
+    # under checkpointing the forward runs twice per gradient (checkpoints, then recompute)
+    passes = 2 if (dom == "fwd" and history_fwd < 1.0) else 1
+    per_launch_steps = passes * g.nt / max(1, cnt / steps)
+    algo = algorithmic_bytes_per_launch(dom, wl, per_launch_steps, history_fwd)
+    avg_s = tot_ms / 1e3 / max(1, cnt)
+    peak, peak_kind = hbm_peak()
+    achieved = algo / avg_s / 1e9
+    key = f"{dom}@{kernel_source_tag()}@{g.nx}x{g.ny}x{wl.nshots}@{tiling}"
+    cell_steps = wl.nshots * g.ncells * per_launch_steps
+    tpc = NCU_TRAFFIC_PER_CELL_STEP.get(key)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": tpc * cell_steps if tpc else None,
+            "kernel": f"{dom}_tile_kernel", "peak_source": f"hbm_gbs of {peak_kind}",
+            "algorithmic_bytes_per_launch": algo, "steps_per_launch": per_launch_steps,
+            "avg_launch_us": avg_s * 1e6, "launches": cnt,
+            "phase_ms_per_step": {k: v[0] / steps for k, v in prof.items()}}
+    ipc = NCU_WARP_INST_PER_CELL_STEP.get(key)
+    if ipc:
+        # the bound that holds the kernel: warp instructions issued per second against the
+        # issue rate of all schedulers at the SM clock sampled during the timed region
+        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+        inst = ipc * cell_steps
+        peak_issue = sms * ISSUE_SLOTS_PER_SM_CLK * mhz * 1e6
+        roof["issue"] = {"achieved": inst / avg_s / 1e9, "peak": peak_issue / 1e9,
+                         "unit": "G warp-instructions/s", "frac": inst / avg_s / peak_issue,
+                         "warp_instructions_per_launch": inst,
+                         "peak_source": "SMs x 4 schedulers x sampled SM clock"}
+    return roof
+
+
+def fwi_leg(args, fd, wl, eps_t, sig_t, eps0, sig0) -> dict:
+    """The multishot workload's inversion as specified for it: L-BFGS over three Ricker bands
+    (100, 200, 400 MHz peak) with TV regularisation on, ``args.fwi_iters`` iterations in all,
+    from the smoothed starting model.  Reports seconds, FDTD evaluations and forward-equivalent
+    passes per iteration, and the iteration's HBM fraction: the algorithmic bytes of all its
+    FDTD time loops over its wall time."""
+    import torch
+    from paper_2506_20513_gb300.fdtd import ricker
+    from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
+    g = wl.grid
+    dev = fd.device
+    freqs = (100e6, 200e6, 400e6)
+    n = args.fwi_iters
+    iters = (n // 3, n // 3, n - 2 * (n // 3))
+    wav = lambda f0: torch.tensor(np.broadcast_to(ricker(f0, g.dt, g.nt), (wl.nshots, 1, g.nt)),
+                                  dtype=torch.float32, device=dev)
+    observed = {f0: fd.forward_model(eps_t, sig_t, wav(f0)) for f0 in freqs}
+    mask = interior_mask(g, rows_below_top=4)
+    # an untimed two-iteration run first: the driver's first iterations otherwise include the
+    # one-time loading of the PyTorch kernels its L-BFGS algebra uses
+    FWI(fd, observed.get, mask, FWIConfig(bands=((freqs[0], 2),), tv=True)).run(eps0, sig0)
+    cfg = FWIConfig(bands=tuple(zip(freqs, iters)), tv=True)
+    drv = FWI(fd, observed.get, mask, cfg)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    eps, sig, hist = drv.run(eps0, sig0)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    its = len(hist.seconds)
+    evals, passes = sum(hist.evaluations), sum(hist.passes)
+    grads, misfits = passes - evals, 2 * evals - passes
+    t = fd.tiling()
+    nl = -(-g.nt // t.steps)
+    k_eff = g.nt / nl
+    b_mis = nl * algorithmic_bytes_per_launch("fwd", wl, k_eff, 0.0)
+    b_grad = nl * (algorithmic_bytes_per_launch("fwd", wl, k_eff, 1.0)
+                   + algorithmic_bytes_per_launch("adj", wl, k_eff))
+    sec = sum(hist.seconds)
+    peak, peak_kind = hbm_peak()
+    achieved = (grads * b_grad + misfits * b_mis) / sec / 1e9
+    err = lambda e: float(torch.linalg.vector_norm(e - eps_t) / torch.linalg.vector_norm(eps_t))
+    return {"bands": [[f, i] for f, i in zip(freqs, iters)], "tv": True,
+            "iterations": its, "s_per_iteration": sec / max(1, its), "wall_s": wall,
+            "evaluations_per_iteration": evals / max(1, its),
+            "forward_equivalent_passes_per_iteration": passes / max(1, its),
+            "gradients": grads, "misfit_only_forwards": misfits,
+            "misfit_first_last": [hist.misfit[0], hist.final_misfit] if hist.misfit else None,
+            "eps_rel_error_start_end": [err(eps0), err(eps)],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
+                         "meaning": "algorithmic bytes of every FDTD time loop of the "
+                                    "iterations / their wall time (L-BFGS algebra, TV and "
+                                    "line search included in the time)"}}
+
+
+def large_leg(args, dev, sms: int) -> dict:
+    """The large-grid checkpointed gradient: 2108x1084 cells (30-cell CPML inside), 16 shots,
+    nt 8000, 400 receivers, forward wavefield checkpointed every ``args.large_checkpoint``
+    steps and recomputed per segment.  One warm-up gradient, two timed, one profiled."""
+    import torch
+    from paper_2506_20513_gb300 import FDTD
+    from paper_2506_20513_gb300.fdtd import ricker
+    wl = workload(0, 16, 8000, "large")
+    g = wl.grid
+    k = args.large_checkpoint
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    fd.set_storage(k)
+    t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
+    obs = fd.forward_model(t32(wl.eps_true), t32(wl.sig_true), wav)
+    e0, s0 = t32(wl.eps_init), t32(wl.sig_init)
+    fd.misfit_and_gradient(e0, s0, wav, obs)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 2
+    ev0.record()
+    for _ in range(reps):
+        fd.misfit_and_gradient(e0, s0, wav, obs)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / reps
+    fd.lib.gf_profile(fd.ctx, 1)
+    fd.misfit_and_gradient(e0, s0, wav, obs)
+    torch.cuda.synchronize(dev)
+    prof = read_profile(fd.lib, fd.ctx)
+    fd.lib.gf_profile(fd.ctx, 0)
+    clk = clocks.stop()
+    fd.status()
+    t = fd.tiling()
+    rec = {"workload": wl.name, "grid": f"{g.nx}x{g.ny}", "npml": g.npml, "nshots": wl.nshots,
+           "nt": g.nt, "nrec": wl.nrec, "checkpoint_every": k,
+           "s_per_gradient": ms / 1e3, "gcell_updates_per_s": wl.cell_updates() / ms / 1e6,
+           "workspace_gb": fd.workspace_bytes() / 1e9,
+           "tiling": f"{t.tile_w}x{t.tile_h}, K {t.steps}, variant {t.variant}",
+           "steps": reps, "warmup": 1, "clocks": clk,
+           "roofline": tile_roofline(prof, wl, 1, 0.5, f"default/k{k}", clk, sms)}
+    fd.close()
+    return rec
 
 
 def ours(args):
@@ -259,7 +433,8 @@ def ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2506_20513_gb300 import FDTD, Tiling, _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    from paper_2506_20513_gb300 import FDTD, Tiling
     from paper_2506_20513_gb300.fdtd import ricker
 
     if args.workload == "large":
@@ -269,6 +444,7 @@ def ours(args):
             args.checkpoint = 100
         # the FP64 oracle would need ~146 GB of host memory per shot for this grid
         args.no_cpu_baseline = True
+        args.no_large = True
     wl = workload(rank, args.nshots, args.nt, args.workload)
     g = wl.grid
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
@@ -315,50 +491,18 @@ def ours(args):
     for _ in range(args.steps):
         step()
     barrier()
-    import ctypes
-    prof = {}
-    for name, kind in (("fwd", _lib.GF_KERNEL_FWD), ("adj", _lib.GF_KERNEL_ADJ),
-                       ("aux", _lib.GF_KERNEL_AUX)):
-        tot, cnt = ctypes.c_double(), ctypes.c_longlong()
-        lib.gf_profile_read(ctx, kind, ctypes.byref(tot), ctypes.byref(cnt))
-        prof[name] = (tot.value, cnt.value)
+    prof = read_profile(lib, ctx)
     lib.gf_profile(ctx, 0)
     clk = clocks.stop()
     fd.status()
     ms = reduce_max(ms, dev)
     cells = wl.cell_updates() * args.steps * world
     value = job_value(wl.cell_updates() * args.steps, world, ms)
-
-    # roofline of the dominant tile kernel (its own launches, CUDA events on its stream)
-    dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
-    tot_ms, cnt = prof[dom]
-    nt = g.nt
-    # launches of K steps except a possibly shorter last one: use the mean steps per launch
-    per_launch_steps = nt / max(1, cnt / args.steps)
-    algo = algorithmic_bytes_per_launch(dom, wl, per_launch_steps)
-    avg_s = tot_ms / 1e3 / max(1, cnt)
-    peak, peak_kind = hbm_peak()
-    achieved = algo / avg_s / 1e9
-    key = f"{dom}@{kernel_source_tag()}@{g.nx}x{g.ny}x{wl.nshots}@{args.tile or 'default'}"
-    tpc = NCU_TRAFFIC_PER_CELL_STEP.get(key)
-    traffic = tpc * wl.nshots * g.ncells * per_launch_steps if tpc else None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": f"{dom}_tile",
-            "peak_source": f"hbm_gbs of {peak_kind}",
-            "avg_launch_us": avg_s * 1e6, "launches": cnt,
-            "phase_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}
-    ipc = NCU_WARP_INST_PER_CELL_STEP.get(key)
-    if ipc:
-        # the bound that holds the kernel: warp instructions issued per second against the
-        # issue rate of all schedulers at the SM clock sampled during the timed region
-        mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-        inst = ipc * wl.nshots * g.ncells * per_launch_steps
-        peak_issue = torch.cuda.get_device_properties(dev).multi_processor_count * \
-            ISSUE_SLOTS_PER_SM_CLK * mhz * 1e6
-        roof["issue"] = {"achieved": inst / avg_s / 1e9, "peak": peak_issue / 1e9,
-                         "unit": "G warp-instructions/s", "frac": inst / avg_s / peak_issue,
-                         "warp_instructions_per_launch": inst,
-                         "peak_source": "SMs x 4 schedulers x sampled SM clock"}
+    t = fd.tiling()
+    tiling_key = args.tile or "default"
+    roof = tile_roofline(prof, wl, args.steps, 0.5 if args.checkpoint else 1.0, tiling_key,
+                         clk, sms)
+    peak = roof["peak"]
     if not args.checkpoint:
         # the whole step against the bytes an untiled stencil moves per cell-update (forward:
         # fields read+written 24 B, Ca/Cb 8 B, history write 4 B; adjoint: 24 + 8 B, history
@@ -386,28 +530,23 @@ def ours(args):
         e2e = {"value": cells / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    # seconds per dual-parameter FWI iteration (L-BFGS with its line-search evaluations)
+    # seconds per dual-parameter FWI iteration, and the large-grid checkpointed gradient
+    # (on one GPU only: a multi-GPU run reports the scaling of the gradient step alone)
     fwi = None
-    if args.fwi_iters > 0:
-        from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
-        drv = FWI(fd, lambda f0: obs, interior_mask(g, rows_below_top=4),
-                  FWIConfig(bands=((wl.f0, args.fwi_iters),)))
-        # an untimed pass first: the FWI driver's first iterations otherwise include the one-time
-        # loading of the PyTorch kernels its L-BFGS algebra uses (seconds on a fresh process)
-        drv.run(eps0, sig0)
-        _, _, hist = drv.run(eps0, sig0)
-        fwi = {"iterations": len(hist.seconds),
-               "s_per_iteration": sum(hist.seconds) / max(1, len(hist.seconds)),
-               "evaluations_per_iteration": sum(hist.evaluations) / max(1, len(hist.evaluations)),
-               "misfit_first_last": [hist.misfit[0], hist.final_misfit] if hist.misfit else None}
+    if args.fwi_iters > 0 and world == 1 and args.workload == "multishot":
+        fwi = fwi_leg(args, fd, wl, eps_t, sig_t, eps0, sig0)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        shots = cpu_sample_shots(args.cpu_shots)
-        v, t = run_oracle_sample(wl, shots)
-        cpu = {"value": v, "unit": UNIT, "cores": shots, "kind": "oracle",
-               "sample": (f"{shots} of {wl.nshots} shots, full grid and nt, forward + adjoint "
-                          f"gradient, FP64 C oracle, one thread per shot, {t:.1f} s")}
+        shots = cpu_sample_shots(args.cpu_shots, wl.nshots)
+        v, tcpu = run_oracle_sample(wl, shots)
+        cpu = {"value": v, "unit": UNIT, "cores": shots, "nproc": host_cores(),
+               "kind": "oracle", "sample": oracle_sample_text(wl, shots, tcpu)}
+    workspace_gb = fd.workspace_bytes() / 1e9
+    fd.close()
+    large = None
+    if not args.no_large and world == 1:
+        large = large_leg(args, dev, sms)
 
     if rank == 0:
         line = {
@@ -419,22 +558,22 @@ def ours(args):
                        "shots_per_gpu": wl.nshots, "nt": g.nt, "nrec": wl.nrec,
                        "cell_updates_per_step": wl.cell_updates() * world,
                        "s_per_gradient": ms / args.steps / 1e3,
-                       "tiling": args.tile or "default 50,50,7,variant 0",
+                       "tiling": (f"{t.tile_w}x{t.tile_h}, K {t.steps}, variant {t.variant}"
+                                  + (" (--tile)" if args.tile else " (default)")),
                        "l2": "inputs larger than L2: each step streams the "
                              f"{wl.nshots * g.nt * g.ncells * 4 / 1e9:.1f} GB wavefield "
                              "through HBM" if not args.checkpoint else
                              "inputs larger than L2: checkpoints and segment buffers of "
-                             f"{fd.workspace_bytes() / 1e9:.1f} GB",
+                             f"{workspace_gb:.1f} GB",
                        "storage": (f"checkpoint every {args.checkpoint} steps"
                                    if args.checkpoint else "full wavefield"),
-                       "workspace_gb": fd.workspace_bytes() / 1e9,
+                       "workspace_gb": workspace_gb,
                        "parallelism": f"shots x{world} (independent per GPU)",
                        "fwi": fwi},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
-            "clocks": clk,
+            "roofline": roof, "large": large, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    fd.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -63,6 +63,9 @@ class FWIHistory:
     misfit: list = field(default_factory=list)        # J at the start of each iteration
     evaluations: list = field(default_factory=list)   # FDTD evaluations per iteration
                                                       # (misfit-only or misfit + gradient)
+    passes: list = field(default_factory=list)        # forward-equivalent time loops per
+                                                      # iteration: a misfit-only evaluation is
+                                                      # 1 (forward), a gradient 2 (+ adjoint)
     seconds: list = field(default_factory=list)       # wall time per iteration (synchronised)
     band: list = field(default_factory=list)
     learned: list = field(default_factory=list)       # True where the learned update was kept
@@ -88,9 +91,11 @@ class FWI:
             nb = self.fd.lib.gf_tv_scratch_bytes(nx, ny)
             self._tv_scratch = torch.empty(nb, dtype=torch.uint8, device=fdtd.device)
         self._J = torch.empty(1, dtype=torch.float64, device=fdtd.device)
+        self.passes = 0   # forward-equivalent time loops run so far (misfit 1, gradient 2)
 
     # -- evaluations through the library ---------------------------------------------------
     def _misfit(self, eps, sig, wav, obs) -> float:
+        self.passes += 1
         return float(self.fd.misfit(eps, sig, wav, obs, out=self._J).item())
 
     def _tv(self, model, grad):
@@ -109,6 +114,7 @@ class FWI:
         """J and the masked gradient in the variables x = (eps_r, sigma / sigma_ref) (and the
         raw model gradients with ``raw``)."""
         J, ge, gs = self.fd.misfit_and_gradient(eps, sig, wav, obs)
+        self.passes += 2
         if raw:
             ge0, gs0 = ge.clone(), gs.clone()
         if self.cfg.tv:
@@ -144,8 +150,8 @@ class FWI:
         x = x.to(dev)
         st = torch.load(resume, map_location=dev, weights_only=False) if resume else None
         if st is not None:
-            for k in ("misfit", "evaluations", "seconds", "band", "learned"):
-                getattr(hist, k).extend(st["hist"][k])
+            for k in ("misfit", "evaluations", "passes", "seconds", "band", "learned"):
+                getattr(hist, k).extend(st["hist"].get(k, []))
         logf = open(log, "a") if log else None
         J = float("nan")
         for bi, (f0, iters) in enumerate(c.bands):
@@ -183,6 +189,7 @@ class FWI:
                     break
                 torch.cuda.synchronize(dev)
                 t0 = time.perf_counter()
+                p0 = self.passes
                 tries = 0
                 kept = False
                 if learned and not use_net and 0 <= retry_at <= it:
@@ -257,7 +264,8 @@ class FWI:
                             break
                         alpha *= 0.5
                     if not accepted:
-                        self._record(hist, logf, f0, it, J, tries, time.perf_counter() - t0, False)
+                        self._record(hist, logf, f0, it, J, tries, self.passes - p0,
+                                     time.perf_counter() - t0, False)
                         eps, sig = self._split(x.float())
                         break
                 # the accepted model (projected onto the physical ranges), then its gradient
@@ -283,14 +291,16 @@ class FWI:
                         S.pop(0)
                         Y.pop(0)
                 torch.cuda.synchronize(dev)
-                self._record(hist, logf, f0, it, J, tries, time.perf_counter() - t0, kept)
+                self._record(hist, logf, f0, it, J, tries, self.passes - p0,
+                             time.perf_counter() - t0, kept)
                 x, g, J, first = x_new, g_new, J_next, False
                 if checkpoint and checkpoint_every > 0 and (it + 1) % checkpoint_every == 0:
                     state = dict(band_index=bi, iteration=it + 1, x=x.cpu(), g=g.cpu(), J=J,
                                  S=[t.cpu() for t in S], Y=[t.cpu() for t in Y], first=first,
                                  use_net=use_net, retry_at=retry_at,
                                  hist={k: list(getattr(hist, k)) for k in
-                                       ("misfit", "evaluations", "seconds", "band", "learned")})
+                                       ("misfit", "evaluations", "passes", "seconds", "band",
+                                        "learned")})
                     if learned:
                         state.update(ge=ge.cpu(), gs=gs.cpu(), illum=illum.cpu())
                     torch.save(state, checkpoint)
@@ -303,15 +313,16 @@ class FWI:
         return eps, sig, hist
 
     @staticmethod
-    def _record(hist, logf, f0, it, J, evals, seconds, learned):
+    def _record(hist, logf, f0, it, J, evals, passes, seconds, learned):
         hist.misfit.append(J)
         hist.evaluations.append(evals)
+        hist.passes.append(passes)
         hist.seconds.append(seconds)
         hist.band.append(f0)
         hist.learned.append(learned)
         if logf:
             logf.write(json.dumps({"band_f0": f0, "iteration": it, "misfit": J,
-                                   "evaluations": evals, "seconds": seconds,
+                                   "evaluations": evals, "passes": passes, "seconds": seconds,
                                    "learned": learned}) + "\n")
             logf.flush()
 

@@ -12,10 +12,11 @@ pytest.importorskip("torch")
 import bench  # noqa: E402
 
 
-def _tag_of(text, tmp_path, monkeypatch):
+def _tag_of(text, tmp_path, monkeypatch, common="__device__ int g(int x) { return x; }\n"):
     csrc = tmp_path / "paper_2506_20513_gb300" / "csrc"
     csrc.mkdir(parents=True, exist_ok=True)
     (csrc / "gf_tile_kernels.cu").write_text(text)
+    (csrc / "gf_tile_common.cuh").write_text(common)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     return bench.kernel_source_tag()
 
@@ -27,6 +28,14 @@ def test_code_tag_ignores_comments_and_blank_lines(tmp_path, monkeypatch):
     assert _tag_of(edited, tmp_path, monkeypatch) == base
     changed = "// header\nint f(int x) {\n    return x + 2;  // add one\n}\n"
     assert _tag_of(changed, tmp_path, monkeypatch) != base
+    # the shared device code counts too
+    other = "__device__ int g(int x) { return x + 1; }\n"
+    assert _tag_of(src, tmp_path, monkeypatch, common=other) != base
+
+
+def test_real_sources_have_a_tag():
+    tag = bench.kernel_source_tag()
+    assert len(tag) == 12 and int(tag, 16) >= 0
 
 
 def test_algorithmic_bytes_per_cell_step():
@@ -41,3 +50,13 @@ def test_algorithmic_bytes_per_cell_step():
     assert 7.5 < fwd < 8.5
     assert 10.3 < adj < 11.3
     assert adj > fwd
+    # a misfit-only forward stores no history: 4 B per step less
+    nohist = bench.algorithmic_bytes_per_launch("fwd", wl, 7, 0.0) / cells
+    assert fwd - nohist == pytest.approx(4.0)
+
+
+def test_cpu_sample_is_bounded_by_shots_and_cores():
+    n = bench.cpu_sample_shots(0, 32)
+    assert 1 <= n <= min(32, bench.host_cores())
+    assert bench.cpu_sample_shots(0, 2) <= 2
+    assert bench.cpu_sample_shots(5, 3) == 3

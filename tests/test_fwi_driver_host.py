@@ -74,6 +74,9 @@ def test_accepted_lbfgs_steps_cost_one_evaluation(no_cuda_sync):
     assert hist.evaluations[1:] == [1] * (len(hist.evaluations) - 1)  # alpha = 1 on a quadratic
     # one gradient per iteration at most (reused or computed once at the accepted point)
     assert fd.calls["gradient"] <= 1 + len(hist.evaluations)
+    # forward-equivalent passes: a misfit-only evaluation is one time loop, a gradient two
+    assert sum(hist.passes) == fd.calls["misfit"] + 2 * fd.calls["gradient"] - 2
+    assert hist.passes[1:] == [2] * (len(hist.passes) - 1)
 
 
 def test_iteration_converges_on_the_quadratic(no_cuda_sync):
