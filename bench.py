@@ -9,8 +9,9 @@ advanced one time step in one shot, counted once for the forward and once for th
 2 * N * nt * nshots per step.
 
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle instead, on a
-bounded sample of the same workload.  Under torchrun every rank runs its own 32-shot batch
-(independent shots, no data-path collective: weak scaling).
+bounded sample of the same workload.  Under torchrun the ranks share one acquisition of
+32 x N shots over one model, split round-robin (32 shots per GPU: weak scaling); every step
+ends with an NCCL all-reduce of (J, g_eps_r, g_sigma), as one sharded inversion needs.
 """
 from __future__ import annotations
 
@@ -83,11 +84,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def workload(rank: int, nshots: int, nt: int, kind: str = "multishot"):
+def workload(rank: int, nshots: int, nt: int, kind: str = "multishot", world: int = 1):
+    """This rank's share of one acquisition of nshots x world shots over one seeded model:
+    shots split round-robin over the ranks (weak scaling: nshots per GPU)."""
+    from dataclasses import replace
     from paper_2506_20513_gb300 import workloads as W
+    from paper_2506_20513_gb300.shard import shard_shots
     if kind == "large":
-        return W.large_checkpointed(seed=4000 + rank, nshots=min(nshots, 16), nt=nt)
-    return W.multishot_layered(seed=1000 + rank, nshots=nshots, nt=nt)
+        wl = W.large_checkpointed(seed=4000, nshots=min(nshots, 16) * world, nt=nt)
+    else:
+        wl = W.multishot_layered(seed=1000, nshots=nshots * world, nt=nt)
+    if world == 1:
+        return wl
+    mine = shard_shots(wl.nshots, rank, world)
+    return replace(wl, src=wl.src[mine], rec=wl.rec[mine])
 
 
 def reduce_max(x: float, device) -> float:
@@ -445,7 +455,7 @@ def ours(args):
         # the FP64 oracle would need ~146 GB of host memory per shot for this grid
         args.no_cpu_baseline = True
         args.no_large = True
-    wl = workload(rank, args.nshots, args.nt, args.workload)
+    wl = workload(rank, args.nshots, args.nt, args.workload, world)
     g = wl.grid
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
     fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=tiling)
@@ -458,8 +468,11 @@ def ours(args):
     obs = fd.forward_model(eps_t, sig_t, wav)
     fd.status()
 
+    from paper_2506_20513_gb300.shard import allreduce_sum
+
     def step():
-        return fd.misfit_and_gradient(eps0, sig0, wav, obs)
+        # this rank's shots, then the sum over the ranks (the identity on one GPU)
+        return allreduce_sum(*fd.misfit_and_gradient(eps0, sig0, wav, obs))
 
     for _ in range(args.warmup):
         step()
@@ -518,11 +531,19 @@ def ours(args):
     if not args.no_e2e:
         h = lambda t: t.detach().to("cpu").pin_memory()
         he, hs, hw, ho = h(eps0), h(sig0), h(wav), h(obs)
-        fd.misfit_and_gradient(he, hs, hw, ho)
+
+        def e2e_step():
+            if world == 1:
+                return fd.misfit_and_gradient(he, hs, hw, ho)
+            d = lambda x: x.to(dev, non_blocking=True)
+            out = allreduce_sum(*fd.misfit_and_gradient(d(he), d(hs), d(hw), d(ho)))
+            return tuple(x.cpu() for x in out)
+
+        e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            Jh, geh, gsh = fd.misfit_and_gradient(he, hs, hw, ho)
+            Jh, geh, gsh = e2e_step()
         barrier()
         te = reduce_max(time.perf_counter() - t0, dev)
         h2d = sum(x.numel() * x.element_size() for x in (he, hs, hw, ho))
@@ -568,7 +589,10 @@ def ours(args):
                        "storage": (f"checkpoint every {args.checkpoint} steps"
                                    if args.checkpoint else "full wavefield"),
                        "workspace_gb": workspace_gb,
-                       "parallelism": f"shots x{world} (independent per GPU)",
+                       "parallelism": (f"{wl.nshots * world} shots split round-robin over "
+                                       f"{world} GPUs, (J, g_eps, g_sigma) summed by an NCCL "
+                                       "all-reduce every step" if world > 1 else
+                                       "one GPU, all shots"),
                        "fwi": fwi},
             "roofline": roof, "large": large, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
