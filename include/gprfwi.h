@@ -190,6 +190,19 @@ size_t gf_tv_scratch_bytes(int nx, int ny);
 int gf_tv_gradient(int nx, int ny, const float* model, float* grad, void* scratch, float lambda,
                    float mu, int iters, float weight, void* stream);
 
+/* One Adam step (Sec. 2.3: the updates of eps_r and sigma with bias-corrected first and
+ * second moments) on n cells of one model parameter, in place, on `stream`:
+ *   g' = gscale * grad;  m = beta1 m + (1 - beta1) g';  v = beta2 v + (1 - beta2) g'^2;
+ *   x  = max(xmin, x - lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps))
+ * at the cells where mask != 0 (mask NULL: every cell); masked cells keep x, m and v.
+ * x, grad, m, v, mask: device float32 [n], owned by the caller (m, v zeroed before t = 1).
+ * t >= 1 is this parameter's step count; 0 <= beta < 1, eps > 0, lr >= 0, else GF_EINVAL
+ * (message via gf_last_error(NULL)).  The clamp at xmin is the paper's eps_r >= 1,
+ * sigma >= 0 projection (Sec. 3.1 demo). */
+int gf_adam_update(long long n, float* x, const float* grad, float* m, float* v,
+                   const float* mask, float gscale, float lr, float beta1, float beta2, float eps,
+                   int t, float xmin, void* stream);
+
 /* Synchronise `stream` and return the device status word (GF_OK or the first device-side
  * error since the last gf_status call), then clear it. */
 int gf_status(gf_ctx* ctx, void* stream);

@@ -37,7 +37,7 @@ EXPORTS = (
     "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_set_wait_budget", "gf_profile",
     "gf_profile_read", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
-    "gf_tv_gradient", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
+    "gf_tv_gradient", "gf_adam_update", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
     "gf_batch_last_error", "gf_batch_misfit_and_gradient",
     "gf_unet_param_count", "gf_unet_create", "gf_unet_destroy", "gf_unet_last_error",
     "gf_unet_set_params", "gf_unet_get_params", "gf_unet_forward", "gf_unet_loss_and_grad",
@@ -120,6 +120,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_tv_scratch_bytes": (sz, [i, i]),
             "gf_tv_gradient": (i, [i, i, vp, vp, vp, ctypes.c_float, ctypes.c_float, i,
                                    ctypes.c_float, vp]),
+            "gf_adam_update": (i, [ctypes.c_longlong, vp, vp, vp, vp, vp] + [ctypes.c_float] * 5
+                               + [i, ctypes.c_float, vp]),
             "gf_autotune": (i, [vp, vp, vp, vp, ctypes.c_char_p, i, vp]),
             "gf_batch_create": (i, [P(vp), P(vp), i]),
             "gf_batch_destroy": (None, [vp]),

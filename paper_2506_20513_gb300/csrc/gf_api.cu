@@ -940,6 +940,26 @@ int gf_tv_gradient(int nx, int ny, const float* model, float* grad, void* scratc
     return GF_OK;
 }
 
+int gf_adam_update(long long n, float* x, const float* grad, float* m, float* v,
+                   const float* mask, float gscale, float lr, float beta1, float beta2, float eps,
+                   int t, float xmin, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !grad || !m || !v)) || t < 1 || !(lr >= 0.f) ||
+        !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f) ||
+        !isfinite(gscale)) {
+        create_fail("gf_adam_update: invalid argument");
+        return GF_EINVAL;
+    }
+    if (n == 0) return GF_OK;
+    cudaError_t e = gf::adam_update(n, x, grad, m, v, mask, gscale, lr, beta1, beta2, eps, t,
+                                    xmin, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        create_fail("gf_adam_update: %s", cudaGetErrorString(e));
+        return GF_ECUDA;
+    }
+    return GF_OK;
+}
+
 int gf_status(gf_ctx* c, void* stream) {
     if (!c) return GF_EINVAL;
     if (!c->ws) return GF_OK;

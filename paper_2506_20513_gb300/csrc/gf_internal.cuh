@@ -128,6 +128,9 @@ cudaError_t launch_residual_misfit(const float* traces, const float* observed, f
 cudaError_t launch_finish_misfit(const double* partial, int nblocks, double* misfit,
                                  cudaStream_t st);
 size_t tv_scratch_floats(long long n);
+cudaError_t adam_update(long long n, float* x, const float* g, float* m, float* v,
+                        const float* mask, float gscale, float lr, float b1, float b2, float eps,
+                        int t, float xmin, cudaStream_t st);
 cudaError_t tv_gradient(int nx, int ny, const float* X, float* G, float* scratch, float lambda,
                         float mu, int iters, float weight, cudaStream_t st);
 // out[gy * nx + gx] = sum over shots of per_shot[s * pitch * ny + gy * pitch + gx].

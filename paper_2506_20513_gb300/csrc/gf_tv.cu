@@ -9,6 +9,9 @@
 // (1 + 4 mu) u - mu * sum(neighbours) = x + mu D^T (Z - B) per iteration,
 // Z = shrink(D u + B, lambda / mu) (isotropic) and B += D u - Z.  The TV gradient pulls the
 // model towards its denoised version, in normalised units: G += weight * max|G| * (x - u).
+//
+// Also here: the Adam update of one model parameter (Sec. 2.3), the other model-space kernel
+// of the inversion drivers.
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -103,7 +106,37 @@ int blocks_for(long long n) {
     return (int)(b < 1 ? 1 : (b > 152 * 8 ? 152 * 8 : b));
 }
 
+// One Adam step where the mask is non-zero: g' = gscale g, first and second moments
+// m = b1 m + (1 - b1) g', v = b2 v + (1 - b2) g'^2, then
+// x = max(xmin, x - lr (m c1) / (sqrt(v c2) + eps)) with the bias corrections
+// c1 = 1 / (1 - b1^t), c2 = 1 / (1 - b2^t).  Masked cells keep x, m and v.
+__global__ void adam_kernel(long long n, float* __restrict__ x, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v,
+                            const float* __restrict__ mask, float gscale, float lr, float b1,
+                            float b2, float eps, float c1, float c2, float xmin) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (mask && mask[k] == 0.f) continue;
+        const float gk = gscale * g[k];
+        const float mk = b1 * m[k] + (1.f - b1) * gk;
+        const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        x[k] = fmaxf(xmin, x[k] - lr * (mk * c1) / (sqrtf(vk * c2) + eps));
+    }
+}
+
 }  // namespace
+
+cudaError_t adam_update(long long n, float* x, const float* g, float* m, float* v,
+                        const float* mask, float gscale, float lr, float b1, float b2, float eps,
+                        int t, float xmin, cudaStream_t st) {
+    const float c1 = (float)(1.0 / (1.0 - pow((double)b1, t)));
+    const float c2 = (float)(1.0 / (1.0 - pow((double)b2, t)));
+    adam_kernel<<<blocks_for(n), 256, 0, st>>>(n, x, g, m, v, mask, gscale, lr, b1, b2, eps, c1,
+                                               c2, xmin);
+    return cudaGetLastError();
+}
 
 size_t tv_scratch_floats(long long n) { return 7 * (size_t)n + 64; }
 

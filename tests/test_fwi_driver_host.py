@@ -84,3 +84,12 @@ def test_iteration_converges_on_the_quadratic(no_cuda_sync):
     eps, sig, hist = run(fd, 30)
     assert hist.misfit[-1] < 1e-3 * hist.misfit[0]
     assert float((eps - fd.eps_true).abs().max()) < 0.05
+
+
+def test_adam_stage_schedule():
+    from paper_2506_20513_gb300.adam import AdamConfig, Stage, stage_of
+    st = (Stage(3, 0.2, 0.0), Stage(2, 0.1, 1e-4))
+    assert [stage_of(st, e) for e in range(6)] == [0, 0, 0, 1, 1, -1]
+    # the default is the cross-hole schedule: eps_r alone for 50 epochs, then both
+    d = AdamConfig().stages
+    assert d[0].epochs == 50 and d[0].lr_sig == 0.0 and d[1].lr_sig > 0.0
