@@ -239,20 +239,21 @@ int gf_profile_read(gf_ctx* ctx, int kind, double* ms_total, long long* launches
 /* Forward model without any memory allocation.  The paper has no counterpart: this is a
  * service for callers that may not allocate device memory (their memory belongs to another
  * runtime or a fixed pool, or they run under a hard budget or in a loop that must not enter
- * the allocator).  It computes exactly what gf_forward_model computes (48 x 48 tiles, 8 steps
- * per launch), without a context: grid and acq are as for gf_create (HOST pointers, read
- * during the call); eps_r, sigma, wavelet are device inputs and traces the device output
- * [nshots][nt][nrec], all owned by the caller, on `device`.  All working memory (time-stepping
- * state, CPML profiles, geometry, per-tile receiver lists) lives in one static 64 MiB device
- * array that every GPU loading this library holds until the process exits; the call never
- * calls cudaMalloc, cudaFree or another allocating routine.  Limits: nx, ny <= 16384 and
- * about nshots * nx * ny <= 1.1e6 cells (GF_ENOMEM with the exact need otherwise); GF_EINVAL
- * and GF_ECFL as for gf_create; messages via gf_last_error(NULL).  Model values are not
- * checked on the device.  The array is shared by all calls on a device and keeps the last
- * call's contents (each call clears what must start at zero); calls that overlap on the GPU
- * race and must be serialised by the caller.  The first call on a device looks up the
- * array's address and sets kernel attributes with that device current: make it before any
- * stream capture.  The call synchronises `stream` once while uploading the profiles. */
+ * the allocator).  It computes the same forward model as gf_forward_model, to FP32 rounding,
+ * with its own fixed tiling (48 x 48 tiles, 8 steps per launch), without a context: grid and
+ * acq are as for gf_create (HOST pointers, read only before the call returns); eps_r, sigma,
+ * wavelet are device inputs and traces the device output [nshots][nt][nrec], all owned by the
+ * caller, on `device`.  All working memory (time-stepping state, CPML profiles, geometry,
+ * per-tile receiver lists) lives in one static 64 MiB device array that every GPU loading
+ * this library holds until the process exits; the call never calls cudaMalloc, cudaFree or
+ * another allocating routine.  Limits: nx, ny <= 16384 and about nshots * nx * ny <= 1.1e6
+ * cells (GF_ENOMEM with the exact need otherwise); GF_EINVAL and GF_ECFL as for gf_create;
+ * messages via gf_last_error(NULL).  Model values are not checked on the device.  The array
+ * is shared by all calls on a device and keeps the last call's contents (each call clears
+ * what must start at zero); calls that overlap on the GPU race and must be serialised by the
+ * caller.  Every call copies the geometry from host memory and synchronises `stream` once, so
+ * no call can be captured into a CUDA graph: on a stream that is capturing, the call returns
+ * GF_EINVAL before it touches the stream (the capture stays valid). */
 int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acquisition* acq, int device,
                              const float* eps_r, const float* sigma, const float* wavelet,
                              float* traces, void* stream);

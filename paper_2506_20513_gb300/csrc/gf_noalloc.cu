@@ -195,6 +195,15 @@ extern "C" int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acqui
         if (ij[0] < 1 || ij[0] > g.nx - 2 || ij[1] < 1 || ij[1] > g.ny - 2)
             return fail(GF_EINVAL, "gf_forward_model_noalloc: source or receiver off 1..n-2");
     }
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &capture) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GF_ECUDA, "gf_forward_model_noalloc: cannot query the stream");
+    }
+    if (capture != cudaStreamCaptureStatusNone)
+        return fail(GF_EINVAL, "gf_forward_model_noalloc: the stream is capturing (the call "
+                    "synchronises it and cannot be captured)");
+
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev ||
         device >= kMaxDevices) {
