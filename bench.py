@@ -40,10 +40,16 @@ FALLBACK_HBM_GBS = 6800.0
 # on the multishot workload with nt = 70, default tiling), divided by the launch's cell-steps.
 # Keyed on kernel_source_tag(): any change of the kernel code drops them (reported as null).
 # DRAM bytes (read + write) per cell-step:
-NCU_TRAFFIC_PER_CELL_STEP: dict = {}
+NCU_TRAFFIC_PER_CELL_STEP: dict = {
+    "adj@bb39aa0cbe98@540x290x32@default": 12.1438,   # 426.02 MB / 35.0784 M cell-steps
+    "fwd@bb39aa0cbe98@540x290x32@default": 8.0171,    # 281.24 MB
+}
 # Warp instructions per cell-step (the kernels are bound by instruction issue, so the line
 # also reports the issue roofline):
-NCU_WARP_INST_PER_CELL_STEP: dict = {}
+NCU_WARP_INST_PER_CELL_STEP: dict = {
+    "adj@bb39aa0cbe98@540x290x32@default": 2.9729,    # 104.283 M warp instructions
+    "fwd@bb39aa0cbe98@540x290x32@default": 2.0810,    # 72.997 M
+}
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 # the files holding the tile kernels' device code
 KERNEL_SOURCES = ("gf_tile_kernels.cu", "gf_tile_common.cuh")
