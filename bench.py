@@ -612,11 +612,13 @@ def ours(args):
 def uneven(args):
     """64 independent instances of uneven size (128-768 x 128-384 cells + 20-cell CPML, nt
     800-3000, 1-8 shots, checkpoints every 100 steps), each tuned by the autotuner, one
-    gradient each per step: one after the other vs concurrently as one replayed CUDA graph."""
+    gradient each per step: one after the other, concurrently as one replayed CUDA graph of
+    per-instance streams, and as the persistent multi-instance schedule (the instances'
+    persistent passes merged into single cooperative launches, replayed as one CUDA graph)."""
     import tempfile
 
     import torch
-    from paper_2506_20513_gb300 import FDTD, FDTDBatch, autotune, workloads as W
+    from paper_2506_20513_gb300 import FDTD, FDTDBatch, Tiling, autotune, workloads as W
     from paper_2506_20513_gb300.fdtd import ricker
     dev = torch.device("cuda", 0)
     insts = W.uneven_instances(count=args.nshots if args.nshots != 32 else 64)
@@ -636,11 +638,10 @@ def uneven(args):
         ins.append((e0, s0, wav, obs))
     torch.cuda.synchronize(dev)
     t_tune = time.perf_counter() - t_tune
-    batch = FDTDBatch(fds)
     cols = [list(x) for x in zip(*ins)]
     cells = sum(w.cell_updates() for w in insts)
-    out = {}
-    for mode in (0, 2):
+
+    def timed(batch, mode):
         for _ in range(max(1, args.warmup)):
             batch.misfit_and_gradient(*cols, mode=mode)
         torch.cuda.synchronize(dev)
@@ -650,21 +651,45 @@ def uneven(args):
             batch.misfit_and_gradient(*cols, mode=mode)
         e1.record()
         torch.cuda.synchronize(dev)
-        out[mode] = e0.elapsed_time(e1) / args.steps
-    tilings = {}
+        for fd in fds:
+            fd.status()
+        return e0.elapsed_time(e1) / args.steps
+
+    def tilings():
+        out = {}
+        for fd in fds:
+            t = fd.tiling()
+            key = f"{t.tile_w}x{t.tile_h}/K{t.steps}/v{t.variant}"
+            out[key] = out.get(key, 0) + 1
+        return out
+
+    # the autotuned tilings: one instance after the other, and the graph of their streams
+    batch = FDTDBatch(fds)
+    out = {0: timed(batch, 0), 2: timed(batch, 2)}
+    tuned = tilings()
+    batch.close()
+    # the persistent multi-instance schedule: every instance on the persistent variant with
+    # its tuned time-block depth, the passes of all instances merged into single launches
     for fd in fds:
-        t = fd.tiling()
-        key = f"{t.tile_w}x{t.tile_h}/K{t.steps}/v{t.variant}"
-        tilings[key] = tilings.get(key, 0) + 1
-    line = {"metric": METRIC + " (uneven-instance batch)", "value": cells / (out[2] / 1e3) / 1e9,
+        fd.set_tiling(Tiling(0, 0, fd.tiling().steps, 3))
+    batch = FDTDBatch(fds)
+    flow_seq = timed(batch, 0)
+    out[4] = timed(batch, 4)
+    out[3] = timed(batch, 3)
+    line = {"metric": METRIC + " (uneven-instance batch)", "value": cells / (out[4] / 1e3) / 1e9,
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": out[2], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": out[4], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{len(insts)} uneven instances (128-768 x 128-384 + CPML, "
                                    "nt 800-3000, 1-8 shots), checkpoint every 100 steps",
-                       "cell_updates_per_step": cells, "ms_sequential": out[0],
-                       "ms_graph": out[2], "speedup_graph_vs_sequential": out[0] / out[2],
-                       "autotune_s": t_tune, "tilings_chosen": tilings}}
+                       "cell_updates_per_step": cells,
+                       "ms_sequential_tuned": out[0], "ms_stream_graph_tuned": out[2],
+                       "ms_sequential_persistent_variant": flow_seq,
+                       "ms_merged_persistent": out[3], "ms_merged_persistent_graph": out[4],
+                       "speedup_vs_sequential_tuned": out[0] / out[4],
+                       "speedup_stream_graph_vs_sequential": out[0] / out[2],
+                       "autotune_s": t_tune, "tilings_chosen": tuned,
+                       "tilings_persistent": tilings()}}
     print(json.dumps(line), flush=True)
     batch.close()
     return 0

@@ -281,8 +281,17 @@ const char* gf_batch_last_error(const gf_batch* batch);
  * `stream`; mode 1: all instances concurrently on the batch's streams, forked from and joined
  * back into `stream`; mode 2: mode 1 captured once into a CUDA graph and replayed (a single
  * graph launch per call) while the argument pointers and every context's configuration stay
- * the same, re-captured otherwise.  Each context's workspace is allocated before the first
- * fork; profiling must be off.  Asynchronous on `stream`. */
+ * the same, re-captured otherwise; mode 3: the persistent multi-instance schedule (every
+ * context must use the persistent variant 3): each context's operations run in its own order
+ * on `stream`, and the persistent passes that the contexts have pending at the same point
+ * (forward with the wavefield store, forward without it, or adjoint) run as ONE cooperative
+ * launch over all of their work items, block-major across the instances, each item waiting
+ * (bounded, GF_ETIMEOUT via gf_status of its context) only for its own instance's neighbours;
+ * mode 4: mode 3 captured once into a CUDA graph and replayed under the same rule as mode 2.
+ * The schedule of modes 3 and 4 is recorded on the first call and kept (with a device copy of
+ * its work items) while the argument pointers and the contexts' configuration, wait budget
+ * included, stay the same.  Each context's workspace is allocated before the first fork;
+ * profiling must be off.  Asynchronous on `stream`. */
 int gf_batch_misfit_and_gradient(gf_batch* batch, const float* const* eps_r,
                                  const float* const* sigma, const float* const* wavelet,
                                  const float* const* observed, double* misfit,

@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -34,6 +35,21 @@ struct Layout {
 };
 
 }  // namespace
+
+// The stream operations of one context while a batch records them instead of running them
+// (the persistent multi-instance schedule runs every context's operations in its own order,
+// merging the persistent passes of several contexts into one launch).
+struct StreamOp {
+    int kind = -1;      // -1: copy or memset; GF_KERNEL_*: a kernel of that family
+    bool flow = false;  // a persistent pass (inst, adjoint): mergeable across contexts
+    bool adjoint = false;
+    gf::FlowInstance inst{};
+    std::function<cudaError_t(cudaStream_t)> run;  // the operation itself (non-flow)
+    const char* what = "";
+};
+struct OpList {
+    std::vector<StreamOp> ops;
+};
 
 struct gf_ctx {
     gf_grid_desc g;
@@ -70,6 +86,7 @@ struct gf_ctx {
     long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
     long long launches = 0;
+    OpList* rec = nullptr;  // set while a batch records this context's operations
     bool profiling = false;
     // per kernel family: recorded (start, stop) event pairs not yet read
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
@@ -138,6 +155,48 @@ cudaError_t launch(gf_ctx* c, int kind, cudaStream_t st, F&& f) {
     if (e == cudaSuccess) ++c->launches;
     return e;
 }
+
+// Run a stream operation now, or append it to the context's recorder.
+int stream_op(gf_ctx* c, cudaStream_t st, int kind, const char* what,
+              std::function<cudaError_t(cudaStream_t)> f) {
+    if (c->rec) {
+        StreamOp op;
+        op.kind = kind;
+        op.run = std::move(f);
+        op.what = what;
+        c->rec->ops.push_back(std::move(op));
+        return GF_OK;
+    }
+    const cudaError_t e = kind >= 0 ? launch(c, kind, st, [&] { return f(st); }) : f(st);
+    return e == cudaSuccess ? GF_OK : cuda_fail(c, e, what);
+}
+
+// One persistent pass of the context, now or recorded.
+int flow_op(gf_ctx* c, cudaStream_t st, const gf::FlowInstance& inst, bool adjoint,
+            const char* what) {
+    if (c->rec) {
+        StreamOp op;
+        op.kind = adjoint ? GF_KERNEL_ADJ : GF_KERNEL_FWD;
+        op.flow = true;
+        op.adjoint = adjoint;
+        op.inst = inst;
+        op.what = what;
+        c->rec->ops.push_back(std::move(op));
+        return GF_OK;
+    }
+    const cudaError_t e = launch(c, adjoint ? GF_KERNEL_ADJ : GF_KERNEL_FWD, st,
+                                 [&] { return gf::launch_flow_pass(inst, adjoint, st); });
+    return e == cudaSuccess ? GF_OK : cuda_fail(c, e, what);
+}
+
+// A stream operation: the expression after `what` runs on stream s_ (now or when a recorded
+// schedule replays it; it captures by value).
+#define GF_OP(ctx, st, kind, what, ...)                                                    \
+    do {                                                                                  \
+        const int rc_ = stream_op((ctx), (st), (kind), (what),                            \
+                                  [=](cudaStream_t s_) -> cudaError_t { return __VA_ARGS__; }); \
+        if (rc_) return rc_;                                                              \
+    } while (0)
 
 void drop_profile(gf_ctx* c) {
     for (auto& v : c->prof_ev) {
@@ -306,12 +365,12 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
 int prepare_model(gf_ctx* c, const Layout& L, const float* eps_r, const float* sigma,
                   cudaStream_t st) {
     float* ca = (float*)(c->ws + L.coef);
-    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
-                return gf::launch_prepare_model(eps_r, sigma, c->g.nx, c->g.ny, c->pitch,
-                                                (float)(c->g.dt / kEps0), ca, ca + c->Np,
-                                                (int*)(c->ws + L.status), st);
-            }),
-            "prepare_model");
+    int* status = (int*)(c->ws + L.status);
+    const int nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+    const float dt_eps0 = (float)(c->g.dt / kEps0);
+    const long long Np = c->Np;
+    GF_OP(c, st, GF_KERNEL_AUX, "prepare_model",
+          gf::launch_prepare_model(eps_r, sigma, nx, ny, pitch, dt_eps0, ca, ca + Np, status, s_));
     return GF_OK;
 }
 
@@ -339,16 +398,17 @@ int forward_steps(gf_ctx* c, const Layout& L, gf::TileParams& p, float* const bu
     if (n_end <= n_begin) return GF_OK;
     if (c->variant == gf::kFlowVariant) {
         int* done = (int*)(c->ws + L.done);
-        GF_CUDA(c, cudaMemsetAsync(done, 0, sizeof(int) * (size_t)p.ntiles * c->nshots, st), "clear counters");
+        const size_t nb = sizeof(int) * (size_t)p.ntiles * c->nshots;
+        GF_OP(c, st, -1, "clear counters", cudaMemsetAsync(done, 0, nb, s_));
         p.K = c->K;
-        GF_CUDA(c, launch(c, GF_KERNEL_FWD, st, [&] {
-                    return gf::launch_flow_pass(p, buf[cur], buf[cur ^ 1], done, n_begin, n_end - 1,
-                                                c->K, c->wait_budget, false, st);
-                }),
-                "fwd_flow");
+        const gf::FlowInstance fi{p, gf::make_flow_args(buf[cur], buf[cur ^ 1], done, n_begin,
+                                                        n_end - 1, c->K, c->wait_budget)};
+        const int rc = flow_op(c, st, fi, false, "fwd_flow");
+        if (rc) return rc;
         cur ^= ((n_end - n_begin + c->K - 1) / c->K) & 1;
         return GF_OK;
     }
+    if (c->rec) return fail(c, GF_ESTATE, "only the persistent variant's passes can be merged");
     for (int n0 = n_begin; n0 < n_end; n0 += c->K) {
         p.n0 = n0;
         p.K = std::min(c->K, n_end - n0);
@@ -368,16 +428,17 @@ int adjoint_steps(gf_ctx* c, const Layout& L, gf::TileParams& p, float* const bu
     if (n_end <= n_begin) return GF_OK;
     if (c->variant == gf::kFlowVariant) {
         int* done = (int*)(c->ws + L.done);
-        GF_CUDA(c, cudaMemsetAsync(done, 0, sizeof(int) * (size_t)p.ntiles * c->nshots, st), "clear counters");
+        const size_t nb = sizeof(int) * (size_t)p.ntiles * c->nshots;
+        GF_OP(c, st, -1, "clear counters", cudaMemsetAsync(done, 0, nb, s_));
         p.K = c->K;
-        GF_CUDA(c, launch(c, GF_KERNEL_ADJ, st, [&] {
-                    return gf::launch_flow_pass(p, buf[cur], buf[cur ^ 1], done, n_begin, n_end - 1,
-                                                c->K, c->wait_budget, true, st);
-                }),
-                "adj_flow");
+        const gf::FlowInstance fi{p, gf::make_flow_args(buf[cur], buf[cur ^ 1], done, n_begin,
+                                                        n_end - 1, c->K, c->wait_budget)};
+        const int rc = flow_op(c, st, fi, true, "adj_flow");
+        if (rc) return rc;
         cur ^= ((n_end - n_begin + c->K - 1) / c->K) & 1;
         return GF_OK;
     }
+    if (c->rec) return fail(c, GF_ESTATE, "only the persistent variant's passes can be merged");
     for (int n1 = n_end - 1; n1 >= n_begin; n1 -= c->K) {
         const int k = std::min(c->K, n1 - n_begin + 1);
         p.n0 = n1 - k + 1;
@@ -406,8 +467,15 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
     const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
     float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
-    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear state");
-    if (illum) GF_CUDA(c, cudaMemsetAsync(p.illum, 0, state / gf::kNumFields, st), "clear illumination");
+    {
+        float* b0 = st_buf[0];
+        GF_OP(c, st, -1, "clear state", cudaMemsetAsync(b0, 0, state, s_));
+        if (illum) {
+            float* ill = p.illum;
+            GF_OP(c, st, -1, "clear illumination",
+                  cudaMemsetAsync(ill, 0, state / gf::kNumFields, s_));
+        }
+    }
     rc = prepare_model(c, L, eps_r, sigma, st);
     if (rc) return rc;
     int cur = 0;
@@ -415,9 +483,10 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         // the state at every k-th step is saved before the segment that starts there
         for (int j = 0; j < num_checkpoints(c); ++j) {
             const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
-            GF_CUDA(c, cudaMemcpyAsync(c->ws + L.ckpt + state * (size_t)j, st_buf[cur], state,
-                                       cudaMemcpyDeviceToDevice, st),
-                    "save checkpoint");
+            char* dst = c->ws + L.ckpt + state * (size_t)j;
+            const float* src = st_buf[cur];
+            GF_OP(c, st, -1, "save checkpoint",
+                  cudaMemcpyAsync(dst, src, state, cudaMemcpyDeviceToDevice, s_));
             rc = forward_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
             if (rc) return rc;
         }
@@ -425,8 +494,13 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         rc = forward_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
         if (rc) return rc;
     }
-    if (illum)
-        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.illum, c->nshots, c->g.nx, c->g.ny, c->pitch, illum, p.status, st); }), "sum illum");
+    if (illum) {
+        const float* per = p.illum;
+        int* status = p.status;
+        const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+        GF_OP(c, st, GF_KERNEL_AUX, "sum illum",
+              gf::launch_sum_shots(per, ns, nx, ny, pitch, illum, status, s_));
+    }
     c->have_forward = store;
     c->last_wavelet = wavelet;
     return GF_OK;
@@ -442,8 +516,12 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     const size_t field = plane * (size_t)c->nshots;
     const size_t state = gf::kNumFields * field;
     float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
-    GF_CUDA(c, cudaMemsetAsync(st_buf[0], 0, state, st), "clear adjoint state");
-    GF_CUDA(c, cudaMemsetAsync(p.grad, 0, 2 * field, st), "clear gradients");
+    {
+        float* b0 = st_buf[0];
+        float* gr = p.grad;
+        GF_OP(c, st, -1, "clear adjoint state", cudaMemsetAsync(b0, 0, state, s_));
+        GF_OP(c, st, -1, "clear gradients", cudaMemsetAsync(gr, 0, 2 * field, s_));
+    }
     int rc0 = prepare_model(c, L, eps_r, sigma, st);
     if (rc0) return rc0;
     int cur = 0;
@@ -463,12 +541,15 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         for (int j = num_checkpoints(c) - 1; j >= 0; --j) {
             const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
             const char* ck = c->ws + L.ckpt + state * (size_t)j;
-            GF_CUDA(c, cudaMemcpyAsync(fw_buf[0], ck, state, cudaMemcpyDeviceToDevice, st),
-                    "restore checkpoint");
+            float* fb0 = fw_buf[0];
+            GF_OP(c, st, -1, "restore checkpoint",
+                  cudaMemcpyAsync(fb0, ck, state, cudaMemcpyDeviceToDevice, s_));
             // Ez plane of every shot -> slot 0 of its segment
-            GF_CUDA(c, cudaMemcpy2DAsync(seg, (size_t)(c->ckpt_k + 1) * plane, ck, plane, plane,
-                                         (size_t)c->nshots, cudaMemcpyDeviceToDevice, st),
-                    "segment start");
+            const size_t seg_pitch = (size_t)(c->ckpt_k + 1) * plane;
+            const size_t nsh = (size_t)c->nshots;
+            GF_OP(c, st, -1, "segment start",
+                  cudaMemcpy2DAsync(seg, seg_pitch, ck, plane, plane, nsh,
+                                    cudaMemcpyDeviceToDevice, s_));
             q.hist_slot0 = n_begin - 1;
             p.hist_slot0 = n_begin - 1;
             int fcur = 0;
@@ -482,14 +563,18 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         int rc = adjoint_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
         if (rc) return rc;
     }
-    if (g_eps_r)
-        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] { return gf::launch_sum_shots(p.grad, c->nshots, c->g.nx, c->g.ny, c->pitch, g_eps_r, p.status, st); }), "sum g_eps_r");
-    if (g_sigma)
-        GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
-                    return gf::launch_sum_shots(p.grad + (size_t)c->nshots * c->Np, c->nshots,
-                                                c->g.nx, c->g.ny, c->pitch, g_sigma, p.status, st);
-                }),
-                "sum g_sigma");
+    {
+        const float* gr = p.grad;
+        int* status = p.status;
+        const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+        const size_t off = (size_t)c->nshots * c->Np;
+        if (g_eps_r)
+            GF_OP(c, st, GF_KERNEL_AUX, "sum g_eps_r",
+                  gf::launch_sum_shots(gr, ns, nx, ny, pitch, g_eps_r, status, s_));
+        if (g_sigma)
+            GF_OP(c, st, GF_KERNEL_AUX, "sum g_sigma",
+                  gf::launch_sum_shots(gr + off, ns, nx, ny, pitch, g_sigma, status, s_));
+    }
     return GF_OK;
 }
 
@@ -883,16 +968,13 @@ int gf_misfit_and_gradient(gf_ctx* c, const float* eps_r, const float* sigma,
     float* tr = traces ? traces : (float*)(c->ws + L.traces);
     float* resid = (float*)(c->ws + L.resid);
     const long long count = (long long)c->nshots * c->g.nt * c->nrec;
-    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
-                return gf::launch_residual_misfit(tr, observed, resid, count,
-                                                  (double*)(c->ws + L.partial), kMisfitBlocks,
-                                                  (int*)(c->ws + L.status), st);
-            }),
-            "residual_misfit");
-    GF_CUDA(c, launch(c, GF_KERNEL_AUX, st, [&] {
-                return gf::launch_finish_misfit((double*)(c->ws + L.partial), kMisfitBlocks, misfit, st);
-            }),
-            "finish_misfit");
+    double* partial = (double*)(c->ws + L.partial);
+    int* status = (int*)(c->ws + L.status);
+    GF_OP(c, st, GF_KERNEL_AUX, "residual_misfit",
+          gf::launch_residual_misfit(tr, observed, resid, count, partial, kMisfitBlocks, status,
+                                     s_));
+    GF_OP(c, st, GF_KERNEL_AUX, "finish_misfit",
+          gf::launch_finish_misfit(partial, kMisfitBlocks, misfit, s_));
     return run_adjoint(c, eps_r, sigma, resid, g_eps_r, g_sigma, st);
 }
 
@@ -980,6 +1062,7 @@ long long gf_kernel_launches(const gf_ctx* c) { return c ? c->launches : 0; }
 
 int gf_set_wait_budget(gf_ctx* c, long long polls) {
     if (!c || polls < 0) return GF_EINVAL;
+    if (polls != c->wait_budget) ++c->generation;  // recorded schedules carry the budget
     c->wait_budget = polls;
     return GF_OK;
 }
@@ -1071,6 +1154,26 @@ std::string tune_key(const gf_ctx* c) {
 }  // namespace
 
 struct gf_batch {
+    // the persistent multi-instance schedule (modes 3 and 4): every context's recorded
+    // operations, in its own order, with the persistent passes of several contexts merged
+    struct Merged {
+        std::vector<int> members;               // contexts whose pass this launch runs
+        std::vector<gf::FlowInstance> h_inst;   // their passes (host copy)
+        bool adjoint = false, hist = false;
+        size_t inst_off = 0, items_off = 0;     // device copies in d_plan
+        long long total = 0;                    // work items
+    };
+    struct Step {
+        int inst, op, merged;                   // merged < 0: operation op of context inst
+    };
+    std::vector<OpList> lists;
+    std::vector<Merged> merged;
+    std::vector<Step> steps;
+    char* d_plan = nullptr;
+    std::vector<const void*> plan_key;
+    std::vector<long long> plan_gens;
+    cudaGraph_t graph4 = nullptr;
+    cudaGraphExec_t exec4 = nullptr;
     std::vector<gf_ctx*> ctx;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
@@ -1083,6 +1186,137 @@ struct gf_batch {
     int device = 0;
     char err[512] = {0};
 };
+
+namespace {
+
+int batch_fail(gf_batch* b, int code, const char* what, const gf_ctx* c) {
+    snprintf(b->err, sizeof(b->err), "%s%s%s", what, c ? ": " : "", c ? c->err : "");
+    return code;
+}
+
+// Record every context's gradient operations, then merge: run each context's operations in
+// its order up to its next persistent pass; one launch runs the pending passes of the same
+// kind (forward with or without the wavefield store, or adjoint) of all contexts at once.
+int build_plan(gf_batch* b, const float* const* eps_r, const float* const* sigma,
+               const float* const* wavelet, const float* const* observed, double* misfit,
+               float* const* g_eps_r, float* const* g_sigma) {
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i)
+        if (b->ctx[i]->variant != gf::kFlowVariant)
+            return batch_fail(b, GF_EINVAL,
+                              "modes 3 and 4 need every context on the persistent variant (3)",
+                              nullptr);
+    b->lists.assign(n, OpList());
+    for (int i = 0; i < n; ++i) {
+        gf_ctx* c = b->ctx[i];
+        c->rec = &b->lists[i];
+        const int rc = gf_misfit_and_gradient(c, eps_r[i], sigma[i], wavelet[i], observed[i],
+                                              misfit + i, g_eps_r[i], g_sigma[i], nullptr,
+                                              nullptr);
+        c->rec = nullptr;
+        if (rc) return batch_fail(b, rc, "recording an instance", c);
+    }
+    b->merged.clear();
+    b->steps.clear();
+    std::vector<size_t> pos(n, 0);
+    size_t bytes = 0;
+    auto align = [](size_t x) { return (x + 255) / 256 * 256; };
+    for (;;) {
+        int first = -1;
+        for (int i = 0; i < n; ++i) {
+            const auto& ops = b->lists[i].ops;
+            while (pos[i] < ops.size() && !ops[pos[i]].flow) {
+                b->steps.push_back({i, (int)pos[i], -1});
+                ++pos[i];
+            }
+            if (pos[i] < ops.size() && first < 0) first = i;
+        }
+        if (first < 0) break;
+        const StreamOp& f0 = b->lists[first].ops[pos[first]];
+        gf_batch::Merged m;
+        m.adjoint = f0.adjoint;
+        m.hist = f0.inst.p.hist != nullptr;
+        for (int i = 0; i < n; ++i) {
+            const auto& ops = b->lists[i].ops;
+            if (pos[i] >= ops.size()) continue;
+            const StreamOp& op = ops[pos[i]];
+            if (!op.flow || op.adjoint != m.adjoint || (op.inst.p.hist != nullptr) != m.hist)
+                continue;
+            m.members.push_back(i);
+            m.h_inst.push_back(op.inst);
+            m.total += (long long)op.inst.f.nblocks * op.inst.p.nshots * op.inst.p.ntiles;
+            ++pos[i];
+        }
+        if (m.total > 0x7fffffffLL)
+            return batch_fail(b, GF_EINVAL, "a merged pass has more than 2^31 work items",
+                              nullptr);
+        m.inst_off = align(bytes);
+        bytes = m.inst_off + sizeof(gf::FlowInstance) * m.members.size();
+        m.items_off = align(bytes);
+        bytes = m.items_off + sizeof(int2) * (size_t)m.total;
+        b->steps.push_back({-1, -1, (int)b->merged.size()});
+        b->merged.push_back(std::move(m));
+    }
+    // the launches' instance arrays and work items (block-major over the instances), on the
+    // device for as long as the plan is kept
+    std::vector<char> h(bytes);
+    for (const auto& m : b->merged) {
+        memcpy(h.data() + m.inst_off, m.h_inst.data(), sizeof(gf::FlowInstance) * m.h_inst.size());
+        int2* it = reinterpret_cast<int2*>(h.data() + m.items_off);
+        int maxb = 0;
+        for (const auto& fi : m.h_inst) maxb = std::max(maxb, fi.f.nblocks);
+        long long k = 0;
+        for (int blk = 0; blk < maxb; ++blk)
+            for (size_t s = 0; s < m.h_inst.size(); ++s) {
+                const gf::FlowInstance& fi = m.h_inst[s];
+                if (blk >= fi.f.nblocks) continue;
+                const int ipb = fi.p.nshots * fi.p.ntiles;
+                for (int t = 0; t < ipb; ++t) it[k++] = make_int2((int)s, blk * ipb + t);
+            }
+    }
+    cudaFree(b->d_plan);
+    b->d_plan = nullptr;
+    if (bytes) {
+        cudaError_t e = cudaMalloc(&b->d_plan, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_plan, h.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return batch_fail(b, GF_ENOMEM, "device copy of the merged schedule", nullptr);
+        }
+    }
+    return GF_OK;
+}
+
+int run_plan(gf_batch* b, cudaStream_t st) {
+    for (const auto& s : b->steps) {
+        if (s.merged < 0) {
+            gf_ctx* c = b->ctx[s.inst];
+            const StreamOp& op = b->lists[s.inst].ops[s.op];
+            const cudaError_t e = op.run(st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cuda_fail(c, e, op.what);
+                return batch_fail(b, GF_ECUDA, "instance operation", c);
+            }
+            if (op.kind >= 0) ++c->launches;
+            continue;
+        }
+        const gf_batch::Merged& m = b->merged[s.merged];
+        const cudaError_t e = gf::launch_flow_multi(
+            m.h_inst.data(), reinterpret_cast<const gf::FlowInstance*>(b->d_plan + m.inst_off),
+            (int)m.members.size(), reinterpret_cast<const int2*>(b->d_plan + m.items_off),
+            m.total, m.adjoint, m.hist, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            snprintf(b->err, sizeof(b->err), "merged persistent pass: %s", cudaGetErrorString(e));
+            return GF_ECUDA;
+        }
+        ++b->ctx[m.members[0]]->launches;
+    }
+    return GF_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1188,6 +1422,9 @@ void gf_batch_destroy(gf_batch* b) {
     DeviceGuard guard(b->device);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->exec4) cudaGraphExecDestroy(b->exec4);
+    if (b->graph4) cudaGraphDestroy(b->graph4);
+    cudaFree(b->d_plan);
     for (auto s : b->streams)
         if (s) cudaStreamDestroy(s);
     for (auto e : b->join)
@@ -1204,7 +1441,7 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
                                  double* misfit, float* const* g_eps_r, float* const* g_sigma,
                                  int mode, void* stream) {
     if (!b || !eps_r || !sigma || !wavelet || !observed || !misfit || !g_eps_r || !g_sigma ||
-        mode < 0 || mode > 2)
+        mode < 0 || mode > 4)
         return GF_EINVAL;
     DeviceGuard guard(b->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1238,7 +1475,6 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
         return GF_OK;
     };
     if (mode < 2) return run_all(mode == 1, st);
-    // graph mode: capture the concurrent schedule once, replay while nothing changed
     std::vector<const void*> key;
     std::vector<long long> gens;
     for (int i = 0; i < n; ++i) {
@@ -1246,6 +1482,51 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
                                g_eps_r[i], g_sigma[i]});
         gens.push_back(b->ctx[i]->generation);
     }
+    if (mode >= 3) {
+        const bool rebuilt = b->steps.empty() || key != b->plan_key || gens != b->plan_gens;
+        if (rebuilt) {
+            if (b->exec4) cudaGraphExecDestroy(b->exec4);
+            if (b->graph4) cudaGraphDestroy(b->graph4);
+            b->exec4 = nullptr;
+            b->graph4 = nullptr;
+            b->steps.clear();
+            const int rc = build_plan(b, eps_r, sigma, wavelet, observed, misfit, g_eps_r,
+                                      g_sigma);
+            if (rc) {
+                b->steps.clear();
+                return rc;
+            }
+            b->plan_key = key;
+            b->plan_gens = gens;
+        }
+        if (mode == 3) return run_plan(b, st);
+        if (!b->exec4) {
+            if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                return fail_b(GF_ECUDA, "begin capture", nullptr);
+            }
+            const int rc = run_plan(b, b->capture);
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(b->capture, &g);
+            if (rc || e != cudaSuccess) {
+                cudaGetLastError();
+                if (g) cudaGraphDestroy(g);
+                return rc ? rc : fail_b(GF_ECUDA, "end capture", nullptr);
+            }
+            if (cudaGraphInstantiate(&b->exec4, g, 0) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphDestroy(g);
+                return fail_b(GF_ECUDA, "instantiate graph", nullptr);
+            }
+            b->graph4 = g;
+        }
+        if (cudaGraphLaunch(b->exec4, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail_b(GF_ECUDA, "graph launch", nullptr);
+        }
+        return GF_OK;
+    }
+    // graph mode: capture the concurrent schedule once, replay while nothing changed
     if (!b->exec || key != b->key || gens != b->gens) {
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->graph) cudaGraphDestroy(b->graph);

@@ -23,27 +23,19 @@
 namespace gf {
 namespace {
 
-struct FlowArgs {
-    float* buf0;          // ping-pong state buffers [kNumFields][nshots][Np]
-    float* buf1;
-    int* done;            // [nshots][ntiles] completed blocks (zero at launch)
-    int n_first, n_last;  // steps of the pass (the adjoint runs them in reverse)
-    int kb;               // steps per block
-    int nblocks;
-    long long budget;     // polls of one dependency wait
-};
-
 // One work item.
 struct Item {
     int b, shot, tile, n0, K;
 };
 
-__device__ __forceinline__ Item decode(const TileParams& p, const FlowArgs& f, int i,
+// Item `local` of an instance: block b = local / (nshots * ntiles), then the (shot, tile) of
+// the launch order.
+__device__ __forceinline__ Item decode(const TileParams& p, const FlowArgs& f, int local,
                                        bool reverse) {
     Item it;
     const int ipb = p.nshots * p.ntiles;
-    it.b = i / ipb;
-    const int code = __ldg(p.cta_order + (i - it.b * ipb));
+    it.b = local / ipb;
+    const int code = __ldg(p.cta_order + (local - it.b * ipb));
     it.shot = code >> 16;
     it.tile = code & 0xffff;
     if (!reverse) {
@@ -55,6 +47,20 @@ __device__ __forceinline__ Item decode(const TileParams& p, const FlowArgs& f, i
         it.K = n1 - it.n0 + 1;
     }
     return it;
+}
+
+// {instance, item of the instance} of launch item k (one instance: {0, k}).
+__device__ __forceinline__ int2 item_code(const int2* items, int k) {
+    return items ? __ldg(items + k) : make_int2(0, k);
+}
+
+// Copy the parameters of instance `id` (the launch parameter when there is one instance) into
+// a shared-memory slot, words shared out over `n` threads from `t`.
+__device__ __forceinline__ void copy_instance(FlowInstance* dst, const FlowInstance& one,
+                                              const FlowInstance* many, int id, int t, int n) {
+    const int* s = reinterpret_cast<const int*>(many ? many + id : &one);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int k = t; k < (int)(sizeof(FlowInstance) / 4); k += n) d[k] = s[k];
 }
 
 __device__ __forceinline__ int load_acquire(const int* a) {
@@ -184,34 +190,52 @@ __device__ __forceinline__ void unstage_state(const Pos<R>& w, const float* sm, 
 // ---------------------------------------------------------------------------------------
 // Forward pass
 // ---------------------------------------------------------------------------------------
+// Launch items are items[k] = {instance, item of the instance} (items == NULL: the one
+// instance `one`, item k).  The parameters of the current item's instance and of the next
+// one's sit in two shared-memory slots at float offset slot_off: warp 0 fills the next slot
+// while the current item computes (the slot it overwrites was the previous item's, which no
+// thread reads after the barrier at the top of the iteration).
 template <int R, int NW, bool kHist, bool kIllum, bool kStaged>
-__global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p, const FlowArgs f) {
+__global__ void __launch_bounds__(32 * NW, 1)
+    fwd_flow_kernel(const __grid_constant__ FlowInstance one, const FlowInstance* many,
+                    const int2* __restrict__ items, long long total, int slot_off) {
     using Gm = G<R, NW>;
     extern __shared__ float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
     volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
-    const int total = f.nblocks * p.nshots * p.ntiles;
-    int i = blockIdx.x;
+    FlowInstance* const slots = reinterpret_cast<FlowInstance*>(sm + slot_off);
+    long long i = blockIdx.x;
     if (i >= total) return;
-    Item it = decode(p, f, i, false);
-    if (!cta_wait_deps<R, NW>(p, f, it, sm)) return;
-    prefetch_state<R, NW>(p, f, sm, it);
-    prefetch_coef<R, NW>(p, sm, Gm::oCoef2, it);
+    int s = 0;
+    const int2 c0 = item_code(items, (int)i);
+    copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
+    __syncthreads();
+    Item it = decode(slots[0].p, slots[0].f, c0.y, false);
+    if (!cta_wait_deps<R, NW>(slots[0].p, slots[0].f, it, sm)) return;
+    prefetch_state<R, NW>(slots[0].p, slots[0].f, sm, it);
+    prefetch_coef<R, NW>(slots[0].p, sm, Gm::oCoef2, it);
     cp_async_commit();
     for (; i < total; i += gridDim.x) {
-        const int j = i + gridDim.x;
+        const TileParams& p = slots[s].p;
+        const FlowArgs& f = slots[s].f;
+        const long long j = i + gridDim.x;
         const bool more = j < total;
-        const Item nx = decode(p, f, more ? j : i, false);
+        const int2 ncode = item_code(items, (int)(more ? j : i));
         const Pos<R> w = position<R>(p, it.tile, it.K);
         cp_async_wait<0>();
         __syncthreads();  // item i's staged state and coefficients have landed
-        note_ready(p, f, nx, more, flag);
+        if (threadIdx.x < 32) {
+            copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
+            __syncwarp();
+            note_ready(slots[s ^ 1].p, slots[s ^ 1].f,
+                       decode(slots[s ^ 1].p, slots[s ^ 1].f, ncode.y, false), more, flag);
+        }
         const bool strip = tile_in_strip<R>(p, w, it.K);
         const float* st_in = (it.b & 1) ? f.buf1 : f.buf0;
         float* st_out = (it.b & 1) ? f.buf0 : f.buf1;
         TileLoads<R> L;
-        issue_loads<R, NW, false, false, true, true, true>(p, w, st_in, it.shot, it.tile, it.n0, it.K,
-                                                     strip, L);
+        issue_loads<R, NW, false, false, true, true, true>(p, w, st_in, it.shot, it.tile, it.n0,
+                                                           it.K, strip, L);
         float2 ez[R], hx[R], hy[R], ill[R];
         unstage_state<R, NW>(w, sm, ez, hx, hy);
         {
@@ -227,11 +251,14 @@ __global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p
         store_loads<R, NW, false, true, true>(p, w, sm, it.K, strip, L);
         const int nrl = L.d.y;
         const int2* ents = stage_receivers<R, NW, kStaged, false>(p, sm, it.shot, L.d, 0, it.K);
-        __syncthreads();
+        __syncthreads();  // also publishes the next slot to every thread
+        const TileParams& pn = slots[s ^ 1].p;
+        const FlowArgs& fn = slots[s ^ 1].f;
+        const Item nx = decode(pn, fn, ncode.y, false);
         const bool ahead = flag[0] != 0;
         if (ahead) {  // the staging planes are free: fetch the next item during this one
-            prefetch_state<R, NW>(p, f, sm, nx);
-            prefetch_coef<R, NW>(p, sm, Gm::oCoef2, nx);
+            prefetch_state<R, NW>(pn, fn, sm, nx);
+            prefetch_coef<R, NW>(pn, sm, Gm::oCoef2, nx);
             cp_async_commit();
         }
         int rlo, rhi;
@@ -250,12 +277,13 @@ __global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p
         if (kIllum) add_illumination<R>(p, w, it.shot, ill);
         publish<R, NW>(p, f, it);
         if (!ahead && more) {
-            if (!cta_wait_deps<R, NW>(p, f, nx, sm)) break;
-            prefetch_state<R, NW>(p, f, sm, nx);
-            prefetch_coef<R, NW>(p, sm, Gm::oCoef2, nx);
+            if (!cta_wait_deps<R, NW>(pn, fn, nx, sm)) break;
+            prefetch_state<R, NW>(pn, fn, sm, nx);
+            prefetch_coef<R, NW>(pn, sm, Gm::oCoef2, nx);
             cp_async_commit();
         }
         it = nx;
+        s ^= 1;
     }
     cp_async_wait<0>();
 }
@@ -264,29 +292,43 @@ __global__ void __launch_bounds__(32 * NW, 1) fwd_flow_kernel(const TileParams p
 // Adjoint pass
 // ---------------------------------------------------------------------------------------
 template <int R, int NW, bool kStaged>
-__global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p, const FlowArgs f) {
+__global__ void __launch_bounds__(32 * NW, 1)
+    adj_flow_kernel(const __grid_constant__ FlowInstance one, const FlowInstance* many,
+                    const int2* __restrict__ items, long long total, int slot_off) {
     using Gm = G<R, NW>;
     extern __shared__ float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
     volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
-    const int total = f.nblocks * p.nshots * p.ntiles;
-    int i = blockIdx.x;
+    FlowInstance* const slots = reinterpret_cast<FlowInstance*>(sm + slot_off);
+    long long i = blockIdx.x;
     if (i >= total) return;
-    Item it = decode(p, f, i, true);
-    if (!cta_wait_deps<R, NW>(p, f, it, sm)) return;
-    prefetch_state<R, NW>(p, f, sm, it);
-    prefetch_coef<R, NW>(p, sm, Gm::oCoef, it);
+    int s = 0;
+    const int2 c0 = item_code(items, (int)i);
+    copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
+    __syncthreads();
+    Item it = decode(slots[0].p, slots[0].f, c0.y, true);
+    if (!cta_wait_deps<R, NW>(slots[0].p, slots[0].f, it, sm)) return;
+    prefetch_state<R, NW>(slots[0].p, slots[0].f, sm, it);
+    prefetch_coef<R, NW>(slots[0].p, sm, Gm::oCoef, it);
     cp_async_commit();
     for (; i < total; i += gridDim.x) {
-        const int j = i + gridDim.x;
+        const TileParams& p = slots[s].p;
+        const FlowArgs& f = slots[s].f;
+        const long long j = i + gridDim.x;
         const bool more = j < total;
+        const int2 ncode = item_code(items, (int)(more ? j : i));
         const int K = it.K, n1 = it.n0 + K - 1;
         const Pos<R> w = position<R>(p, it.tile, K);
         cp_async_wait<0>();
         __syncthreads();  // item i's staged state and coefficients have landed
         // (the next item is decoded where it is needed: holding it through the time steps
         // would cost registers)
-        note_ready(p, f, decode(p, f, more ? j : i, true), more, flag);
+        if (threadIdx.x < 32) {
+            copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
+            __syncwarp();
+            note_ready(slots[s ^ 1].p, slots[s ^ 1].f,
+                       decode(slots[s ^ 1].p, slots[s ^ 1].f, ncode.y, true), more, flag);
+        }
         float2 aez[R], ahx[R], ahy[R], ge[R], gs[R];
         const float* hp = p.hist + ((long long)it.shot * p.hist_stride - p.hist_slot0) * p.Np +
                           (long long)(w.Y0 + w.ly0) * p.pitch + w.gx0;
@@ -302,13 +344,13 @@ __global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p
         const float* st_in = (it.b & 1) ? f.buf1 : f.buf0;
         float* st_out = (it.b & 1) ? f.buf0 : f.buf1;
         TileLoads<R> L;
-        issue_loads<R, NW, false, false, true, true, false>(p, w, st_in, it.shot, it.tile, it.n0, K,
-                                                      strip, L);
+        issue_loads<R, NW, false, false, true, true, false>(p, w, st_in, it.shot, it.tile, it.n0,
+                                                            K, strip, L);
         unstage_state<R, NW>(w, sm, aez, ahx, ahy);
         store_loads<R, NW, false, true, false>(p, w, sm, K, strip, L);
         const int nrl = L.d.y;
         const int2* ents = stage_receivers<R, NW, kStaged, true>(p, sm, it.shot, L.d, n1, K);
-        __syncthreads();
+        __syncthreads();  // also publishes the next slot to every thread
         const bool ahead = flag[0] != 0;
         int rlo, rhi;
         warp_rec_range<kStaged, R>(p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl,
@@ -317,14 +359,15 @@ __global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p
             p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl, K, rlo, rhi, false);
         // after phase A 0 the staging planes are free: fetch the next item's state; after the
         // last phase A this item no longer reads its coefficients: fetch the next item's
+        const FlowInstance& nxi = slots[s ^ 1];
         auto after_a = [&](int a) {
             if (!more) return;
             if (a == 0 && ahead) {
-                prefetch_state<R, NW>(p, f, sm, decode(p, f, j, true));
+                prefetch_state<R, NW>(nxi.p, nxi.f, sm, decode(nxi.p, nxi.f, ncode.y, true));
                 cp_async_commit();
             }
             if (a == K - 1) {
-                prefetch_coef<R, NW>(p, sm, Gm::oCoef, decode(p, f, j, true));
+                prefetch_coef<R, NW>(nxi.p, sm, Gm::oCoef, decode(nxi.p, nxi.f, ncode.y, true));
                 cp_async_commit();
             }
         };
@@ -338,12 +381,13 @@ __global__ void __launch_bounds__(32 * NW, 1) adj_flow_kernel(const TileParams p
         add_gradients<R>(p, w, it.shot, ge, gs);
         publish<R, NW>(p, f, it);
         if (!more) break;
-        it = decode(p, f, j, true);
+        it = decode(nxi.p, nxi.f, ncode.y, true);
         if (!ahead) {
-            if (!cta_wait_deps<R, NW>(p, f, it, sm)) break;
-            prefetch_state<R, NW>(p, f, sm, it);
+            if (!cta_wait_deps<R, NW>(nxi.p, nxi.f, it, sm)) break;
+            prefetch_state<R, NW>(nxi.p, nxi.f, sm, it);
             cp_async_commit();
         }
+        s ^= 1;
     }
     cp_async_wait<0>();
 }
@@ -357,37 +401,73 @@ cudaError_t allow_flow_smem(Kern k, size_t optin) {
                                 (int)(optin - a.sharedSizeBytes));
 }
 
+// Float offset of the two instance slots after `floats` of other shared memory (16-byte
+// aligned), and the launch's dynamic shared memory with them.
+int slot_offset(size_t floats) { return (int)((floats + 3) & ~(size_t)3); }
+size_t with_slots(size_t floats) {
+    return sizeof(float) * slot_offset(floats) + 2 * sizeof(FlowInstance);
+}
+
 template <class Kern>
-cudaError_t launch_flow(Kern k, const TileParams& p, const FlowArgs& f, int threads, size_t smem,
+cudaError_t launch_flow(Kern k, const FlowInstance& one, const FlowInstance* many,
+                        const int2* items, long long total, int threads, size_t floats,
                         cudaStream_t st) {
     int dev = 0, sms = 0, per_sm = 0;
+    const size_t smem = with_slots(floats);
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long total = (long long)f.nblocks * p.nshots * p.ntiles;
+    if (total < 1) return cudaSuccess;
     const int grid = (int)(total < (long long)sms * per_sm ? total : (long long)sms * per_sm);
-    TileParams pc = p;
-    FlowArgs fc = f;
-    void* args[] = {&pc, &fc};
+    FlowInstance oc = one;
+    const FlowInstance* mc = many;
+    const int2* ic = items;
+    long long tc = total;
+    int so = slot_offset(floats);
+    void* args[] = {&oc, &mc, &ic, &tc, &so};
     return cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(threads), args, smem, st);
 }
 
 template <int R, int NW, bool kHist, bool kIllum>
-cudaError_t launch_fwd_flow_v(const TileParams& p, const FlowArgs& f, bool staged, cudaStream_t st) {
+cudaError_t launch_fwd_flow_v(const FlowInstance& one, const FlowInstance* many,
+                              const int2* items, long long total, bool staged, cudaStream_t st) {
     using Gm = G<R, NW>;
-    const size_t smem = sizeof(float) * Gm::fwd_flow_floats;
-    if (staged) return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, true>, p, f, Gm::NT, smem, st);
-    return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, false>, p, f, Gm::NT, smem, st);
+    const size_t floats = Gm::fwd_flow_floats;
+    if (staged)
+        return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, true>, one, many, items, total,
+                           Gm::NT, floats, st);
+    return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, false>, one, many, items, total,
+                       Gm::NT, floats, st);
+}
+
+cudaError_t launch_any(const FlowInstance& one, const FlowInstance* many, const int2* items,
+                       long long total, bool adjoint, bool hist, bool illum, bool staged,
+                       int ring, cudaStream_t st) {
+    using Gm = G<4, 16>;
+    if (!adjoint) {
+        if (hist && illum) return launch_fwd_flow_v<4, 16, true, true>(one, many, items, total, staged, st);
+        if (hist) return launch_fwd_flow_v<4, 16, true, false>(one, many, items, total, staged, st);
+        if (illum) return launch_fwd_flow_v<4, 16, false, true>(one, many, items, total, staged, st);
+        return launch_fwd_flow_v<4, 16, false, false>(one, many, items, total, staged, st);
+    }
+    const size_t floats = Gm::adj_ring_off + (size_t)kRing * ring;
+    if (staged)
+        return launch_flow(adj_flow_kernel<4, 16, true>, one, many, items, total, Gm::NT, floats, st);
+    return launch_flow(adj_flow_kernel<4, 16, false>, one, many, items, total, Gm::NT, floats, st);
+}
+
+bool staged_receivers(const TileParams& p, int kb, bool adjoint) {
+    return adjoint ? (long long)p.rec_max * (kb + 2) <= kRecStage : 2LL * p.rec_max <= kRecStage;
 }
 
 }  // namespace
 
 size_t flow_smem_bytes(int tile_w, int tile_h) {
     using Gm = G<4, 16>;
-    const size_t f = sizeof(float) * Gm::fwd_flow_floats;
-    const size_t a = sizeof(float) * (Gm::adj_ring_off + (size_t)kRing * tile_w * tile_h);
+    const size_t f = with_slots(Gm::fwd_flow_floats);
+    const size_t a = with_slots(Gm::adj_ring_off + (size_t)kRing * tile_w * tile_h);
     return f > a ? f : a;
 }
 
@@ -409,12 +489,8 @@ cudaError_t configure_flow_kernels(size_t optin) {
     return cudaSuccess;
 }
 
-// One cooperative launch for the forward steps [n_first, n_last] (blocks of kb steps) or, with
-// `adjoint`, the adjoint steps n_last down to n_first; the pass starts from buf0 and ends in
-// buf[nblocks % 2].  done must hold nshots * ntiles zeros.
-cudaError_t launch_flow_pass(const TileParams& p, float* buf0, float* buf1, int* done,
-                             int n_first, int n_last, int kb, long long budget, bool adjoint,
-                             cudaStream_t st) {
+FlowArgs make_flow_args(float* buf0, float* buf1, int* done, int n_first, int n_last, int kb,
+                        long long budget) {
     FlowArgs f;
     f.buf0 = buf0;
     f.buf1 = buf1;
@@ -424,18 +500,30 @@ cudaError_t launch_flow_pass(const TileParams& p, float* buf0, float* buf1, int*
     f.kb = kb;
     f.nblocks = (n_last - n_first + kb) / kb;
     f.budget = budget;
-    using Gm = G<4, 16>;
-    if (!adjoint) {
-        const bool staged = 2LL * p.rec_max <= kRecStage;
-        if (p.hist && p.illum) return launch_fwd_flow_v<4, 16, true, true>(p, f, staged, st);
-        if (p.hist) return launch_fwd_flow_v<4, 16, true, false>(p, f, staged, st);
-        if (p.illum) return launch_fwd_flow_v<4, 16, false, true>(p, f, staged, st);
-        return launch_fwd_flow_v<4, 16, false, false>(p, f, staged, st);
+    return f;
+}
+
+cudaError_t launch_flow_pass(const FlowInstance& inst, bool adjoint, cudaStream_t st) {
+    const TileParams& p = inst.p;
+    const long long total = (long long)inst.f.nblocks * p.nshots * p.ntiles;
+    return launch_any(inst, nullptr, nullptr, total, adjoint, p.hist != nullptr,
+                      p.illum != nullptr, staged_receivers(p, inst.f.kb, adjoint),
+                      p.tile_w * p.tile_h, st);
+}
+
+cudaError_t launch_flow_multi(const FlowInstance* h_inst, const FlowInstance* d_inst, int n,
+                              const int2* d_items, long long total, bool adjoint, bool hist,
+                              cudaStream_t st) {
+    if (n < 1) return cudaErrorInvalidValue;
+    bool staged = true;
+    int ring = 0;
+    for (int k = 0; k < n; ++k) {
+        staged = staged && staged_receivers(h_inst[k].p, h_inst[k].f.kb, adjoint);
+        ring = ring > h_inst[k].p.tile_w * h_inst[k].p.tile_h
+                   ? ring : h_inst[k].p.tile_w * h_inst[k].p.tile_h;
+        if ((h_inst[k].p.hist != nullptr) != hist || h_inst[k].p.illum) return cudaErrorInvalidValue;
     }
-    const bool staged = (long long)p.rec_max * (kb + 2) <= kRecStage;
-    const size_t smem = sizeof(float) * (Gm::adj_ring_off + (size_t)kRing * p.tile_w * p.tile_h);
-    if (staged) return launch_flow(adj_flow_kernel<4, 16, true>, p, f, Gm::NT, smem, st);
-    return launch_flow(adj_flow_kernel<4, 16, false>, p, f, Gm::NT, smem, st);
+    return launch_any(h_inst[0], d_inst, d_items, total, adjoint, hist, false, staged, ring, st);
 }
 
 }  // namespace gf

@@ -107,13 +107,35 @@ int max_tile_extent();              // staged window width
 int max_tile_height(int variant);   // staged window height of a per-launch variant (0-2)
 size_t tile_smem_bytes(int variant, int tile_w, int tile_h);  // per-launch variants (0-2)
 cudaError_t configure_tile_kernels(size_t optin);
-// Persistent dataflow pass: forward steps [n_first, n_last] in blocks of kb steps, or the
-// adjoint steps n_last down to n_first, from buf0 to buf[nblocks % 2]; done: nshots * ntiles
-// zeroed ints; budget: polls of one dependency wait.  The tiling needs tile_w a multiple of 4,
+// Persistent dataflow passes.  One pass of one instance (a context's shots on its grid):
+// forward steps [n_first, n_last] in blocks of kb steps, or the adjoint steps n_last down to
+// n_first, ping-ponging from buf0 (the pass ends in buf[nblocks % 2]); done: nshots * ntiles
+// zeroed ints (completed blocks per (shot, tile)); budget: polls of one dependency wait.
+struct FlowArgs {
+    float* buf0;
+    float* buf1;
+    int* done;
+    int n_first, n_last;
+    int kb;
+    int nblocks;
+    long long budget;
+};
+struct FlowInstance {
+    TileParams p;
+    FlowArgs f;
+};
+FlowArgs make_flow_args(float* buf0, float* buf1, int* done, int n_first, int n_last, int kb,
+                        long long budget);
+// One cooperative launch for one instance's pass.  The tiling needs tile_w a multiple of 4,
 // kl a multiple of 4 and tile_w, tile_h >= kb.
-cudaError_t launch_flow_pass(const TileParams& p, float* buf0, float* buf1, int* done,
-                             int n_first, int n_last, int kb, long long budget, bool adjoint,
-                             cudaStream_t st);
+cudaError_t launch_flow_pass(const FlowInstance& inst, bool adjoint, cudaStream_t st);
+// One cooperative launch for the passes of several instances (host array h_inst, its device
+// copy d_inst): work item k of the launch is items[k] = {instance, item of that instance},
+// block-major over all instances (an item may only depend on earlier items).  All instances
+// store the forward wavefield (hist) or none does; ring = largest tile_w * tile_h (adjoint).
+cudaError_t launch_flow_multi(const FlowInstance* h_inst, const FlowInstance* d_inst, int n,
+                              const int2* d_items, long long total, bool adjoint, bool hist,
+                              cudaStream_t st);
 size_t flow_smem_bytes(int tile_w, int tile_h);
 cudaError_t configure_flow_kernels(size_t optin);
 

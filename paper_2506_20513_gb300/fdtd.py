@@ -290,7 +290,10 @@ def autotune(fdtd: FDTD, eps_r, sigma, wavelet, cache_path: str | None = None,
 
 class FDTDBatch:
     """Many independent instances (possibly different grids, shots, nt) advanced together:
-    mode 0 one after the other, 1 concurrently on one stream each, 2 as one CUDA graph."""
+    mode 0 one after the other, 1 concurrently on one stream each, 2 as one CUDA graph of
+    those streams, 3 the persistent multi-instance schedule (the instances' persistent passes
+    merged into single cooperative launches; every instance on variant 3), 4 mode 3 as one
+    CUDA graph."""
 
     def __init__(self, fdtds):
         self.fds = list(fdtds)

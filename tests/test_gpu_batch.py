@@ -114,3 +114,96 @@ def test_autotune_picks_a_valid_tiling_and_caches_it(dev, tmp_path):
     J64, ge64, gs64 = O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl.src,
                                             wav.cpu().double().numpy(), wl.rec, obs)
     assert np.linalg.norm(ge.cpu().numpy() - ge64) <= 1e-3 * np.linalg.norm(ge64)
+
+
+def _flow_batch(dev, ks=(4, 6, 7)):
+    from paper_2506_20513_gb300 import FDTD, Tiling
+    wls = _instances()
+    fds, args = [], []
+    for k, wl in enumerate(wls):
+        g = wl.grid
+        fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=Tiling(0, 0, ks[k], 3))
+        if k == 1:
+            fd.set_storage(30)  # one checkpointed instance in the batch
+        wav = np.broadcast_to(O.ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt))
+        obs = O.forward(g, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+        args.append((t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), t32(obs, dev),
+                     wav, obs))
+        fds.append(fd)
+    return wls, fds, args
+
+
+@pytest.mark.parametrize("mode", [3, 4])
+def test_persistent_batch_matches_single_instances_and_oracle(dev, mode):
+    """Modes 3 and 4 merge the instances' persistent passes (different grids, shots, nt and
+    time-block depths; one instance checkpointed, so its segment passes meet the others' full
+    passes) into single cooperative launches: every gradient is bit-identical to the
+    instance's own run (the per-item arithmetic and the per-cell summation order do not depend
+    on which CTA runs an item) and matches the oracle."""
+    from paper_2506_20513_gb300 import FDTDBatch
+    wls, fds, args = _flow_batch(dev)
+    singles = [fd.misfit_and_gradient(*a[:4]) for fd, a in zip(fds, args)]
+    for fd in fds:
+        fd.status()
+    batch = FDTDBatch(fds)
+    for rep in range(2):  # recorded on the first call, kept (and replayed) on the second
+        J, ge, gs = batch.misfit_and_gradient([a[0] for a in args], [a[1] for a in args],
+                                              [a[2] for a in args], [a[3] for a in args], mode)
+        torch.cuda.synchronize(dev)
+        for fd in fds:
+            fd.status()
+        for k, (Js, ges, gss) in enumerate(singles):
+            assert J[k].item() == Js.item()
+            assert torch.equal(ge[k], ges) and torch.equal(gs[k], gss)
+    for k, (wl, a) in enumerate(zip(wls, args)):
+        J64, ge64, gs64 = O.misfit_and_gradient(wl.grid, wl.eps_init, wl.sig_init, wl.src, a[4],
+                                                wl.rec, a[5])
+        rel = lambda x, y: np.linalg.norm(x.cpu().numpy() - y) / np.linalg.norm(y)
+        assert rel(ge[k], ge64) <= 1e-3 and rel(gs[k], gs64) <= 1e-3
+    batch.close()
+
+
+def test_persistent_batch_wait_timeout_is_reported_and_recovered(dev):
+    """With a dependency-wait budget of zero polls, the merged launches' waits that are not
+    already satisfied give up: the CTAs end, the contexts report GF_ETIMEOUT and nothing hangs.
+    With the budget restored (the recorded schedule carries it, so it is recorded again) the
+    next call is exact."""
+    from paper_2506_20513_gb300 import FDTDBatch, _lib
+    wls, fds, args = _flow_batch(dev)
+    singles = [[x.clone() for x in fd.misfit_and_gradient(*a[:4])] for fd, a in zip(fds, args)]
+    batch = FDTDBatch(fds)
+    cols = [[a[i] for a in args] for i in range(4)]
+    for fd in fds:
+        fd.lib.gf_set_wait_budget(fd.ctx, 0)
+    batch.misfit_and_gradient(*cols, mode=3)
+    torch.cuda.synchronize(dev)
+    codes = []
+    for fd in fds:
+        try:
+            fd.status()
+            codes.append(_lib.GF_OK)
+        except _lib.GfError as e:
+            codes.append(e.code)
+    assert _lib.GF_ETIMEOUT in codes
+    assert all(c in (_lib.GF_OK, _lib.GF_ETIMEOUT) for c in codes)
+    for fd in fds:
+        fd.lib.gf_set_wait_budget(fd.ctx, 1 << 22)
+    J, ge, gs = batch.misfit_and_gradient(*cols, mode=3)
+    torch.cuda.synchronize(dev)
+    for fd in fds:
+        fd.status()
+    for k, (Js, ges, gss) in enumerate(singles):
+        assert J[k].item() == Js.item()
+        assert torch.equal(ge[k], ges) and torch.equal(gs[k], gss)
+    batch.close()
+
+
+def test_persistent_batch_needs_the_persistent_variant(dev):
+    from paper_2506_20513_gb300 import FDTD, FDTDBatch, _lib
+    wls, fds, args = _flow_batch(dev)
+    fds[2].set_tiling(type(fds[2].tiling())(0, 0, 5, 0))
+    batch = FDTDBatch(fds)
+    with pytest.raises(_lib.GfError) as e:
+        batch.misfit_and_gradient(*[[a[i] for a in args] for i in range(4)], mode=3)
+    assert e.value.code == _lib.GF_EINVAL
+    batch.close()
