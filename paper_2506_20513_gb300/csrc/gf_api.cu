@@ -1362,6 +1362,10 @@ int gf_autotune(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     for (const Cand& k : cands) {
         if (gf_set_variant(c, k.variant) != GF_OK || gf_set_tiling(c, 0, 0, k.K) != GF_OK) continue;
         rc = forward_prefix(c, eps_r, sigma, wavelet, steps, st);  // warm-up
+        if (rc == GF_ENOMEM) {  // a caller workspace too small for this candidate's tiling
+            rc = GF_OK;
+            continue;
+        }
         if (rc) break;
         cudaEventRecord(e0, st);
         rc = forward_prefix(c, eps_r, sigma, wavelet, steps, st);

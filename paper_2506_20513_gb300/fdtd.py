@@ -278,7 +278,11 @@ def autotune(fdtd: FDTD, eps_r, sigma, wavelet, cache_path: str | None = None,
     """Pick the fastest tiling / kernel variant for this context's shape (cached on disk)."""
     e, s = fdtd._model(eps_r, sigma)
     w = fdtd._wavelet(wavelet)
-    fdtd._workspace(full=False)
+    # the candidates' workspaces differ in size (per-tile counters): let the library hold its
+    # own while it probes them
+    _lib.check(fdtd.lib, fdtd.ctx, fdtd.lib.gf_set_workspace(fdtd.ctx, None, 0))
+    fdtd._ws = None
+    fdtd._ws_full = False
     path = cache_path.encode() if cache_path else None
     rc = fdtd.lib.gf_autotune(fdtd.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), path,
                               probe_steps, fdtd._stream())

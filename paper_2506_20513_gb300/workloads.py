@@ -236,14 +236,16 @@ def large_checkpointed(seed: int = 4000, nshots: int = 16, nt: int = 8000) -> Wo
                     pad_edges(sig_i, npml), seed=seed)
 
 
-def preconditioner_model(seed: int, nshots: int = 16, nt: int = 1500) -> Workload:
-    """256x128 cells (+20-cell CPML), dx 0.01 m, dt 15 ps, nt 1500, 400 MHz, 16 shots."""
-    npml, nxp, nyp, dx, f0 = 20, 256, 128, 0.01, 400e6
+def preconditioner_model(seed: int, nshots: int = 16, nt: int = 1500, nxp: int = 256,
+                         nyp: int = 128, npml: int = 20, nrec: int = 64) -> Workload:
+    """256x128 cells (+20-cell CPML), dx 0.01 m, dt 15 ps, nt 1500, 400 MHz, 16 shots, 64
+    receivers (smaller grids for tests through nxp, nyp, npml, nrec)."""
+    dx, f0 = 0.01, 400e6
     g = default_pml(GridSpec(nx=nxp + 2 * npml, ny=nyp + 2 * npml, npml=npml, nt=nt, dx=dx,
                              dy=dx, dt=15e-12), f0)
     eps, sig = layered_blob_model(seed, nxp, nyp, dx)
     eps_i, sig_i = smooth(eps, 0.2, dx), np.exp(smooth(np.log(sig), 0.2, dx))
-    src, rec = surface_acquisition(nshots, 64, nxp, dx, npml)
+    src, rec = surface_acquisition(nshots, nrec, nxp, dx, npml)
     return Workload(f"precond_{g.nx}x{g.ny}_{nshots}shots_nt{nt}", g, f0, src, rec,
                     pad_edges(eps, npml), pad_edges(sig, npml), pad_edges(eps_i, npml),
                     pad_edges(sig_i, npml), seed=seed)

@@ -427,7 +427,9 @@ def test_large_grid_gradient_vs_central_differences(dev):
     JB = float(fdB.misfit(e0, s0, wav, obs).item())
     fdB.close()
     JA = float(fd.misfit(e0, s0, wav, obs).item())
-    assert JA == pytest.approx(J, rel=1e-9)
+    # the gradient's forward runs in checkpoint segments (launches split at their ends):
+    # the same misfit to FP32 rounding
+    assert JA == pytest.approx(J, rel=1e-5)
     eta = float((dA - dB).double().norm() / dA.double().norm())
     r_norm = float((dA - obs).double().norm())
     noise = max(abs(JA - JB), eta * r_norm * float(dA.double().norm()) / math.sqrt(dA.numel()))
