@@ -70,6 +70,9 @@ def parse_args():
                          "16 shots, nt 8000 with checkpointing")
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="checkpoint every k steps instead of storing the whole wavefield")
+    ap.add_argument("--reconstruct", action="store_true",
+                    help="with --checkpoint: reconstruct each segment backwards from a stored "
+                         "boundary ring instead of keeping its Ez (experimental)")
     ap.add_argument("--cpu-shots", type=int, default=0, help="oracle sample size (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -466,7 +469,7 @@ def ours(args):
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
     fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=tiling)
     if args.checkpoint > 0:
-        fd.set_storage(args.checkpoint)
+        fd.set_storage(args.checkpoint, reconstruct=args.reconstruct)
     t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
     eps_t, sig_t = t32(wl.eps_true), t32(wl.sig_true)
@@ -593,6 +596,8 @@ def ours(args):
                              "inputs larger than L2: checkpoints and segment buffers of "
                              f"{workspace_gb:.1f} GB",
                        "storage": (f"checkpoint every {args.checkpoint} steps"
+                                   + (", segments reconstructed backwards from a boundary ring"
+                                      if args.reconstruct else "")
                                    if args.checkpoint else "full wavefield"),
                        "workspace_gb": workspace_gb,
                        "parallelism": (f"{wl.nshots * world} shots split round-robin over "

@@ -87,6 +87,9 @@ typedef struct gf_ctx gf_ctx;
 #define GF_STORE_FULL 0       /* every Ez^n of every shot kept in the workspace */
 #define GF_STORE_CHECKPOINT 1 /* whole state every k steps; the adjoint recomputes each
                                  k-step segment from its checkpoint (one extra forward) */
+#define GF_STORE_RECONSTRUCT 2 /* checkpoints every k steps; the adjoint recomputes each
+                                  segment keeping only a boundary ring per step, then runs
+                                  the updates backwards inside the segment (experimental) */
 
 /* Create a context on CUDA device `device`: validates the grid (CFL, Eq. cfl) and the
  * geometry, builds the CPML profiles in FP64 on the host and uploads them with the
@@ -125,13 +128,22 @@ int gf_set_tiling(gf_ctx* ctx, int tile_w, int tile_h, int steps_per_launch);
  * needs ceil(nt/k) * 7 * nshots * nx * ny * 4 bytes of checkpoints plus (k + 1) * nshots * nx
  * * ny * 4 bytes of segment buffer instead of nt * nshots * nx * ny * 4, for one extra
  * forward pass.  Results agree with GF_STORE_FULL up to FP32 rounding (launches split at
- * segment boundaries group some sums differently).  Invalidates a stored forward. */
+ * segment boundaries group some sums differently).  GF_STORE_RECONSTRUCT with 1 <= k <= nt:
+ * the same checkpoints; each segment's recomputation (one step per launch) keeps Ez, Hx, Hy
+ * of a boundary ring (cells within npml + 2 of an edge) per step, (k + 1) * 3 * nshots *
+ * ring_cells * 4 bytes, and the adjoint reconstructs Ez backwards from the segment's last
+ * state (Algorithm 1's updates run in reverse outside the ring) into a (K + 1)-slot buffer
+ * before each adjoint launch.  In lossy media the reversed E update divides by Ca < 1, so
+ * FP32 rounding grows by about e^{sigma dt k / eps} over a segment: the gradient error
+ * depends on k and sigma (experimental; GF_STORE_CHECKPOINT is exact to FP32 rounding).
+ * Invalidates a stored forward. */
 int gf_set_storage(gf_ctx* ctx, int mode, int k);
 
-/* Kernel variant.  0-2: one kernel launch per time block, one CTA per (tile, shot): 0 = four
- * rows per thread, 512-thread CTAs, 64 x 64 window; 1 = four rows per thread, 256-thread CTAs
+/* Kernel variant.  0-2: one kernel launch per time block, one CTA per (tile, shot): 0
+ * (default) = four rows per thread, 512-thread CTAs, 64 x 64 window; 1 = four rows per
+ * thread, 256-thread CTAs
  * on a 64 x 32 window, two CTAs per SM (tile height + 2 steps <= 32; a taller current tile is
- * shrunk to fit); 2 = eight rows per thread, 256-thread CTAs, 64 x 64.  3 (default) = the
+ * shrunk to fit); 2 = eight rows per thread, 256-thread CTAs, 64 x 64.  3 = the
  * persistent dataflow kernels: one cooperative launch per pass, CTAs pulling (time block,
  * shot, tile) items with per-tile completion counters and bounded waits (GF_ETIMEOUT from
  * gf_status when one runs out), variant 0's window, the next item's state prefetched while

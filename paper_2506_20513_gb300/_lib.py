@@ -25,6 +25,7 @@ GF_ETIMEOUT = -6
 GF_ESTATE = -7
 GF_STORE_FULL = 0
 GF_STORE_CHECKPOINT = 1
+GF_STORE_RECONSTRUCT = 2
 
 ERROR_NAMES = {
     GF_EINVAL: "GF_EINVAL", GF_ECFL: "GF_ECFL", GF_ENOMEM: "GF_ENOMEM", GF_ECUDA: "GF_ECUDA",

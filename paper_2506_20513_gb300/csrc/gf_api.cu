@@ -31,7 +31,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Offsets (bytes) of the workspace regions.
 struct Layout {
     size_t status, partial, coef, done, stA, stB, illum, traces, resid, grad, hist, stC, stD, ckpt,
-        seg, total;
+        seg, ring, total;
 };
 
 }  // namespace
@@ -76,6 +76,8 @@ struct gf_ctx {
     MapEntry maps[4];
     int maps_next = 0;
     int store_mode = GF_STORE_FULL, ckpt_k = 0;
+    int* d_ring_map = nullptr;  // [ny][nx] ring index (reconstruction mode), -1 inside
+    int ring_cells = 0;
     const float* last_wavelet = nullptr;  // wavelet of the stored forward (recomputation)
     std::vector<int> h_rec;  // host copies of the receiver and source cells ([nshots][nrec],
     std::vector<int> h_src;  // [nshots][nsrc], linear j * nx + i)
@@ -286,13 +288,22 @@ Layout layout_of(const gf_ctx* c, bool forward_only) {
     }
     L.resid = o; o = align_up(o + tr);
     L.grad = o; o = align_up(o + 2 * field);
-    if (c->store_mode == GF_STORE_CHECKPOINT) {
-        // checkpoints of the whole state every k steps, a (k + 1)-slot Ez segment buffer and
-        // the state buffers of the segment recomputation
+    if (c->store_mode == GF_STORE_CHECKPOINT || c->store_mode == GF_STORE_RECONSTRUCT) {
+        // checkpoints of the whole state every k steps, the state buffers of the segment
+        // recomputation, and either a (k + 1)-slot Ez segment buffer or, when the adjoint
+        // reconstructs the segment backwards, (k + 1) boundary-ring slots and a (K + 1)-slot
+        // Ez buffer
         L.stC = o; o = align_up(o + gf::kNumFields * field);
         L.stD = o; o = align_up(o + gf::kNumFields * field);
         L.ckpt = o; o = align_up(o + gf::kNumFields * field * (size_t)num_checkpoints(c));
-        L.seg = o; o = align_up(o + field * (size_t)(c->ckpt_k + 1));
+        if (c->store_mode == GF_STORE_CHECKPOINT) {
+            L.seg = o; o = align_up(o + field * (size_t)(c->ckpt_k + 1));
+        } else {
+            L.seg = o; o = align_up(o + field * (size_t)(c->K + 1));
+            L.ring = o;
+            o = align_up(o + sizeof(float) * 3 * (size_t)c->nshots * c->ring_cells *
+                                 (size_t)(c->ckpt_k + 1));
+        }
     } else {
         L.hist = o; o = align_up(o + field * (size_t)c->g.nt);
     }
@@ -462,7 +473,8 @@ int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
     gf::TileParams p = base_params(c, L);
     p.wavelet = wavelet;
     p.traces = traces ? traces : (float*)(c->ws + L.traces);
-    const bool ckpt = store && c->store_mode == GF_STORE_CHECKPOINT;
+    const bool ckpt = store && (c->store_mode == GF_STORE_CHECKPOINT ||
+                                c->store_mode == GF_STORE_RECONSTRUCT);
     p.hist = store && !ckpt ? (float*)(c->ws + L.hist) : nullptr;
     p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
     const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
@@ -557,6 +569,74 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
             if (rc) return rc;
             rc = adjoint_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
             if (rc) return rc;
+        }
+    } else if (c->store_mode == GF_STORE_RECONSTRUCT) {
+        // segments in reverse: restore the checkpoint, recompute the segment one step per
+        // launch keeping the boundary ring of every step, then, block by block from the
+        // segment's end, run the updates backwards into a (K + 1)-slot Ez buffer and run the
+        // adjoint steps of that block
+        float* small = (float*)(c->ws + L.seg);
+        float* ring = (float*)(c->ws + L.ring);
+        const size_t ring_slot = 3 * (size_t)c->nshots * c->ring_cells;
+        float* const fw_buf[2] = {(float*)(c->ws + L.stC), (float*)(c->ws + L.stD)};
+        gf::TileParams q = p;
+        q.wavelet = c->last_wavelet;
+        q.traces = (float*)(c->ws + L.traces);  // recomputed traces are not needed
+        q.illum = nullptr;
+        q.hist = nullptr;
+        p.hist = small;
+        p.hist_stride = c->K + 1;
+        const size_t small_bytes = plane * (size_t)c->nshots * (c->K + 1);
+        GF_OP(c, st, -1, "clear Ez buffer", cudaMemsetAsync(small, 0, small_bytes, s_));
+        const int* map = c->d_ring_map;
+        const int rc_cells = c->ring_cells, nsh = c->nshots, nx = c->g.nx, ny = c->g.ny;
+        const int pitch = c->pitch, nsrc = c->nsrc, nt = c->g.nt;
+        const long long Np = c->Np;
+        const float rdx = p.rdx, rdy = p.rdy, ch = p.ch, sscale = p.src_scale;
+        const float* ca = p.ca;
+        const float* cb = p.cb;
+        const int2* sxy = c->d_src_xy;
+        const float* wav = c->last_wavelet;
+        for (int j = num_checkpoints(c) - 1; j >= 0; --j) {
+            const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
+            const char* ck = c->ws + L.ckpt + state * (size_t)j;
+            float* fb0 = fw_buf[0];
+            GF_OP(c, st, -1, "restore checkpoint",
+                  cudaMemcpyAsync(fb0, ck, state, cudaMemcpyDeviceToDevice, s_));
+            GF_OP(c, st, GF_KERNEL_AUX, "ring store",
+                  gf::launch_ring_store(fb0, nsh, Np, pitch, nx, ny, map, rc_cells, ring, s_));
+            int fcur = 0;
+            for (int n = n_begin; n < n_end; ++n) {
+                int rc = forward_steps(c, L, q, fw_buf, fcur, n, n + 1, st);
+                if (rc) return rc;
+                const float* sb = fw_buf[fcur];
+                float* slot = ring + ring_slot * (size_t)(n + 1 - n_begin);
+                GF_OP(c, st, GF_KERNEL_AUX, "ring store",
+                      gf::launch_ring_store(sb, nsh, Np, pitch, nx, ny, map, rc_cells, slot, s_));
+            }
+            float* rec = fw_buf[fcur];  // the state at the segment's end, reversed in place
+            for (int n1 = n_end - 1; n1 >= n_begin; n1 -= c->K) {
+                const int k = std::min(c->K, n1 - n_begin + 1), n0 = n1 - k + 1;
+                // slot m of the buffer holds Ez^{n0 + m}: the current Ez first, then the
+                // reversed steps n1 .. n0
+                const size_t sp = (size_t)(c->K + 1) * plane;
+                float* top = small + (size_t)k * (size_t)Np;
+                GF_OP(c, st, -1, "block end",
+                      cudaMemcpy2DAsync(top, sp, rec, plane, plane, (size_t)nsh,
+                                        cudaMemcpyDeviceToDevice, s_));
+                for (int n = n1; n >= n0; --n) {
+                    const float* slot = ring + ring_slot * (size_t)(n - n_begin);
+                    float* hist = small + (size_t)(n - n0) * (size_t)Np;
+                    const long long hs = (long long)(c->K + 1) * Np;
+                    GF_OP(c, st, GF_KERNEL_AUX, "reverse step",
+                          gf::launch_reverse_step(rec, nsh, Np, pitch, nx, ny, map, rc_cells,
+                                                  slot, ca, cb, rdx, rdy, ch, sxy, nsrc, wav,
+                                                  nt, n, sscale, hist, hs, s_));
+                }
+                p.hist_slot0 = n0 - 1;
+                int rc = adjoint_steps(c, L, p, st_buf, cur, n0, n1 + 1, st);
+                if (rc) return rc;
+            }
         }
     } else {
         p.hist = (float*)(c->ws + L.hist);
@@ -824,6 +904,7 @@ void gf_destroy(gf_ctx* c) {
     if (c->ws_owned && c->ws) cudaFree(c->ws);
     cudaFree(c->d_prof);
     cudaFree(c->d_src_xy);
+    cudaFree(c->d_ring_map);
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
     cudaFree(c->d_cta_order);
@@ -882,8 +963,32 @@ int gf_set_storage(gf_ctx* c, int mode, int k) {
     ++c->generation;
     if (mode == GF_STORE_FULL) {
         k = 0;
-    } else if (mode != GF_STORE_CHECKPOINT || k < 1 || k > c->g.nt) {
+    } else if ((mode != GF_STORE_CHECKPOINT && mode != GF_STORE_RECONSTRUCT) || k < 1 ||
+               k > c->g.nt) {
         return fail(c, GF_EINVAL, "storage mode %d with k = %d is not valid", mode, k);
+    }
+    if (mode == GF_STORE_RECONSTRUCT && !c->d_ring_map) {
+        // the ring: cells within npml + 2 of an edge (every CPML memory and every neighbour
+        // of a CPML cell), numbered row by row
+        const int nx = c->g.nx, ny = c->g.ny, W = c->g.npml + 2;
+        std::vector<int> map((size_t)nx * ny);
+        int cnt = 0;
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                map[(size_t)j * nx + i] =
+                    (i < W || i >= nx - W || j < W || j >= ny - W) ? cnt++ : -1;
+        DeviceGuard guard(c->device);
+        int* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, map.size() * sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            return cuda_fail(c, e, "ring map");
+        }
+        c->d_ring_map = d;
+        c->ring_cells = cnt;
     }
     c->store_mode = mode;
     c->ckpt_k = k;

@@ -195,7 +195,7 @@ __device__ __forceinline__ void unstage_state(const Pos<R>& w, const float* sm, 
 // one's sit in two shared-memory slots at float offset slot_off: warp 0 fills the next slot
 // while the current item computes (the slot it overwrites was the previous item's, which no
 // thread reads after the barrier at the top of the iteration).
-template <int R, int NW, bool kHist, bool kIllum, bool kStaged>
+template <int R, int NW, bool kHist, bool kIllum, bool kStaged, bool kMulti>
 __global__ void __launch_bounds__(32 * NW, 1)
     fwd_flow_kernel(const __grid_constant__ FlowInstance one, const FlowInstance* many,
                     const int2* __restrict__ items, long long total, int slot_off) {
@@ -204,20 +204,24 @@ __global__ void __launch_bounds__(32 * NW, 1)
     float* sm = reinterpret_cast<float*>(smem_raw);
     volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
     FlowInstance* const slots = reinterpret_cast<FlowInstance*>(sm + slot_off);
+    // one instance: its parameters straight from the launch parameter (constant bank)
+    auto inst = [&](int k) -> const FlowInstance& { return kMulti ? slots[k] : one; };
     long long i = blockIdx.x;
     if (i >= total) return;
     int s = 0;
     const int2 c0 = item_code(items, (int)i);
-    copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
-    __syncthreads();
-    Item it = decode(slots[0].p, slots[0].f, c0.y, false);
-    if (!cta_wait_deps<R, NW>(slots[0].p, slots[0].f, it, sm)) return;
-    prefetch_state<R, NW>(slots[0].p, slots[0].f, sm, it);
-    prefetch_coef<R, NW>(slots[0].p, sm, Gm::oCoef2, it);
+    if (kMulti) {
+        copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    Item it = decode(inst(0).p, inst(0).f, c0.y, false);
+    if (!cta_wait_deps<R, NW>(inst(0).p, inst(0).f, it, sm)) return;
+    prefetch_state<R, NW>(inst(0).p, inst(0).f, sm, it);
+    prefetch_coef<R, NW>(inst(0).p, sm, Gm::oCoef2, it);
     cp_async_commit();
     for (; i < total; i += gridDim.x) {
-        const TileParams& p = slots[s].p;
-        const FlowArgs& f = slots[s].f;
+        const TileParams& p = inst(s).p;
+        const FlowArgs& f = inst(s).f;
         const long long j = i + gridDim.x;
         const bool more = j < total;
         const int2 ncode = item_code(items, (int)(more ? j : i));
@@ -225,10 +229,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
         cp_async_wait<0>();
         __syncthreads();  // item i's staged state and coefficients have landed
         if (threadIdx.x < 32) {
-            copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
-            __syncwarp();
-            note_ready(slots[s ^ 1].p, slots[s ^ 1].f,
-                       decode(slots[s ^ 1].p, slots[s ^ 1].f, ncode.y, false), more, flag);
+            if (kMulti) {
+                copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
+                __syncwarp();
+            }
+            note_ready(inst(s ^ 1).p, inst(s ^ 1).f,
+                       decode(inst(s ^ 1).p, inst(s ^ 1).f, ncode.y, false), more, flag);
         }
         const bool strip = tile_in_strip<R>(p, w, it.K);
         const float* st_in = (it.b & 1) ? f.buf1 : f.buf0;
@@ -252,8 +258,8 @@ __global__ void __launch_bounds__(32 * NW, 1)
         const int nrl = L.d.y;
         const int2* ents = stage_receivers<R, NW, kStaged, false>(p, sm, it.shot, L.d, 0, it.K);
         __syncthreads();  // also publishes the next slot to every thread
-        const TileParams& pn = slots[s ^ 1].p;
-        const FlowArgs& fn = slots[s ^ 1].f;
+        const TileParams& pn = inst(s ^ 1).p;
+        const FlowArgs& fn = inst(s ^ 1).f;
         const Item nx = decode(pn, fn, ncode.y, false);
         const bool ahead = flag[0] != 0;
         if (ahead) {  // the staging planes are free: fetch the next item during this one
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // ---------------------------------------------------------------------------------------
 // Adjoint pass
 // ---------------------------------------------------------------------------------------
-template <int R, int NW, bool kStaged>
+template <int R, int NW, bool kStaged, bool kMulti>
 __global__ void __launch_bounds__(32 * NW, 1)
     adj_flow_kernel(const __grid_constant__ FlowInstance one, const FlowInstance* many,
                     const int2* __restrict__ items, long long total, int slot_off) {
@@ -300,20 +306,24 @@ __global__ void __launch_bounds__(32 * NW, 1)
     float* sm = reinterpret_cast<float*>(smem_raw);
     volatile int* flag = reinterpret_cast<volatile int*>(sm + Gm::oFlag);
     FlowInstance* const slots = reinterpret_cast<FlowInstance*>(sm + slot_off);
+    // one instance: its parameters straight from the launch parameter (constant bank)
+    auto inst = [&](int k) -> const FlowInstance& { return kMulti ? slots[k] : one; };
     long long i = blockIdx.x;
     if (i >= total) return;
     int s = 0;
     const int2 c0 = item_code(items, (int)i);
-    copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
-    __syncthreads();
-    Item it = decode(slots[0].p, slots[0].f, c0.y, true);
-    if (!cta_wait_deps<R, NW>(slots[0].p, slots[0].f, it, sm)) return;
-    prefetch_state<R, NW>(slots[0].p, slots[0].f, sm, it);
-    prefetch_coef<R, NW>(slots[0].p, sm, Gm::oCoef, it);
+    if (kMulti) {
+        copy_instance(slots, one, many, c0.x, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    Item it = decode(inst(0).p, inst(0).f, c0.y, true);
+    if (!cta_wait_deps<R, NW>(inst(0).p, inst(0).f, it, sm)) return;
+    prefetch_state<R, NW>(inst(0).p, inst(0).f, sm, it);
+    prefetch_coef<R, NW>(inst(0).p, sm, Gm::oCoef, it);
     cp_async_commit();
     for (; i < total; i += gridDim.x) {
-        const TileParams& p = slots[s].p;
-        const FlowArgs& f = slots[s].f;
+        const TileParams& p = inst(s).p;
+        const FlowArgs& f = inst(s).f;
         const long long j = i + gridDim.x;
         const bool more = j < total;
         const int2 ncode = item_code(items, (int)(more ? j : i));
@@ -324,10 +334,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
         // (the next item is decoded where it is needed: holding it through the time steps
         // would cost registers)
         if (threadIdx.x < 32) {
-            copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
-            __syncwarp();
-            note_ready(slots[s ^ 1].p, slots[s ^ 1].f,
-                       decode(slots[s ^ 1].p, slots[s ^ 1].f, ncode.y, true), more, flag);
+            if (kMulti) {
+                copy_instance(slots + (s ^ 1), one, many, ncode.x, threadIdx.x, 32);
+                __syncwarp();
+            }
+            note_ready(inst(s ^ 1).p, inst(s ^ 1).f,
+                       decode(inst(s ^ 1).p, inst(s ^ 1).f, ncode.y, true), more, flag);
         }
         float2 aez[R], ahx[R], ahy[R], ge[R], gs[R];
         const float* hp = p.hist + ((long long)it.shot * p.hist_stride - p.hist_slot0) * p.Np +
@@ -359,7 +371,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
             p, w, reinterpret_cast<const int*>(sm + Gm::oRec), ents, nrl, K, rlo, rhi, false);
         // after phase A 0 the staging planes are free: fetch the next item's state; after the
         // last phase A this item no longer reads its coefficients: fetch the next item's
-        const FlowInstance& nxi = slots[s ^ 1];
+        const FlowInstance& nxi = inst(s ^ 1);
         auto after_a = [&](int a) {
             if (!more) return;
             if (a == 0 && ahead) {
@@ -430,16 +442,16 @@ cudaError_t launch_flow(Kern k, const FlowInstance& one, const FlowInstance* man
     return cudaLaunchCooperativeKernel((const void*)k, dim3(grid), dim3(threads), args, smem, st);
 }
 
-template <int R, int NW, bool kHist, bool kIllum>
+template <int R, int NW, bool kHist, bool kIllum, bool kMulti>
 cudaError_t launch_fwd_flow_v(const FlowInstance& one, const FlowInstance* many,
                               const int2* items, long long total, bool staged, cudaStream_t st) {
     using Gm = G<R, NW>;
     const size_t floats = Gm::fwd_flow_floats;
     if (staged)
-        return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, true>, one, many, items, total,
-                           Gm::NT, floats, st);
-    return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, false>, one, many, items, total,
-                       Gm::NT, floats, st);
+        return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, true, kMulti>, one, many, items,
+                           total, Gm::NT, floats, st);
+    return launch_flow(fwd_flow_kernel<R, NW, kHist, kIllum, false, kMulti>, one, many, items,
+                       total, Gm::NT, floats, st);
 }
 
 cudaError_t launch_any(const FlowInstance& one, const FlowInstance* many, const int2* items,
@@ -447,15 +459,24 @@ cudaError_t launch_any(const FlowInstance& one, const FlowInstance* many, const 
                        int ring, cudaStream_t st) {
     using Gm = G<4, 16>;
     if (!adjoint) {
-        if (hist && illum) return launch_fwd_flow_v<4, 16, true, true>(one, many, items, total, staged, st);
-        if (hist) return launch_fwd_flow_v<4, 16, true, false>(one, many, items, total, staged, st);
-        if (illum) return launch_fwd_flow_v<4, 16, false, true>(one, many, items, total, staged, st);
-        return launch_fwd_flow_v<4, 16, false, false>(one, many, items, total, staged, st);
+        if (many) {  // merged instances: no wavefield-less illumination pass is merged
+            if (hist) return launch_fwd_flow_v<4, 16, true, false, true>(one, many, items, total, staged, st);
+            return launch_fwd_flow_v<4, 16, false, false, true>(one, many, items, total, staged, st);
+        }
+        if (hist && illum) return launch_fwd_flow_v<4, 16, true, true, false>(one, many, items, total, staged, st);
+        if (hist) return launch_fwd_flow_v<4, 16, true, false, false>(one, many, items, total, staged, st);
+        if (illum) return launch_fwd_flow_v<4, 16, false, true, false>(one, many, items, total, staged, st);
+        return launch_fwd_flow_v<4, 16, false, false, false>(one, many, items, total, staged, st);
     }
     const size_t floats = Gm::adj_ring_off + (size_t)kRing * ring;
+    if (many) {
+        if (staged)
+            return launch_flow(adj_flow_kernel<4, 16, true, true>, one, many, items, total, Gm::NT, floats, st);
+        return launch_flow(adj_flow_kernel<4, 16, false, true>, one, many, items, total, Gm::NT, floats, st);
+    }
     if (staged)
-        return launch_flow(adj_flow_kernel<4, 16, true>, one, many, items, total, Gm::NT, floats, st);
-    return launch_flow(adj_flow_kernel<4, 16, false>, one, many, items, total, Gm::NT, floats, st);
+        return launch_flow(adj_flow_kernel<4, 16, true, false>, one, many, items, total, Gm::NT, floats, st);
+    return launch_flow(adj_flow_kernel<4, 16, false, false>, one, many, items, total, Gm::NT, floats, st);
 }
 
 bool staged_receivers(const TileParams& p, int kb, bool adjoint) {
@@ -475,16 +496,22 @@ cudaError_t configure_flow_kernels(size_t optin) {
     cudaError_t e;
 #define GF_ALLOW(...) \
     if ((e = allow_flow_smem(__VA_ARGS__, optin)) != cudaSuccess) return e
-    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, true>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, true>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, true>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, true>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, false>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, false>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, false>);
-    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, false>);
-    GF_ALLOW(adj_flow_kernel<4, 16, true>);
-    GF_ALLOW(adj_flow_kernel<4, 16, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, true, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, true, false, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, false, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, true, false, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, false, false>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, true, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, true, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, true, false, false, true>);
+    GF_ALLOW(fwd_flow_kernel<4, 16, false, false, false, true>);
+    GF_ALLOW(adj_flow_kernel<4, 16, true, false>);
+    GF_ALLOW(adj_flow_kernel<4, 16, false, false>);
+    GF_ALLOW(adj_flow_kernel<4, 16, true, true>);
+    GF_ALLOW(adj_flow_kernel<4, 16, false, true>);
 #undef GF_ALLOW
     return cudaSuccess;
 }

@@ -155,6 +155,20 @@ cudaError_t adam_update(long long n, float* x, const float* g, float* m, float* 
                         int t, float xmin, cudaStream_t st);
 cudaError_t tv_gradient(int nx, int ny, const float* X, float* G, float* scratch, float lambda,
                         float mu, int iters, float weight, cudaStream_t st);
+// Reverse-time reconstruction inside checkpoint segments (gf_reconstruct.cu).  ring_map:
+// [ny][nx] ring index of each cell (-1 outside the ring); a ring slot holds Ez, Hx, Hy of the
+// ring cells of every shot ([3][nshots][ring_cells]).
+cudaError_t launch_ring_store(const float* st, int nshots, long long Np, int pitch, int nx,
+                             int ny, const int* ring_map, int ring_cells, float* slot,
+                             cudaStream_t stream);
+// Undo step n (state_{n+1} -> state_n in place) and write Ez^n of shot s to
+// hist + s * hist_stride_np.
+cudaError_t launch_reverse_step(float* st, int nshots, long long Np, int pitch, int nx, int ny,
+                                const int* ring_map, int ring_cells, const float* slot,
+                                const float* ca, const float* cb, float rdx, float rdy,
+                                float ch, const int2* src_xy, int nsrc, const float* wavelet,
+                                int nt, int n, float src_scale, float* hist,
+                                long long hist_stride_np, cudaStream_t stream);
 // out[gy * nx + gx] = sum over shots of per_shot[s * pitch * ny + gy * pitch + gx].
 cudaError_t launch_sum_shots(const float* per_shot, int nshots, int nx, int ny, int pitch,
                              float* out, int* status, cudaStream_t st);

@@ -173,6 +173,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
+// Programmatic dependent launch (the tile kernels of a pass are launched with programmatic
+// stream serialisation): launch_dependents lets the next launch's CTAs start their prologue
+// on the SMs this launch's last wave leaves idle; wait blocks the calling thread until the
+// previous kernel on the stream has completed and its memory operations are visible.  Data a
+// previous launch writes or reads (the state buffers, the gradient and illumination sums,
+// the wavefield store) are touched only after the wait.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // One 3-D TMA box (fp32, 64 x WY x 1 at (x, y, z)) into shared memory, completion counted in
 // bytes on the mbarrier.  x must be a multiple of 4 (16 bytes); x, y may lie outside the
 // array (zero fill).
@@ -373,12 +384,15 @@ __device__ __forceinline__ void tma_window(const TileMaps& m, float* sm, uint32_
     constexpr uint32_t kPlane = Gm::WY * WX * sizeof(float);
     mbar_init(bar, 1);
     mbar_expect_tx(bar, (strip ? 9u : 5u) * kPlane);
-#pragma unroll
-    for (int f = 0; f < 3; ++f)
-        tma_load_3d(smem_u32(sm + Gm::oStage + f * 2 * Gm::PL), &m.st, X0, Y0, f * nshots + shot, bar);
+    // the coefficients first: no kernel of the pass writes them, so they may load while the
+    // previous launch of the pass still runs; the state only after it has completed
 #pragma unroll
     for (int c = 0; c < 2; ++c)
         tma_load_3d(smem_u32(sm + Gm::oCoef + c * 2 * Gm::PL), &m.coef, X0, Y0, c, bar);
+    pdl_wait();
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+        tma_load_3d(smem_u32(sm + Gm::oStage + f * 2 * Gm::PL), &m.st, X0, Y0, f * nshots + shot, bar);
     if (strip) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)

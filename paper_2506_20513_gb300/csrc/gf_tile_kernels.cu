@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     fwd_tile_kernel(const TileParams p, const __grid_constant__ TileMaps m) {
     extern __shared__ __align__(1024) float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
+    pdl_launch_dependents();
     const int code = __ldg(p.cta_order + blockIdx.x);
     const int shot = code >> 16, tile = code & 0xffff, K = p.K;
     const Pos<R> w = position<R>(p, tile, K);
@@ -57,6 +58,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
     using Gm = G<R, NW>;
     extern __shared__ __align__(1024) float4 smem_raw[];
     float* sm = reinterpret_cast<float*>(smem_raw);
+    pdl_launch_dependents();
     const int code = __ldg(p.cta_order + blockIdx.x);
     const int shot = code >> 16, tile = code & 0xffff, K = p.K;
     const int n1 = p.n0 + K - 1;
@@ -77,10 +79,12 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
         ge[r] = gs[r] = make_float2(0.f, 0.f);
     }
     const Ring rg = make_ring<R, NW>(p, w, sm, Gm::adj_ring_off, K);
-    for (int a = -1; a < kRingLead; ++a) ring_fetch<R>(p, rg, hp, own, n1, K, a);
     TileLoads<R> L;
     issue_loads<R, NW, false, false, false, false, false>(p, w, p.st_in, shot, tile, p.n0, K,
                                                           strip, L);
+    // the stored wavefield may come from the launch just before (a segment's recomputation)
+    pdl_wait();
+    for (int a = -1; a < kRingLead; ++a) ring_fetch<R>(p, rg, hp, own, n1, K, a);
     store_loads<R, NW, false, false, false>(p, w, sm, K, strip, L);
     const int nrl = L.d.y;
     const int2* ents = stage_receivers<R, NW, kStaged, true>(p, sm, shot, L.d, n1, K);
@@ -135,17 +139,32 @@ cudaError_t configure_variant(size_t optin) {
     return cudaSuccess;
 }
 
+// A tile launch with programmatic stream serialisation: it may begin while the previous
+// kernel on the stream finishes (each CTA waits for it before touching its data).
+template <class Kern>
+cudaError_t launch_pdl(Kern k, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       const TileParams& p, const TileMaps& m) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, p, m);
+}
+
 template <int R, int NW, bool kHist, bool kIllum>
 cudaError_t launch_fwd_variant(const TileParams& p, const TileMaps& m, bool staged,
                                cudaStream_t st) {
     using Gm = G<R, NW>;
     const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = sizeof(float) * Gm::fwd_floats;
-    if (staged)
-        fwd_tile_kernel<R, NW, kHist, kIllum, true><<<grid, block, smem, st>>>(p, m);
-    else
-        fwd_tile_kernel<R, NW, kHist, kIllum, false><<<grid, block, smem, st>>>(p, m);
-    return cudaGetLastError();
+    if (staged) return launch_pdl(fwd_tile_kernel<R, NW, kHist, kIllum, true>, grid, block, smem, st, p, m);
+    return launch_pdl(fwd_tile_kernel<R, NW, kHist, kIllum, false>, grid, block, smem, st, p, m);
 }
 
 template <int R, int NW>
@@ -166,11 +185,8 @@ cudaError_t launch_adj_r(const TileParams& p, const TileMaps& m, bool staged, cu
     using Gm = G<R, NW>;
     const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = adj_smem<R, NW>(p.tile_w, p.tile_h);
-    if (staged)
-        adj_tile_kernel<R, NW, true><<<grid, block, smem, st>>>(p, m);
-    else
-        adj_tile_kernel<R, NW, false><<<grid, block, smem, st>>>(p, m);
-    return cudaGetLastError();
+    if (staged) return launch_pdl(adj_tile_kernel<R, NW, true>, grid, block, smem, st, p, m);
+    return launch_pdl(adj_tile_kernel<R, NW, false>, grid, block, smem, st, p, m);
 }
 
 }  // namespace

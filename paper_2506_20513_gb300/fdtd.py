@@ -118,10 +118,14 @@ class FDTD:
         _lib.check(self.lib, self.ctx, self.lib.gf_get_tiling(self.ctx, *[ctypes.byref(x) for x in v]))
         return Tiling(*[x.value for x in v])
 
-    def set_storage(self, checkpoint_every: int = 0):
+    def set_storage(self, checkpoint_every: int = 0, reconstruct: bool = False):
         """0: keep the full forward wavefield; k > 0: checkpoint every k steps and recompute
-        each segment during the adjoint (same results, less memory, one extra forward)."""
-        mode = _lib.GF_STORE_CHECKPOINT if checkpoint_every > 0 else _lib.GF_STORE_FULL
+        each segment during the adjoint (same results, less memory, one extra forward); with
+        ``reconstruct`` the recomputation keeps only a boundary ring per step and the adjoint
+        runs the updates backwards inside each segment (experimental: its error grows with k
+        and the conductivity)."""
+        mode = ((_lib.GF_STORE_RECONSTRUCT if reconstruct else _lib.GF_STORE_CHECKPOINT)
+                if checkpoint_every > 0 else _lib.GF_STORE_FULL)
         _lib.check(self.lib, self.ctx, self.lib.gf_set_storage(self.ctx, mode, checkpoint_every))
         self._store_mode = mode
         self._ws = None

@@ -135,14 +135,17 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
             h_plain, t_plain = _fwi(fd, wl, obs, wl.f0, args.iters)
             p = dict(J0=h_plain.misfit[0] if h_plain.misfit else None,
                      J_plain=h_plain.final_misfit, it_plain=len(h_plain.misfit),
-                     ev_plain=int(sum(h_plain.evaluations)), s_plain=t_plain)
+                     ev_plain=int(sum(h_plain.evaluations)),
+                     passes_plain=int(sum(h_plain.passes)), s_plain=t_plain)
         target = p["J_plain"]
         h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target, retry=args.retry,
                         scales=[float(v) for v in args.scales.split(",")])
         rows.append(dict(seed=int(s), J0=p["J0"], J_plain=target, it_plain=p["it_plain"],
-                         ev_plain=p["ev_plain"], s_plain=p["s_plain"],
+                         ev_plain=p["ev_plain"], passes_plain=p.get("passes_plain"),
+                         s_plain=p["s_plain"],
                          J_learned=h_l.final_misfit, it_learned=len(h_l.misfit),
-                         ev_learned=int(sum(h_l.evaluations)), s_learned=t_l,
+                         ev_learned=int(sum(h_l.evaluations)),
+                         passes_learned=int(sum(h_l.passes)), s_learned=t_l,
                          reached=bool(h_l.final_misfit <= target),
                          learned_accepted=int(sum(h_l.learned))))
     reached = [r for r in rows if r["reached"]]
@@ -160,6 +163,10 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
         "median_iters_learned": float(np.median([r["it_learned"] for r in rows])),
         "median_evals_plain": float(np.median([r["ev_plain"] for r in rows])),
         "median_evals_learned": float(np.median([r["ev_learned"] for r in rows])),
+        # forward-equivalent time loops: a misfit-only evaluation 1, a gradient 2
+        "median_passes_plain": (float(np.median([r["passes_plain"] for r in rows]))
+                                if all(r["passes_plain"] is not None for r in rows) else None),
+        "median_passes_learned": float(np.median([r["passes_learned"] for r in rows])),
         "median_s_plain": float(np.median([r["s_plain"] for r in rows])),
         "median_s_learned": float(np.median([r["s_learned"] for r in rows])),
         "learned_steps_accepted": int(sum(r["learned_accepted"] for r in rows)),
