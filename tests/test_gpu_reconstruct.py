@@ -71,19 +71,23 @@ def test_reconstruction_in_a_nearly_lossless_medium(dev, k):
 
 
 def test_reconstruction_error_grows_with_k_and_sigma(dev):
+    """Growth per reversed step is about 1 / Ca = 1 + sigma dt / eps: on this grid (dt 42 ps,
+    eps_r 3-12) about 1.007 at 10 mS/m, 1.14 at 200 mS/m and 2 at 1 S/m, so the error stays at
+    FP32 rounding for the first, grows by orders of magnitude with k for the second, and is
+    lost within a short segment for the third."""
     rows = {}
-    for sig_max in (1.0, 10.0, 50.0):
+    for sig_max in (10.0, 200.0, 1000.0):
         wl, sig_t, sig_i = _case(sig_max)
         (_, gec, gsc), _, _ = _gradients(wl, sig_t, sig_i, dev, (300, False))
-        for k in (25, 100, 300):
+        for k in (10, 40, 150):
             (_, ge, gs), _, _ = _gradients(wl, sig_t, sig_i, dev, (k, True))
             rows[(sig_max, k)] = max(rel(ge, gec), rel(gs, gsc)) if np.isfinite(ge).all() \
                 and np.isfinite(gs).all() else float("inf")
     print("\nsigma_max (mS/m), k, max rel-L2 gradient error vs checkpointing")
     for key, v in sorted(rows.items()):
-        print(f"{key[0]:6.1f} {key[1]:4d} {v:.3e}")
-    for sig_max in (1.0, 10.0, 50.0):
-        errs = [rows[(sig_max, k)] for k in (25, 100, 300)]
-        assert errs[0] <= errs[1] * 1.5 and errs[1] <= errs[2] * 1.5
-    assert rows[(1.0, 25)] <= 1e-3
-    assert rows[(50.0, 300)] >= rows[(1.0, 300)]
+        print(f"{key[0]:7.1f} {key[1]:4d} {v:.3e}")
+    assert rows[(10.0, 150)] <= 1e-3
+    for k in (10, 40, 150):
+        assert rows[(1000.0, k)] >= rows[(200.0, k)] >= 0.5 * rows[(10.0, k)]
+    assert rows[(200.0, 150)] > 10 * rows[(200.0, 10)]
+    assert rows[(1000.0, 150)] > 1e-2
