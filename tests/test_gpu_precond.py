@@ -81,56 +81,53 @@ def test_training_and_guarded_fwi_step(setup, dev):
 
 
 def test_trained_network_gains_on_held_out_models(dev):
-    """What the trained network gains over plain L-BFGS, on a reduced preconditioner workload
-    (64 x 32 physical cells + 10-cell CPML, dx 0.01 m, 400 MHz, 8 shots, 24 receivers, nt 700):
-    the U-Net is trained here on 480 seeded models (pairs from the FDTD/adjoint kernels, the
-    library's BF16 training kernels), then on 12 held-out models plain L-BFGS runs 25
+    """What the trained network gains over plain L-BFGS, on the preconditioner workload
+    (256 x 128 cells + 20-cell CPML, 16 shots, 64 receivers, nt 1500): the U-Net is trained
+    here on 1500 seeded models (pairs from the FDTD/adjoint kernels, 30 epochs of the
+    library's BF16 training kernels), then on 12 held-out models plain L-BFGS runs 50
     iterations and sets the target misfit, and the learned run (network update tried first,
     plain step as fallback) runs until it reaches that misfit.  At the median over the
-    held-out models the learned run needs fewer forward-equivalent FDTD time loops (a
-    misfit-only evaluation 1, a gradient 2) and fewer iterations, and most models reach the
-    target."""
+    held-out models the learned run needs at most 3/4 of the plain run's forward-equivalent
+    FDTD time loops (a misfit-only evaluation 1, a gradient 2; measured 56.5 against 108.5)
+    and fewer iterations and less time, and at least 8 of the 12 models reach the target
+    (measured 10)."""
     import time
 
     from paper_2506_20513_gb300 import FDTD
     from paper_2506_20513_gb300.fdtd import ricker
     from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
     from paper_2506_20513_gb300.precond import (LearnedPreconditioner, PreconditionerScales,
-                                                generate_pairs, pair_fractions, train)
+                                                generate_pairs, pair_fractions, seeded_models,
+                                                train)
     from paper_2506_20513_gb300.unet import UNet
-    nt = 700
-    mk = lambda s: W.preconditioner_model(s, nshots=8, nt=nt, nxp=64, nyp=32, npml=10, nrec=24)
-    first = mk(500000)
+    nt = 1500
+    first = W.preconditioner_model(100000, nt=nt)
     g = first.grid
     fd = FDTD(g, first.src, first.rec, device=dev)
     wav = torch.tensor(ricker(first.f0, g.dt, g.nt), device=dev)
-    seeds = np.arange(500000, 500480)
-
-    def models():
-        for s in seeds:
-            w = mk(int(s))
-            yield w.eps_true, w.sig_true, w.eps_init, w.sig_init
-
-    X, T, _ = generate_pairs(fd, models(), len(seeds), wav, PreconditionerScales(), g.npml,
-                             fractions=pair_fractions(seeds))
+    seeds = np.arange(100000, 101500)
+    # the host-side model generation runs in 4 spawned processes, overlapping the GPU work
+    X, T, _ = generate_pairs(fd, seeded_models(seeds, nt, workers=4), len(seeds), wav,
+                             PreconditionerScales(), g.npml, fractions=pair_fractions(seeds))
     net = UNet(4, 32, 4, 2, g.ny - 2 * g.npml, g.nx - 2 * g.npml, max_batch=16, device=dev)
     net.init_params(5)
-    losses = train(net, X, T, epochs=60, batch=16, lr=1e-3, seed=5, decay_every=20)
+    losses = train(net, X, T, epochs=30, batch=16, lr=1e-3, seed=5, decay_every=10)
+    del X, T
     assert losses[-1] < 0.5 * losses[0]
     pre = LearnedPreconditioner(net, g.npml)
     mask = interior_mask(g, rows_below_top=4)
     t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
     rows = []
-    for s in range(600000, 600012):
-        w = mk(s)
+    for s in range(1100000, 1100012):
+        w = W.preconditioner_model(s, nt=nt)
         obs = fd.forward_model(t32(w.eps_true), t32(w.sig_true), wav)
         runs = []
-        for p, stop in ((None, None), (pre, "target")):
-            inv = FWI(fd, lambda f: obs, mask, FWIConfig(bands=((w.f0, 25),)), preconditioner=p)
+        for p in (None, pre):
+            inv = FWI(fd, lambda f: obs, mask, FWIConfig(bands=((w.f0, 50),)), preconditioner=p)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             _, _, h = inv.run(t32(w.eps_init), t32(w.sig_init),
-                              stop_misfit=runs[0][0] if stop else None)
+                              stop_misfit=runs[0][0] if p is not None else None)
             torch.cuda.synchronize(dev)
             runs.append((h.final_misfit, sum(h.passes), len(h.misfit), sum(h.evaluations),
                          time.perf_counter() - t0))
@@ -142,7 +139,8 @@ def test_trained_network_gains_on_held_out_models(dev):
           f"passes {med(0, 1)} -> {med(1, 1)}, iterations {med(0, 2)} -> {med(1, 2)}, "
           f"evaluations {med(0, 3)} -> {med(1, 3)}, seconds {med(0, 4):.3f} -> {med(1, 4):.3f}")
     assert reached >= 8
-    assert med(1, 1) < med(0, 1)
+    assert med(1, 1) <= 0.75 * med(0, 1)
     assert med(1, 2) < med(0, 2)
+    assert med(1, 4) < med(0, 4)
     net.close()
     fd.close()

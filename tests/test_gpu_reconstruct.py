@@ -71,10 +71,12 @@ def test_reconstruction_in_a_nearly_lossless_medium(dev, k):
 
 
 def test_reconstruction_error_grows_with_k_and_sigma(dev):
-    """Growth per reversed step is about 1 / Ca = 1 + sigma dt / eps: on this grid (dt 42 ps,
-    eps_r 3-12) about 1.007 at 10 mS/m, 1.14 at 200 mS/m and 2 at 1 S/m, so the error stays at
-    FP32 rounding for the first, grows by orders of magnitude with k for the second, and is
-    lost within a short segment for the third."""
+    """The reversed E update divides by Ca every step (1 / Ca = 1 + sigma dt / eps, about
+    1.007 at 10 mS/m, 1.14 at 200 mS/m and 2 at 1 S/m on this grid: dt 42 ps, eps_r 3-12):
+    rounding errors grow backwards through a segment wherever the true field does not grow
+    with them.  Measured: up to 200 mS/m and k = 150 the gradient stays at FP32 rounding
+    (about 2e-7); at 1 S/m it is 1.8e-7 at k = 10, 1.5e-6 at k = 40 and lost (overflow or
+    1e7) at k = 150."""
     rows = {}
     for sig_max in (10.0, 200.0, 1000.0):
         wl, sig_t, sig_i = _case(sig_max)
@@ -86,8 +88,9 @@ def test_reconstruction_error_grows_with_k_and_sigma(dev):
     print("\nsigma_max (mS/m), k, max rel-L2 gradient error vs checkpointing")
     for key, v in sorted(rows.items()):
         print(f"{key[0]:7.1f} {key[1]:4d} {v:.3e}")
-    assert rows[(10.0, 150)] <= 1e-3
-    for k in (10, 40, 150):
-        assert rows[(1000.0, k)] >= rows[(200.0, k)] >= 0.5 * rows[(10.0, k)]
-    assert rows[(200.0, 150)] > 10 * rows[(200.0, 10)]
+    for sig_max in (10.0, 200.0):
+        for k in (10, 40, 150):
+            assert rows[(sig_max, k)] <= 1e-5
+    assert rows[(1000.0, 10)] <= 1e-5
+    assert rows[(1000.0, 40)] > 3 * rows[(1000.0, 10)]
     assert rows[(1000.0, 150)] > 1e-2
