@@ -293,24 +293,29 @@ def algorithmic_bytes_per_launch(kind: str, wl, K: float, history: float = 1.0) 
 
 
 def read_profile(lib, ctx) -> dict:
-    """Per launch class: (total ms, launches) from the library's CUDA-event profile."""
+    """Per launch class: (busy ms, launches, summed ms) from the library's CUDA-event
+    profile; busy = the union of the launches' intervals (the launches of concurrent shot
+    lanes, and consecutive launches under programmatic dependent launch, overlap)."""
     import ctypes
     from paper_2506_20513_gb300 import _lib
     prof = {}
     for name, kind in (("fwd", _lib.GF_KERNEL_FWD), ("adj", _lib.GF_KERNEL_ADJ),
                        ("aux", _lib.GF_KERNEL_AUX)):
-        tot, cnt = ctypes.c_double(), ctypes.c_longlong()
-        lib.gf_profile_read(ctx, kind, ctypes.byref(tot), ctypes.byref(cnt))
-        prof[name] = (tot.value, cnt.value)
+        tot, span, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        lib.gf_profile_read_span(ctx, kind, ctypes.byref(tot), ctypes.byref(span),
+                                 ctypes.byref(cnt))
+        prof[name] = (span.value, cnt.value, tot.value)
     return prof
 
 
 def tile_roofline(prof: dict, wl, steps: int, history_fwd: float, tiling: str, clk: dict,
                   sms: int) -> dict:
-    """Roofline of the dominant tile kernel from its own launches' CUDA-event durations."""
+    """Roofline of the dominant tile kernel from its own launches' CUDA-event intervals: the
+    algorithmic bytes of all its launches over the time they kept the GPU busy (the union
+    of their intervals), i.e. bytes per launch over the effective launch duration."""
     g = wl.grid
     dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
-    tot_ms, cnt = prof[dom]
+    tot_ms, cnt, sum_ms = prof[dom]
     # launches of K steps except a possibly shorter last one: use the mean steps per launch;
     # under checkpointing the forward runs twice per gradient (checkpoints, then recompute)
     passes = 2 if (dom == "fwd" and history_fwd < 1.0) else 1
@@ -327,6 +332,7 @@ def tile_roofline(prof: dict, wl, steps: int, history_fwd: float, tiling: str, c
             "kernel": f"{dom}_tile_kernel", "peak_source": f"hbm_gbs of {peak_kind}",
             "algorithmic_bytes_per_launch": algo, "steps_per_launch": per_launch_steps,
             "avg_launch_us": avg_s * 1e6, "launches": cnt,
+            "avg_launch_event_us": sum_ms / 1e3 / max(1, cnt) * 1e6,
             "phase_ms_per_step": {k: v[0] / steps for k, v in prof.items()}}
     ipc = NCU_WARP_INST_PER_CELL_STEP.get(key)
     if ipc:

@@ -151,6 +151,15 @@ int gf_set_storage(gf_ctx* ctx, int mode, int k);
  * same result up to FP32 rounding. */
 int gf_set_variant(gf_ctx* ctx, int variant);
 
+/* Shot lanes (1-4, default 2): the shots are split into that many contiguous groups whose
+ * passes run concurrently on the context's own streams, forked from and joined back into the
+ * caller's stream, so that one group's launches fill the SMs the other's last wave leaves
+ * idle.  Results do not depend on the lanes (every shot's arithmetic and every sum's order
+ * are the same).  Used by the per-launch variants (0-2) with GF_STORE_FULL or
+ * GF_STORE_CHECKPOINT; the persistent variant, GF_STORE_RECONSTRUCT and recorded batch
+ * schedules run one lane. */
+int gf_set_lanes(gf_ctx* ctx, int lanes);
+
 /* Current tiling and variant (for autotuners). */
 int gf_get_tiling(const gf_ctx* ctx, int* tile_w, int* tile_h, int* steps_per_launch,
                   int* variant);
@@ -247,6 +256,12 @@ int gf_profile(gf_ctx* ctx, int enable);
  * time in milliseconds and the number of launches recorded since the last read (or since
  * profiling was enabled); the family's record is then cleared. */
 int gf_profile_read(gf_ctx* ctx, int kind, double* ms_total, long long* launches);
+
+/* As gf_profile_read, and also the length in milliseconds of the union of the launches'
+ * intervals (launches of concurrent lanes, and consecutive launches under programmatic
+ * dependent launch, overlap: the union is the time the family kept the GPU busy). */
+int gf_profile_read_span(gf_ctx* ctx, int kind, double* ms_total, double* ms_span,
+                         long long* launches);
 
 /* Forward model without any memory allocation.  The paper has no counterpart: this is a
  * service for callers that may not allocate device memory (their memory belongs to another

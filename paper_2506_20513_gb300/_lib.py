@@ -36,8 +36,8 @@ ERROR_NAMES = {
 EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
     "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
-    "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_set_wait_budget", "gf_profile",
-    "gf_profile_read", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
+    "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_set_wait_budget", "gf_set_lanes", "gf_profile",
+    "gf_profile_read", "gf_profile_read_span", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
     "gf_tv_gradient", "gf_adam_update", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
     "gf_batch_last_error", "gf_batch_misfit_and_gradient",
     "gf_unet_param_count", "gf_unet_create", "gf_unet_destroy", "gf_unet_last_error",
@@ -115,8 +115,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_version": (ctypes.c_char_p, []),
             "gf_kernel_launches": (ctypes.c_longlong, [vp]),
             "gf_set_wait_budget": (i, [vp, ctypes.c_longlong]),
+            "gf_set_lanes": (i, [vp, i]),
             "gf_profile": (i, [vp, i]),
             "gf_profile_read": (i, [vp, i, P(ctypes.c_double), P(ctypes.c_longlong)]),
+            "gf_profile_read_span": (i, [vp, i, P(ctypes.c_double), P(ctypes.c_double),
+                                         P(ctypes.c_longlong)]),
             "gf_misfit": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "gf_tv_scratch_bytes": (sz, [i, i]),
             "gf_tv_gradient": (i, [i, i, vp, vp, vp, ctypes.c_float, ctypes.c_float, i,

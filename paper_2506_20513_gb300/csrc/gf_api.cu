@@ -83,7 +83,12 @@ struct gf_ctx {
     std::vector<int> h_src;  // [nshots][nsrc], linear j * nx + i)
     int4* d_tile_desc = nullptr;    // per (shot, tile) descriptors for the current tiling
     int2* d_tile_rec = nullptr;     // their receiver entries
-    int* d_cta_order = nullptr;     // launch order of the (shot, tile) pairs
+    int* d_cta_order = nullptr;     // launch order of the (shot, tile) pairs: all shots, then
+                                    // the shots of each lane
+    int lanes = 2;                  // shot groups run concurrently on their own streams
+    int lane_off[4] = {0}, lane_cnt[4] = {0};  // each lane's part of d_cta_order
+    cudaStream_t lane_st[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t lane_fork = nullptr, lane_join[4] = {nullptr, nullptr, nullptr, nullptr};
     int tile_rec_max = 0;           // longest per (shot, tile) list of the current tiling
     long long generation = 0;        // bumped when launch parameters or buffers change
     size_t smem_optin = 0;
@@ -273,7 +278,7 @@ Layout layout_of(const gf_ctx* c, bool forward_only) {
     const size_t tr = sizeof(float) * (size_t)c->nshots * c->g.nt * c->nrec;
     size_t o = 0;
     L.status = o; o = align_up(o + sizeof(int));
-    L.partial = o; o = align_up(o + sizeof(double) * kMisfitBlocks);
+    L.partial = o; o = align_up(o + sizeof(double) * kMisfitBlocks * 5);  // total + 4 lanes
     L.coef = o; o = align_up(o + 2 * sizeof(float) * (size_t)c->Np);
     const size_t ntiles = (size_t)((c->g.nx + c->tile_w - 1) / c->tile_w) *
                           ((c->g.ny + c->tile_h - 1) / c->tile_h);
@@ -365,6 +370,7 @@ gf::TileParams base_params(const gf_ctx* c, const Layout& L) {
     p.tile_desc = c->d_tile_desc;
     p.tile_rec = c->d_tile_rec;
     p.cta_order = c->d_cta_order;
+    p.ncta = p.ntiles * c->nshots;
     p.rec_max = c->tile_rec_max;
     p.kl = gf::left_halo(c->K);
     p.hist_stride = c->g.nt;
@@ -464,78 +470,215 @@ int adjoint_steps(gf_ctx* c, const Layout& L, gf::TileParams& p, float* const bu
     return GF_OK;
 }
 
-int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
-                float* traces, float* illum, bool store, cudaStream_t st) {
+// ---------------------------------------------------------------------------------------
+// Lanes: the shots are split into contiguous groups that run their passes concurrently on
+// the context's own streams (forked from and joined back into the caller's stream), so that
+// one group's launches fill the SMs the other's last wave leaves idle and the groups' TMA
+// prologues do not all hit HBM at once.  Every shot's arithmetic is the same in any lane.
+// ---------------------------------------------------------------------------------------
+struct LaneRange {
+    int index, n, s0, s1;
+    cudaStream_t st;
+};
+
+int lanes_in_use(const gf_ctx* c) {
+    if (c->rec || c->variant == gf::kFlowVariant || c->store_mode == GF_STORE_RECONSTRUCT)
+        return 1;
+    return std::max(1, std::min(c->lanes, c->nshots));
+}
+
+// Restrict the tile launches of p to the lane's shots.
+void lane_params(const gf_ctx* c, gf::TileParams& p, const LaneRange& ln) {
+    if (ln.n == 1) return;
+    p.cta_order = c->d_cta_order + c->lane_off[ln.index];
+    p.ncta = c->lane_cnt[ln.index];
+}
+
+// Run body(lane) for every lane; with more than one lane on the context's lane streams,
+// ordered after everything enqueued on `st` so far and before everything enqueued on it next.
+template <class F>
+int run_lanes(gf_ctx* c, cudaStream_t st, F&& body) {
+    const int n = lanes_in_use(c);
+    if (n == 1) return body(LaneRange{0, 1, 0, c->nshots, st});
+    if (!c->lane_fork) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->lane_fork, cudaEventDisableTiming);
+        for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+            e = cudaStreamCreateWithFlags(&c->lane_st[l], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->lane_join[l], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "lane streams");
+    }
+    GF_CUDA(c, cudaEventRecord(c->lane_fork, st), "fork lanes");
+    int rc = GF_OK;
+    for (int l = 0; l < n; ++l) {
+        GF_CUDA(c, cudaStreamWaitEvent(c->lane_st[l], c->lane_fork, 0), "fork lanes");
+        const int s0 = (int)((long long)c->nshots * l / n);
+        const int s1 = (int)((long long)c->nshots * (l + 1) / n);
+        if (rc == GF_OK) rc = body(LaneRange{l, n, s0, s1, c->lane_st[l]});
+        // joined even after a failure, so that the caller's stream orders after the lane
+        cudaEventRecord(c->lane_join[l], c->lane_st[l]);
+        cudaStreamWaitEvent(st, c->lane_join[l], 0);
+    }
+    return rc;
+}
+
+// Slices of the lane's shots in [fields][nshots][Np] arrays: clear / copy them.
+int clear_shots(gf_ctx* c, cudaStream_t st, float* base, int fields, const LaneRange& ln,
+                const char* what) {
+    const size_t F = sizeof(float) * (size_t)c->nshots * c->Np;
+    char* p0 = (char*)(base) + sizeof(float) * (size_t)ln.s0 * c->Np;
+    const size_t w = sizeof(float) * (size_t)(ln.s1 - ln.s0) * c->Np;
+    GF_OP(c, st, -1, what, cudaMemset2DAsync(p0, F, 0, w, (size_t)fields, s_));
+    return GF_OK;
+}
+int copy_shots(gf_ctx* c, cudaStream_t st, void* dst, const void* src, int fields,
+               const LaneRange& ln, const char* what) {
+    const size_t F = sizeof(float) * (size_t)c->nshots * c->Np;
+    const size_t off = sizeof(float) * (size_t)ln.s0 * c->Np;
+    char* d = (char*)dst + off;
+    const char* s = (const char*)src + off;
+    const size_t w = sizeof(float) * (size_t)(ln.s1 - ln.s0) * c->Np;
+    GF_OP(c, st, -1, what,
+          cudaMemcpy2DAsync(d, F, s, F, w, (size_t)fields, cudaMemcpyDeviceToDevice, s_));
+    return GF_OK;
+}
+
+// The forward pass of one call: setup on the caller's stream, the time loop per lane, the
+// illumination sum after the lanes.
+struct Forward {
+    Layout L;
+    gf::TileParams p;
+    bool ckpt = false;
+    size_t state = 0;
+    float* st_buf[2] = {nullptr, nullptr};
+};
+
+int forward_setup(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                  float* traces, float* illum, bool store, cudaStream_t st, Forward& f) {
     if (!eps_r || !sigma || !wavelet) return fail(c, GF_EINVAL, "NULL model or wavelet pointer");
     int rc = ensure_workspace(c, !store);
     if (rc) return rc;
-    const Layout L = layout_of(c, !store);
-    gf::TileParams p = base_params(c, L);
-    p.wavelet = wavelet;
-    p.traces = traces ? traces : (float*)(c->ws + L.traces);
-    const bool ckpt = store && (c->store_mode == GF_STORE_CHECKPOINT ||
-                                c->store_mode == GF_STORE_RECONSTRUCT);
-    p.hist = store && !ckpt ? (float*)(c->ws + L.hist) : nullptr;
-    p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
-    const size_t state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
-    float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
+    f.L = layout_of(c, !store);
+    const Layout& L = f.L;
+    f.p = base_params(c, L);
+    f.p.wavelet = wavelet;
+    f.p.traces = traces ? traces : (float*)(c->ws + L.traces);
+    f.ckpt = store && (c->store_mode == GF_STORE_CHECKPOINT ||
+                       c->store_mode == GF_STORE_RECONSTRUCT);
+    f.p.hist = store && !f.ckpt ? (float*)(c->ws + L.hist) : nullptr;
+    f.p.illum = illum ? (float*)(c->ws + L.illum) : nullptr;
+    f.state = gf::kNumFields * sizeof(float) * (size_t)c->nshots * (size_t)c->Np;
+    f.st_buf[0] = (float*)(c->ws + L.stA);
+    f.st_buf[1] = (float*)(c->ws + L.stB);
     {
-        float* b0 = st_buf[0];
+        float* b0 = f.st_buf[0];
+        const size_t state = f.state;
         GF_OP(c, st, -1, "clear state", cudaMemsetAsync(b0, 0, state, s_));
         if (illum) {
-            float* ill = p.illum;
+            float* ill = f.p.illum;
             GF_OP(c, st, -1, "clear illumination",
                   cudaMemsetAsync(ill, 0, state / gf::kNumFields, s_));
         }
     }
     rc = prepare_model(c, L, eps_r, sigma, st);
     if (rc) return rc;
-    int cur = 0;
-    if (ckpt) {
-        // the state at every k-th step is saved before the segment that starts there
-        for (int j = 0; j < num_checkpoints(c); ++j) {
-            const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
-            char* dst = c->ws + L.ckpt + state * (size_t)j;
-            const float* src = st_buf[cur];
-            GF_OP(c, st, -1, "save checkpoint",
-                  cudaMemcpyAsync(dst, src, state, cudaMemcpyDeviceToDevice, s_));
-            rc = forward_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
-            if (rc) return rc;
-        }
-    } else {
-        rc = forward_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
-        if (rc) return rc;
-    }
-    if (illum) {
-        const float* per = p.illum;
-        int* status = p.status;
-        const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
-        GF_OP(c, st, GF_KERNEL_AUX, "sum illum",
-              gf::launch_sum_shots(per, ns, nx, ny, pitch, illum, status, s_));
-    }
     c->have_forward = store;
     c->last_wavelet = wavelet;
     return GF_OK;
 }
 
-int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* resid,
-                float* g_eps_r, float* g_sigma, cudaStream_t st) {
-    const Layout L = layout_of(c, false);
-    gf::TileParams p = base_params(c, L);
-    p.resid = resid;
-    p.grad = (float*)(c->ws + L.grad);
-    const size_t plane = sizeof(float) * (size_t)c->Np;
-    const size_t field = plane * (size_t)c->nshots;
-    const size_t state = gf::kNumFields * field;
-    float* const st_buf[2] = {(float*)(c->ws + L.stA), (float*)(c->ws + L.stB)};
-    {
-        float* b0 = st_buf[0];
-        float* gr = p.grad;
+int forward_lane(gf_ctx* c, const Forward& f, const LaneRange& ln) {
+    gf::TileParams p = f.p;
+    lane_params(c, p, ln);
+    int cur = 0;
+    if (f.ckpt) {
+        // the state at every k-th step is saved before the segment that starts there
+        for (int j = 0; j < num_checkpoints(c); ++j) {
+            const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
+            char* dst = c->ws + f.L.ckpt + f.state * (size_t)j;
+            int rc = copy_shots(c, ln.st, dst, f.st_buf[cur], gf::kNumFields, ln,
+                                "save checkpoint");
+            if (rc) return rc;
+            rc = forward_steps(c, f.L, p, f.st_buf, cur, n_begin, n_end, ln.st);
+            if (rc) return rc;
+        }
+        return GF_OK;
+    }
+    return forward_steps(c, f.L, p, f.st_buf, cur, 0, c->g.nt, ln.st);
+}
+
+int forward_finish(gf_ctx* c, const Forward& f, float* illum, cudaStream_t st) {
+    if (illum) {
+        const float* per = f.p.illum;
+        int* status = f.p.status;
+        const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+        GF_OP(c, st, GF_KERNEL_AUX, "sum illum",
+              gf::launch_sum_shots(per, ns, nx, ny, pitch, illum, status, s_));
+    }
+    return GF_OK;
+}
+
+int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                float* traces, float* illum, bool store, cudaStream_t st) {
+    Forward f;
+    int rc = forward_setup(c, eps_r, sigma, wavelet, traces, illum, store, st, f);
+    if (rc) return rc;
+    rc = run_lanes(c, st, [&](const LaneRange& ln) { return forward_lane(c, f, ln); });
+    if (rc) return rc;
+    return forward_finish(c, f, illum, st);
+}
+
+// The adjoint pass of one call: setup on the caller's stream (clears, coefficients), the
+// time loop per lane (with its checkpoint restores and segment recomputations), the shot sums
+// after the lanes.
+struct Adjoint {
+    Layout L;
+    gf::TileParams p;
+    size_t plane = 0, field = 0, state = 0;
+    float* st_buf[2] = {nullptr, nullptr};
+};
+
+// clear: clear the adjoint state and the gradients here (else each lane clears its shots).
+int adjoint_setup(gf_ctx* c, const float* eps_r, const float* sigma, const float* resid,
+                  bool clear, bool prepare, cudaStream_t st, Adjoint& a) {
+    a.L = layout_of(c, false);
+    const Layout& L = a.L;
+    a.p = base_params(c, L);
+    a.p.resid = resid;
+    a.p.grad = (float*)(c->ws + L.grad);
+    a.plane = sizeof(float) * (size_t)c->Np;
+    a.field = a.plane * (size_t)c->nshots;
+    a.state = gf::kNumFields * a.field;
+    a.st_buf[0] = (float*)(c->ws + L.stA);
+    a.st_buf[1] = (float*)(c->ws + L.stB);
+    if (clear) {
+        float* b0 = a.st_buf[0];
+        float* gr = a.p.grad;
+        const size_t state = a.state, field = a.field;
         GF_OP(c, st, -1, "clear adjoint state", cudaMemsetAsync(b0, 0, state, s_));
         GF_OP(c, st, -1, "clear gradients", cudaMemsetAsync(gr, 0, 2 * field, s_));
     }
-    int rc0 = prepare_model(c, L, eps_r, sigma, st);
-    if (rc0) return rc0;
+    if (prepare) {
+        const int rc = prepare_model(c, L, eps_r, sigma, st);
+        if (rc) return rc;
+    }
+    return GF_OK;
+}
+
+int adjoint_lane(gf_ctx* c, const Adjoint& a, const LaneRange& ln, bool clear) {
+    const Layout& L = a.L;
+    gf::TileParams p = a.p;
+    lane_params(c, p, ln);
+    const size_t plane = a.plane;
+    const size_t state = a.state;
+    float* const* st_buf = a.st_buf;
+    const cudaStream_t st = ln.st;
+    if (clear) {
+        int rc = clear_shots(c, st, st_buf[0], gf::kNumFields, ln, "clear adjoint state");
+        if (rc) return rc;
+        rc = clear_shots(c, st, p.grad, 2, ln, "clear gradients");
+        if (rc) return rc;
+    }
     int cur = 0;
     if (c->store_mode == GF_STORE_CHECKPOINT) {
         // segments in reverse: restore the checkpoint, recompute the segment's Ez into the
@@ -553,19 +696,20 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         for (int j = num_checkpoints(c) - 1; j >= 0; --j) {
             const int n_begin = j * c->ckpt_k, n_end = std::min(c->g.nt, n_begin + c->ckpt_k);
             const char* ck = c->ws + L.ckpt + state * (size_t)j;
-            float* fb0 = fw_buf[0];
-            GF_OP(c, st, -1, "restore checkpoint",
-                  cudaMemcpyAsync(fb0, ck, state, cudaMemcpyDeviceToDevice, s_));
-            // Ez plane of every shot -> slot 0 of its segment
+            int rc = copy_shots(c, st, fw_buf[0], ck, gf::kNumFields, ln, "restore checkpoint");
+            if (rc) return rc;
+            // Ez plane of every shot of the lane -> slot 0 of its segment
             const size_t seg_pitch = (size_t)(c->ckpt_k + 1) * plane;
-            const size_t nsh = (size_t)c->nshots;
+            const size_t nsh = (size_t)(ln.s1 - ln.s0);
+            float* seg0 = seg + (size_t)ln.s0 * (c->ckpt_k + 1) * (size_t)c->Np;
+            const char* ck0 = ck + plane * (size_t)ln.s0;
             GF_OP(c, st, -1, "segment start",
-                  cudaMemcpy2DAsync(seg, seg_pitch, ck, plane, plane, nsh,
+                  cudaMemcpy2DAsync(seg0, seg_pitch, ck0, plane, plane, nsh,
                                     cudaMemcpyDeviceToDevice, s_));
             q.hist_slot0 = n_begin - 1;
             p.hist_slot0 = n_begin - 1;
             int fcur = 0;
-            int rc = forward_steps(c, L, q, fw_buf, fcur, n_begin, n_end, st);
+            rc = forward_steps(c, L, q, fw_buf, fcur, n_begin, n_end, st);
             if (rc) return rc;
             rc = adjoint_steps(c, L, p, st_buf, cur, n_begin, n_end, st);
             if (rc) return rc;
@@ -643,9 +787,14 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
         int rc = adjoint_steps(c, L, p, st_buf, cur, 0, c->g.nt, st);
         if (rc) return rc;
     }
+    return GF_OK;
+}
+
+int adjoint_finish(gf_ctx* c, const Adjoint& a, float* g_eps_r, float* g_sigma,
+                   cudaStream_t st) {
     {
-        const float* gr = p.grad;
-        int* status = p.status;
+        const float* gr = a.p.grad;
+        int* status = a.p.status;
         const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
         const size_t off = (size_t)c->nshots * c->Np;
         if (g_eps_r)
@@ -656,6 +805,16 @@ int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* 
                   gf::launch_sum_shots(gr + off, ns, nx, ny, pitch, g_sigma, status, s_));
     }
     return GF_OK;
+}
+
+int run_adjoint(gf_ctx* c, const float* eps_r, const float* sigma, const float* resid,
+                float* g_eps_r, float* g_sigma, cudaStream_t st) {
+    Adjoint a;
+    int rc = adjoint_setup(c, eps_r, sigma, resid, true, true, st, a);
+    if (rc) return rc;
+    rc = run_lanes(c, st, [&](const LaneRange& ln) { return adjoint_lane(c, a, ln, false); });
+    if (rc) return rc;
+    return adjoint_finish(c, a, g_eps_r, g_sigma, st);
 }
 
 // Per (shot, tile) descriptors of the tiling (tile_w x tile_h, K steps per block) for the
@@ -719,6 +878,20 @@ int build_tile_tables(gf_ctx* c, int tw, int th, int K) {
             const int kc = !lists[k].empty() ? 0 : strip_tile(t) ? 1 : 2;
             if (kc == cls) order.push_back((int)(k / nt_) << 16 | t);
         }
+    // then each lane's shots [nshots l / n, nshots (l + 1) / n) in the same order
+    const size_t all = order.size();
+    const int nl = std::max(1, std::min(c->lanes, c->nshots));
+    int lane_off[4] = {0}, lane_cnt[4] = {0};
+    for (int l = 0; l < nl; ++l) {
+        const int s0 = (int)((long long)c->nshots * l / nl);
+        const int s1 = (int)((long long)c->nshots * (l + 1) / nl);
+        lane_off[l] = (int)order.size();
+        for (size_t k = 0; k < all; ++k) {
+            const int shot = order[k] >> 16;
+            if (shot >= s0 && shot < s1) order.push_back(order[k]);
+        }
+        lane_cnt[l] = (int)order.size() - lane_off[l];
+    }
     int4* d_desc = nullptr;
     int2* d_ents = nullptr;
     int* d_order = nullptr;
@@ -745,6 +918,10 @@ int build_tile_tables(gf_ctx* c, int tw, int th, int K) {
     c->d_tile_rec = d_ents;
     c->d_cta_order = d_order;
     c->tile_rec_max = longest;
+    for (int l = 0; l < 4; ++l) {
+        c->lane_off[l] = lane_off[l];
+        c->lane_cnt[l] = lane_cnt[l];
+    }
     return GF_OK;
 }
 
@@ -908,7 +1085,27 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
     cudaFree(c->d_cta_order);
+    for (int l = 0; l < 4; ++l) {
+        if (c->lane_st[l]) cudaStreamDestroy(c->lane_st[l]);
+        if (c->lane_join[l]) cudaEventDestroy(c->lane_join[l]);
+    }
+    if (c->lane_fork) cudaEventDestroy(c->lane_fork);
     delete c;
+}
+
+int gf_set_lanes(gf_ctx* c, int lanes) {
+    if (!c) return GF_EINVAL;
+    if (lanes < 1 || lanes > 4) return fail(c, GF_EINVAL, "lanes must be 1 to 4, not %d", lanes);
+    DeviceGuard guard(c->device);
+    const int old = c->lanes;
+    c->lanes = lanes;
+    const int rc = build_tile_tables(c, c->tile_w, c->tile_h, c->K);
+    if (rc) {
+        c->lanes = old;
+        return rc;
+    }
+    ++c->generation;
+    return GF_OK;
 }
 
 int gf_workspace_size(const gf_ctx* c, int store_mode, int forward_only, size_t* bytes) {
@@ -1067,20 +1264,44 @@ int gf_misfit_and_gradient(gf_ctx* c, const float* eps_r, const float* sigma,
     if (!observed || !misfit) return fail(c, GF_EINVAL, "NULL observed or misfit pointer");
     DeviceGuard guard(c->device);
     cudaStream_t st = (cudaStream_t)stream;
-    int rc = run_forward(c, eps_r, sigma, wavelet, traces, nullptr, true, st);
+    Forward f;
+    int rc = forward_setup(c, eps_r, sigma, wavelet, traces, nullptr, true, st, f);
     if (rc) return rc;
-    const Layout L = layout_of(c, false);
-    float* tr = traces ? traces : (float*)(c->ws + L.traces);
+    Adjoint a;
+    const Layout& L = f.L;
     float* resid = (float*)(c->ws + L.resid);
-    const long long count = (long long)c->nshots * c->g.nt * c->nrec;
+    rc = adjoint_setup(c, eps_r, sigma, resid, false, false, st, a);
+    if (rc) return rc;
+    const float* tr = f.p.traces;
     double* partial = (double*)(c->ws + L.partial);
     int* status = (int*)(c->ws + L.status);
-    GF_OP(c, st, GF_KERNEL_AUX, "residual_misfit",
-          gf::launch_residual_misfit(tr, observed, resid, count, partial, kMisfitBlocks, status,
-                                     s_));
+    const long long per_shot = (long long)c->g.nt * c->nrec;
+    const int nl = lanes_in_use(c);
+    // per lane: forward, residual of its traces, adjoint.  With one lane the residual kernel
+    // also sums the misfit; with several, the misfit is summed after the lanes by the same
+    // kernel over all traces, so that J does not depend on the lanes.
+    rc = run_lanes(c, st, [&](const LaneRange& ln) {
+        int r = forward_lane(c, f, ln);
+        if (r) return r;
+        const long long o = per_shot * ln.s0, cnt = per_shot * (ln.s1 - ln.s0);
+        double* part = partial + (size_t)kMisfitBlocks * (nl == 1 ? 0 : 1 + ln.index);
+        const float* trl = tr + o;
+        const float* obl = observed + o;
+        float* rsl = resid + o;
+        GF_OP(c, ln.st, GF_KERNEL_AUX, "residual_misfit",
+              gf::launch_residual_misfit(trl, obl, rsl, cnt, part, kMisfitBlocks, status, s_));
+        return adjoint_lane(c, a, ln, true);
+    });
+    if (rc) return rc;
+    if (nl > 1) {
+        const long long count = per_shot * c->nshots;
+        GF_OP(c, st, GF_KERNEL_AUX, "misfit",
+              gf::launch_residual_misfit(tr, observed, nullptr, count, partial, kMisfitBlocks,
+                                         status, s_));
+    }
     GF_OP(c, st, GF_KERNEL_AUX, "finish_misfit",
           gf::launch_finish_misfit(partial, kMisfitBlocks, misfit, s_));
-    return run_adjoint(c, eps_r, sigma, resid, g_eps_r, g_sigma, st);
+    return adjoint_finish(c, a, g_eps_r, g_sigma, st);
 }
 
 int gf_misfit(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
@@ -1194,6 +1415,46 @@ int gf_profile_read(gf_ctx* c, int kind, double* ms_total, long long* launches) 
         c->ev_pool.push_back(pr.second);
     }
     *ms_total = total;
+    *launches = (long long)v.size();
+    v.clear();
+    return GF_OK;
+}
+
+int gf_profile_read_span(gf_ctx* c, int kind, double* ms_total, double* ms_span,
+                         long long* launches) {
+    if (!c || kind < 0 || kind > 2 || !ms_total || !ms_span || !launches) return GF_EINVAL;
+    DeviceGuard guard(c->device);
+    auto& v = c->prof_ev[kind];
+    std::vector<std::pair<double, double>> iv;
+    double total = 0.0;
+    for (auto& pr : v) {
+        GF_CUDA(c, cudaEventSynchronize(pr.second), "event synchronize");
+        float a = 0.f, b = 0.f;
+        GF_CUDA(c, cudaEventElapsedTime(&a, v[0].first, pr.first), "event elapsed");
+        GF_CUDA(c, cudaEventElapsedTime(&b, v[0].first, pr.second), "event elapsed");
+        iv.emplace_back(a, b);
+        total += b - a;
+    }
+    // the union of the launches' intervals: launches of concurrent lanes, and consecutive
+    // launches under programmatic dependent launch, overlap
+    std::sort(iv.begin(), iv.end());
+    double span = 0.0, lo = 0.0, hi = -1.0;
+    for (const auto& x : iv) {
+        if (x.first > hi) {
+            if (hi > lo) span += hi - lo;
+            lo = x.first;
+            hi = x.second;
+        } else {
+            hi = std::max(hi, x.second);
+        }
+    }
+    if (hi > lo) span += hi - lo;
+    for (auto& pr : v) {
+        c->ev_pool.push_back(pr.first);
+        c->ev_pool.push_back(pr.second);
+    }
+    *ms_total = total;
+    *ms_span = span;
     *launches = (long long)v.size();
     v.clear();
     return GF_OK;

@@ -77,7 +77,8 @@ struct TileParams {
     // Launch order of the (shot, tile) pairs, shot << 16 | tile: tiles with receivers first,
     // then tiles touching a CPML strip, then the rest (the slow ones start early, the last wave
     // is short)
-    const int* cta_order;   // [nshots * ntiles]
+    const int* cta_order;   // [nshots * ntiles], or one lane's part of it
+    int ncta;               // CTAs of a per-launch tile kernel: entries of cta_order (0: all)
     int rec_max;            // longest list (decides shared-memory staging)
     int* status;
 };

@@ -161,7 +161,7 @@ template <int R, int NW, bool kHist, bool kIllum>
 cudaError_t launch_fwd_variant(const TileParams& p, const TileMaps& m, bool staged,
                                cudaStream_t st) {
     using Gm = G<R, NW>;
-    const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
+    const dim3 grid(p.ncta > 0 ? p.ncta : p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = sizeof(float) * Gm::fwd_floats;
     if (staged) return launch_pdl(fwd_tile_kernel<R, NW, kHist, kIllum, true>, grid, block, smem, st, p, m);
     return launch_pdl(fwd_tile_kernel<R, NW, kHist, kIllum, false>, grid, block, smem, st, p, m);
@@ -183,7 +183,7 @@ size_t adj_smem(int tile_w, int tile_h) {
 template <int R, int NW>
 cudaError_t launch_adj_r(const TileParams& p, const TileMaps& m, bool staged, cudaStream_t st) {
     using Gm = G<R, NW>;
-    const dim3 grid(p.ntiles * p.nshots), block(Gm::NT);
+    const dim3 grid(p.ncta > 0 ? p.ncta : p.ntiles * p.nshots), block(Gm::NT);
     const size_t smem = adj_smem<R, NW>(p.tile_w, p.tile_h);
     if (staged) return launch_pdl(adj_tile_kernel<R, NW, true>, grid, block, smem, st, p, m);
     return launch_pdl(adj_tile_kernel<R, NW, false>, grid, block, smem, st, p, m);

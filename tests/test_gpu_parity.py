@@ -494,3 +494,34 @@ def test_dependency_wait_timeout_is_reported_and_recovered(dev):
     for a, b in zip(got[1:], ref[1:]):
         assert torch.equal(a, b)
     fd.close()
+
+
+@pytest.mark.parametrize("k", [0, 40])
+def test_shot_lanes_give_identical_results(dev, k):
+    """Shots split into 1, 2, 3 or 4 lanes running concurrently (full store and checkpoints
+    every k steps): bit-identical misfit and gradients, since every shot's arithmetic and
+    every sum's order are the same; and the oracle's gradient within tolerance."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(77, nxp=120, nyp=70, npml=8, nt=260, nshots=5, nrec=11, with_pec=True)
+    g = wl.grid
+    wav = wavelets(wl)
+    obs = O.forward(g, wl.eps_true, wl.sig_true, wl.src, wav, wl.rec)
+    out = []
+    for lanes in (1, 2, 3, 4):
+        fd = FDTD(g, wl.src, wl.rec, device=dev)
+        assert fd.lib.gf_set_lanes(fd.ctx, lanes) == 0
+        if k:
+            fd.set_storage(k)
+        J, ge, gs = fd.misfit_and_gradient(t32(wl.eps_init, dev), t32(wl.sig_init, dev),
+                                           t32(wav, dev), t32(obs, dev))
+        tr = fd.forward_model(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev))
+        Jm = fd.misfit(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev), t32(obs, dev))
+        fd.status()
+        out.append((J.item(), ge.cpu(), gs.cpu(), tr.cpu(), Jm.item()))
+        fd.close()
+    for J, ge, gs, tr, Jm in out[1:]:
+        assert J == out[0][0] and Jm == out[0][4]
+        assert torch.equal(ge, out[0][1]) and torch.equal(gs, out[0][2])
+        assert torch.equal(tr, out[0][3])
+    J64, ge64, gs64 = O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl.src, wav, wl.rec, obs)
+    assert rel(out[0][1].numpy(), ge64) <= GRAD_TOL and rel(out[0][2].numpy(), gs64) <= GRAD_TOL
