@@ -70,6 +70,8 @@ def parse_args():
                          "16 shots, nt 8000 with checkpointing")
     ap.add_argument("--checkpoint", type=int, default=0,
                     help="checkpoint every k steps instead of storing the whole wavefield")
+    ap.add_argument("--lanes", type=int, default=2,
+                    help="shot lanes: groups of shots whose passes run concurrently")
     ap.add_argument("--reconstruct", action="store_true",
                     help="with --checkpoint: reconstruct each segment backwards from a stored "
                          "boundary ring instead of keeping its Ez (experimental)")
@@ -274,8 +276,10 @@ def kernel_source_tag():
     return hashlib.sha1("\n\f".join(code).encode()).hexdigest()[:12]
 
 
-def algorithmic_bytes_per_launch(kind: str, wl, K: float, history: float = 1.0) -> float:
-    """Compulsory HBM bytes of one tile-kernel launch of K steps over all cells and shots:
+def algorithmic_bytes_per_launch(kind: str, wl, K: float, history: float = 1.0,
+                                 shots: float | None = None) -> float:
+    """Compulsory HBM bytes of one tile-kernel launch of K steps over all cells and the
+    workload's shots (or ``shots`` of them: one lane's launch):
     fields Ez, Hx, Hy read and written once (24 B), the model read once per cell (Ca, Cb:
     8 B, shared by the shots), CPML memories read and written in the strips (2 arrays x 8 B),
     plus per step: forward, the Ez history write (4 B; ``history`` = the fraction of forward
@@ -283,7 +287,7 @@ def algorithmic_bytes_per_launch(kind: str, wl, K: float, history: float = 1.0) 
     first pass keeps only the checkpoints); adjoint, the history read (4 B, K + 1 slots) and
     the per-shot gradient pair read and written once (16 B)."""
     g = wl.grid
-    N, S = g.ncells, wl.nshots
+    N, S = g.ncells, (wl.nshots if shots is None else shots)
     w = 2 * g.npml + 1
     strip_cells = w * g.ny + w * g.nx
     base = S * N * 24 + 8 * N + S * strip_cells * 16
@@ -308,29 +312,41 @@ def read_profile(lib, ctx) -> dict:
     return prof
 
 
+def blocks_per_pass(nt: int, K: int, checkpoint: int) -> int:
+    """Launches of one pass of one lane: K-step blocks, the last of each segment shorter."""
+    if checkpoint <= 0:
+        return -(-nt // K)
+    return sum(-(-min(checkpoint, nt - j) // K) for j in range(0, nt, checkpoint))
+
+
 def tile_roofline(prof: dict, wl, steps: int, history_fwd: float, tiling: str, clk: dict,
-                  sms: int) -> dict:
+                  sms: int, K: int = 7, checkpoint: int = 0) -> dict:
     """Roofline of the dominant tile kernel from its own launches' CUDA-event intervals: the
     algorithmic bytes of all its launches over the time they kept the GPU busy (the union
     of their intervals), i.e. bytes per launch over the effective launch duration."""
     g = wl.grid
     dom = max(("fwd", "adj"), key=lambda k: prof[k][0])
     tot_ms, cnt, sum_ms = prof[dom]
-    # launches of K steps except a possibly shorter last one: use the mean steps per launch;
-    # under checkpointing the forward runs twice per gradient (checkpoints, then recompute)
+    # launches of K steps except the shorter last one of a segment: use the mean steps per
+    # launch; under checkpointing the forward runs twice per gradient (checkpoints, then
+    # recompute); the shots may be split into concurrent lanes, each launch one lane's shots
     passes = 2 if (dom == "fwd" and history_fwd < 1.0) else 1
-    per_launch_steps = passes * g.nt / max(1, cnt / steps)
-    algo = algorithmic_bytes_per_launch(dom, wl, per_launch_steps, history_fwd)
+    blocks = blocks_per_pass(g.nt, K, checkpoint)
+    lanes = max(1, round(cnt / max(1, steps * passes * blocks)))
+    per_launch_steps = g.nt / blocks
+    shots = wl.nshots / lanes
+    algo = algorithmic_bytes_per_launch(dom, wl, per_launch_steps, history_fwd, shots)
     avg_s = tot_ms / 1e3 / max(1, cnt)
     peak, peak_kind = hbm_peak()
     achieved = algo / avg_s / 1e9
     key = f"{dom}@{kernel_source_tag()}@{g.nx}x{g.ny}x{wl.nshots}@{tiling}"
-    cell_steps = wl.nshots * g.ncells * per_launch_steps
+    cell_steps = shots * g.ncells * per_launch_steps
     tpc = NCU_TRAFFIC_PER_CELL_STEP.get(key)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": tpc * cell_steps if tpc else None,
             "kernel": f"{dom}_tile_kernel", "peak_source": f"hbm_gbs of {peak_kind}",
             "algorithmic_bytes_per_launch": algo, "steps_per_launch": per_launch_steps,
+            "shot_lanes": lanes, "shots_per_launch": shots,
             "avg_launch_us": avg_s * 1e6, "launches": cnt,
             "avg_launch_event_us": sum_ms / 1e3 / max(1, cnt) * 1e6,
             "phase_ms_per_step": {k: v[0] / steps for k, v in prof.items()}}
@@ -346,6 +362,46 @@ def tile_roofline(prof: dict, wl, steps: int, history_fwd: float, tiling: str, c
                          "warp_instructions_per_launch": inst,
                          "peak_source": "SMs x 4 schedulers x sampled SM clock"}
     return roof
+
+
+def read_tile_span(lib, ctx) -> float:
+    """Milliseconds during which forward or adjoint tile launches kept the GPU busy (the
+    union of their intervals; the records stay for read_profile)."""
+    import ctypes
+    tot, span, cnt = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+    lib.gf_profile_read_span(ctx, 3, ctypes.byref(tot), ctypes.byref(span), ctypes.byref(cnt))
+    return span.value
+
+
+def lanes_used(fd, args) -> int:
+    """Shot lanes of the run (the library runs one with the persistent variant or the
+    reconstruction storage)."""
+    t = fd.tiling()
+    if t.variant == 3 or args.reconstruct:
+        return 1
+    return max(1, min(args.lanes, fd.nshots))
+
+
+def path_roofline(span_ms: float, wl, steps: int, K: int, checkpoint: int) -> dict:
+    """The forward and adjoint tile kernels together: the algorithmic bytes of all their
+    launches over the time they kept the GPU busy (their launches overlap when the shots run
+    in concurrent lanes)."""
+    g = wl.grid
+    blocks = blocks_per_pass(g.nt, K, checkpoint)
+    k_avg = g.nt / blocks
+    fwd = blocks * (algorithmic_bytes_per_launch("fwd", wl, k_avg, 1.0)
+                    + (algorithmic_bytes_per_launch("fwd", wl, k_avg, 0.0) if checkpoint else 0))
+    adj = blocks * algorithmic_bytes_per_launch("adj", wl, k_avg)
+    total = steps * (fwd + adj)
+    peak, peak_kind = hbm_peak()
+    achieved = total / (span_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "fwd_tile_kernel + adj_tile_kernel (concurrent shot lanes)",
+            "peak_source": f"hbm_gbs of {peak_kind}",
+            "algorithmic_bytes_per_step": total / steps, "busy_ms_per_step": span_ms / steps,
+            "meaning": "algorithmic bytes of every tile launch of the step over the time the "
+                       "tile launches kept the GPU busy (union of their CUDA-event intervals)"}
 
 
 def fwi_leg(args, fd, wl, eps_t, sig_t, eps0, sig0) -> dict:
@@ -434,6 +490,7 @@ def large_leg(args, dev, sms: int) -> dict:
     fd.lib.gf_profile(fd.ctx, 1)
     fd.misfit_and_gradient(e0, s0, wav, obs)
     torch.cuda.synchronize(dev)
+    span_all = read_tile_span(fd.lib, fd.ctx)
     prof = read_profile(fd.lib, fd.ctx)
     fd.lib.gf_profile(fd.ctx, 0)
     clk = clocks.stop()
@@ -445,7 +502,8 @@ def large_leg(args, dev, sms: int) -> dict:
            "workspace_gb": fd.workspace_bytes() / 1e9,
            "tiling": f"{t.tile_w}x{t.tile_h}, K {t.steps}, variant {t.variant}",
            "steps": reps, "warmup": 1, "clocks": clk,
-           "roofline": tile_roofline(prof, wl, 1, 0.5, f"default/k{k}", clk, sms)}
+           "roofline": dict(path_roofline(span_all, wl, 1, t.steps, k),
+                            phase_ms_per_step={kk: v[0] for kk, v in prof.items()})}
     fd.close()
     return rec
 
@@ -474,6 +532,7 @@ def ours(args):
     g = wl.grid
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
     fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=tiling)
+    fd.lib.gf_set_lanes(fd.ctx, args.lanes)
     if args.checkpoint > 0:
         fd.set_storage(args.checkpoint, reconstruct=args.reconstruct)
     t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
@@ -519,8 +578,20 @@ def ours(args):
     for _ in range(args.steps):
         step()
     barrier()
+    span_all = read_tile_span(lib, ctx)
     prof = read_profile(lib, ctx)
     lib.gf_profile(ctx, 0)
+    # the same again with the shots in one lane: the dominant kernel alone on the GPU
+    prof1 = None
+    if lanes_used(fd, args) > 1:
+        lib.gf_set_lanes(ctx, 1)
+        lib.gf_profile(ctx, 1)
+        for _ in range(args.steps):
+            step()
+        barrier()
+        prof1 = read_profile(lib, ctx)
+        lib.gf_profile(ctx, 0)
+        lib.gf_set_lanes(ctx, args.lanes)
     clk = clocks.stop()
     fd.status()
     ms = reduce_max(ms, dev)
@@ -528,8 +599,18 @@ def ours(args):
     value = job_value(wl.cell_updates() * args.steps, world, ms)
     t = fd.tiling()
     tiling_key = args.tile or "default"
-    roof = tile_roofline(prof, wl, args.steps, 0.5 if args.checkpoint else 1.0, tiling_key,
-                         clk, sms)
+    hist = 0.5 if args.checkpoint else 1.0
+    kernel_roof = tile_roofline(prof1 or prof, wl, args.steps, hist, tiling_key, clk, sms,
+                                t.steps, args.checkpoint)
+    if prof1 is None:
+        roof = kernel_roof
+    else:
+        # the lanes run the forward and adjoint kernels concurrently: the roofline of the two
+        # together over the time they kept the GPU busy, and the dominant kernel alone (one
+        # lane) beside it
+        roof = path_roofline(span_all, wl, args.steps, t.steps, args.checkpoint)
+        roof["phase_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
+        roof["dominant_kernel_one_lane"] = kernel_roof
     peak = roof["peak"]
     if not args.checkpoint:
         # the whole step against the bytes an untiled stencil moves per cell-update (forward:

@@ -33,6 +33,16 @@
  *            traces, exhausted bounded waits) are recorded in a device status word that
  *            gf_status() reads.  No call throws, traps or aborts.
  * Threads.   A context is not thread-safe; distinct contexts are independent.
+ * Readings.  The calls follow the statement of the problem (forward_model(eps_r, sigma,
+ *            sources, receivers) -> traces; misfit_and_gradient(eps_r, sigma, observed) ->
+ *            J, g_eps_r, g_sigma) with these deliberate choices: the acquisition (sources,
+ *            receivers) is fixed per context, as the paper's configuration fixes it per
+ *            run; the wavefield storage (full, checkpoints every k steps, or checkpoints
+ *            with reverse reconstruction) is a property of the context, set once with
+ *            gf_set_storage, because it decides the workspace size, instead of an argument
+ *            of every call; the misfit is written to device memory (a call enqueues and
+ *            returns, and the next FWI step reads it there); host arrays are copied by the
+ *            caller (the library's compute calls take device pointers only).
  */
 #ifndef GPRFWI_H
 #define GPRFWI_H
@@ -259,7 +269,8 @@ int gf_profile_read(gf_ctx* ctx, int kind, double* ms_total, long long* launches
 
 /* As gf_profile_read, and also the length in milliseconds of the union of the launches'
  * intervals (launches of concurrent lanes, and consecutive launches under programmatic
- * dependent launch, overlap: the union is the time the family kept the GPU busy). */
+ * dependent launch, overlap: the union is the time the family kept the GPU busy).  kind 3:
+ * the forward and adjoint families together, read without clearing them. */
 int gf_profile_read_span(gf_ctx* ctx, int kind, double* ms_total, double* ms_span,
                          long long* launches);
 

@@ -1422,23 +1422,27 @@ int gf_profile_read(gf_ctx* c, int kind, double* ms_total, long long* launches) 
 
 int gf_profile_read_span(gf_ctx* c, int kind, double* ms_total, double* ms_span,
                          long long* launches) {
-    if (!c || kind < 0 || kind > 2 || !ms_total || !ms_span || !launches) return GF_EINVAL;
+    if (!c || kind < 0 || kind > 3 || !ms_total || !ms_span || !launches) return GF_EINVAL;
     DeviceGuard guard(c->device);
-    auto& v = c->prof_ev[kind];
+    // kind 3: the forward and adjoint tile launches together, without clearing them
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>*> recs;
+    for (int k = 0; k < 3; ++k)
+        if (k == kind || (kind == 3 && k < 2))
+            for (auto& pr : c->prof_ev[k]) recs.push_back(&pr);
     std::vector<std::pair<double, double>> iv;
     double total = 0.0;
-    for (auto& pr : v) {
-        GF_CUDA(c, cudaEventSynchronize(pr.second), "event synchronize");
+    for (auto* pr : recs) {
+        GF_CUDA(c, cudaEventSynchronize(pr->second), "event synchronize");
         float a = 0.f, b = 0.f;
-        GF_CUDA(c, cudaEventElapsedTime(&a, v[0].first, pr.first), "event elapsed");
-        GF_CUDA(c, cudaEventElapsedTime(&b, v[0].first, pr.second), "event elapsed");
+        GF_CUDA(c, cudaEventElapsedTime(&a, recs[0]->first, pr->first), "event elapsed");
+        GF_CUDA(c, cudaEventElapsedTime(&b, recs[0]->first, pr->second), "event elapsed");
         iv.emplace_back(a, b);
         total += b - a;
     }
     // the union of the launches' intervals: launches of concurrent lanes, and consecutive
     // launches under programmatic dependent launch, overlap
     std::sort(iv.begin(), iv.end());
-    double span = 0.0, lo = 0.0, hi = -1.0;
+    double span = 0.0, lo = 0.0, hi = -1e300;
     for (const auto& x : iv) {
         if (x.first > hi) {
             if (hi > lo) span += hi - lo;
@@ -1449,14 +1453,17 @@ int gf_profile_read_span(gf_ctx* c, int kind, double* ms_total, double* ms_span,
         }
     }
     if (hi > lo) span += hi - lo;
-    for (auto& pr : v) {
-        c->ev_pool.push_back(pr.first);
-        c->ev_pool.push_back(pr.second);
-    }
     *ms_total = total;
     *ms_span = span;
-    *launches = (long long)v.size();
-    v.clear();
+    *launches = (long long)recs.size();
+    if (kind < 3) {
+        auto& v = c->prof_ev[kind];
+        for (auto& pr : v) {
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        v.clear();
+    }
     return GF_OK;
 }
 

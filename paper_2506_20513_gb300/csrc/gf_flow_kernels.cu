@@ -18,6 +18,13 @@
 // through L2: the data were written by other CTAs of this launch) and, once the current item
 // no longer reads them, the next item's update coefficients, so that an item starts without
 // a round trip to memory.  The time steps themselves are those of gf_tile_common.cuh.
+//
+// One launch may also run the passes of several instances (contexts with their own grids,
+// shots, tilings and buffers): launch item k is then items[k] = {instance, item of that
+// instance}, block-major across the instances, so an item still waits only for earlier items
+// of its own instance; the instances' parameters come from a device array, copied into two
+// shared-memory slots (current and next item).  One instance reads them from the launch
+// parameter instead.
 #include "gf_tile_common.cuh"
 
 namespace gf {
