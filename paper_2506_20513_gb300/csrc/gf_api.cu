@@ -94,6 +94,7 @@ struct gf_ctx {
     size_t smem_optin = 0;
     long long launches = 0;
     OpList* rec = nullptr;  // set while a batch records this context's operations
+    bool one_lane = false;  // set while a batch runs this context beside others
     bool profiling = false;
     // per kernel family: recorded (start, stop) event pairs not yet read
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev[3];
@@ -482,7 +483,8 @@ struct LaneRange {
 };
 
 int lanes_in_use(const gf_ctx* c) {
-    if (c->rec || c->variant == gf::kFlowVariant || c->store_mode == GF_STORE_RECONSTRUCT)
+    if (c->rec || c->one_lane || c->variant == gf::kFlowVariant ||
+        c->store_mode == GF_STORE_RECONSTRUCT)
         return 1;
     return std::max(1, std::min(c->lanes, c->nshots));
 }
@@ -1841,8 +1843,11 @@ int gf_batch_misfit_and_gradient(gf_batch* b, const float* const* eps_r, const f
         for (int i = 0; i < n; ++i) {
             cudaStream_t si = concurrent ? b->streams[i] : st;
             if (concurrent && cudaStreamWaitEvent(si, b->fork, 0) != cudaSuccess) return GF_ECUDA;
+            // instances that run beside each other need no shot lanes of their own
+            b->ctx[i]->one_lane = concurrent;
             int rc = gf_misfit_and_gradient(b->ctx[i], eps_r[i], sigma[i], wavelet[i], observed[i],
                                             misfit + i, g_eps_r[i], g_sigma[i], nullptr, si);
+            b->ctx[i]->one_lane = false;
             if (rc) return fail_b(rc, "instance", b->ctx[i]);
             if (concurrent) {
                 if (cudaEventRecord(b->join[i], si) != cudaSuccess) return GF_ECUDA;
