@@ -35,20 +35,20 @@ METRIC = "Gcell-updates/s (fwd+adjoint) and s per dual-param FWI iteration vs HB
 UNIT = "Gcell-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 
-# Per-launch figures from one ncu capture of the tile kernels (`ncu --clock-control none -k
-# regex:<kernel> --metrics dram__bytes_read.sum,dram__bytes_write.sum,smsp__inst_executed.sum`
-# on the multishot workload with nt = 70, default tiling), divided by the launch's cell-steps.
+# Per-launch figures from one ncu capture of the tile kernels (`ncu --set full --clock-control
+# none -k regex:<kernel>` on the multishot workload with nt = 70, default tiling, one shot lane:
+# launches of all 32 shots), divided by the launch's cell-steps.
 # Keyed on kernel_source_tag(): any change of the kernel code drops them (reported as null).
 # DRAM bytes (read + write) per cell-step:
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    "adj@bb39aa0cbe98@540x290x32@default": 12.1438,   # 426.02 MB / 35.0784 M cell-steps
-    "fwd@bb39aa0cbe98@540x290x32@default": 8.0171,    # 281.24 MB
+    "adj@a900bcde84e7@540x290x32@default": 12.1322,   # 425.58 MB / 35.0784 M cell-steps
+    "fwd@a900bcde84e7@540x290x32@default": 8.0138,    # 281.11 MB
 }
 # Warp instructions per cell-step (the kernels are bound by instruction issue, so the line
 # also reports the issue roofline):
 NCU_WARP_INST_PER_CELL_STEP: dict = {
-    "adj@bb39aa0cbe98@540x290x32@default": 2.9729,    # 104.283 M warp instructions
-    "fwd@bb39aa0cbe98@540x290x32@default": 2.0810,    # 72.997 M
+    "adj@a900bcde84e7@540x290x32@default": 2.9761,    # 104.396 M warp instructions
+    "fwd@a900bcde84e7@540x290x32@default": 2.0820,    # 73.032 M
 }
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 # the files holding the tile kernels' device code
