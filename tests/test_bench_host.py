@@ -60,3 +60,36 @@ def test_cpu_sample_is_bounded_by_shots_and_cores():
     assert 1 <= n <= min(32, bench.host_cores())
     assert bench.cpu_sample_shots(0, 2) <= 2
     assert bench.cpu_sample_shots(5, 3) == 3
+
+
+def test_blocks_per_pass_counts_segment_ends():
+    assert bench.blocks_per_pass(2000, 7, 0) == 286
+    assert bench.blocks_per_pass(2000, 7, 100) == 20 * 15      # 100 = 14 x 7 + 2
+    assert bench.blocks_per_pass(250, 7, 100) == 15 + 15 + 8   # segments 100, 100, 50
+    assert bench.blocks_per_pass(8000, 7, 200) == 40 * 29
+
+
+def test_kernel_roofline_counts_lane_launches():
+    """Two lanes double the launches of a pass and halve the shots of each: the bytes per
+    launch halve and the steps per launch stay K, so the same busy time per pass gives the
+    same achieved bandwidth as one lane."""
+    wl = bench.workload(0, nshots=32, nt=2000)
+    clk = {"sm_mhz": 2070.0}
+    one = {"fwd": (40.0, 286, 40.0), "adj": (50.0, 286, 50.0), "aux": (0.1, 5, 0.1)}
+    two = {"fwd": (40.0, 572, 40.0), "adj": (50.0, 572, 50.0), "aux": (0.1, 6, 0.1)}
+    r1 = bench.tile_roofline(one, wl, 1, 1.0, "x", clk, 152, 7, 0)
+    r2 = bench.tile_roofline(two, wl, 1, 1.0, "x", clk, 152, 7, 0)
+    assert r1["shot_lanes"] == 1 and r2["shot_lanes"] == 2
+    assert r2["algorithmic_bytes_per_launch"] == pytest.approx(
+        r1["algorithmic_bytes_per_launch"] / 2, rel=0.01)
+    assert r2["achieved"] == pytest.approx(r1["achieved"], rel=0.01)
+    assert r1["kernel"] == "adj_tile_kernel"
+
+
+def test_path_roofline_adds_both_kernels():
+    wl = bench.workload(0, nshots=32, nt=2000)
+    r = bench.path_roofline(100.0, wl, 1, 7, 0)
+    cells = wl.nshots * wl.grid.ncells * 2000
+    # about 8.0 (forward) + 10.8 (adjoint) algorithmic bytes per cell-step
+    assert 18.0 < r["algorithmic_bytes_per_step"] / cells < 19.6
+    assert r["achieved"] == pytest.approx(r["algorithmic_bytes_per_step"] / 0.1 / 1e9)
