@@ -524,24 +524,39 @@ int run_lanes(gf_ctx* c, cudaStream_t st, F&& body) {
     return rc;
 }
 
-// Slices of the lane's shots in [fields][nshots][Np] arrays: clear / copy them.
+// Slices of the lane's shots in [fields][nshots][Np] arrays: clear / copy them (one
+// contiguous operation for all shots, else one per field).
 int clear_shots(gf_ctx* c, cudaStream_t st, float* base, int fields, const LaneRange& ln,
                 const char* what) {
     const size_t F = sizeof(float) * (size_t)c->nshots * c->Np;
-    char* p0 = (char*)(base) + sizeof(float) * (size_t)ln.s0 * c->Np;
+    const size_t off = sizeof(float) * (size_t)ln.s0 * c->Np;
     const size_t w = sizeof(float) * (size_t)(ln.s1 - ln.s0) * c->Np;
-    GF_OP(c, st, -1, what, cudaMemset2DAsync(p0, F, 0, w, (size_t)fields, s_));
+    if (w == F) {
+        const size_t n = F * (size_t)fields;
+        GF_OP(c, st, -1, what, cudaMemsetAsync(base, 0, n, s_));
+        return GF_OK;
+    }
+    for (int f = 0; f < fields; ++f) {
+        char* p0 = (char*)base + F * (size_t)f + off;
+        GF_OP(c, st, -1, what, cudaMemsetAsync(p0, 0, w, s_));
+    }
     return GF_OK;
 }
 int copy_shots(gf_ctx* c, cudaStream_t st, void* dst, const void* src, int fields,
                const LaneRange& ln, const char* what) {
     const size_t F = sizeof(float) * (size_t)c->nshots * c->Np;
     const size_t off = sizeof(float) * (size_t)ln.s0 * c->Np;
-    char* d = (char*)dst + off;
-    const char* s = (const char*)src + off;
     const size_t w = sizeof(float) * (size_t)(ln.s1 - ln.s0) * c->Np;
-    GF_OP(c, st, -1, what,
-          cudaMemcpy2DAsync(d, F, s, F, w, (size_t)fields, cudaMemcpyDeviceToDevice, s_));
+    if (w == F) {
+        const size_t n = F * (size_t)fields;
+        GF_OP(c, st, -1, what, cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToDevice, s_));
+        return GF_OK;
+    }
+    for (int f = 0; f < fields; ++f) {
+        char* d = (char*)dst + F * (size_t)f + off;
+        const char* s = (const char*)src + F * (size_t)f + off;
+        GF_OP(c, st, -1, what, cudaMemcpyAsync(d, s, w, cudaMemcpyDeviceToDevice, s_));
+    }
     return GF_OK;
 }
 
@@ -705,9 +720,18 @@ int adjoint_lane(gf_ctx* c, const Adjoint& a, const LaneRange& ln, bool clear) {
             const size_t nsh = (size_t)(ln.s1 - ln.s0);
             float* seg0 = seg + (size_t)ln.s0 * (c->ckpt_k + 1) * (size_t)c->Np;
             const char* ck0 = ck + plane * (size_t)ln.s0;
-            GF_OP(c, st, -1, "segment start",
-                  cudaMemcpy2DAsync(seg0, seg_pitch, ck0, plane, plane, nsh,
-                                    cudaMemcpyDeviceToDevice, s_));
+            if (seg_pitch < ((size_t)1 << 30)) {
+                GF_OP(c, st, -1, "segment start",
+                      cudaMemcpy2DAsync(seg0, seg_pitch, ck0, plane, plane, nsh,
+                                        cudaMemcpyDeviceToDevice, s_));
+            } else {  // a pitch beyond what 2-D copies take: one copy per shot
+                for (size_t i = 0; i < nsh; ++i) {
+                    char* d = (char*)seg0 + seg_pitch * i;
+                    const char* s = ck0 + plane * i;
+                    GF_OP(c, st, -1, "segment start",
+                          cudaMemcpyAsync(d, s, plane, cudaMemcpyDeviceToDevice, s_));
+                }
+            }
             q.hist_slot0 = n_begin - 1;
             p.hist_slot0 = n_begin - 1;
             int fcur = 0;
