@@ -131,53 +131,6 @@ def generate_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales, np
     return X, T, time.perf_counter() - t0
 
 
-def generate_iterate_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales,
-                           npml: int, mask, at=(3, 6, 10, 15), f0: float = 400e6,
-                           progress=None):
-    """Training pairs taken along plain L-BFGS runs (the iterates the network meets in FWI
-    after its first steps): for each of the N models (as in :func:`generate_pairs`), run
-    plain L-BFGS from the start model and, at the iterations listed in ``at``, pair the
-    gradient and illumination at the iterate with the remaining update to the truth.
-    Returns X [N * len(at), H, W, 4], T [N * len(at), H, W, 2] on the device (iterations a
-    run does not reach repeat its last iterate) and the seconds spent."""
-    from .fwi import FWI, FWIConfig
-    ny, nx = fd.shape
-    H, W = ny - 2 * npml, nx - 2 * npml
-    dev = fd.device
-    K = len(at)
-    X = torch.empty(N * K, H, W, 4, dtype=torch.float32, device=dev)
-    T = torch.empty(N * K, H, W, 2, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for i, (et, st, ei, si) in enumerate(models):
-        et, st, ei, si = (torch.as_tensor(a, dtype=torch.float32).to(dev) for a in (et, st, ei, si))
-        obs = fd.forward_model(et, st, wavelet)
-        snaps = {}
-        drv = FWI(fd, lambda f: obs, mask, FWIConfig(bands=((f0, max(at)),)))
-
-        def keep(it, J, x, snaps=snaps):
-            if it + 1 in at:
-                snaps[it + 1] = x.detach().clone()
-
-        drv.run(ei, si, callback=keep)
-        last = None
-        for k, a in enumerate(at):
-            x = snaps.get(a, last)
-            last = x
-            if x is None:
-                e, s = ei, si
-            else:
-                e, s = drv._split(x.float())
-            _, illum = fd.forward_model(e, s, wavelet, illumination=True)
-            _, ge, gs = fd.misfit_and_gradient(e, s, wavelet, obs)
-            features(ge, gs, e, illum, npml, out=X[i * K + k])
-            targets(e, s, et, st, npml, scales, out=T[i * K + k])
-        if progress:
-            progress(i)
-    torch.cuda.synchronize(dev)
-    return X, T, time.perf_counter() - t0
-
-
 def train(net: UNet, X, T, epochs: int, batch: int, lr: float, seed: int = 0,
           lr_decay: float = 0.5, decay_every: int | None = None, log=None):
     """Adam on minibatches of (X, T) resident on the device; returns per-epoch mean losses."""

@@ -24,8 +24,8 @@ import torch
 from . import workloads as W
 from .fdtd import FDTD, ricker
 from .fwi import FWI, FWIConfig, interior_mask
-from .precond import (LearnedPreconditioner, PreconditionerScales, generate_iterate_pairs,
-                      generate_pairs, pair_fractions, seeded_models, train, validation_loss)
+from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pairs,
+                      pair_fractions, seeded_models, train, validation_loss)
 from .unet import UNet
 
 
@@ -62,8 +62,6 @@ def main(argv=None):
                     help="L-BFGS iterations after a rejected learned update before the network "
                          "is consulted again (0 = not again)")
     ap.add_argument("--scales", default="1,0.5", help="scales of the learned update tried in turn")
-    ap.add_argument("--iterate-models", type=int, default=0,
-                    help="models whose plain L-BFGS iterates 3, 6, 10, 15 add training pairs")
     ap.add_argument("--plain-from", default=None,
                     help="JSON of an earlier evaluation of the same models: reuse its plain "
                          "L-BFGS rows (the plain runs are deterministic) instead of rerunning them")
@@ -97,10 +95,6 @@ def main(argv=None):
                      val0, val1)
 
 
-def first_f0(g, args) -> float:
-    return W.preconditioner_model(args.seed, nt=args.nt).f0
-
-
 def _train(args, fd, wav, scales, g, net, seeds_train, seeds_val):
     dev = fd.device
     t_gen = time.perf_counter()
@@ -110,14 +104,6 @@ def _train(args, fd, wav, scales, g, net, seeds_train, seeds_val):
     Xv, Tv, _ = generate_pairs(fd, seeded_models(seeds_val, args.nt, args.workers),
                                len(seeds_val), wav, scales, g.npml,
                                fractions=pair_fractions(seeds_val))
-    if args.iterate_models > 0:
-        # pairs along plain L-BFGS runs of further training models (disjoint seeds)
-        seeds_it = np.arange(args.seed + 2 * 10 ** 6, args.seed + 2 * 10 ** 6 + args.iterate_models)
-        Xi, Ti, _ = generate_iterate_pairs(fd, seeded_models(seeds_it, args.nt, args.workers),
-                                           len(seeds_it), wav, scales, g.npml,
-                                           interior_mask(g, rows_below_top=4), f0=first_f0(g, args))
-        X = torch.cat([X, Xi])
-        T = torch.cat([T, Ti])
     t_gen = time.perf_counter() - t_gen
     net.init_params(args.seed)
     val0 = validation_loss(net, Xv, Tv, args.batch)
