@@ -65,7 +65,7 @@ def parse_args():
     ap.add_argument("--nt", type=int, default=2000)
     ap.add_argument("--tile", default="", help="tile_w,tile_h,steps_per_launch[,variant]")
     ap.add_argument("--workload", default="multishot",
-                    choices=["multishot", "large", "uneven", "unet"],
+                    choices=["multishot", "large", "disc", "precond", "uneven", "unet"],
                     help="multishot: 540x290, 32 shots, nt 2000 (default); large: 2108x1084, "
                          "16 shots, nt 8000 with checkpointing")
     ap.add_argument("--checkpoint", type=int, default=0,
@@ -103,6 +103,10 @@ def workload(rank: int, nshots: int, nt: int, kind: str = "multishot", world: in
     from paper_2506_20513_gb300.shard import shard_shots
     if kind == "large":
         wl = W.large_checkpointed(seed=4000, nshots=min(nshots, 16) * world, nt=nt)
+    elif kind == "disc":
+        return W.single_shot_disc()
+    elif kind == "precond":
+        return W.preconditioner_model(5000000, nshots=16 * world, nt=nt)
     else:
         wl = W.multishot_layered(seed=1000, nshots=nshots * world, nt=nt)
     if world == 1:
@@ -528,6 +532,14 @@ def ours(args):
         # the FP64 oracle would need ~146 GB of host memory per shot for this grid
         args.no_cpu_baseline = True
         args.no_large = True
+    if args.workload in ("disc", "precond"):
+        # the single-shot disc model (100 x 100 + 10-cell CPML, nt 600) and the learned
+        # preconditioner's workload (256 x 128 + 20-cell CPML, 16 shots, nt 1500): working
+        # sets that L2 holds, so latency, not HBM, is the binding roof
+        if args.workload == "precond" and args.nt == 2000:
+            args.nt = 1500
+        args.no_large = True
+        args.fwi_iters = 0
     wl = workload(rank, args.nshots, args.nt, args.workload, world)
     g = wl.grid
     tiling = Tiling(*[int(x) for x in args.tile.split(",")]) if args.tile else None
@@ -691,7 +703,10 @@ def ours(args):
                                        f"{world} GPUs, (J, g_eps, g_sigma) summed by an NCCL "
                                        "all-reduce every step" if world > 1 else
                                        "one GPU, all shots"),
-                       "fwi": fwi},
+                       "fwi": fwi,
+                       "binding_roof": ("L2 / latency: the working set fits in L2, HBM is "
+                                        "not the binding roof"
+                                        if args.workload in ("disc", "precond") else "HBM")},
             "roofline": roof, "large": large, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
