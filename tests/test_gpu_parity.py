@@ -207,6 +207,33 @@ def test_adjoint_of_arbitrary_cotangent(dev):
     assert rel(gs.cpu().numpy(), gs64) <= GRAD_TOL
 
 
+def test_dot_product_of_gpu_adjoint_with_oracle_tangent(dev):
+    """<J dm, r> = <dm, J^T r>: the oracle's FP64 tangent-linear traces along a smooth random
+    model perturbation dm, against the GPU adjoint's gradient for a random trace cotangent r
+    (CPML with kappa_max = 2, PEC cells, two shots).  FP32 bound 1e-5 relative."""
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(13, nxp=52, nyp=36, npml=7, nt=150, nshots=2, nrec=9, kappa_max=2.0,
+                        with_pec=True)
+    g = wl.grid
+    wav = wavelets(wl)
+    rng = np.random.default_rng(17)
+    r = rng.standard_normal((wl.nshots, g.nt, wl.nrec))
+    from scipy.ndimage import gaussian_filter
+    de = gaussian_filter(rng.standard_normal((g.ny, g.nx)), 2.0)
+    ds = 1e-3 * gaussian_filter(rng.standard_normal((g.ny, g.nx)), 2.0)
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    fd.forward(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev))
+    ge, gs = fd.adjoint(t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(r, dev))
+    fd.status()
+    lhs = sum(float((O.tangent(g, wl.eps_init, wl.sig_init, de, ds, wl.src[k], wav[k],
+                                wl.rec[k]) * r[k]).sum()) for k in range(wl.nshots))
+    rhs = float((de * ge.cpu().numpy().astype(np.float64)).sum()
+                + (ds * gs.cpu().numpy().astype(np.float64)).sum())
+    assert abs(lhs) > 0
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    fd.close()
+
+
 def test_autograd_function_matches_misfit_and_gradient(dev):
     from paper_2506_20513_gb300 import FDTD, FDTDFunction
     wl = W.small_random(14, nxp=36, nyp=24, npml=5, nt=100, nshots=2, nrec=5)
