@@ -132,6 +132,9 @@ static void or_coefficients(const or_grid* g, const double* eps_r, const double*
 /* ---------------------------------------------------------------------------------------
  * Forward model of one shot (Algorithm 1).  Outputs (each may be NULL):
  *   traces [nt][nrec]            d^n = Ez^n at the receivers
+ *   h_traces [nt][nrec][2]       Hx^{n-1/2} at (i, j+1/2) and Hy^{n-1/2} at (i+1/2, j) of
+ *                                the receiver cells, sampled with d^n (the paper's receivers
+ *                                store every field component, Sec. 3.2 store_outputs)
  *   ez_hist [(nt+1)][ny*nx]      Ez^0 .. Ez^nt
  *   q_hist [nt][ny*nx]           Q^n, the bracket multiplied by Cb in the step-n E update,
  *                                including the source term
@@ -142,7 +145,8 @@ static void or_coefficients(const or_grid* g, const double* eps_r, const double*
 int or_forward_shot(const or_grid* g, const double* eps_r, const double* sigma,
                     int nsrc, const int32_t* src, const double* wav,
                     int nrec, const int32_t* rec,
-                    double* traces, double* ez_hist, double* q_hist, double* energy) {
+                    double* traces, double* h_traces, double* ez_hist, double* q_hist,
+                    double* energy) {
     const int nx = g->nx, ny = g->ny, nt = g->nt;
     const size_t N = (size_t)nx * ny;
     const double dx = g->dx, dy = g->dy, dt = g->dt;
@@ -162,6 +166,12 @@ int or_forward_shot(const or_grid* g, const double* eps_r, const double* sigma,
         if (traces)
             for (int r = 0; r < nrec; ++r)
                 traces[(size_t)n * nrec + r] = Ez[(size_t)rec[2 * r + 1] * nx + rec[2 * r]];
+        if (h_traces)
+            for (int r = 0; r < nrec; ++r) {
+                const size_t c = (size_t)rec[2 * r + 1] * nx + rec[2 * r];
+                h_traces[((size_t)n * nrec + r) * 2] = Hx[c];
+                h_traces[((size_t)n * nrec + r) * 2 + 1] = Hy[c];
+            }
         double wsum = 0.0;
         if (energy)
             for (size_t c = 0; c < N; ++c) wsum += OR_EPS0 * eps_r[c] * Ez[c] * Ez[c];
@@ -421,7 +431,7 @@ int or_forward(const or_grid* g, const double* eps_r, const double* sigma,
     for (int s = 0; s < nshots; ++s)
         err |= or_forward_shot(g, eps_r, sigma, nsrc, src + (size_t)s * nsrc * 2,
                                wav + (size_t)s * nsrc * g->nt, nrec, rec + (size_t)s * nrec * 2,
-                               traces + (size_t)s * g->nt * nrec, NULL, NULL, NULL);
+                               traces + (size_t)s * g->nt * nrec, NULL, NULL, NULL, NULL);
     return err ? -1 : 0;
 }
 
@@ -448,7 +458,7 @@ int or_misfit_gradient(const or_grid* g, const double* eps_r, const double* sigm
         const int32_t* ss = src + (size_t)s * nsrc * 2;
         const int32_t* rr = rec + (size_t)s * nrec * 2;
         err |= or_forward_shot(g, eps_r, sigma, nsrc, ss, wav + (size_t)s * nsrc * nt, nrec, rr,
-                               tr, hist, NULL, NULL);
+                               tr, NULL, hist, NULL, NULL);
         double J = 0.0;
         for (size_t k = 0; k < (size_t)nt * nrec; ++k) {
             res[k] = tr[k] - observed[(size_t)s * nt * nrec + k];

@@ -109,7 +109,7 @@ def _load():
             pd, pi = P(d), P(i32)
             g = P(OrGrid)
             lib.or_forward_shot.argtypes = [g, pd, pd, ctypes.c_int, pi, pd, ctypes.c_int, pi,
-                                            pd, pd, pd, pd]
+                                            pd, pd, pd, pd, pd]
             lib.or_adjoint_shot.argtypes = [g, pd, pd, ctypes.c_int, pi, ctypes.c_int, pi,
                                             pd, pd, pd, pd, pd, pd, pd, pd]
             lib.or_tangent_shot.argtypes = [g, pd, pd, pd, pd, ctypes.c_int, pi, pd,
@@ -168,11 +168,12 @@ def ricker(f0: float, dt: float, nt: int, amp: float = 1.0, t0: float | None = N
 # Single-shot routines
 # ------------------------------------------------------------------------------------------
 def forward_shot(grid, eps_r, sigma, src, wav, rec, history=False, qhistory=False,
-                 energy=False):
+                 energy=False, fields=False):
     """One shot.  src [nsrc,2], wav [nsrc,nt], rec [nrec,2] (cell indices i, j).
 
     Returns a dict with ``traces`` [nt, nrec] and optionally ``ez_hist`` [nt+1, ny, nx],
-    ``q_hist`` [nt, ny, nx], ``energy`` [nt]."""
+    ``q_hist`` [nt, ny, nx], ``energy`` [nt], ``h_traces`` [nt, nrec, 2] (Hx^{n-1/2},
+    Hy^{n-1/2} at the receiver cells' staggered nodes, sampled with Ez^n)."""
     g = as_grid(grid)
     lib = _load()
     shape = (g.ny, g.nx)
@@ -186,10 +187,12 @@ def forward_shot(grid, eps_r, sigma, src, wav, rec, history=False, qhistory=Fals
         out["q_hist"] = np.zeros((g.nt,) + shape)
     if energy:
         out["energy"] = np.zeros(g.nt)
+    if fields:
+        out["h_traces"] = np.zeros((g.nt, len(rec), 2))
     rc = lib.or_forward_shot(ctypes.byref(g.c_struct()), _pd(e), _pd(s), len(src), _pi(src),
                              _pd(wav), len(rec), _pi(rec), _pd(out["traces"]),
-                             _pd(out.get("ez_hist")), _pd(out.get("q_hist")),
-                             _pd(out.get("energy")))
+                             _pd(out.get("h_traces")), _pd(out.get("ez_hist")),
+                             _pd(out.get("q_hist")), _pd(out.get("energy")))
     _check(rc, "forward_shot")
     return out
 
@@ -282,6 +285,28 @@ def misfit_and_gradient(grid, eps_r, sigma, src, wav, rec, observed, nthreads: i
 # ------------------------------------------------------------------------------------------
 # Analytic 2-D line-source solution (pin for the continuous equations)
 # ------------------------------------------------------------------------------------------
+def line_source_hy_trace(current: np.ndarray, dt: float, x: float, eps_r: float,
+                         sigma: float, pad: int = 8) -> np.ndarray:
+    """Hy(x, 0, t_n), t_n = n dt, of the same line current at a point on the +x axis.
+
+    Faraday's law with the e^{+j w t} convention, j w mu0 H = -curl E, gives for E = Ez z:
+    Hy = (1 / (j w mu0)) dEz/dx; with Ez = -(w mu0 / 4) I H0^(2)(k rho) and
+    dH0^(2)(z)/dz = -H1^(2)(z) this is Hy = -(j k / 4) I(w) H1^(2)(k x) on the axis."""
+    from scipy.special import hankel2
+
+    n = len(current)
+    nfft = int(2 ** np.ceil(np.log2(n * pad)))
+    I = np.fft.rfft(current, nfft)
+    w = 2.0 * np.pi * np.fft.rfftfreq(nfft, dt)
+    H = np.zeros_like(I)
+    wk = w[1:]
+    eps = EPS0 * eps_r
+    k = np.sqrt(wk * wk * MU0 * eps - 1j * wk * MU0 * sigma)
+    k = np.where(k.imag > 0, -k, k)
+    H[1:] = -(1j * k / 4.0) * I[1:] * hankel2(1, k * x)
+    return np.fft.irfft(H, nfft)[:n]
+
+
 def line_source_trace(current: np.ndarray, dt: float, rho: float, eps_r: float,
                       sigma: float, pad: int = 8) -> np.ndarray:
     """Ez(rho, t_n), t_n = n dt, radiated by an infinite line current I(t_n) = current[n]
