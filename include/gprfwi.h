@@ -180,6 +180,16 @@ int gf_get_tiling(const gf_ctx* ctx, int* tile_w, int* tile_h, int* steps_per_la
 int gf_forward_model(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
                      float* traces, float* illum, void* stream);
 
+/* gf_forward_model that also records the receivers' magnetic components (the paper's
+ * receivers store every field component, Sec. 3.2 store_outputs; in the 2-D TM mode those
+ * are Ez, Hx, Hy): h_traces, device [nshots][nt][nrec][2] or NULL, gets Hx^{n-1/2} at (i,
+ * j+1/2) and Hy^{n-1/2} at (i+1/2, j) of each receiver cell (i, j), sampled with d^n = Ez^n
+ * (before step n's updates; zero at n = 0).  Forward only: the misfit and its gradient use
+ * Ez. */
+int gf_forward_model_fields(gf_ctx* ctx, const float* eps_r, const float* sigma,
+                            const float* wavelet, float* traces, float* h_traces, float* illum,
+                            void* stream);
+
 /* Forward run that also stores the wavefield (mode GF_STORE_FULL) in the workspace for a
  * later gf_adjoint on the same model, wavelet and stream. */
 int gf_forward(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,

@@ -571,7 +571,8 @@ struct Forward {
 };
 
 int forward_setup(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
-                  float* traces, float* illum, bool store, cudaStream_t st, Forward& f) {
+                  float* traces, float* illum, bool store, cudaStream_t st, Forward& f,
+                  float* traces_h = nullptr) {
     if (!eps_r || !sigma || !wavelet) return fail(c, GF_EINVAL, "NULL model or wavelet pointer");
     int rc = ensure_workspace(c, !store);
     if (rc) return rc;
@@ -580,6 +581,7 @@ int forward_setup(gf_ctx* c, const float* eps_r, const float* sigma, const float
     f.p = base_params(c, L);
     f.p.wavelet = wavelet;
     f.p.traces = traces ? traces : (float*)(c->ws + L.traces);
+    f.p.traces_h = traces_h;
     f.ckpt = store && (c->store_mode == GF_STORE_CHECKPOINT ||
                        c->store_mode == GF_STORE_RECONSTRUCT);
     f.p.hist = store && !f.ckpt ? (float*)(c->ws + L.hist) : nullptr;
@@ -636,9 +638,10 @@ int forward_finish(gf_ctx* c, const Forward& f, float* illum, cudaStream_t st) {
 }
 
 int run_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
-                float* traces, float* illum, bool store, cudaStream_t st) {
+                float* traces, float* illum, bool store, cudaStream_t st,
+                float* traces_h = nullptr) {
     Forward f;
-    int rc = forward_setup(c, eps_r, sigma, wavelet, traces, illum, store, st, f);
+    int rc = forward_setup(c, eps_r, sigma, wavelet, traces, illum, store, st, f, traces_h);
     if (rc) return rc;
     rc = run_lanes(c, st, [&](const LaneRange& ln) { return forward_lane(c, f, ln); });
     if (rc) return rc;
@@ -1261,6 +1264,16 @@ int gf_forward_model(gf_ctx* c, const float* eps_r, const float* sigma, const fl
     if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
     DeviceGuard guard(c->device);
     return run_forward(c, eps_r, sigma, wavelet, traces, illum, false, (cudaStream_t)stream);
+}
+
+int gf_forward_model_fields(gf_ctx* c, const float* eps_r, const float* sigma,
+                            const float* wavelet, float* traces, float* h_traces, float* illum,
+                            void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
+    DeviceGuard guard(c->device);
+    return run_forward(c, eps_r, sigma, wavelet, traces, illum, false, (cudaStream_t)stream,
+                       h_traces);
 }
 
 int gf_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,

@@ -60,6 +60,7 @@ struct TileParams {
     int hist_stride;        // slots per shot (nt for the full store, k + 1 for a segment)
     int hist_slot0;         // step whose Ez^{n+1} is slot 0 (0, or the segment start - 1)
     float* traces;          // forward: [nshots][nt][nrec] output
+    float* traces_h;        // forward: [nshots][nt][nrec][2] Hx, Hy output (NULL = skip)
     const float* resid;     // adjoint: [nshots][nt][nrec] trace cotangent
     float* illum;           // forward: [nshots][Np] accumulated (NULL = skip)
     float* grad;            // adjoint: [2][nshots][Np] accumulated

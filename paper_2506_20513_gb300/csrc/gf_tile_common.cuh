@@ -820,6 +820,17 @@ __device__ __forceinline__ void ring_fetch(const TileParams& p, const Ring& rg, 
     cp_async_commit();
 }
 
+// The magnetic components of receiver ri at step n (H^{n-1/2}: Hx at (i, j+1/2), Hy at
+// (i+1/2, j), the values the registers hold before the step's H update).
+template <int R>
+__device__ __forceinline__ void record_h(const TileParams& p, int shot, int n, int ri,
+                                         const float2 (&hx)[R], const float2 (&hy)[R], int r,
+                                         int c) {
+    float* th = p.traces_h + (((long long)shot * p.nt + n) * p.nrec + ri) * 2;
+    th[0] = pick<R>(hx, r, c);
+    th[1] = pick<R>(hy, r, c);
+}
+
 // ---------------------------------------------------------------------------------------
 // Time-step loops of one tile
 // ---------------------------------------------------------------------------------------
@@ -859,8 +870,11 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
             for (int e = rlo; e < rhi; ++e) {
                 int pos, ri;
                 rec_entry<kStaged>(p, srec, ents, nrl, e, K, pos, ri);
-                if (((pos & 0xff) >> 1) == w.lane && (pos >> 16))
-                    tr[(long long)n * p.nrec + ri] = pick<R>(ez, rec_row(pos) - w.ly0, pos & 1);
+                if (((pos & 0xff) >> 1) == w.lane && (pos >> 16)) {
+                    const int rr = rec_row(pos) - w.ly0, cc = pos & 1;
+                    tr[(long long)n * p.nrec + ri] = pick<R>(ez, rr, cc);
+                    if (p.traces_h) record_h<R>(p, shot, n, ri, hx, hy, rr, cc);
+                }
             }
         } else {
 #pragma unroll
@@ -870,6 +884,7 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
                     const int e = code >> 4;
                     const int ri = kStaged ? srec[nrl + e] : __ldg(ents + e).x;
                     tr[(long long)n * p.nrec + ri] = pick<R>(ez, (code >> 1) & 7, code & 1);
+                    if (p.traces_h) record_h<R>(p, shot, n, ri, hx, hy, (code >> 1) & 7, code & 1);
                 }
             }
         }

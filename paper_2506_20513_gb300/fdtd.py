@@ -175,18 +175,28 @@ class FDTD:
         _lib.check(self.lib, self.ctx, self.lib.gf_status(self.ctx, self._stream()))
 
     # -- the calls of the paper's statement of the problem ---------------------------------
-    def forward_model(self, eps_r, sigma, wavelet, illumination: bool = False):
-        """traces [nshots, nt, nrec] (and the illumination [ny, nx] if asked)."""
+    def forward_model(self, eps_r, sigma, wavelet, illumination: bool = False,
+                      fields: bool = False):
+        """traces [nshots, nt, nrec] (Ez), then the illumination [ny, nx] if asked, then the
+        receivers' magnetic components [nshots, nt, nrec, 2] (Hx^{n-1/2}, Hy^{n-1/2} at the
+        staggered nodes of each receiver cell) if ``fields``."""
         e, s = self._model(eps_r, sigma)
         w = self._wavelet(wavelet)
         self._workspace(full=False)
         tr = torch.empty(self.trace_shape, dtype=torch.float32, device=self.device)
         ill = torch.empty(self.shape, dtype=torch.float32, device=self.device) if illumination else None
-        rc = self.lib.gf_forward_model(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(),
-                                       tr.data_ptr(), ill.data_ptr() if ill is not None else None,
-                                       self._stream())
+        if fields:
+            h = torch.empty(self.trace_shape + (2,), dtype=torch.float32, device=self.device)
+            rc = self.lib.gf_forward_model_fields(
+                self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), tr.data_ptr(), h.data_ptr(),
+                ill.data_ptr() if ill is not None else None, self._stream())
+        else:
+            rc = self.lib.gf_forward_model(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(),
+                                           tr.data_ptr(), ill.data_ptr() if ill is not None else None,
+                                           self._stream())
         _lib.check(self.lib, self.ctx, rc)
-        return (tr, ill) if illumination else tr
+        out = (tr,) + ((ill,) if illumination else ()) + ((h,) if fields else ())
+        return out if len(out) > 1 else tr
 
     def misfit_and_gradient(self, eps_r, sigma, wavelet, observed, return_traces: bool = False):
         """J = 1/2 sum (d - o)^2 (FP64 device scalar), dJ/deps_r and dJ/dsigma [ny, nx].

@@ -552,3 +552,29 @@ def test_shot_lanes_give_identical_results(dev, k):
         assert torch.equal(tr, out[0][3])
     J64, ge64, gs64 = O.misfit_and_gradient(g, wl.eps_init, wl.sig_init, wl.src, wav, wl.rec, obs)
     assert rel(out[0][1].numpy(), ge64) <= GRAD_TOL and rel(out[0][2].numpy(), gs64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("tiling", [None, (20, 14, 5, 3), (0, 0, 4, 1)])
+def test_magnetic_receiver_components(dev, tiling):
+    """gf_forward_model_fields: the receivers' Hx^{n-1/2}, Hy^{n-1/2} against the oracle's
+    (traces tolerance), the Ez traces bit-identical to gf_forward_model's; dense receivers,
+    a kappa_max = 2 CPML, two lanes, the persistent and the two-CTA variants."""
+    from paper_2506_20513_gb300 import FDTD, Tiling
+    wl = W.small_random(81, nxp=64, nyp=40, npml=7, nt=170, nshots=3, nrec=40, kappa_max=2.0)
+    g = wl.grid
+    wav = wavelets(wl)
+    fd = FDTD(g, wl.src, wl.rec, device=dev, tiling=Tiling(*fit_variant(tiling)) if tiling else None)
+    args = (t32(wl.eps_true, dev), t32(wl.sig_true, dev), t32(wav, dev))
+    tr, h = fd.forward_model(*args, fields=True)
+    tr0 = fd.forward_model(*args)
+    fd.status()
+    assert torch.equal(tr, tr0)
+    hx = np.zeros((wl.nshots, g.nt, wl.nrec))
+    hy = np.zeros_like(hx)
+    for s in range(wl.nshots):
+        o = O.forward_shot(g, wl.eps_true, wl.sig_true, wl.src[s], wav[s], wl.rec[s], fields=True)
+        hx[s], hy[s] = o["h_traces"][..., 0], o["h_traces"][..., 1]
+    h = h.cpu().numpy()
+    assert rel(h[..., 0], hx) <= TRACE_TOL and rel(h[..., 1], hy) <= TRACE_TOL
+    assert np.all(h[:, 0] == 0.0)   # H^{-1/2} = 0
+    fd.close()
