@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(32 * NW, 1)
             fwd_steps<R, NW, false, kHist, kIllum, kStaged>(p, w, sm, it.shot, it.n0, it.K, ez, hx,
                                                             hy, ill, rlo, rhi, nrl, ents, orc, srcany);
         store_state<R, NW>(p, w, sm, st_out, it.shot, ez, hx, hy);
-        if (kIllum) add_illumination<R>(p, w, it.shot, ill);
+        if (kIllum && p.illum) add_illumination<R>(p, w, it.shot, ill);
         publish<R, NW>(p, f, it);
         if (!ahead && more) {
             if (!cta_wait_deps<R, NW>(pn, fn, nx, sm)) break;
@@ -541,7 +541,8 @@ cudaError_t launch_flow_pass(const FlowInstance& inst, bool adjoint, cudaStream_
     const TileParams& p = inst.p;
     const long long total = (long long)inst.f.nblocks * p.nshots * p.ntiles;
     return launch_any(inst, nullptr, nullptr, total, adjoint, p.hist != nullptr,
-                      p.illum != nullptr, staged_receivers(p, inst.f.kb, adjoint),
+                      p.illum != nullptr || p.traces_h != nullptr,
+                      staged_receivers(p, inst.f.kb, adjoint),
                       p.tile_w * p.tile_h, st);
 }
 
@@ -555,7 +556,8 @@ cudaError_t launch_flow_multi(const FlowInstance* h_inst, const FlowInstance* d_
         staged = staged && staged_receivers(h_inst[k].p, h_inst[k].f.kb, adjoint);
         ring = ring > h_inst[k].p.tile_w * h_inst[k].p.tile_h
                    ? ring : h_inst[k].p.tile_w * h_inst[k].p.tile_h;
-        if ((h_inst[k].p.hist != nullptr) != hist || h_inst[k].p.illum) return cudaErrorInvalidValue;
+        if ((h_inst[k].p.hist != nullptr) != hist || h_inst[k].p.illum || h_inst[k].p.traces_h)
+            return cudaErrorInvalidValue;
     }
     return launch_any(h_inst[0], d_inst, d_items, total, adjoint, hist, false, staged, ring, st);
 }

@@ -873,7 +873,7 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
                 if (((pos & 0xff) >> 1) == w.lane && (pos >> 16)) {
                     const int rr = rec_row(pos) - w.ly0, cc = pos & 1;
                     tr[(long long)n * p.nrec + ri] = pick<R>(ez, rr, cc);
-                    if (p.traces_h) record_h<R>(p, shot, n, ri, hx, hy, rr, cc);
+                    if (kIllum && p.traces_h) record_h<R>(p, shot, n, ri, hx, hy, rr, cc);
                 }
             }
         } else {
@@ -884,7 +884,8 @@ __device__ __forceinline__ void fwd_steps(const TileParams& p, const Pos<R>& w, 
                     const int e = code >> 4;
                     const int ri = kStaged ? srec[nrl + e] : __ldg(ents + e).x;
                     tr[(long long)n * p.nrec + ri] = pick<R>(ez, (code >> 1) & 7, code & 1);
-                    if (p.traces_h) record_h<R>(p, shot, n, ri, hx, hy, (code >> 1) & 7, code & 1);
+                    if (kIllum && p.traces_h)
+                        record_h<R>(p, shot, n, ri, hx, hy, (code >> 1) & 7, code & 1);
                 }
             }
         }

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(32 * NW, NW <= 8 && R <= 4 ? 2 : 1)
                                                         ill, rlo, rhi, nrl, ents, orc, srcany);
 
     store_state<R, NW>(p, w, sm, p.st_out, shot, L.f0, L.f1, L.f2);
-    if (kIllum) add_illumination<R>(p, w, shot, ill);
+    if (kIllum && p.illum) add_illumination<R>(p, w, shot, ill);
 }
 
 template <int R, int NW, bool kStaged>
@@ -169,9 +169,12 @@ cudaError_t launch_fwd_variant(const TileParams& p, const TileMaps& m, bool stag
 
 template <int R, int NW>
 cudaError_t launch_fwd_r(const TileParams& p, const TileMaps& m, bool staged, cudaStream_t st) {
-    if (p.hist && p.illum) return launch_fwd_variant<R, NW, true, true>(p, m, staged, st);
+    // the observation extras (illumination, the receivers' magnetic components) share one
+    // instantiation: the gradient's forward pass carries neither
+    const bool obs = p.illum || p.traces_h;
+    if (p.hist && obs) return launch_fwd_variant<R, NW, true, true>(p, m, staged, st);
     if (p.hist) return launch_fwd_variant<R, NW, true, false>(p, m, staged, st);
-    if (p.illum) return launch_fwd_variant<R, NW, false, true>(p, m, staged, st);
+    if (obs) return launch_fwd_variant<R, NW, false, true>(p, m, staged, st);
     return launch_fwd_variant<R, NW, false, false>(p, m, staged, st);
 }
 
