@@ -41,14 +41,14 @@ FALLBACK_HBM_GBS = 6800.0
 # Keyed on kernel_source_tag(): any change of the kernel code drops them (reported as null).
 # DRAM bytes (read + write) per cell-step:
 NCU_TRAFFIC_PER_CELL_STEP: dict = {
-    "adj@a900bcde84e7@540x290x32@default": 12.1322,   # 425.58 MB / 35.0784 M cell-steps
-    "fwd@a900bcde84e7@540x290x32@default": 8.0138,    # 281.11 MB
+    "adj@1f1660801c10@540x290x32@default": 12.1320,   # 425.57 MB / 35.0784 M cell-steps
+    "fwd@1f1660801c10@540x290x32@default": 8.0039,    # 280.77 MB
 }
 # Warp instructions per cell-step (the kernels are bound by instruction issue, so the line
 # also reports the issue roofline):
 NCU_WARP_INST_PER_CELL_STEP: dict = {
-    "adj@a900bcde84e7@540x290x32@default": 2.9761,    # 104.396 M warp instructions
-    "fwd@a900bcde84e7@540x290x32@default": 2.0820,    # 73.032 M
+    "adj@1f1660801c10@540x290x32@default": 2.9761,    # 104.396 M warp instructions
+    "fwd@1f1660801c10@540x290x32@default": 2.0820,    # 73.032 M
 }
 ISSUE_SLOTS_PER_SM_CLK = 4  # one warp instruction per scheduler per clock, 4 schedulers per SM
 # the files holding the tile kernels' device code
