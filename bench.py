@@ -386,7 +386,8 @@ def lanes_used(fd, args) -> int:
     return max(1, min(args.lanes, fd.nshots))
 
 
-def path_roofline(span_ms: float, wl, steps: int, K: int, checkpoint: int) -> dict:
+def path_roofline(span_ms: float, wl, steps: int, K: int, checkpoint: int,
+                  tiling: str = "default") -> dict:
     """The forward and adjoint tile kernels together: the algorithmic bytes of all their
     launches over the time they kept the GPU busy (their launches overlap when the shots run
     in concurrent lanes)."""
@@ -399,8 +400,14 @@ def path_roofline(span_ms: float, wl, steps: int, K: int, checkpoint: int) -> di
     total = steps * (fwd + adj)
     peak, peak_kind = hbm_peak()
     achieved = total / (span_ms / 1e3) / 1e9
+    # ncu's DRAM bytes per cell-step of both kernels (same code), over the step's cell-steps
+    tag = kernel_source_tag()
+    key = lambda k: f"{k}@{tag}@{g.nx}x{g.ny}x{wl.nshots}@{tiling}"
+    tf, ta = (NCU_TRAFFIC_PER_CELL_STEP.get(key(k)) for k in ("fwd", "adj"))
+    cells = wl.nshots * g.ncells * g.nt
+    traffic = (tf * cells * (2 if checkpoint else 1) + ta * cells) if tf and ta else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per step",
             "kernel": "fwd_tile_kernel + adj_tile_kernel (concurrent shot lanes)",
             "peak_source": f"hbm_gbs of {peak_kind}",
             "algorithmic_bytes_per_step": total / steps, "busy_ms_per_step": span_ms / steps,
@@ -620,7 +627,7 @@ def ours(args):
         # the lanes run the forward and adjoint kernels concurrently: the roofline of the two
         # together over the time they kept the GPU busy, and the dominant kernel alone (one
         # lane) beside it
-        roof = path_roofline(span_all, wl, args.steps, t.steps, args.checkpoint)
+        roof = path_roofline(span_all, wl, args.steps, t.steps, args.checkpoint, tiling_key)
         roof["phase_ms_per_step"] = {k: v[0] / args.steps for k, v in prof.items()}
         roof["dominant_kernel_one_lane"] = kernel_roof
     peak = roof["peak"]
