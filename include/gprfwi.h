@@ -309,10 +309,13 @@ int gf_forward_model_noalloc(const gf_grid_desc* grid, const gf_acquisition* acq
 /* Autotuner (tile shape, time-block depth, kernel variant).  Looks up the context's shape
  * (device name, nx, ny, npml, shots, sources, receivers) in the text cache `cache_path`
  * (NULL = no cache); on a miss, times a forward pass over the first `probe_steps` steps (0 =
- * 48) for each candidate (variants 0 and 1 with 3..10 steps per launch, variant 2 with 4 and
- * 6, variant 3 with 3..6), with CUDA events on `stream`, keeps the fastest and appends it to the cache.  Leaves
- * the chosen tiling set on the context (read it back with gf_get_tiling).  Synchronises
- * `stream`.  eps_r, sigma, wavelet: device inputs as for gf_forward_model. */
+ * 48) for each candidate (variants 0 and 3 with 4, 5, 6, 7, 8 or 10 steps per launch,
+ * variant 1 with 3..6, variant 2 with 5 and 7; each with its default tile for that depth),
+ * with CUDA events on `stream`, keeps the fastest and appends it to the cache.  Candidates a
+ * caller workspace cannot hold are skipped (give the context no workspace, or a library-
+ * owned one, to probe them all).  Leaves the chosen tiling set on the context (read it back
+ * with gf_get_tiling).  Synchronises `stream`.  eps_r, sigma, wavelet: device inputs as for
+ * gf_forward_model. */
 int gf_autotune(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
                 const char* cache_path, int probe_steps, void* stream);
 
