@@ -165,6 +165,7 @@ class FWI:
                 S = [t.to(dev) for t in st["S"]]
                 Y = [t.to(dev) for t in st["Y"]]
                 first, use_net, it0 = st["first"], st["use_net"], st["iteration"]
+                n_kept = st.get("n_kept", 0)
                 retry_at = st.get("retry_at", -1)
                 if learned:
                     ge, gs, illum = (st[k].to(dev) for k in ("ge", "gs", "illum"))
@@ -181,6 +182,7 @@ class FWI:
                 g = g.double()
                 first = True
                 use_net = learned   # the network is tried until its update is rejected
+                n_kept = 0          # learned updates kept in this band (selects the network)
                 retry_at = -1       # iteration at which a rejected network is tried again
                 it0 = 0
             n = x.numel() // 2
@@ -195,7 +197,7 @@ class FWI:
                 if learned and not use_net and 0 <= retry_at <= it:
                     use_net, retry_at = True, -1
                 if use_net:
-                    de, ds = self.pre.update(ge, gs, eps, illum)
+                    de, ds = self.pre.update(ge, gs, eps, illum, stage=n_kept)
                     d_l = torch.cat([(de * self.mask).reshape(-1).double(),
                                      (ds * self.mask / c.sigma_ref).reshape(-1).double()])
                     J_c = float("inf")
@@ -214,6 +216,7 @@ class FWI:
                             break
                     if J_c < J:
                         kept = True
+                        n_kept += 1
                         eps, sig = e_c, s_c
                     else:
                         use_net = False
@@ -297,7 +300,7 @@ class FWI:
                 if checkpoint and checkpoint_every > 0 and (it + 1) % checkpoint_every == 0:
                     state = dict(band_index=bi, iteration=it + 1, x=x.cpu(), g=g.cpu(), J=J,
                                  S=[t.cpu() for t in S], Y=[t.cpu() for t in Y], first=first,
-                                 use_net=use_net, retry_at=retry_at,
+                                 use_net=use_net, retry_at=retry_at, n_kept=n_kept,
                                  hist={k: list(getattr(hist, k)) for k in
                                        ("misfit", "evaluations", "passes", "seconds", "band",
                                         "learned")})

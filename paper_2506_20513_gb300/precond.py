@@ -71,18 +71,22 @@ def targets(eps, sig, eps_true, sig_true, npml: int, scales: PreconditionerScale
 
 
 class LearnedPreconditioner:
-    """A U-Net over the physical region of an FDTD grid (padding npml cells on each side)."""
+    """A U-Net over the physical region of an FDTD grid (padding npml cells on each side), or
+    a sequence of them: network k proposes the update after k learned updates of the band
+    have been kept (the last one serves any later stage)."""
 
-    def __init__(self, net: UNet, npml: int, scales: PreconditionerScales | None = None):
+    def __init__(self, net, npml: int, scales: PreconditionerScales | None = None):
+        self.nets = list(net) if isinstance(net, (list, tuple)) else [net]
+        net = self.nets[0]
         self.net = net
         self.npml = npml
         self.scales = scales or PreconditionerScales()
         self._x = torch.empty(1, net.height, net.width, 4, dtype=torch.float32, device=net.device)
 
-    def update(self, ge, gs, eps, illum):
+    def update(self, ge, gs, eps, illum, stage: int = 0):
         """(delta eps_r, delta sigma) on the full grid (zero in the absorbing layer)."""
         features(ge, gs, eps, illum, self.npml, out=self._x[0])
-        y = self.net.forward(self._x)[0]
+        y = self.nets[min(stage, len(self.nets) - 1)].forward(self._x)[0]
         p = self.npml
         de = torch.zeros_like(ge)
         ds = torch.zeros_like(gs)
@@ -125,6 +129,42 @@ def generate_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales, np
         _, ge, gs = fd.misfit_and_gradient(ei, si, wavelet, obs)
         features(ge, gs, ei, illum, npml, out=X[i])
         targets(ei, si, et, st, npml, scales, out=T[i])
+        if progress:
+            progress(i)
+    torch.cuda.synchronize(dev)
+    return X, T, time.perf_counter() - t0
+
+
+def generate_stage_pairs(fd, models, N: int, wavelet, scales: PreconditionerScales, npml: int,
+                         pre: "LearnedPreconditioner", mask, fractions=None, progress=None):
+    """Training pairs for the next network of a sequence: for each of the N models (as in
+    :func:`generate_pairs`), apply ``pre``'s update at the start model as the FWI driver does
+    (masked, then eps_r >= 1, sigma >= 0), and pair the gradient at the updated model (with
+    the start model's illumination, which the driver keeps for the band) with the remaining
+    update to the truth.  Returns X, T on the device and the seconds spent."""
+    ny, nx = fd.shape
+    H, W = ny - 2 * npml, nx - 2 * npml
+    dev = fd.device
+    m = mask.to(device=dev, dtype=torch.float32)
+    X = torch.empty(N, H, W, 4, dtype=torch.float32, device=dev)
+    T = torch.empty(N, H, W, 2, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i, (et, st, ei, si) in enumerate(models):
+        et, st, ei, si = (torch.as_tensor(a, dtype=torch.float32).to(dev) for a in (et, st, ei, si))
+        if fractions is not None and fractions[i] > 0:
+            a = float(fractions[i])
+            ei = (ei + a * (et - ei)).contiguous()
+            si = (si + a * (st - si)).contiguous()
+        obs = fd.forward_model(et, st, wavelet)
+        _, illum = fd.forward_model(ei, si, wavelet, illumination=True)
+        _, ge, gs = fd.misfit_and_gradient(ei, si, wavelet, obs)
+        de, ds = pre.update(ge, gs, ei, illum)
+        e1 = (ei + de * m).clamp_min(1.0).contiguous()
+        s1 = (si + ds * m).clamp_min(0.0).contiguous()
+        _, ge1, gs1 = fd.misfit_and_gradient(e1, s1, wavelet, obs)
+        features(ge1, gs1, e1, illum, npml, out=X[i])
+        targets(e1, s1, et, st, npml, scales, out=T[i])
         if progress:
             progress(i)
     torch.cuda.synchronize(dev)

@@ -11,6 +11,11 @@ normalised true-minus-start update.  Evaluation on held-out seeds: plain L-BFGS 
 ``--iters`` iterations gives a target misfit; the learned-preconditioned run (network
 update tried first, plain step as fallback) counts the iterations, FDTD evaluations and
 wall time it needs to reach that misfit.  Prints one JSON line.
+
+With ``--stage2 N`` a second network, initialised from the first, is fine-tuned on N further
+models at the model the first network's update reaches (:func:`generate_stage_pairs`) and
+proposes the band's learned updates after the first kept one; the evaluation then also runs
+the first network alone on the same held-out models.
 """
 from __future__ import annotations
 
@@ -25,7 +30,8 @@ from . import workloads as W
 from .fdtd import FDTD, ricker
 from .fwi import FWI, FWIConfig, interior_mask
 from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pairs,
-                      pair_fractions, seeded_models, train, validation_loss)
+                      generate_stage_pairs, pair_fractions, seeded_models, train,
+                      validation_loss)
 from .unet import UNet
 
 
@@ -65,6 +71,12 @@ def main(argv=None):
     ap.add_argument("--plain-from", default=None,
                     help="JSON of an earlier evaluation of the same models: reuse its plain "
                          "L-BFGS rows (the plain runs are deterministic) instead of rerunning them")
+    ap.add_argument("--stage2", type=int, default=0,
+                    help="models for a second network, used after the first kept learned update")
+    ap.add_argument("--stage2-val", type=int, default=100)
+    ap.add_argument("--stage2-epochs", type=int, default=20)
+    ap.add_argument("--stage2-lr", type=float, default=3e-4)
+    ap.add_argument("--save2", default=None, help="write the second network's parameters (.npy)")
     args = ap.parse_args(argv)
     dev = torch.device("cuda:0")
     first = W.preconditioner_model(args.seed, nt=args.nt)
@@ -91,8 +103,50 @@ def main(argv=None):
         if args.save:
             np.save(args.save, net.get_params().cpu().numpy())
     pre = LearnedPreconditioner(net, g.npml, scales)
+    stage2 = None
+    if args.stage2 > 0:
+        net2, stage2 = _train_stage2(args, fd, wav, scales, g, net, pre, first)
+        if args.save2:
+            np.save(args.save2, net2.get_params().cpu().numpy())
+        stage2["single"] = pre
+        pre = LearnedPreconditioner([net, net2], g.npml, scales)
+        stage2["nets"] = (net, net2)
     return _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr, losses,
-                     val0, val1)
+                     val0, val1, stage2)
+
+
+def _train_stage2(args, fd, wav, scales, g, net, pre, first):
+    """Pairs at the first network's updated model on further seeded models; the second
+    network starts from the first's parameters."""
+    dev = fd.device
+    mask = interior_mask(g, rows_below_top=4)
+    base = args.seed + 2 * 10 ** 6
+    seeds = np.arange(base, base + args.stage2)
+    seeds_val = np.arange(base + args.stage2, base + args.stage2 + args.stage2_val)
+    t = time.perf_counter()
+    X, T, gpu_gen = generate_stage_pairs(fd, seeded_models(seeds, args.nt, args.workers),
+                                         len(seeds), wav, scales, g.npml, pre, mask)
+    Xv, Tv, _ = generate_stage_pairs(fd, seeded_models(seeds_val, args.nt, args.workers),
+                                     len(seeds_val), wav, scales, g.npml, pre, mask)
+    t_gen = time.perf_counter() - t
+    H, Wd = g.ny - 2 * g.npml, g.nx - 2 * g.npml
+    net2 = UNet(4, 32, 4, 2, H, Wd, max_batch=args.batch, device=dev)
+    net2.set_params(net.get_params().clone())
+    val0 = validation_loss(net2, Xv, Tv, args.batch)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    losses = train(net2, X, T, args.stage2_epochs, args.batch, args.stage2_lr,
+                   seed=args.seed + 1, decay_every=max(1, args.stage2_epochs // 3))
+    torch.cuda.synchronize(dev)
+    t_tr = time.perf_counter() - t
+    val1 = validation_loss(net2, Xv, Tv, args.batch)
+    del X, T, Xv, Tv
+    return net2, dict(stage2_models=args.stage2, stage2_val_models=args.stage2_val,
+                      stage2_epochs=args.stage2_epochs, stage2_lr=args.stage2_lr,
+                      stage2_pair_generation_s=t_gen, stage2_pair_generation_gpu_s=gpu_gen,
+                      stage2_training_s=t_tr, stage2_train_loss_first_epoch=losses[0],
+                      stage2_train_loss_last_epoch=losses[-1],
+                      stage2_val_loss_before=val0, stage2_val_loss_after=val1)
 
 
 def _train(args, fd, wav, scales, g, net, seeds_train, seeds_val):
@@ -118,7 +172,7 @@ def _train(args, fd, wav, scales, g, net, seeds_train, seeds_val):
 
 
 def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr, losses, val0,
-              val1):
+              val1, stage2=None):
     dev = fd.device
     rows = []
     plain = {}
@@ -140,6 +194,14 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
         target = p["J_plain"]
         h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target, retry=args.retry,
                         scales=[float(v) for v in args.scales.split(",")])
+        one = {}
+        if stage2 is not None:
+            h_1, t_1 = _fwi(fd, wl, obs, wl.f0, args.iters, pre=stage2["single"], stop=target,
+                            retry=args.retry, scales=[float(v) for v in args.scales.split(",")])
+            one = dict(it_learned1=len(h_1.misfit), ev_learned1=int(sum(h_1.evaluations)),
+                       passes_learned1=int(sum(h_1.passes)), s_learned1=t_1,
+                       reached1=bool(h_1.final_misfit <= target),
+                       learned_accepted1=int(sum(h_1.learned)))
         rows.append(dict(seed=int(s), J0=p["J0"], J_plain=target, it_plain=p["it_plain"],
                          ev_plain=p["ev_plain"], passes_plain=p.get("passes_plain"),
                          s_plain=p["s_plain"],
@@ -147,7 +209,7 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
                          ev_learned=int(sum(h_l.evaluations)),
                          passes_learned=int(sum(h_l.passes)), s_learned=t_l,
                          reached=bool(h_l.final_misfit <= target),
-                         learned_accepted=int(sum(h_l.learned))))
+                         learned_accepted=int(sum(h_l.learned)), **one))
     reached = [r for r in rows if r["reached"]]
     out = {
         "workload": f"precond_{g.nx}x{g.ny}_16shots_nt{g.nt}",
@@ -172,6 +234,18 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
         "learned_steps_accepted": int(sum(r["learned_accepted"] for r in rows)),
         "unet_kernel_launches": net.kernel_launches,
     }
+    if stage2 is not None:
+        out.update({k: v for k, v in stage2.items() if k not in ("single", "nets")})
+        out["unet_kernel_launches"] = sum(n.kernel_launches for n in stage2["nets"])
+        out.update({
+            "first_network_alone": {
+                "reached_fraction": sum(r["reached1"] for r in rows) / max(len(rows), 1),
+                "median_iters": float(np.median([r["it_learned1"] for r in rows])),
+                "median_evals": float(np.median([r["ev_learned1"] for r in rows])),
+                "median_passes": float(np.median([r["passes_learned1"] for r in rows])),
+                "median_s": float(np.median([r["s_learned1"] for r in rows])),
+                "learned_steps_accepted": int(sum(r["learned_accepted1"] for r in rows)),
+            }})
     out["train_loss_per_epoch"] = losses
     print(json.dumps(out))
     if args.out:

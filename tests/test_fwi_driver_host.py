@@ -48,6 +48,9 @@ class QuadraticFD:
         gs = (self.w_sig * ds / 1e-2).float()  # dJ/dsigma in S/m
         return torch.tensor([J], dtype=torch.float64), ge, gs
 
+    def forward_model(self, eps, sig, wav, illumination=False):
+        return None, torch.ones(self.shape)
+
 
 @pytest.fixture
 def no_cuda_sync(monkeypatch):
@@ -93,3 +96,65 @@ def test_adam_stage_schedule():
     # the default is the cross-hole schedule: eps_r alone for 50 epochs, then both
     d = AdamConfig().stages
     assert d[0].epochs == 50 and d[0].lr_sig == 0.0 and d[1].lr_sig > 0.0
+
+
+class HalfwayPreconditioner:
+    """Proposes half of the remaining update at every stage; a stage in ``bad`` proposes a
+    step away from the truth instead (its misfit rises, so the driver rejects it)."""
+
+    def __init__(self, fd, bad=()):
+        self.fd, self.bad, self.stages = fd, set(bad), []
+
+    def update(self, ge, gs, eps, illum, stage=0):
+        self.stages.append(stage)
+        f = -1.0 if stage in self.bad else 0.5
+        # eps and sigma of the driver's current model from the quadratic's gradients
+        de = -ge.double() / self.fd.w_eps
+        ds = -gs.double() * 1e-2 / self.fd.w_sig * 1e-2
+        return (f * de).float(), (f * ds).float()
+
+
+def test_learned_stage_counts_kept_updates(no_cuda_sync):
+    fd = QuadraticFD()
+    pre = HalfwayPreconditioner(fd)
+    mask = torch.ones(fd.shape)
+    drv = F.FWI(fd, lambda f0: None, mask, F.FWIConfig(bands=((4e8, 4),)), preconditioner=pre)
+    _, _, hist = drv.run(fd.eps_true + 0.5, fd.sig_true * 0.5)
+    # every learned update lowers the quadratic misfit: all kept, stage = updates kept so far
+    assert pre.stages == [0, 1, 2, 3]
+    assert hist.learned == [True] * 4
+
+
+def test_rejected_stage_ends_the_learned_updates(no_cuda_sync):
+    fd = QuadraticFD()
+    pre = HalfwayPreconditioner(fd, bad={1})
+    mask = torch.ones(fd.shape)
+    drv = F.FWI(fd, lambda f0: None, mask, F.FWIConfig(bands=((4e8, 5),)), preconditioner=pre)
+    _, _, hist = drv.run(fd.eps_true + 0.5, fd.sig_true * 0.5)
+    # stage 1 is rejected (every scale tried raises the misfit): L-BFGS for the rest
+    assert pre.stages == [0, 1]
+    assert hist.learned[:2] == [True, False] and not any(hist.learned[2:])
+
+
+def test_preconditioner_selects_the_network_of_the_stage():
+    from paper_2506_20513_gb300.precond import LearnedPreconditioner
+
+    class Const:
+        height, width, device = 4, 6, torch.device("cpu")
+
+        def __init__(self, v):
+            self.v = v
+
+        def forward(self, x):
+            return torch.full((1, 4, 6, 2), self.v)
+
+    pre = LearnedPreconditioner([Const(1.0), Const(2.0)], npml=2)
+    z = torch.zeros(8, 10)
+    ill = torch.ones(8, 10)
+    got = [float(pre.update(z, z, z + 4.0, ill, stage=k)[0][4, 5]) for k in range(4)]
+    # network k after k kept updates; the last network serves every later stage
+    assert got == [1.0, 2.0, 2.0, 2.0]
+    # a single network serves every stage; the absorbing layer gets no update
+    one = LearnedPreconditioner(Const(3.0), npml=2)
+    de, ds = one.update(z, z, z + 4.0, ill, stage=5)
+    assert float(de[4, 5]) == 3.0 and float(de[0, 0]) == 0.0 and float(ds[1, 1]) == 0.0
