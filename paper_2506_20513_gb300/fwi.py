@@ -56,6 +56,8 @@ class FWIConfig:
     # iterations have passed (0 = not again in this band)
     learned_scales: tuple = (1.0, 0.5)
     learned_retry: int = 0
+    # most learned updates kept per band before the rest is plain L-BFGS (0 = no limit)
+    learned_max: int = 2
 
 
 @dataclass
@@ -218,6 +220,8 @@ class FWI:
                         kept = True
                         n_kept += 1
                         eps, sig = e_c, s_c
+                        if 0 < c.learned_max <= n_kept:
+                            use_net = False
                     else:
                         use_net = False
                         if c.learned_retry > 0:

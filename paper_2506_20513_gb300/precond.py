@@ -17,7 +17,10 @@ solutions (Sec. 1) but trains none; this module is the library's own design:
   update (1 - a)(m_true - m0); the pairs stay resident in device memory;
 * use in FWI: the network's update is tried first (full, then half size); it is kept only
   if the true FDTD misfit decreases, otherwise the plain L-BFGS step is taken (see
-  :class:`FWI`).
+  :class:`FWI`); at most two updates are kept per band by default;
+* a sequence of networks: network k proposes the update after k kept ones; the second is
+  fine-tuned from the first on pairs taken at the model the first network's update reaches
+  (:func:`generate_stage_pairs`).
 
 Feature scaling, cropping and batching are a few elementwise tensor operations (PyTorch as
 plumbing); the network runs in the library's BF16 kernels (:mod:`.unet`), the gradients in

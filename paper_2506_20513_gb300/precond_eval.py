@@ -35,8 +35,9 @@ from .precond import (LearnedPreconditioner, PreconditionerScales, generate_pair
 from .unet import UNet
 
 
-def _fwi(fd, wl, obs, f0, iters, pre=None, stop=None, retry=0, scales=(1.0, 0.5)):
-    cfg = FWIConfig(bands=((f0, iters),), learned_retry=retry, learned_scales=tuple(scales))
+def _fwi(fd, wl, obs, f0, iters, pre=None, stop=None, retry=0, scales=(1.0, 0.5), most=2):
+    cfg = FWIConfig(bands=((f0, iters),), learned_retry=retry, learned_scales=tuple(scales),
+                    learned_max=most)
     mask = interior_mask(wl.grid, rows_below_top=4)
     inv = FWI(fd, lambda f: obs, mask, cfg, preconditioner=pre)
     e0 = torch.tensor(wl.eps_init, dtype=torch.float32, device=fd.device)
@@ -77,6 +78,10 @@ def main(argv=None):
     ap.add_argument("--stage2-epochs", type=int, default=20)
     ap.add_argument("--stage2-lr", type=float, default=3e-4)
     ap.add_argument("--save2", default=None, help="write the second network's parameters (.npy)")
+    ap.add_argument("--load2", default=None,
+                    help="second network's parameters (.npy) to evaluate instead of training it")
+    ap.add_argument("--learned-max", type=int, default=2,
+                    help="most learned updates kept per band (0 = no limit)")
     args = ap.parse_args(argv)
     dev = torch.device("cuda:0")
     first = W.preconditioner_model(args.seed, nt=args.nt)
@@ -104,9 +109,14 @@ def main(argv=None):
             np.save(args.save, net.get_params().cpu().numpy())
     pre = LearnedPreconditioner(net, g.npml, scales)
     stage2 = None
-    if args.stage2 > 0:
+    if args.load2:
+        net2 = UNet(4, 32, 4, 2, H, Wd, max_batch=args.batch, device=dev)
+        net2.set_params(torch.from_numpy(np.load(args.load2).astype(np.float32)).to(dev))
+        stage2 = dict(stage2_loaded_params=args.load2)
+    elif args.stage2 > 0:
         net2, stage2 = _train_stage2(args, fd, wav, scales, g, net, pre, first)
-        if args.save2:
+    if stage2 is not None:
+        if args.save2 and not args.load2:
             np.save(args.save2, net2.get_params().cpu().numpy())
         stage2["single"] = pre
         pre = LearnedPreconditioner([net, net2], g.npml, scales)
@@ -193,11 +203,13 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
                      passes_plain=int(sum(h_plain.passes)), s_plain=t_plain)
         target = p["J_plain"]
         h_l, t_l = _fwi(fd, wl, obs, wl.f0, args.iters, pre=pre, stop=target, retry=args.retry,
-                        scales=[float(v) for v in args.scales.split(",")])
+                        scales=[float(v) for v in args.scales.split(",")],
+                        most=args.learned_max)
         one = {}
         if stage2 is not None:
             h_1, t_1 = _fwi(fd, wl, obs, wl.f0, args.iters, pre=stage2["single"], stop=target,
-                            retry=args.retry, scales=[float(v) for v in args.scales.split(",")])
+                            retry=args.retry, scales=[float(v) for v in args.scales.split(",")],
+                            most=args.learned_max)
             one = dict(it_learned1=len(h_1.misfit), ev_learned1=int(sum(h_1.evaluations)),
                        passes_learned1=int(sum(h_1.passes)), s_learned1=t_1,
                        reached1=bool(h_1.final_misfit <= target),
@@ -215,6 +227,7 @@ def _evaluate(args, fd, wav, pre, net, gen, g, seeds_eval, t_gen, gpu_gen, t_tr,
         "workload": f"precond_{g.nx}x{g.ny}_16shots_nt{g.nt}",
         "train_models": args.train, "val_models": args.val, "eval_models": args.eval,
         "loaded_params": args.load, "learned_retry": args.retry, "learned_scales": args.scales,
+        "learned_max": args.learned_max,
         "plain_rows_from": args.plain_from,
         "epochs": args.epochs, "batch": args.batch,
         "pair_generation_s": t_gen, "pair_generation_gpu_s": gpu_gen,

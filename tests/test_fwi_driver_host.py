@@ -118,9 +118,11 @@ def test_learned_stage_counts_kept_updates(no_cuda_sync):
     fd = QuadraticFD()
     pre = HalfwayPreconditioner(fd)
     mask = torch.ones(fd.shape)
-    drv = F.FWI(fd, lambda f0: None, mask, F.FWIConfig(bands=((4e8, 4),)), preconditioner=pre)
+    drv = F.FWI(fd, lambda f0: None, mask, F.FWIConfig(bands=((4e8, 4),), learned_max=0),
+                preconditioner=pre)
     _, _, hist = drv.run(fd.eps_true + 0.5, fd.sig_true * 0.5)
-    # every learned update lowers the quadratic misfit: all kept, stage = updates kept so far
+    # no cap: every learned update lowers the quadratic misfit: all kept, stage = updates kept
+    # so far
     assert pre.stages == [0, 1, 2, 3]
     assert hist.learned == [True] * 4
 
@@ -158,3 +160,15 @@ def test_preconditioner_selects_the_network_of_the_stage():
     one = LearnedPreconditioner(Const(3.0), npml=2)
     de, ds = one.update(z, z, z + 4.0, ill, stage=5)
     assert float(de[4, 5]) == 3.0 and float(de[0, 0]) == 0.0 and float(ds[1, 1]) == 0.0
+
+
+def test_learned_max_caps_the_kept_updates(no_cuda_sync):
+    fd = QuadraticFD()
+    pre = HalfwayPreconditioner(fd)
+    mask = torch.ones(fd.shape)
+    drv = F.FWI(fd, lambda f0: None, mask, F.FWIConfig(bands=((4e8, 5),), learned_max=2),
+                preconditioner=pre)
+    _, _, hist = drv.run(fd.eps_true + 0.5, fd.sig_true * 0.5)
+    # two updates kept, then the network is not consulted again in the band
+    assert pre.stages == [0, 1]
+    assert hist.learned == [True, True, False, False, False]
