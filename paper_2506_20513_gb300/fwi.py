@@ -20,8 +20,9 @@ driver keeps those pieces around a limited-memory BFGS update:
   illumination of the band's starting model (full size, then half); the update is kept only
   if the FDTD misfit decreases, otherwise the plain L-BFGS step is taken and the network is
   not consulted again in that band (its prediction no longer helps there, and each try costs
-  a forward model).  Accepted steps of either kind feed
-  the L-BFGS memory.
+  a forward model); after ``learned_max`` kept updates (default 2) the rest of the band is
+  plain L-BFGS too.  The k-th update of a band comes from the preconditioner's k-th network
+  where it holds several.  Accepted steps of either kind feed the L-BFGS memory.
 """
 from __future__ import annotations
 
