@@ -52,6 +52,41 @@ def test_training_pairs(setup):
         assert float(X[i, ..., 3].min()) >= 0.0
 
 
+def test_stage_pairs_at_the_updated_model(setup, dev):
+    """Pairs for a second network: features and target at the model the first network's
+    update reaches (masked below the top rows, eps_r >= 1), with the start model's
+    illumination."""
+    from paper_2506_20513_gb300.fwi import interior_mask
+    from paper_2506_20513_gb300.precond import (LearnedPreconditioner, PreconditionerScales,
+                                                generate_stage_pairs, seeded_models)
+    from paper_2506_20513_gb300.unet import UNet
+    fd, wl, wav, seeds, X, T = setup
+    g = wl.grid
+    p = g.npml
+    net = UNet(4, 32, 4, 2, 128, 256, max_batch=2, device=dev)
+    net.init_params(11)
+    pre = LearnedPreconditioner(net, p)
+    n = 3
+    X2, T2, _ = generate_stage_pairs(fd, seeded_models(seeds[:n], NT), n, wav,
+                                     PreconditionerScales(), p, pre, interior_mask(g, 4))
+    assert X2.shape == (n, 128, 256, 4) and T2.shape == (n, 128, 256, 2)
+    assert torch.isfinite(X2).all() and torch.isfinite(T2).all()
+    for i, s in enumerate(seeds[:n]):
+        w = W.preconditioner_model(s, nt=NT)
+        e1 = X2[i, ..., 2].double().cpu().numpy() * 10.0
+        e0 = w.eps_init[p:-p, p:-p]
+        # the update leaves the masked top rows alone and keeps eps_r >= 1
+        np.testing.assert_allclose(e1[:4], e0[:4], rtol=1e-6)
+        assert e1.min() >= 1.0 - 1e-6
+        assert np.abs(e1[4:] - e0[4:]).max() > 1e-3
+        # target: the truth minus the updated model
+        np.testing.assert_allclose(T2[i, ..., 0].cpu().numpy(), w.eps_true[p:-p, p:-p] - e1,
+                                   rtol=1e-5, atol=2e-5)
+        # the gradient is taken at the updated model, the illumination at the start model
+        assert not torch.equal(X2[i, ..., 0], X[i, ..., 0])
+        torch.testing.assert_close(X2[i, ..., 3], X[i, ..., 3], rtol=1e-5, atol=1e-6)
+
+
 def test_training_and_guarded_fwi_step(setup, dev):
     from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
     from paper_2506_20513_gb300.precond import LearnedPreconditioner, train
