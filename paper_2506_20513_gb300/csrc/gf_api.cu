@@ -489,6 +489,18 @@ int lanes_in_use(const gf_ctx* c) {
     return std::max(1, std::min(c->lanes, c->nshots));
 }
 
+// Destroy the lane streams and events (those that exist) and clear their handles.
+void release_lanes(gf_ctx* c) {
+    for (int l = 0; l < 4; ++l) {
+        if (c->lane_st[l]) cudaStreamDestroy(c->lane_st[l]);
+        if (c->lane_join[l]) cudaEventDestroy(c->lane_join[l]);
+        c->lane_st[l] = nullptr;
+        c->lane_join[l] = nullptr;
+    }
+    if (c->lane_fork) cudaEventDestroy(c->lane_fork);
+    c->lane_fork = nullptr;
+}
+
 // Restrict the tile launches of p to the lane's shots.
 void lane_params(const gf_ctx* c, gf::TileParams& p, const LaneRange& ln) {
     if (ln.n == 1) return;
@@ -508,12 +520,18 @@ int run_lanes(gf_ctx* c, cudaStream_t st, F&& body) {
             e = cudaStreamCreateWithFlags(&c->lane_st[l], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->lane_join[l], cudaEventDisableTiming);
         }
-        if (e != cudaSuccess) return cuda_fail(c, e, "lane streams");
+        if (e != cudaSuccess) {
+            // all or nothing: the next call creates the whole set again
+            release_lanes(c);
+            return cuda_fail(c, e, "lane streams");
+        }
     }
     GF_CUDA(c, cudaEventRecord(c->lane_fork, st), "fork lanes");
     int rc = GF_OK;
     for (int l = 0; l < n; ++l) {
-        GF_CUDA(c, cudaStreamWaitEvent(c->lane_st[l], c->lane_fork, 0), "fork lanes");
+        // a lane whose fork fails runs nothing but is still joined, like one whose body fails
+        cudaError_t e = cudaStreamWaitEvent(c->lane_st[l], c->lane_fork, 0);
+        if (e != cudaSuccess && rc == GF_OK) rc = cuda_fail(c, e, "fork lanes");
         const int s0 = (int)((long long)c->nshots * l / n);
         const int s1 = (int)((long long)c->nshots * (l + 1) / n);
         if (rc == GF_OK) rc = body(LaneRange{l, n, s0, s1, c->lane_st[l]});
@@ -1114,11 +1132,7 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
     cudaFree(c->d_cta_order);
-    for (int l = 0; l < 4; ++l) {
-        if (c->lane_st[l]) cudaStreamDestroy(c->lane_st[l]);
-        if (c->lane_join[l]) cudaEventDestroy(c->lane_join[l]);
-    }
-    if (c->lane_fork) cudaEventDestroy(c->lane_fork);
+    release_lanes(c);
     delete c;
 }
 
