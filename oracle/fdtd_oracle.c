@@ -41,6 +41,9 @@
  *   (the discrete counterpart of Eqs. grad_eps / grad_sigma), returned per relative
  *   permittivity (times eps0) and per S/m.
  *
+ * The TE mode an x- or y-polarised source excites (Ex, Ey, Hz) has its own forward model,
+ * or_forward_te_shot, at the end of this file.
+ *
  * Nothing here is tuned.  Shots are independent and may run on separate OpenMP threads;
  * the per-shot gradients are then summed in shot order, so results do not depend on the
  * thread count.
@@ -483,4 +486,116 @@ int or_misfit_gradient(const or_grid* g, const double* eps_r, const double* sigm
     *misfit = J;
     free(ge); free(gs); free(Js);
     return err ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * TE-mode forward model of one shot: the fields an x- or y-polarised hertzian line source
+ * excites (Sec. 3.2 source listing, polarisation 0 / 1; in 2-D they drive Ex, Ey, Hz,
+ * the dual of the TM mode above).
+ *   fields  Hz(i,j) at (i+1/2, j+1/2), Ex(i,j) at (i+1/2, j), Ey(i,j) at (i, j+1/2).
+ *   Faraday:  mu0 dHz/dt = dEx/dy - dEy/dx
+ *   Ampere:   eps dEx/dt + sigma Ex = dHz/dy - Jx,  eps dEy/dt + sigma Ey = -dHz/dx - Jy
+ *   Each E component takes Ca, Cb of the cell whose index it carries (the coefficient
+ *   listing evaluates every component's coefficients from the material at that index).
+ *   PEC walls on the outermost nodes: Ex is held at zero on rows j = 0 and j = ny-1, Ey on
+ *   columns i = 0 and i = nx-1 (their tangential components); Hz is updated for
+ *   0 <= i <= nx-2, 0 <= j <= ny-2; Ex for 0 <= i <= nx-2, 1 <= j <= ny-2; Ey for
+ *   1 <= i <= nx-2, 0 <= j <= ny-2.  PEC cells (sigma > 100 S/m) hold their E at zero.
+ *   CPML: the same profiles as the TM model; Hz's x difference sits on half-integer x
+ *   nodes (H profile), its y difference on half-integer y nodes; Ex's y difference of Hz on
+ *   integer y nodes (E profile), Ey's x difference on integer x nodes.
+ *   One step n: record Ex^n, Ey^n, Hz^{n-1/2} at the receiver cells; Hz update; E update;
+ *   the source enters the bracket of its component: Q(src) -= w^n / (dx dy).
+ * Outputs (each may be NULL):
+ *   traces [nt][nrec][3]   Ex^n, Ey^n, Hz^{n-1/2} at each receiver cell's nodes
+ *   energy [nt]            dx dy sum(eps (Ex^n^2 + Ey^n^2) + mu0 Hz^{n-1/2} Hz^{n+1/2}),
+ *                          conserved by the lossless scheme
+ * -------------------------------------------------------------------------------------*/
+int or_forward_te_shot(const or_grid* g, const double* eps_r, const double* sigma, int pol,
+                       int nsrc, const int32_t* src, const double* wav,
+                       int nrec, const int32_t* rec, double* traces, double* energy) {
+    const int nx = g->nx, ny = g->ny, nt = g->nt;
+    const size_t N = (size_t)nx * ny;
+    const double dx = g->dx, dy = g->dy, dt = g->dt;
+    const double Ch = dt / OR_MU0;
+    if (pol != 0 && pol != 1) return -2;
+    or_axis ax, ay;
+    if (or_axis_init(g, nx, dx, &ax) || or_axis_init(g, ny, dy, &ay)) return -1;
+    double *Ex = calloc(N, sizeof(double)), *Ey = calloc(N, sizeof(double)), *Hz = calloc(N, sizeof(double));
+    double *pHzx = calloc(N, sizeof(double)), *pHzy = calloc(N, sizeof(double));
+    double *pExy = calloc(N, sizeof(double)), *pEyx = calloc(N, sizeof(double));
+    double *Ca = calloc(N, sizeof(double)), *Cb = calloc(N, sizeof(double));
+    double *Qx = calloc(N, sizeof(double)), *Qy = calloc(N, sizeof(double));
+    if (!Ex || !Ey || !Hz || !pHzx || !pHzy || !pExy || !pEyx || !Ca || !Cb || !Qx || !Qy)
+        return -1;
+    /* per-cell coefficients without the ring rule (the walls are handled by the loop
+     * bounds below) */
+    for (size_t c = 0; c < N; ++c) {
+        if (sigma[c] > 100.0) { Ca[c] = 0.0; Cb[c] = 0.0; continue; }
+        double EA = OR_EPS0 * eps_r[c] / dt + 0.5 * sigma[c];
+        double EB = OR_EPS0 * eps_r[c] / dt - 0.5 * sigma[c];
+        Ca[c] = EB / EA;
+        Cb[c] = 1.0 / EA;
+    }
+    for (int n = 0; n < nt; ++n) {
+        if (traces)
+            for (int r = 0; r < nrec; ++r) {
+                const size_t c = (size_t)rec[2 * r + 1] * nx + rec[2 * r];
+                traces[((size_t)n * nrec + r) * 3 + 0] = Ex[c];
+                traces[((size_t)n * nrec + r) * 3 + 1] = Ey[c];
+                traces[((size_t)n * nrec + r) * 3 + 2] = Hz[c];
+            }
+        double wsum = 0.0;
+        if (energy)
+            for (size_t c = 0; c < N; ++c)
+                wsum += OR_EPS0 * eps_r[c] * (Ex[c] * Ex[c] + Ey[c] * Ey[c]);
+        /* magnetic field and its CPML memory */
+        for (int j = 0; j <= ny - 2; ++j)
+            for (int i = 0; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                double Dy = (Ex[c + nx] - Ex[c]) / dy;
+                double Dx = (Ey[c + 1] - Ey[c]) / dx;
+                pHzy[c] = ay.bH[j] * pHzy[c] + ay.cH[j] * Dy;
+                pHzx[c] = ax.bH[i] * pHzx[c] + ax.cH[i] * Dx;
+                double old = Hz[c];
+                Hz[c] = old + Ch * (Dy / ay.kH[j] + pHzy[c] - Dx / ax.kH[i] - pHzx[c]);
+                if (energy) wsum += OR_MU0 * old * Hz[c];
+            }
+        if (energy) energy[n] = wsum * dx * dy;
+        /* electric brackets and their CPML memory */
+        for (int j = 1; j <= ny - 2; ++j)
+            for (int i = 0; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                double D = (Hz[c] - Hz[c - nx]) / dy;
+                pExy[c] = ay.bE[j] * pExy[c] + ay.cE[j] * D;
+                Qx[c] = D / ay.kE[j] + pExy[c];
+            }
+        for (int j = 0; j <= ny - 2; ++j)
+            for (int i = 1; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                double D = (Hz[c] - Hz[c - 1]) / dx;
+                pEyx[c] = ax.bE[i] * pEyx[c] + ax.cE[i] * D;
+                Qy[c] = -(D / ax.kE[i] + pEyx[c]);
+            }
+        /* the source current enters the bracket of its component */
+        for (int s = 0; s < nsrc; ++s) {
+            size_t c = (size_t)src[2 * s + 1] * nx + src[2 * s];
+            double* Q = pol == 0 ? Qx : Qy;
+            Q[c] -= wav[(size_t)s * nt + n] / (dx * dy);
+        }
+        for (int j = 1; j <= ny - 2; ++j)
+            for (int i = 0; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                Ex[c] = Ca[c] * Ex[c] + Cb[c] * Qx[c];
+            }
+        for (int j = 0; j <= ny - 2; ++j)
+            for (int i = 1; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                Ey[c] = Ca[c] * Ey[c] + Cb[c] * Qy[c];
+            }
+    }
+    free(Ex); free(Ey); free(Hz); free(pHzx); free(pHzy); free(pExy); free(pEyx);
+    free(Ca); free(Cb); free(Qx); free(Qy);
+    or_axis_free(&ax); or_axis_free(&ay);
+    return 0;
 }

@@ -119,8 +119,10 @@ def _load():
             lib.or_misfit_gradient.argtypes = [g, pd, pd, ctypes.c_int, ctypes.c_int, pi, pd,
                                                ctypes.c_int, pi, pd, pd, pd, pd, pd,
                                                ctypes.c_int]
+            lib.or_forward_te_shot.argtypes = [g, pd, pd, ctypes.c_int, ctypes.c_int, pi, pd,
+                                               ctypes.c_int, pi, pd, pd]
             for f in (lib.or_forward_shot, lib.or_adjoint_shot, lib.or_tangent_shot,
-                      lib.or_forward, lib.or_misfit_gradient):
+                      lib.or_forward, lib.or_misfit_gradient, lib.or_forward_te_shot):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -194,6 +196,28 @@ def forward_shot(grid, eps_r, sigma, src, wav, rec, history=False, qhistory=Fals
                              _pd(out.get("h_traces")), _pd(out.get("ez_hist")),
                              _pd(out.get("q_hist")), _pd(out.get("energy")))
     _check(rc, "forward_shot")
+    return out
+
+
+def forward_te_shot(grid, eps_r, sigma, polarisation, src, wav, rec, energy=False):
+    """One shot of the TE mode (``polarisation`` 0: x-directed source current on Ex,
+    1: y-directed on Ey).  Returns ``traces`` [nt, nrec, 3] (Ex^n, Ey^n, Hz^{n-1/2} at the
+    receiver cells' nodes) and optionally ``energy`` [nt]."""
+    g = as_grid(grid)
+    lib = _load()
+    shape = (g.ny, g.nx)
+    e, s = _f64(eps_r, shape), _f64(sigma, shape)
+    src, rec = _i32(src).reshape(-1, 2), _i32(rec).reshape(-1, 2)
+    wav = _f64(wav).reshape(len(src), g.nt)
+    out = {"traces": np.zeros((g.nt, len(rec), 3))}
+    if energy:
+        out["energy"] = np.zeros(g.nt)
+    rc = lib.or_forward_te_shot(ctypes.byref(g.c_struct()), _pd(e), _pd(s), int(polarisation),
+                                len(src), _pi(src), _pd(wav), len(rec), _pi(rec),
+                                _pd(out["traces"]), _pd(out.get("energy")))
+    if rc == -2:
+        raise ValueError("polarisation must be 0 (x) or 1 (y)")
+    _check(rc, "forward_te_shot")
     return out
 
 
@@ -328,4 +352,34 @@ def line_source_trace(current: np.ndarray, dt: float, rho: float, eps_r: float,
     k = np.sqrt(wk * wk * MU0 * eps - 1j * wk * MU0 * sigma)
     k = np.where(k.imag > 0, -k, k)  # decaying branch: Im k <= 0 for e^{-j k rho}
     E[1:] = -(wk * MU0 / 4.0) * I[1:] * hankel2(0, k * rho)
+    return np.fft.irfft(E, nfft)[:n]
+
+
+def dipole_line_source_trace(current: np.ndarray, dt: float, rho: float, eps_r: float,
+                             sigma: float, along: bool, pad: int = 8) -> np.ndarray:
+    """E component parallel to an infinite x-directed line current I(t_n) = current[n]
+    (the TE mode's source), at distance rho on the line through the source perpendicular to
+    the current (``along`` False) or along it (``along`` True), homogeneous medium.
+
+    With the e^{+j w t} convention the vector potential A = x mu0 I G, G = -(j/4)
+    H0^(2)(k rho), gives E = -j w (A + grad div A / k^2), so
+    Ex = -j w mu0 I (G + d^2 G / dx^2 / k^2).  Off the current's line (x = 0) the second
+    derivative is G'(rho) / rho, and with dH0^(2)/dz = -H1^(2):
+        Ex = -(w mu0 / 4) I [H0^(2)(k rho) - H1^(2)(k rho) / (k rho)];
+    along it the second derivative is G''(rho), and with H0'' = -H0 + H1 / z:
+        Ex = -(w mu0 / 4) I H1^(2)(k rho) / (k rho)."""
+    from scipy.special import hankel2
+
+    n = len(current)
+    nfft = int(2 ** np.ceil(np.log2(n * pad)))
+    I = np.fft.rfft(current, nfft)
+    w = 2.0 * np.pi * np.fft.rfftfreq(nfft, dt)
+    E = np.zeros_like(I)
+    wk = w[1:]
+    eps = EPS0 * eps_r
+    k = np.sqrt(wk * wk * MU0 * eps - 1j * wk * MU0 * sigma)
+    k = np.where(k.imag > 0, -k, k)
+    z = k * rho
+    shape = hankel2(1, z) / z if along else hankel2(0, z) - hankel2(1, z) / z
+    E[1:] = -(wk * MU0 / 4.0) * I[1:] * shape
     return np.fft.irfft(E, nfft)[:n]

@@ -35,13 +35,29 @@ MUTANTS = [
      "traces[(size_t)n * nrec + r] = n > 0 ? ez_hist_unused_guard(Ez, rec, r, nx) : 0.0;"),
 ]
 
+# mistakes in the TE-mode forward model, caught by the pins of test_oracle_te_pins.py
+TE_MUTANTS = [
+    ("te_hz_update_sign", "Hz[c] = old + Ch * (Dy / ay.kH[j]", "Hz[c] = old - Ch * (Dy / ay.kH[j]"),
+    ("te_hz_cpml_term_dropped", "- Dx / ax.kH[i] - pHzx[c]);", "- Dx / ax.kH[i]);"),
+    ("te_ex_stencil_index", "double D = (Hz[c] - Hz[c - nx]) / dy;",
+     "double D = (Hz[c + nx] - Hz[c]) / dy;"),
+    ("te_ey_sign", "Qy[c] = -(D / ax.kE[i] + pEyx[c]);", "Qy[c] = (D / ax.kE[i] + pEyx[c]);"),
+    ("te_source_component", "double* Q = pol == 0 ? Qx : Qy;", "double* Q = pol == 0 ? Qy : Qx;"),
+    ("te_coefficient_cell", "Ex[c] = Ca[c] * Ex[c] + Cb[c] * Qx[c];",
+     "Ex[c] = Ca[c + 1] * Ex[c] + Cb[c + 1] * Qx[c];"),
+    ("te_receiver_node", "traces[((size_t)n * nrec + r) * 3 + 0] = Ex[c];",
+     "traces[((size_t)n * nrec + r) * 3 + 0] = Ex[c + 1];"),
+    ("te_source_scale", "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / (dx * dy);",
+     "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / dx;"),
+]
+
 PREAMBLE = "static double ez_hist_unused_guard(const double* E, const int32_t* rec, int r, int nx) { return 2.0 * E[(size_t)rec[2 * r + 1] * nx + rec[2 * r]]; }\n"
 
 PINS = ("energy or reciprocity or dot_product or analytic or zero_lag or fd_every_cell "
         "or tangent_linear or wavelet_gradient or cpml_reflection")
 
 
-def _run_mutant(tmp, name, a, b):
+def _run_mutant(tmp, name, a, b, pins_file="test_oracle_pins.py", pins=PINS):
     src = open(SRC).read()
     assert a in src, name
     mutated = src.replace("#define OR_MU0", PREAMBLE + "#define OR_MU0", 1).replace(a, b, 1)
@@ -51,7 +67,7 @@ def _run_mutant(tmp, name, a, b):
     lib = O.build(src=path, out=os.path.join(tmp, f"lib{name}.so"))
     env = dict(os.environ, GPRFWI_ORACLE_LIB=lib, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", PINS],
+                        os.path.join(ROOT, "tests", pins_file), "-k", pins],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     last = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else ""
     # caught = a pin assertion failed (not an import, collection or build error)
@@ -60,7 +76,8 @@ def _run_mutant(tmp, name, a, b):
 
 
 def test_every_planted_mistake_fails_a_pin(tmp_path):
+    te = [m + ("test_oracle_te_pins.py", "te_") for m in TE_MUTANTS]
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        results = list(ex.map(lambda m: _run_mutant(str(tmp_path), *m), MUTANTS))
+        results = list(ex.map(lambda m: _run_mutant(str(tmp_path), *m), MUTANTS + te))
     survivors = [(n, last) for n, caught, last in results if not caught]
     assert not survivors, f"mutants not caught by any pin: {survivors}"
