@@ -83,6 +83,8 @@ def parse_args():
                          "thread-staged operands, 0 = explicit im2col and mma.sync GEMMs")
     ap.add_argument("--fwi-iters", type=int, default=50,
                     help="L-BFGS iterations of the timed three-band FWI run (0 = skip)")
+    ap.add_argument("--no-te", action="store_true",
+                    help="skip the TE-mode forward model sub-record")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 2108x1084, 16-shot, nt 8000 checkpointed-gradient sub-record")
     ap.add_argument("--large-checkpoint", type=int, default=200,
@@ -470,6 +472,55 @@ def fwi_leg(args, fd, wl, eps_t, sig_t, eps0, sig0) -> dict:
                                     "line search included in the time)"}}
 
 
+# TE forward, bytes per cell and step that a design with one H launch and one E launch per
+# step must move: the H launch reads Ex, Ey, Hz and writes Hz (16 B), the E launch reads Hz,
+# Ex, Ey and writes Ex, Ey (20 B); Ca, Cb (one plane pair for all shots) stay in L2, the
+# CPML memories are touched in the strips only (not counted).
+TE_BYTES_PER_CELL_STEP = 36.0
+
+
+def te_leg(args, dev) -> dict:
+    """The TE-mode forward model (x-directed sources: Ex, Ey, Hz at the receivers) on the
+    benchmark's workload.  One warm-up call, three timed with CUDA events on the launching
+    stream around whole calls (2 nt launches, the field clears and the coefficient kernel)."""
+    import torch
+    from paper_2506_20513_gb300 import FDTD
+    from paper_2506_20513_gb300.fdtd import ricker
+    wl = workload(0, args.nshots, args.nt, "multishot")
+    g = wl.grid
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    t32 = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+    wav = t32(np.broadcast_to(ricker(wl.f0, g.dt, g.nt), (wl.nshots, 1, g.nt)))
+    e, s = t32(wl.eps_true), t32(wl.sig_true)
+    fd.forward_model_te(e, s, wav, 0)
+    torch.cuda.synchronize(dev)
+    l0 = fd.lib.gf_kernel_launches(fd.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    ev0.record()
+    for _ in range(reps):
+        fd.forward_model_te(e, s, wav, 0)
+    ev1.record()
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / reps
+    launches = (fd.lib.gf_kernel_launches(fd.ctx) - l0) // reps
+    fd.status()
+    fd.close()
+    cell_steps = wl.nshots * g.nt * (g.nx - 1) * (g.ny - 1)   # cells each step updates
+    peak, kind = hbm_peak()
+    achieved = TE_BYTES_PER_CELL_STEP * cell_steps / (ms / 1e3) / 1e9
+    return {"workload": f"{wl.name}_te_x", "grid": f"{g.nx}x{g.ny}", "nshots": wl.nshots,
+            "nt": g.nt, "nrec": wl.nrec, "polarisation": "x (traces of Ex, Ey, Hz)",
+            "ms_per_forward": ms,
+            "gcell_updates_per_s": wl.nshots * g.nt * g.ncells / ms / 1e6,
+            "launches_per_forward": int(launches), "steps": reps, "warmup": 1,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "te_h_kernel + te_e_kernel (whole calls)",
+                         "peak_source": f"hbm_gbs of {kind}",
+                         "algorithmic_bytes_per_cell_step": TE_BYTES_PER_CELL_STEP}}
+
+
 def large_leg(args, dev, sms: int) -> dict:
     """The large-grid checkpointed gradient: 2108x1084 cells (30-cell CPML inside), 16 shots,
     nt 8000, 400 receivers, forward wavefield checkpointed every ``args.large_checkpoint``
@@ -683,6 +734,9 @@ def ours(args):
     large = None
     if not args.no_large and world == 1:
         large = large_leg(args, dev, sms)
+    te_rec = None
+    if not args.no_te and world == 1 and args.workload == "multishot" and not args.checkpoint:
+        te_rec = te_leg(args, dev)
 
     if rank == 0:
         line = {
@@ -714,7 +768,7 @@ def ours(args):
                        "binding_roof": ("L2 / latency: the working set fits in L2, HBM is "
                                         "not the binding roof"
                                         if args.workload in ("disc", "precond") else "HBM")},
-            "roofline": roof, "large": large, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "large": large, "te": te_rec, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -190,6 +190,25 @@ int gf_forward_model_fields(gf_ctx* ctx, const float* eps_r, const float* sigma,
                             const float* wavelet, float* traces, float* h_traces, float* illum,
                             void* stream);
 
+/* Forward model of the TE mode: the fields of an x-directed (polarisation 0) or y-directed
+ * (polarisation 1) hertzian line source (Sec. 3.2 source listing, polarisations 0 and 1; in
+ * 2-D they excite Ex, Ey, Hz, while the z-directed source of the calls above drives the TM
+ * mode).  Same context, grid, CPML, acquisition and wavelet layout as gf_forward_model; the
+ * sources and receivers sit at the E node of their component in cell (i, j): Ex at
+ * (i+1/2, j), Ey at (i, j+1/2), Hz at (i+1/2, j+1/2).  Every E component takes Ca, Cb of the
+ * cell whose index it carries (the coefficient listing's per-index material); PEC walls on
+ * the outermost rows and columns; perfect conductors (sigma > 100 S/m) hold E at zero.
+ * One step n: record, H update, E update with the source current w^n / (dx dy) of the
+ * polarisation's component (as for Ez).
+ * traces: device [nshots][nt][nrec][3] written with Ex^n, Ey^n and Hz^{n-1/2} of each
+ * receiver cell (before step n's updates; zero at n = 0).  Forward only, one step per
+ * launch pair (no temporal blocking, no lanes); it uses the forward workspace's state
+ * buffers, so a wavefield stored by gf_forward is dropped (gf_adjoint then returns
+ * GF_ESTATE).  A bad model sets the status word (gf_status).  GF_EINVAL for a NULL
+ * pointer or another polarisation. */
+int gf_forward_model_te(gf_ctx* ctx, const float* eps_r, const float* sigma,
+                        const float* wavelet, int polarisation, float* traces, void* stream);
+
 /* Forward run that also stores the wavefield (mode GF_STORE_FULL) in the workspace for a
  * later gf_adjoint on the same model, wavelet and stream. */
 int gf_forward(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,

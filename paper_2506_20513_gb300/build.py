@@ -12,7 +12,7 @@ BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libgprfwi.so")
 SOURCES = ("gf_api.cu", "gf_tile_kernels.cu", "gf_flow_kernels.cu", "gf_misc_kernels.cu",
            "gf_noalloc.cu", "gf_tv.cu", "gf_nn.cu", "gf_nn_tc.cu", "gf_unet.cu",
-           "gf_reconstruct.cu")
+           "gf_reconstruct.cu", "gf_te.cu")
 HEADERS = ("gf_internal.cuh", "gf_tile_common.cuh", "gf_nn.cuh")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

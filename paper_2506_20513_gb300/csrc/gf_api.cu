@@ -59,6 +59,7 @@ struct gf_ctx {
     long long Np;             // pitch * ny
     float* d_prof = nullptr;  // [12][max(nx, ny)] profiles (x: 6 arrays, y: 6 arrays)
     int2* d_src_xy = nullptr;  // [nshots][nsrc] source cells (x, y)
+    int2* d_rec_xy = nullptr;  // [nshots][nrec] receiver cells (x, y), made by the TE model
     gf::AxisProfile px{}, py{};
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -1129,6 +1130,7 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_prof);
     cudaFree(c->d_src_xy);
     cudaFree(c->d_ring_map);
+    cudaFree(c->d_rec_xy);
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
     cudaFree(c->d_cta_order);
@@ -1288,6 +1290,80 @@ int gf_forward_model_fields(gf_ctx* c, const float* eps_r, const float* sigma,
     DeviceGuard guard(c->device);
     return run_forward(c, eps_r, sigma, wavelet, traces, illum, false, (cudaStream_t)stream,
                        h_traces);
+}
+
+int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
+                        const float* wavelet, int polarisation, float* traces, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!eps_r || !sigma || !wavelet || !traces)
+        return fail(c, GF_EINVAL, "NULL model, wavelet or traces pointer");
+    if (polarisation != 0 && polarisation != 1)
+        return fail(c, GF_EINVAL, "polarisation %d: 0 (x-directed) or 1 (y-directed)",
+                    polarisation);
+    const long long cells = (long long)c->nshots * (c->g.nx - 1) * (c->g.ny - 1);
+    if ((cells + (long long)c->nshots * c->nrec) / 256 + 2 > 0x7fffffffLL)
+        return fail(c, GF_EINVAL, "TE model: %lld cells exceed one launch", cells);
+    if (c->rec) return fail(c, GF_ESTATE, "the TE model is not part of a batch schedule");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_workspace(c, true);
+    if (rc) return rc;
+    if (!c->d_rec_xy) {
+        std::vector<int2> rxy(c->h_rec.size());
+        for (size_t k = 0; k < rxy.size(); ++k)
+            rxy[k] = make_int2(c->h_rec[k] % c->g.nx, c->h_rec[k] / c->g.nx);
+        GF_CUDA(c, cudaMalloc(&c->d_rec_xy, rxy.size() * sizeof(int2)), "receiver table");
+        GF_CUDA(c, cudaMemcpy(c->d_rec_xy, rxy.data(), rxy.size() * sizeof(int2),
+                              cudaMemcpyHostToDevice), "receiver table");
+    }
+    // the TE fields reuse the forward workspace's state buffers: a stored TM forward is gone
+    c->have_forward = false;
+    const Layout L = layout_of(c, true);
+    const long long F = (long long)c->nshots * c->Np;
+    float* a = (float*)(c->ws + L.stA);
+    float* b = (float*)(c->ws + L.stB);
+    gf::TeParams p{};
+    p.nx = c->g.nx;
+    p.ny = c->g.ny;
+    p.pitch = c->pitch;
+    p.nshots = c->nshots;
+    p.nsrc = c->nsrc;
+    p.nrec = c->nrec;
+    p.nt = c->g.nt;
+    p.pol = polarisation;
+    p.Np = c->Np;
+    p.ch = (float)(c->g.dt / kMu0);
+    p.src_scale = (float)(1.0 / (c->g.dx * c->g.dy));
+    p.px = c->px;
+    p.py = c->py;
+    p.ex = a;
+    p.ey = a + F;
+    p.hz0 = a + 2 * F;
+    p.psi_hzx = a + 3 * F;
+    p.psi_hzy = a + 4 * F;
+    p.psi_exy = a + 5 * F;
+    p.psi_eyx = a + 6 * F;
+    p.hz1 = b;
+    p.ca = (const float*)(c->ws + L.coef);
+    p.cb = p.ca + c->Np;
+    p.wavelet = wavelet;
+    p.src_xy = c->d_src_xy;
+    p.rec_xy = c->d_rec_xy;
+    p.traces = traces;
+    int* status = (int*)(c->ws + L.status);
+    float* ca = (float*)(c->ws + L.coef);
+    const int nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+    const float dt_eps0 = (float)(c->g.dt / kEps0);
+    const long long Np = c->Np;
+    GF_OP(c, st, -1, "clear TE fields", cudaMemsetAsync(a, 0, 7 * sizeof(float) * F, s_));
+    GF_OP(c, st, -1, "clear TE fields", cudaMemsetAsync(b, 0, sizeof(float) * F, s_));
+    GF_OP(c, st, GF_KERNEL_AUX, "TE coefficients",
+          gf::launch_te_coef(eps_r, sigma, nx, ny, pitch, dt_eps0, ca, ca + Np, status, s_));
+    for (int n = 0; n < c->g.nt; ++n) {
+        GF_OP(c, st, GF_KERNEL_FWD, "TE H update", gf::launch_te_h(p, n, s_));
+        GF_OP(c, st, GF_KERNEL_FWD, "TE E update", gf::launch_te_e(p, n, s_));
+    }
+    return GF_OK;
 }
 
 int gf_forward(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,

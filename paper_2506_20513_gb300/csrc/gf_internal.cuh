@@ -157,6 +157,28 @@ cudaError_t adam_update(long long n, float* x, const float* g, float* m, float* 
                         int t, float xmin, cudaStream_t st);
 cudaError_t tv_gradient(int nx, int ny, const float* X, float* G, float* scratch, float lambda,
                         float mu, int iters, float weight, cudaStream_t st);
+// TE-mode forward model (gf_te.cu): fields of every shot as [nshots][ny][pitch] planes,
+// CPML memory planes touched only inside the strips, Hz in two buffers (step n reads hz0 if
+// n is even, else hz1, and writes the other).
+struct TeParams {
+    int nx, ny, pitch, nshots, nsrc, nrec, nt, pol;  // pol: 0 = x-directed source, 1 = y
+    long long Np;        // pitch * ny
+    float ch;            // dt / mu0
+    float src_scale;     // 1 / (dx dy)
+    AxisProfile px, py;
+    float *ex, *ey, *hz0, *hz1, *psi_hzx, *psi_hzy, *psi_exy, *psi_eyx;
+    const float* ca;     // [ny][pitch] Ca, Cb without the TM ring rule
+    const float* cb;
+    const float* wavelet;  // [nshots][nsrc][nt]
+    const int2* src_xy;    // [nshots][nsrc]
+    const int2* rec_xy;    // [nshots][nrec]
+    float* traces;         // [nshots][nt][nrec][3]: Ex^n, Ey^n, Hz^{n-1/2}
+};
+cudaError_t launch_te_coef(const float* eps_r, const float* sigma, int nx, int ny, int pitch,
+                           float dt_eps0, float* ca, float* cb, int* status, cudaStream_t st);
+// one time step: the H launch (with the receivers of step n), then the E launch
+cudaError_t launch_te_h(const TeParams& p, int n, cudaStream_t st);
+cudaError_t launch_te_e(const TeParams& p, int n, cudaStream_t st);
 // Reverse-time reconstruction inside checkpoint segments (gf_reconstruct.cu).  ring_map:
 // [ny][nx] ring index of each cell (-1 outside the ring); a ring slot holds Ez, Hx, Hy of the
 // ring cells of every shot ([3][nshots][ring_cells]).

@@ -198,6 +198,18 @@ class FDTD:
         out = (tr,) + ((ill,) if illumination else ()) + ((h,) if fields else ())
         return out if len(out) > 1 else tr
 
+    def forward_model_te(self, eps_r, sigma, wavelet, polarisation: int = 0):
+        """Traces of the TE mode [nshots, nt, nrec, 3] (Ex^n, Ey^n, Hz^{n-1/2} at each receiver
+        cell's nodes) for x-directed (``polarisation`` 0) or y-directed (1) sources."""
+        e, s = self._model(eps_r, sigma)
+        w = self._wavelet(wavelet)
+        self._workspace(full=False)
+        tr = torch.empty(self.trace_shape + (3,), dtype=torch.float32, device=self.device)
+        rc = self.lib.gf_forward_model_te(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(),
+                                          int(polarisation), tr.data_ptr(), self._stream())
+        _lib.check(self.lib, self.ctx, rc)
+        return tr
+
     def misfit_and_gradient(self, eps_r, sigma, wavelet, observed, return_traces: bool = False):
         """J = 1/2 sum (d - o)^2 (FP64 device scalar), dJ/deps_r and dJ/dsigma [ny, nx].
 
