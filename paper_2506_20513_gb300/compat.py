@@ -11,7 +11,9 @@ Readings of the parameters (the paper lists names and example values only):
 * positions are metres from the array origin, converted to cells by rounding x/dx half up;
 * shot s (s = 0 .. step-1) has its source at source_location + s * source_step; the nrx
   receivers of every shot are at receiver_location + r * receiver_step (r = 0 .. nrx-1);
-* source = ['hertzian', 'z']: a z-polarised line source; source_amplitudes =
+* source = ['hertzian', 'z']: a z-polarised line source (TM mode, Ez traces, differentiable);
+  ['hertzian', 'x'] or ['hertzian', 'y']: an x- or y-polarised one (TE mode, traces of Ex or
+  Ey, forward only: no TE adjoint is built); source_amplitudes =
   ['ricker', A, f0]: a Ricker wavelet of amplitude A and peak frequency f0, replaced by
   ``freq`` when that is given (a multiscale band, Sec. 3.4);
 * time_windows / dt steps (rounded); miu must be 1 (relative permeability is not inverted).
@@ -61,9 +63,15 @@ def compute(device, dx, ny, nx, nz, time_windows, source, source_location, sourc
             sigma, miu, nsrc, nrx, freq, dt, dy=None):
     """traces [step, nt, nrx] (differentiable in epsilon and sigma) and the time axis."""
     if nz != 1:
-        raise ValueError("2-D TM only: nz must be 1")
-    if list(source) != ["hertzian", "z"]:
-        raise ValueError("only a z-polarised line source ('hertzian', 'z') is supported")
+        raise ValueError("2-D only: nz must be 1")
+    pols = {"x": 0, "y": 1, "z": None}
+    if len(source) != 2 or source[0] != "hertzian" or source[1] not in pols:
+        raise ValueError("source must be ['hertzian', 'x' | 'y' | 'z']")
+    pol = pols[source[1]]
+    if pol is not None and torch.is_grad_enabled() and (
+            getattr(epsilon, "requires_grad", False) or getattr(sigma, "requires_grad", False)):
+        raise ValueError("the x- and y-polarised (TE) model is forward only: run it without "
+                         "gradients (torch.no_grad() or detached epsilon and sigma)")
     kind, amp, f0 = source_amplitudes
     if kind != "ricker":
         raise ValueError("only Ricker source amplitudes are supported")
@@ -81,7 +89,10 @@ def compute(device, dx, ny, nx, nz, time_windows, source, source_location, sourc
             raise ValueError(f"{name} must be [nx, ny, 1] = [{nx}, {ny}, 1]")
     src, rec = paper_geometry(dx, dy, nx, ny, source_location, source_step, receiver_location,
                               receiver_step, step, nsrc, nrx)
-    key = (str(dev), nx, ny, pmlthick, nt, dx, dy, dt, f0, src.tobytes(), rec.tobytes())
+    # one context per source kind: a TE call would drop the TM forward an autograd backward
+    # still needs
+    key = (str(dev), nx, ny, pmlthick, nt, dx, dy, dt, f0, src.tobytes(), rec.tobytes(),
+           pol is None)
     fd = _contexts.get(key)
     if fd is None:
         g = default_pml(GridSpec(nx=nx, ny=ny, npml=pmlthick, nt=nt, dx=dx, dy=dy, dt=dt), f0)
@@ -90,6 +101,10 @@ def compute(device, dx, ny, nx, nz, time_windows, source, source_location, sourc
     wav = torch.tensor(float(amp) * ricker(f0, dt, nt), dtype=torch.float32, device=dev)
     eps2 = epsilon[:, :, 0].transpose(0, 1).to(dev, torch.float32).contiguous()
     sig2 = sigma[:, :, 0].transpose(0, 1).to(dev, torch.float32).contiguous()
-    traces = FDTDFunction.apply(eps2, sig2, fd, wav)
+    if pol is None:
+        traces = FDTDFunction.apply(eps2, sig2, fd, wav)
+    else:
+        # the source's own component of the TE traces (Ex for 'x', Ey for 'y')
+        traces = fd.forward_model_te(eps2, sig2, wav, pol)[..., pol].contiguous()
     t = torch.arange(nt, dtype=torch.float64) * dt
     return traces, t

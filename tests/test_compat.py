@@ -109,3 +109,43 @@ def test_paper_demo_loop_with_adam_reduces_the_loss():
             sigma.clamp_(min=0.0)
         losses.append(float(loss.detach()))
     assert losses[-1] < 0.8 * losses[0]
+
+
+@pytest.mark.gpu
+def test_compute_with_x_and_y_polarised_sources():
+    """['hertzian', 'x' | 'y'] runs the TE model: the traces are the source component of
+    forward_model_te; asking for gradients is refused (no TE adjoint)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_20513_gb300 import FDTD
+    from paper_2506_20513_gb300.compat import compute
+    from paper_2506_20513_gb300.fdtd import ricker
+    from paper_2506_20513_gb300.workloads import GridSpec, default_pml
+    dev = torch.device("cuda:0")
+    nx, ny, pml, dx, dt, f0 = 60, 40, 8, 0.02, 4e-11, 4e8
+    rng = np.random.default_rng(4)
+    eps = torch.tensor(4 + 3 * rng.random((nx, ny, 1)), dtype=torch.float32, device=dev)
+    sig = torch.tensor(1e-3 + 1e-2 * rng.random((nx, ny, 1)), dtype=torch.float32, device=dev)
+    args = dict(device="cuda", dx=dx, ny=ny, nx=nx, nz=1, time_windows=200 * dt,
+                source_location=[0.2, 0.2, 0], source_step=[0.2, 0, 0],
+                receiver_location=[0.2, 0.6, 0], receiver_step=[0.04, 0, 0], pmlthick=pml,
+                source_amplitudes=["ricker", 2.0, f0], step=3, epsilon=eps, sigma=sig, miu=1,
+                nsrc=1, nrx=20, freq=None, dt=dt)
+    src, rec = paper_geometry(dx, dx, nx, ny, [0.2, 0.2, 0], [0.2, 0, 0], [0.2, 0.6, 0],
+                              [0.04, 0, 0], 3, 1, 20)
+    g = default_pml(GridSpec(nx=nx, ny=ny, npml=pml, nt=200, dx=dx, dy=dx, dt=dt), f0)
+    fd = FDTD(g, src, rec, device=dev)
+    wav = torch.tensor(2.0 * ricker(f0, dt, 200), dtype=torch.float32, device=dev)
+    e2 = eps[:, :, 0].transpose(0, 1).contiguous()
+    s2 = sig[:, :, 0].transpose(0, 1).contiguous()
+    for pol, name in ((0, "x"), (1, "y")):
+        tr, t = compute(source=["hertzian", name], **args)
+        assert tr.shape == (3, 200, 20) and t.shape == (200,)
+        ref = fd.forward_model_te(e2, s2, wav, pol)[..., pol]
+        assert torch.equal(tr, ref)
+        assert float(tr.abs().max()) > 0
+    fd.close()
+    with pytest.raises(ValueError):
+        compute(source=["hertzian", "x"], **dict(args, epsilon=eps.clone().requires_grad_()))
+    with pytest.raises(ValueError):
+        compute(source=["hertzian", "w"], **args)
