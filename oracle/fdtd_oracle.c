@@ -510,10 +510,12 @@ int or_misfit_gradient(const or_grid* g, const double* eps_r, const double* sigm
  *   traces [nt][nrec][3]   Ex^n, Ey^n, Hz^{n-1/2} at each receiver cell's nodes
  *   energy [nt]            dx dy sum(eps (Ex^n^2 + Ey^n^2) + mu0 Hz^{n-1/2} Hz^{n+1/2}),
  *                          conserved by the lossless scheme
+ *   ex_hist, ey_hist [(nt+1)][ny*nx]   Ex^0 .. Ex^nt and Ey^0 .. Ey^nt (for the adjoint)
  * -------------------------------------------------------------------------------------*/
 int or_forward_te_shot(const or_grid* g, const double* eps_r, const double* sigma, int pol,
                        int nsrc, const int32_t* src, const double* wav,
-                       int nrec, const int32_t* rec, double* traces, double* energy) {
+                       int nrec, const int32_t* rec, double* traces, double* energy,
+                       double* ex_hist, double* ey_hist) {
     const int nx = g->nx, ny = g->ny, nt = g->nt;
     const size_t N = (size_t)nx * ny;
     const double dx = g->dx, dy = g->dy, dt = g->dt;
@@ -537,6 +539,8 @@ int or_forward_te_shot(const or_grid* g, const double* eps_r, const double* sigm
         Ca[c] = EB / EA;
         Cb[c] = 1.0 / EA;
     }
+    if (ex_hist) memset(ex_hist, 0, N * sizeof(double));
+    if (ey_hist) memset(ey_hist, 0, N * sizeof(double));
     for (int n = 0; n < nt; ++n) {
         if (traces)
             for (int r = 0; r < nrec; ++r) {
@@ -593,9 +597,108 @@ int or_forward_te_shot(const or_grid* g, const double* eps_r, const double* sigm
                 size_t c = (size_t)j * nx + i;
                 Ey[c] = Ca[c] * Ey[c] + Cb[c] * Qy[c];
             }
+        if (ex_hist) memcpy(ex_hist + (size_t)(n + 1) * N, Ex, N * sizeof(double));
+        if (ey_hist) memcpy(ey_hist + (size_t)(n + 1) * N, Ey, N * sizeof(double));
     }
     free(Ex); free(Ey); free(Hz); free(pHzx); free(pHzy); free(pExy); free(pEyx);
     free(Ca); free(Cb); free(Qx); free(Qy);
+    or_axis_free(&ax); or_axis_free(&ay);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Exact discrete adjoint of or_forward_te_shot for one shot, driven by the residual of the
+ * source's own component: resid [nt][nrec] = dJ/d(E_pol^n at receiver r) (Ex for
+ * polarisation 0, Ey for 1).  Needs ex_hist and ey_hist.  Every forward operation is
+ * transposed in reverse order: for n = nt-1 .. 0, the E updates (with their CPML memories),
+ * then the Hz update (with its memories), then the recording of step n.  Adjoint fields
+ * aEx, aEy hold dJ/dE^{n+1} on entry to step n's reversal and dJ/dE^n after it; aHz holds
+ * dJ/dHz^{n+1/2}, then dJ/dHz^{n-1/2}.  The CPML memories' adjoints follow the recursion
+ * backwards: A_n = b A_{n+1} + (cotangent of the bracket that uses the memory of step n).
+ * Gradients (ADDED to g_eps_r, per unit relative permittivity, and g_sigma, per S/m), the
+ * zero-lag form of both E components of each cell, lam = Cb aE^{n+1}:
+ *   dJ/deps_r += -sum_n lam (E^{n+1} - E^n) eps0 / dt,  dJ/dsigma += -sum_n lam (E^{n+1} + E^n) / 2
+ * (the derivative of the update's residual EA E^{n+1} - EB E^n - Q).
+ * -------------------------------------------------------------------------------------*/
+int or_adjoint_te_shot(const or_grid* g, const double* eps_r, const double* sigma, int pol,
+                       int nrec, const int32_t* rec, const double* resid,
+                       const double* ex_hist, const double* ey_hist,
+                       double* g_eps_r, double* g_sigma) {
+    const int nx = g->nx, ny = g->ny, nt = g->nt;
+    const size_t N = (size_t)nx * ny;
+    const double dx = g->dx, dy = g->dy, dt = g->dt;
+    const double Ch = dt / OR_MU0;
+    if (pol != 0 && pol != 1) return -2;
+    or_axis ax, ay;
+    if (or_axis_init(g, nx, dx, &ax) || or_axis_init(g, ny, dy, &ay)) return -1;
+    double *aEx = calloc(N, sizeof(double)), *aEy = calloc(N, sizeof(double)), *aHz = calloc(N, sizeof(double));
+    double *aPExy = calloc(N, sizeof(double)), *aPEyx = calloc(N, sizeof(double));
+    double *aPHzx = calloc(N, sizeof(double)), *aPHzy = calloc(N, sizeof(double));
+    double *Ca = calloc(N, sizeof(double)), *Cb = calloc(N, sizeof(double));
+    if (!aEx || !aEy || !aHz || !aPExy || !aPEyx || !aPHzx || !aPHzy || !Ca || !Cb) return -1;
+    for (size_t c = 0; c < N; ++c) {
+        if (sigma[c] > 100.0) { Ca[c] = 0.0; Cb[c] = 0.0; continue; }
+        double EA = OR_EPS0 * eps_r[c] / dt + 0.5 * sigma[c];
+        double EB = OR_EPS0 * eps_r[c] / dt - 0.5 * sigma[c];
+        Ca[c] = EB / EA;
+        Cb[c] = 1.0 / EA;
+    }
+    for (int n = nt - 1; n >= 0; --n) {
+        const double *X1 = ex_hist + (size_t)(n + 1) * N, *X0 = ex_hist + (size_t)n * N;
+        const double *Y1 = ey_hist + (size_t)(n + 1) * N, *Y0 = ey_hist + (size_t)n * N;
+        /* E updates of step n, reversed (Ex: rows 1..ny-2, columns 0..nx-2) */
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = (size_t)j * nx + i;
+                if (j < 1 || j > ny - 2 || i > nx - 2) { aEx[c] = 0.0; continue; } /* held */
+                double ae = aEx[c];
+                double lam = Cb[c] * ae;
+                if (g_eps_r) g_eps_r[c] += -lam * (X1[c] - X0[c]) * OR_EPS0 / dt;
+                if (g_sigma) g_sigma[c] += -lam * 0.5 * (X1[c] + X0[c]);
+                /* Qx = D / k + psi, psi = b psi_prev + c D, D = (Hz[c] - Hz[c-nx]) / dy */
+                aPExy[c] = ay.bE[j] * aPExy[c] + lam;
+                double aD = ay.cE[j] * aPExy[c] + lam / ay.kE[j];
+                aHz[c] += aD / dy;
+                aHz[c - nx] -= aD / dy;
+                aEx[c] = Ca[c] * ae;
+            }
+        /* Ey: rows 0..ny-2, columns 1..nx-2; Qy = -(D / k + psi), D = (Hz[c] - Hz[c-1]) / dx */
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t c = (size_t)j * nx + i;
+                if (j > ny - 2 || i < 1 || i > nx - 2) { aEy[c] = 0.0; continue; }
+                double ae = aEy[c];
+                double lam = Cb[c] * ae;
+                if (g_eps_r) g_eps_r[c] += -lam * (Y1[c] - Y0[c]) * OR_EPS0 / dt;
+                if (g_sigma) g_sigma[c] += -lam * 0.5 * (Y1[c] + Y0[c]);
+                aPEyx[c] = ax.bE[i] * aPEyx[c] - lam;
+                double aD = ax.cE[i] * aPEyx[c] - lam / ax.kE[i];
+                aHz[c] += aD / dx;
+                aHz[c - 1] -= aD / dx;
+                aEy[c] = Ca[c] * ae;
+            }
+        /* Hz update of step n, reversed: Hz^{n+1/2} = Hz^{n-1/2} + Ch (Dy / ky + psi_y
+         * - Dx / kx - psi_x), Dy = (Ex[c+nx] - Ex[c]) / dy, Dx = (Ey[c+1] - Ey[c]) / dx */
+        for (int j = 0; j <= ny - 2; ++j)
+            for (int i = 0; i <= nx - 2; ++i) {
+                size_t c = (size_t)j * nx + i;
+                double ah = Ch * aHz[c];
+                aPHzy[c] = ay.bH[j] * aPHzy[c] + ah;
+                double aDy = ay.cH[j] * aPHzy[c] + ah / ay.kH[j];
+                aPHzx[c] = ax.bH[i] * aPHzx[c] - ah;
+                double aDx = ax.cH[i] * aPHzx[c] - ah / ax.kH[i];
+                aEx[c + nx] += aDy / dy;
+                aEx[c] -= aDy / dy;
+                aEy[c + 1] += aDx / dx;
+                aEy[c] -= aDx / dx;
+            }
+        /* recording of step n: d^n = E_pol^n at the receivers */
+        double* aE = pol == 0 ? aEx : aEy;
+        for (int r = 0; r < nrec; ++r)
+            aE[(size_t)rec[2 * r + 1] * nx + rec[2 * r]] += resid[(size_t)n * nrec + r];
+    }
+    free(aEx); free(aEy); free(aHz); free(aPExy); free(aPEyx); free(aPHzx); free(aPHzy);
+    free(Ca); free(Cb);
     or_axis_free(&ax); or_axis_free(&ay);
     return 0;
 }

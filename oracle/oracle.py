@@ -120,9 +120,12 @@ def _load():
                                                ctypes.c_int, pi, pd, pd, pd, pd, pd,
                                                ctypes.c_int]
             lib.or_forward_te_shot.argtypes = [g, pd, pd, ctypes.c_int, ctypes.c_int, pi, pd,
-                                               ctypes.c_int, pi, pd, pd]
+                                               ctypes.c_int, pi, pd, pd, pd, pd]
+            lib.or_adjoint_te_shot.argtypes = [g, pd, pd, ctypes.c_int, ctypes.c_int, pi, pd,
+                                               pd, pd, pd, pd]
             for f in (lib.or_forward_shot, lib.or_adjoint_shot, lib.or_tangent_shot,
-                      lib.or_forward, lib.or_misfit_gradient, lib.or_forward_te_shot):
+                      lib.or_forward, lib.or_misfit_gradient, lib.or_forward_te_shot,
+                      lib.or_adjoint_te_shot):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -199,10 +202,12 @@ def forward_shot(grid, eps_r, sigma, src, wav, rec, history=False, qhistory=Fals
     return out
 
 
-def forward_te_shot(grid, eps_r, sigma, polarisation, src, wav, rec, energy=False):
+def forward_te_shot(grid, eps_r, sigma, polarisation, src, wav, rec, energy=False,
+                    history=False):
     """One shot of the TE mode (``polarisation`` 0: x-directed source current on Ex,
     1: y-directed on Ey).  Returns ``traces`` [nt, nrec, 3] (Ex^n, Ey^n, Hz^{n-1/2} at the
-    receiver cells' nodes) and optionally ``energy`` [nt]."""
+    receiver cells' nodes) and optionally ``energy`` [nt] and ``ex_hist``, ``ey_hist``
+    [nt+1, ny, nx]."""
     g = as_grid(grid)
     lib = _load()
     shape = (g.ny, g.nx)
@@ -212,13 +217,56 @@ def forward_te_shot(grid, eps_r, sigma, polarisation, src, wav, rec, energy=Fals
     out = {"traces": np.zeros((g.nt, len(rec), 3))}
     if energy:
         out["energy"] = np.zeros(g.nt)
+    if history:
+        out["ex_hist"] = np.zeros((g.nt + 1,) + shape)
+        out["ey_hist"] = np.zeros((g.nt + 1,) + shape)
     rc = lib.or_forward_te_shot(ctypes.byref(g.c_struct()), _pd(e), _pd(s), int(polarisation),
                                 len(src), _pi(src), _pd(wav), len(rec), _pi(rec),
-                                _pd(out["traces"]), _pd(out.get("energy")))
+                                _pd(out["traces"]), _pd(out.get("energy")),
+                                _pd(out.get("ex_hist")), _pd(out.get("ey_hist")))
     if rc == -2:
         raise ValueError("polarisation must be 0 (x) or 1 (y)")
     _check(rc, "forward_te_shot")
     return out
+
+
+def adjoint_te_shot(grid, eps_r, sigma, polarisation, rec, resid, ex_hist, ey_hist):
+    """Exact adjoint of :func:`forward_te_shot` for the residual of the source's own
+    component, resid [nt, nrec]; returns (dJ/deps_r, dJ/dsigma) [ny, nx]."""
+    g = as_grid(grid)
+    lib = _load()
+    shape = (g.ny, g.nx)
+    e, s = _f64(eps_r, shape), _f64(sigma, shape)
+    rec = _i32(rec).reshape(-1, 2)
+    r = _f64(resid).reshape(g.nt, len(rec))
+    xh = _f64(ex_hist).reshape((g.nt + 1,) + shape)
+    yh = _f64(ey_hist).reshape((g.nt + 1,) + shape)
+    ge, gs = np.zeros(shape), np.zeros(shape)
+    rc = lib.or_adjoint_te_shot(ctypes.byref(g.c_struct()), _pd(e), _pd(s), int(polarisation),
+                                len(rec), _pi(rec), _pd(r), _pd(xh), _pd(yh), _pd(ge), _pd(gs))
+    if rc == -2:
+        raise ValueError("polarisation must be 0 (x) or 1 (y)")
+    _check(rc, "adjoint_te_shot")
+    return ge, gs
+
+
+def misfit_and_gradient_te(grid, eps_r, sigma, polarisation, src, wav, rec, observed):
+    """J = 1/2 sum (d - o)^2 over the source component's traces of every shot, and its
+    gradients summed over shots (in shot order).  src [nshots,nsrc,2], wav [nshots,nsrc,nt],
+    rec [nshots,nrec,2], observed [nshots,nt,nrec]."""
+    src = np.asarray(src)
+    J = 0.0
+    ge = gs = None
+    for k in range(len(src)):
+        out = forward_te_shot(grid, eps_r, sigma, polarisation, src[k], wav[k], rec[k],
+                              history=True)
+        r = out["traces"][:, :, polarisation] - np.asarray(observed[k], dtype=np.float64)
+        J += 0.5 * float(np.sum(r * r))
+        a, b = adjoint_te_shot(grid, eps_r, sigma, polarisation, rec[k], r, out["ex_hist"],
+                               out["ey_hist"])
+        ge = a if ge is None else ge + a
+        gs = b if gs is None else gs + b
+    return J, ge, gs
 
 
 def adjoint_shot(grid, eps_r, sigma, src, rec, resid, ez_hist, q_hist=None):

@@ -49,6 +49,14 @@ TE_MUTANTS = [
      "traces[((size_t)n * nrec + r) * 3 + 0] = Ex[c + 1];"),
     ("te_source_scale", "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / (dx * dy);",
      "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / dx;"),
+    # ... and in its adjoint
+    ("te_adj_psi_decay_dropped", "aPHzx[c] = ax.bH[i] * aPHzx[c] - ah;", "aPHzx[c] = -ah;"),
+    ("te_adj_transposed_index", "aHz[c - 1] -= aD / dx;", "aHz[c + 1] -= aD / dx;"),
+    ("te_adj_gradient_sign", "if (g_sigma) g_sigma[c] += -lam * 0.5 * (Y1[c] + Y0[c]);",
+     "if (g_sigma) g_sigma[c] += lam * 0.5 * (Y1[c] + Y0[c]);"),
+    ("te_adj_ca_dropped", "aEx[c] = Ca[c] * ae;", "aEx[c] = ae;"),
+    ("te_adj_receiver_component", "double* aE = pol == 0 ? aEx : aEy;",
+     "double* aE = pol == 0 ? aEy : aEx;"),
 ]
 
 PREAMBLE = "static double ez_hist_unused_guard(const double* E, const int32_t* rec, int r, int nx) { return 2.0 * E[(size_t)rec[2 * r + 1] * nx + rec[2 * r]]; }\n"

@@ -133,3 +133,48 @@ def test_te_rejects_other_polarisations():
     g, eps, sig = _pec_box(nt=4)
     with pytest.raises(ValueError):
         O.forward_te_shot(g, eps, sig, 2, [[20, 17]], np.zeros((1, 4)), [[30, 30]])
+
+
+@pytest.mark.parametrize("pol,kappa,pec", [(0, 2.0, True), (1, 1.0, False)])
+def test_te_misfit_gradient_fd_every_cell(pol, kappa, pec):
+    """The adjoint gradient of J = 1/2 sum (d - o)^2 over the source component's traces
+    against central differences at every cell of a tiny grid (CPML, two shots, lossy
+    heterogeneous model; kappa_max 2 and a perfect conductor in one case).  Every cell
+    carries a gradient: the cells of the outer rows and columns hold one updated E
+    component each."""
+    wl = W.small_random(13, nxp=12, nyp=10, npml=3, nt=90, nshots=2, nrec=4,
+                        kappa_max=kappa, with_pec=pec)
+    g = wl.grid
+    wav = np.stack([O.ricker(wl.f0, g.dt, g.nt)[None]] * wl.nshots)
+
+    def traces(e, s):
+        return np.stack([O.forward_te_shot(g, e, s, pol, wl.src[k], wav[k], wl.rec[k])
+                         ["traces"][:, :, pol] for k in range(wl.nshots)])
+
+    obs = traces(wl.eps_true, wl.sig_true)
+    e0, s0 = wl.eps_init.copy(), wl.sig_init.copy()
+    J, ge, gs = O.misfit_and_gradient_te(g, e0, s0, pol, wl.src, wav, wl.rec, obs)
+    assert J > 0
+    assert J == pytest.approx(0.5 * np.sum((traces(e0, s0) - obs) ** 2), rel=1e-12)
+
+    def Jof(e, s):
+        return 0.5 * np.sum((traces(e, s) - obs) ** 2)
+
+    fde = np.zeros_like(ge)
+    fds = np.zeros_like(gs)
+    for j in range(g.ny):
+        for i in range(g.nx):
+            he = 1e-6 * e0[j, i]
+            hs = 1e-6 * s0[j, i]
+            ep, em = e0.copy(), e0.copy()
+            ep[j, i] += he
+            em[j, i] -= he
+            fde[j, i] = (Jof(ep, s0) - Jof(em, s0)) / (2 * he)
+            sp, sm = s0.copy(), s0.copy()
+            sp[j, i] += hs
+            sm[j, i] -= hs
+            fds[j, i] = (Jof(e0, sp) - Jof(e0, sm)) / (2 * hs)
+    for a, b in ((ge, fde), (gs, fds)):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
+    # the corner cell (nx-1, ny-1) holds no updated component
+    assert ge[-1, -1] == 0 and gs[-1, -1] == 0
