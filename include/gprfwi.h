@@ -1,7 +1,9 @@
 /*
  * gprfwi.h -- C ABI of the GB300 (sm_103a) library for the hot path of dual-parameter GPR
  * full waveform inversion (arXiv 2506.20513): the 2-D TM Maxwell FDTD time loop with CPML
- * absorbing boundaries and its exact discrete adjoint with zero-lag gradients.
+ * absorbing boundaries and its exact discrete adjoint with zero-lag gradients (and the TE
+ * mode that x- and y-polarised sources excite: gf_forward_model_te,
+ * gf_misfit_and_gradient_te).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -208,6 +210,25 @@ int gf_forward_model_fields(gf_ctx* ctx, const float* eps_r, const float* sigma,
  * pointer or another polarisation. */
 int gf_forward_model_te(gf_ctx* ctx, const float* eps_r, const float* sigma,
                         const float* wavelet, int polarisation, float* traces, void* stream);
+
+/* misfit_and_gradient for the TE mode: J = 1/2 sum (d - o)^2 over the traces of the
+ * source's own component (Ex^n for polarisation 0, Ey^n for 1) and its exact discrete
+ * gradients, summed over shots.  The forward keeps Ex and Ey of every step; the adjoint
+ * transposes each step in reverse (E updates with their CPML memories, Hz update with its
+ * memories, recording).  Each cell's gradient is the zero-lag form of both of its E
+ * components: with lam = Cb * adjoint(E^{n+1}),
+ *   dJ/deps_r = -sum_n lam (E^{n+1} - E^n) eps0 / dt,  dJ/dsigma = -sum_n lam (E^{n+1} + E^n) / 2
+ * (the TE counterpart of Eqs. grad_eps / grad_sigma).
+ * observed: device [nshots][nt][nrec].  misfit: device FP64 scalar.  g_eps_r, g_sigma:
+ * device [ny][nx] or NULL.  traces: optional device [nshots][nt][nrec][3] as in
+ * gf_forward_model_te.  The E history (nt * 2 * nshots * ny * pitch floats) and the trace
+ * buffers are held by the context until gf_destroy; GF_ENOMEM if they cannot be allocated.
+ * One step per launch group, no lanes; it drops a wavefield stored by gf_forward, like
+ * gf_forward_model_te. */
+int gf_misfit_and_gradient_te(gf_ctx* ctx, const float* eps_r, const float* sigma,
+                              const float* wavelet, int polarisation, const float* observed,
+                              double* misfit, float* g_eps_r, float* g_sigma, float* traces,
+                              void* stream);
 
 /* Forward run that also stores the wavefield (mode GF_STORE_FULL) in the workspace for a
  * later gf_adjoint on the same model, wavelet and stream. */

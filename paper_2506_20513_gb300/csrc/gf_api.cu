@@ -60,6 +60,8 @@ struct gf_ctx {
     float* d_prof = nullptr;  // [12][max(nx, ny)] profiles (x: 6 arrays, y: 6 arrays)
     int2* d_src_xy = nullptr;  // [nshots][nsrc] source cells (x, y)
     int2* d_rec_xy = nullptr;  // [nshots][nrec] receiver cells (x, y), made by the TE model
+    float* te_buf = nullptr;   // TE gradient: E history, traces and residual (library-owned)
+    size_t te_bytes = 0;
     gf::AxisProfile px{}, py{};
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -1131,6 +1133,7 @@ void gf_destroy(gf_ctx* c) {
     cudaFree(c->d_src_xy);
     cudaFree(c->d_ring_map);
     cudaFree(c->d_rec_xy);
+    cudaFree(c->te_buf);
     cudaFree(c->d_tile_desc);
     cudaFree(c->d_tile_rec);
     cudaFree(c->d_cta_order);
@@ -1292,11 +1295,11 @@ int gf_forward_model_fields(gf_ctx* c, const float* eps_r, const float* sigma,
                        h_traces);
 }
 
-int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
-                        const float* wavelet, int polarisation, float* traces, void* stream) {
-    if (!c) return GF_EINVAL;
-    if (!eps_r || !sigma || !wavelet || !traces)
-        return fail(c, GF_EINVAL, "NULL model, wavelet or traces pointer");
+// TE model: argument checks, workspace, receiver table, parameters with the forward fields
+// in the state buffers, field clears and the coefficient kernel.
+static int te_setup(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                    int polarisation, cudaStream_t st, gf::TeParams& p, Layout& L) {
+    if (!eps_r || !sigma || !wavelet) return fail(c, GF_EINVAL, "NULL model or wavelet pointer");
     if (polarisation != 0 && polarisation != 1)
         return fail(c, GF_EINVAL, "polarisation %d: 0 (x-directed) or 1 (y-directed)",
                     polarisation);
@@ -1304,8 +1307,6 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     if ((cells + (long long)c->nshots * c->nrec) / 256 + 2 > 0x7fffffffLL)
         return fail(c, GF_EINVAL, "TE model: %lld cells exceed one launch", cells);
     if (c->rec) return fail(c, GF_ESTATE, "the TE model is not part of a batch schedule");
-    DeviceGuard guard(c->device);
-    cudaStream_t st = (cudaStream_t)stream;
     int rc = ensure_workspace(c, true);
     if (rc) return rc;
     if (!c->d_rec_xy) {
@@ -1318,11 +1319,11 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     }
     // the TE fields reuse the forward workspace's state buffers: a stored TM forward is gone
     c->have_forward = false;
-    const Layout L = layout_of(c, true);
+    L = layout_of(c, true);
     const long long F = (long long)c->nshots * c->Np;
     float* a = (float*)(c->ws + L.stA);
     float* b = (float*)(c->ws + L.stB);
-    gf::TeParams p{};
+    p = gf::TeParams{};
     p.nx = c->g.nx;
     p.ny = c->g.ny;
     p.pitch = c->pitch;
@@ -1332,8 +1333,10 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     p.nt = c->g.nt;
     p.pol = polarisation;
     p.Np = c->Np;
+    p.F = F;
     p.ch = (float)(c->g.dt / kMu0);
     p.src_scale = (float)(1.0 / (c->g.dx * c->g.dy));
+    p.geps = (float)(kEps0 / c->g.dt);
     p.px = c->px;
     p.py = c->py;
     p.ex = a;
@@ -1349,7 +1352,6 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     p.wavelet = wavelet;
     p.src_xy = c->d_src_xy;
     p.rec_xy = c->d_rec_xy;
-    p.traces = traces;
     int* status = (int*)(c->ws + L.status);
     float* ca = (float*)(c->ws + L.coef);
     const int nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
@@ -1359,10 +1361,103 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     GF_OP(c, st, -1, "clear TE fields", cudaMemsetAsync(b, 0, sizeof(float) * F, s_));
     GF_OP(c, st, GF_KERNEL_AUX, "TE coefficients",
           gf::launch_te_coef(eps_r, sigma, nx, ny, pitch, dt_eps0, ca, ca + Np, status, s_));
+    return GF_OK;
+}
+
+static int te_forward_steps(gf_ctx* c, const gf::TeParams& p, cudaStream_t st) {
     for (int n = 0; n < c->g.nt; ++n) {
         GF_OP(c, st, GF_KERNEL_FWD, "TE H update", gf::launch_te_h(p, n, s_));
         GF_OP(c, st, GF_KERNEL_FWD, "TE E update", gf::launch_te_e(p, n, s_));
     }
+    return GF_OK;
+}
+
+int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
+                        const float* wavelet, int polarisation, float* traces, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!traces) return fail(c, GF_EINVAL, "traces must not be NULL");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    gf::TeParams p;
+    Layout L;
+    int rc = te_setup(c, eps_r, sigma, wavelet, polarisation, st, p, L);
+    if (rc) return rc;
+    p.traces = traces;
+    return te_forward_steps(c, p, st);
+}
+
+int gf_misfit_and_gradient_te(gf_ctx* c, const float* eps_r, const float* sigma,
+                              const float* wavelet, int polarisation, const float* observed,
+                              double* misfit, float* g_eps_r, float* g_sigma, float* traces,
+                              void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!observed || !misfit) return fail(c, GF_EINVAL, "NULL observed or misfit pointer");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    gf::TeParams p;
+    Layout L;
+    int rc = te_setup(c, eps_r, sigma, wavelet, polarisation, st, p, L);
+    if (rc) return rc;
+    // the E history, the source component's traces and their residual, in a buffer of the
+    // library's own (kept for the next call)
+    const long long F = p.F;
+    const size_t ntr = (size_t)c->nshots * c->g.nt * c->nrec;
+    const size_t need = sizeof(float) * ((size_t)c->g.nt * 2 * (size_t)F + 2 * ntr);
+    if (c->te_bytes < need) {
+        if (c->te_buf) cudaFree(c->te_buf);
+        c->te_buf = nullptr;
+        c->te_bytes = 0;
+        if (cudaMalloc(&c->te_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GF_ENOMEM, "TE gradient: %zu bytes of wavefield history", need);
+        }
+        c->te_bytes = need;
+    }
+    p.hist = c->te_buf;
+    p.traces_p = c->te_buf + (size_t)c->g.nt * 2 * (size_t)F;
+    float* resid = p.traces_p + ntr;
+    p.traces = traces;
+    rc = te_forward_steps(c, p, st);
+    if (rc) return rc;
+    double* partial = (double*)(c->ws + L.partial);
+    int* status = (int*)(c->ws + L.status);
+    const float* tp = p.traces_p;
+    GF_OP(c, st, GF_KERNEL_AUX, "TE residual",
+          gf::launch_residual_misfit(tp, observed, resid, (long long)ntr, partial, kMisfitBlocks,
+                                     status, s_));
+    GF_OP(c, st, GF_KERNEL_AUX, "TE misfit",
+          gf::launch_finish_misfit(partial, kMisfitBlocks, misfit, s_));
+    // adjoint: 7 planes in the first state buffer, 6 in the second
+    float* a = (float*)(c->ws + L.stA);
+    float* b = (float*)(c->ws + L.stB);
+    p.aex = a;
+    p.aey = a + F;
+    p.ahz = a + 2 * F;
+    p.a_exy = a + 3 * F;
+    p.a_eyx = a + 4 * F;
+    p.b_hzx = a + 5 * F;
+    p.b_hzy = a + 6 * F;
+    p.d_ex = b;
+    p.d_ey = b + F;
+    p.d_hy = b + 2 * F;
+    p.d_hx = b + 3 * F;
+    p.g_eps = b + 4 * F;
+    p.g_sig = b + 5 * F;
+    p.resid = resid;
+    GF_OP(c, st, -1, "clear TE adjoint", cudaMemsetAsync(a, 0, 7 * sizeof(float) * F, s_));
+    GF_OP(c, st, -1, "clear TE adjoint", cudaMemsetAsync(b, 0, 6 * sizeof(float) * F, s_));
+    for (int n = c->g.nt - 1; n >= 0; --n)
+        for (int part = 0; part < 4; ++part)
+            GF_OP(c, st, GF_KERNEL_ADJ, "TE adjoint step",
+                  gf::launch_te_adj_step(p, n, part, s_));
+    const int ns = c->nshots, nx = c->g.nx, ny = c->g.ny, pitch = c->pitch;
+    const float *ge = p.g_eps, *gs = p.g_sig;
+    if (g_eps_r)
+        GF_OP(c, st, GF_KERNEL_AUX, "TE gradient shot sum",
+              gf::launch_sum_shots(ge, ns, nx, ny, pitch, g_eps_r, status, s_));
+    if (g_sigma)
+        GF_OP(c, st, GF_KERNEL_AUX, "TE gradient shot sum",
+              gf::launch_sum_shots(gs, ns, nx, ny, pitch, g_sigma, status, s_));
     return GF_OK;
 }
 

@@ -172,13 +172,25 @@ struct TeParams {
     const float* wavelet;  // [nshots][nsrc][nt]
     const int2* src_xy;    // [nshots][nsrc]
     const int2* rec_xy;    // [nshots][nrec]
-    float* traces;         // [nshots][nt][nrec][3]: Ex^n, Ey^n, Hz^{n-1/2}
+    float* traces;         // [nshots][nt][nrec][3]: Ex^n, Ey^n, Hz^{n-1/2} (NULL = skip)
+    long long F;           // nshots * Np: one field plane of every shot
+    float* traces_p;       // [nshots][nt][nrec] the source component's traces (NULL = skip)
+    float* hist;           // [nt][2][nshots][Np]: Ex^{n+1}, Ey^{n+1} of step n (NULL = none)
+    // adjoint (planes [nshots][Np]): adjoint fields, the CPML memories' adjoints, the
+    // differences' cotangents passed between the launches of one step, per-shot gradients
+    float *aex, *aey, *ahz, *a_exy, *a_eyx, *b_hzx, *b_hzy, *d_ex, *d_ey, *d_hy, *d_hx;
+    float *g_eps, *g_sig;
+    const float* resid;    // [nshots][nt][nrec] cotangent of traces_p
+    float geps;            // eps0 / dt
 };
 cudaError_t launch_te_coef(const float* eps_r, const float* sigma, int nx, int ny, int pitch,
                            float dt_eps0, float* ca, float* cb, int* status, cudaStream_t st);
 // one time step: the H launch (with the receivers of step n), then the E launch
 cudaError_t launch_te_h(const TeParams& p, int n, cudaStream_t st);
 cudaError_t launch_te_e(const TeParams& p, int n, cudaStream_t st);
+// one adjoint step n (reverse order): E updates reversed with the zero-lag gradients, Hz
+// update reversed, the E cotangents gathered, the residual of step n injected
+cudaError_t launch_te_adj_step(const TeParams& p, int n, int part, cudaStream_t st);
 // Reverse-time reconstruction inside checkpoint segments (gf_reconstruct.cu).  ring_map:
 // [ny][nx] ring index of each cell (-1 outside the ring); a ring slot holds Ez, Hx, Hy of the
 // ring cells of every shot ([3][nshots][ring_cells]).

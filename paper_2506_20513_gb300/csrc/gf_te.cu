@@ -82,10 +82,13 @@ __global__ void __launch_bounds__(kTeThreads) te_h_kernel(const TeParams p, int 
         const int s = (int)(r / p.nrec);
         const int2 xy = __ldg(p.rec_xy + r);
         const long long o = (long long)s * p.Np + (long long)xy.y * p.pitch + xy.x;
-        float* out = p.traces + (((long long)s * p.nt + n) * p.nrec + (r - (long long)s * p.nrec)) * 3;
-        out[0] = p.ex[o];
-        out[1] = p.ey[o];
-        out[2] = hz_old[o];
+        const long long k = ((long long)s * p.nt + n) * p.nrec + (r - (long long)s * p.nrec);
+        if (p.traces) {
+            p.traces[3 * k] = p.ex[o];
+            p.traces[3 * k + 1] = p.ey[o];
+            p.traces[3 * k + 2] = hz_old[o];
+        }
+        if (p.traces_p) p.traces_p[k] = p.pol == 0 ? p.ex[o] : p.ey[o];
         return;
     }
     const TeCell c = te_cell(p, t);
@@ -135,7 +138,9 @@ __global__ void __launch_bounds__(kTeThreads) te_e_kernel(const TeParams p, int 
             q += s;
         }
         if (p.pol == 0) q -= w;
-        p.ex[c.o] = fmaf(a, p.ex[c.o], b * q);
+        const float e = fmaf(a, p.ex[c.o], b * q);
+        p.ex[c.o] = e;
+        if (p.hist) p.hist[(long long)n * 2 * p.F + c.o] = e;
     }
     if (c.x >= 1) {
         const float d = h - hz[c.o - 1];
@@ -148,8 +153,118 @@ __global__ void __launch_bounds__(kTeThreads) te_e_kernel(const TeParams p, int 
         }
         q = -q;
         if (p.pol == 1) q -= w;
-        p.ey[c.o] = fmaf(a, p.ey[c.o], b * q);
+        const float e = fmaf(a, p.ey[c.o], b * q);
+        p.ey[c.o] = e;
+        if (p.hist) p.hist[(long long)n * 2 * p.F + p.F + c.o] = e;
     }
+}
+
+// ---- adjoint ---------------------------------------------------------------------------
+// Step n reversed.  On entry aex, aey hold dJ/dE^{n+1} and ahz dJ/dHz^{n+1/2} (without the
+// E updates' share); the CPML memories' adjoints follow A_n = b A_{n+1} + (cotangent of the
+// bracket that uses the memory of step n), and only inside the strips (c != 0: outside,
+// b = 0 and the memory's adjoint only ever meets c = 0).
+
+// E updates reversed: lam = Cb aE^{n+1}; the zero-lag gradients of both components of the
+// cell; the bracket's cotangent goes through its CPML memory to the Hz difference (d_ex,
+// d_ey, gathered by the next launch); aE becomes Ca aE^{n+1}.
+__global__ void __launch_bounds__(kTeThreads) te_adj_e_kernel(const TeParams p, int n) {
+    const long long cells = (long long)p.nshots * (p.nx - 1) * (p.ny - 1);
+    const long long t = blockIdx.x * (long long)kTeThreads + threadIdx.x;
+    if (t >= cells) return;
+    const TeCell c = te_cell(p, t);
+    const long long m = (long long)c.y * p.pitch + c.x;
+    const float a = __ldg(p.ca + m), b = __ldg(p.cb + m);
+    const float* h1 = p.hist + (long long)n * 2 * p.F;
+    const float* h0 = n > 0 ? h1 - 2 * p.F : nullptr;
+    float ge = 0.f, gs = 0.f;
+    if (c.y >= 1) {
+        const float ae = p.aex[c.o];
+        const float lam = b * ae;
+        const float e1 = h1[c.o], e0 = h0 ? h0[c.o] : 0.f;
+        ge = fmaf(-lam, e1 - e0, ge);
+        gs = fmaf(-0.5f * lam, e1 + e0, gs);
+        float d = __ldg(p.py.aE + c.y) * lam;
+        const float cy = __ldg(p.py.cE + c.y);
+        if (cy != 0.f) {
+            const float A = fmaf(__ldg(p.py.bE + c.y), p.a_exy[c.o], lam);
+            p.a_exy[c.o] = A;
+            d = fmaf(cy, A, d);
+        }
+        p.d_ex[c.o] = d;
+        p.aex[c.o] = a * ae;
+    }
+    if (c.x >= 1) {
+        const float ae = p.aey[c.o];
+        const float lam = b * ae;
+        const float e1 = h1[p.F + c.o], e0 = h0 ? h0[p.F + c.o] : 0.f;
+        ge = fmaf(-lam, e1 - e0, ge);
+        gs = fmaf(-0.5f * lam, e1 + e0, gs);
+        // Qy = -(a D + psi): the bracket's cotangent is -lam
+        float d = -__ldg(p.px.aE + c.x) * lam;
+        const float cx = __ldg(p.px.cE + c.x);
+        if (cx != 0.f) {
+            const float A = fmaf(__ldg(p.px.bE + c.x), p.a_eyx[c.o], -lam);
+            p.a_eyx[c.o] = A;
+            d = fmaf(cx, A, d);
+        }
+        p.d_ey[c.o] = d;
+        p.aey[c.o] = a * ae;
+    }
+    p.g_eps[c.o] = fmaf(ge, p.geps, p.g_eps[c.o]);
+    p.g_sig[c.o] += gs;
+}
+
+// Hz update reversed: dJ/dHz^{n+1/2} gathers the E brackets' cotangents of the four E
+// nodes around the cell; it is also dJ/dHz^{n-1/2}; the Hz bracket's cotangent goes through
+// the memories to the E differences (d_hy for Ex, d_hx for Ey).
+__global__ void __launch_bounds__(kTeThreads) te_adj_h_kernel(const TeParams p) {
+    const long long cells = (long long)p.nshots * (p.nx - 1) * (p.ny - 1);
+    const long long t = blockIdx.x * (long long)kTeThreads + threadIdx.x;
+    if (t >= cells) return;
+    const TeCell c = te_cell(p, t);
+    const float ah = p.ahz[c.o] + (p.d_ex[c.o] - p.d_ex[c.o + p.pitch]) +
+                     (p.d_ey[c.o] - p.d_ey[c.o + 1]);
+    p.ahz[c.o] = ah;
+    const float h = p.ch * ah;
+    float dy = __ldg(p.py.aH + c.y) * h;
+    const float cy = __ldg(p.py.cH + c.y);
+    if (cy != 0.f) {
+        const float B = fmaf(__ldg(p.py.bH + c.y), p.b_hzy[c.o], h);
+        p.b_hzy[c.o] = B;
+        dy = fmaf(cy, B, dy);
+    }
+    float dx = -__ldg(p.px.aH + c.x) * h;
+    const float cx = __ldg(p.px.cH + c.x);
+    if (cx != 0.f) {
+        const float B = fmaf(__ldg(p.px.bH + c.x), p.b_hzx[c.o], -h);
+        p.b_hzx[c.o] = B;
+        dx = fmaf(cx, B, dx);
+    }
+    p.d_hy[c.o] = dy;
+    p.d_hx[c.o] = dx;
+}
+
+// dJ/dE^n of the updated E nodes: Ca aE^{n+1} plus the two Hz cells whose differences use it.
+__global__ void __launch_bounds__(kTeThreads) te_adj_gather_kernel(const TeParams p) {
+    const long long cells = (long long)p.nshots * (p.nx - 1) * (p.ny - 1);
+    const long long t = blockIdx.x * (long long)kTeThreads + threadIdx.x;
+    if (t >= cells) return;
+    const TeCell c = te_cell(p, t);
+    if (c.y >= 1) p.aex[c.o] += p.d_hy[c.o - p.pitch] - p.d_hy[c.o];
+    if (c.x >= 1) p.aey[c.o] += p.d_hx[c.o - 1] - p.d_hx[c.o];
+}
+
+// The recording of step n reversed: the residual enters the source component's adjoint at
+// each receiver node (atomic: receivers may share a cell).
+__global__ void te_adj_rec_kernel(const TeParams p, int n) {
+    const long long r = blockIdx.x * (long long)kTeThreads + threadIdx.x;
+    if (r >= (long long)p.nshots * p.nrec) return;
+    const int s = (int)(r / p.nrec);
+    const int2 xy = __ldg(p.rec_xy + r);
+    const long long o = (long long)s * p.Np + (long long)xy.y * p.pitch + xy.x;
+    float* ae = p.pol == 0 ? p.aex : p.aey;
+    atomicAdd(ae + o, __ldg(p.resid + ((long long)s * p.nt + n) * p.nrec + (r - (long long)s * p.nrec)));
 }
 
 long long te_blocks(long long n) { return (n + kTeThreads - 1) / kTeThreads; }
@@ -171,6 +286,20 @@ cudaError_t launch_te_h(const TeParams& p, int n, cudaStream_t st) {
     const float* hz_old = (n & 1) ? p.hz1 : p.hz0;
     float* hz_new = (n & 1) ? p.hz0 : p.hz1;
     te_h_kernel<<<(unsigned)(bc + br), kTeThreads, 0, st>>>(p, n, hz_old, hz_new);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_te_adj_step(const TeParams& p, int n, int part, cudaStream_t st) {
+    const long long cells = (long long)p.nshots * (p.nx - 1) * (p.ny - 1);
+    const unsigned bc = (unsigned)te_blocks(cells);
+    switch (part) {
+        case 0: te_adj_e_kernel<<<bc, kTeThreads, 0, st>>>(p, n); break;
+        case 1: te_adj_h_kernel<<<bc, kTeThreads, 0, st>>>(p); break;
+        case 2: te_adj_gather_kernel<<<bc, kTeThreads, 0, st>>>(p); break;
+        default:
+            te_adj_rec_kernel<<<(unsigned)te_blocks((long long)p.nshots * p.nrec), kTeThreads, 0,
+                                st>>>(p, n);
+    }
     return cudaGetLastError();
 }
 

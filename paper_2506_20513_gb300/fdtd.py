@@ -210,6 +210,27 @@ class FDTD:
         _lib.check(self.lib, self.ctx, rc)
         return tr
 
+    def misfit_and_gradient_te(self, eps_r, sigma, wavelet, observed, polarisation: int = 0,
+                               return_traces: bool = False):
+        """TE mode: J = 1/2 sum (d - o)^2 over the source component's traces (observed
+        [nshots, nt, nrec]: Ex for ``polarisation`` 0, Ey for 1), dJ/deps_r and dJ/dsigma
+        [ny, nx]; with ``return_traces`` also the traces [nshots, nt, nrec, 3]."""
+        e, s = self._model(eps_r, sigma)
+        w = self._wavelet(wavelet)
+        o = _dev_f32(observed, self.trace_shape, "observed", self.device)
+        self._workspace(full=False)
+        J = torch.empty(1, dtype=torch.float64, device=self.device)
+        ge = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        gs = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        tr = torch.empty(self.trace_shape + (3,), dtype=torch.float32, device=self.device) \
+            if return_traces else None
+        rc = self.lib.gf_misfit_and_gradient_te(
+            self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(), int(polarisation), o.data_ptr(),
+            J.data_ptr(), ge.data_ptr(), gs.data_ptr(),
+            tr.data_ptr() if tr is not None else None, self._stream())
+        _lib.check(self.lib, self.ctx, rc)
+        return (J, ge, gs, tr) if return_traces else (J, ge, gs)
+
     def misfit_and_gradient(self, eps_r, sigma, wavelet, observed, return_traces: bool = False):
         """J = 1/2 sum (d - o)^2 (FP64 device scalar), dJ/deps_r and dJ/dsigma [ny, nx].
 

@@ -1,5 +1,6 @@
-"""TE-mode forward model (x- and y-directed sources: Ex, Ey, Hz) on the GPU vs the FP64
-oracle, element by element on the same seeded inputs.
+"""TE-mode forward model and gradient (x- and y-directed sources: Ex, Ey, Hz) on the GPU vs
+the FP64 oracle, element by element on the same seeded inputs.  Gradients: misfit, g_eps_r
+and g_sigma to rel-L2 <= 1e-3.
 
 Tolerance: relative L2 <= 1e-4 per shot and component (a component far weaker than its
 unit's strongest one, e.g. a cross-polar trace near a symmetry line, is held to 1e-4 of a
@@ -154,4 +155,80 @@ def test_errors_and_workspace_reuse(dev):
         fd.adjoint(e, s, t32(np.zeros((2, 80, 5)), dev))
     assert ex.value.code == _lib.GF_ESTATE
     fd.status()
+    fd.close()
+
+
+GRAD_TOL = 1e-3
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gradient_case(wl, dev, pol):
+    from paper_2506_20513_gb300 import FDTD
+    g = wl.grid
+    wav = wavelets(wl, wl.src.shape[1])
+    obs = np.stack([O.forward_te_shot(g, wl.eps_true, wl.sig_true, pol, wl.src[k], wav[k],
+                                      wl.rec[k])["traces"][:, :, pol]
+                    for k in range(wl.nshots)])
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    e0, s0, w = t32(wl.eps_init, dev), t32(wl.sig_init, dev), t32(wav, dev)
+    J, ge, gs, tr = fd.misfit_and_gradient_te(e0, s0, w, t32(obs, dev), pol,
+                                              return_traces=True)
+    fd.status()
+    # the gradient call's traces are the forward model's
+    assert torch.equal(tr, fd.forward_model_te(e0, s0, w, pol))
+    # observed = its own traces: J = 0 and no gradient
+    J0, ge0, gs0 = fd.misfit_and_gradient_te(e0, s0, w, tr[..., pol].contiguous(), pol)
+    assert float(J0.item()) == 0.0 and not ge0.any() and not gs0.any()
+    fd.status()
+    fd.close()
+    J64, ge64, gs64 = O.misfit_and_gradient_te(g, wl.eps_init, wl.sig_init, pol, wl.src, wav,
+                                               wl.rec, obs)
+    assert abs(float(J.item()) - J64) <= GRAD_TOL * J64
+    assert rel(ge.cpu().numpy(), ge64) <= GRAD_TOL
+    assert rel(gs.cpu().numpy(), gs64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+@pytest.mark.parametrize("seed,kappa,pec", [(41, 1.0, False), (42, 2.0, True)])
+def test_gradient_small_random(dev, seed, kappa, pec, pol):
+    wl = W.small_random(seed, nxp=46, nyp=27, npml=6, nt=150, nshots=3, nrec=9,
+                        kappa_max=kappa, with_pec=pec)
+    gradient_case(wl, dev, pol)
+
+
+def test_gradient_pec_box_and_several_sources(dev):
+    """No CPML; three sources per shot (two in one cell), duplicate receivers."""
+    wl = W.small_random(43, nxp=37, nyp=22, npml=0, nt=120, nshots=2, nrec=6)
+    rec = wl.rec.copy()
+    rec[..., 0] = np.clip(rec[..., 0], 1, wl.grid.nx - 2)
+    rec[..., 1] = np.clip(rec[..., 1], 1, wl.grid.ny - 2)
+    rec[:, 1] = rec[:, 0]
+    src = np.concatenate([wl.src, wl.src, wl.src], axis=1).copy()
+    src[:, 2] = [20, 12]
+    gradient_case(dataclasses.replace(wl, src=src, rec=rec), dev, 1)
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_gradient_larger_grid(dev, pol):
+    """110 x 84 physical cells with an 8-cell CPML, nt 400, two shots, a perfect conductor."""
+    wl = W.small_random(44, nxp=110, nyp=84, npml=8, nt=400, nshots=2, nrec=12,
+                        with_pec=True)
+    gradient_case(wl, dev, pol)
+
+
+def test_gradient_errors(dev):
+    from paper_2506_20513_gb300 import FDTD
+    wl = W.small_random(45, nxp=20, nyp=14, npml=3, nt=20, nshots=1, nrec=3)
+    fd = FDTD(wl.grid, wl.src, wl.rec, device=dev)
+    e, s = t32(wl.eps_init, dev), t32(wl.sig_init, dev)
+    w = t32(wavelets(wl, 1), dev)
+    obs = t32(np.zeros((1, 20, 3)), dev)
+    with pytest.raises(_lib.GfError) as ex:
+        fd.misfit_and_gradient_te(e, s, w, obs, 2)
+    assert ex.value.code == _lib.GF_EINVAL
     fd.close()
