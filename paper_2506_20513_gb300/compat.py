@@ -13,7 +13,8 @@ Readings of the parameters (the paper lists names and example values only):
   receivers of every shot are at receiver_location + r * receiver_step (r = 0 .. nrx-1);
 * source = ['hertzian', 'z']: a z-polarised line source (TM mode, Ez traces, differentiable);
   ['hertzian', 'x'] or ['hertzian', 'y']: an x- or y-polarised one (TE mode, traces of Ex or
-  Ey, forward only: no TE adjoint is built); source_amplitudes =
+  Ey, not differentiable here: the TE gradient call, gf_misfit_and_gradient_te, takes
+  observed traces, not the arbitrary trace cotangent autograd passes); source_amplitudes =
   ['ricker', A, f0]: a Ricker wavelet of amplitude A and peak frequency f0, replaced by
   ``freq`` when that is given (a multiscale band, Sec. 3.4);
 * time_windows / dt steps (rounded); miu must be 1 (relative permeability is not inverted).
@@ -70,7 +71,8 @@ def compute(device, dx, ny, nx, nz, time_windows, source, source_location, sourc
     pol = pols[source[1]]
     if pol is not None and torch.is_grad_enabled() and (
             getattr(epsilon, "requires_grad", False) or getattr(sigma, "requires_grad", False)):
-        raise ValueError("the x- and y-polarised (TE) model is forward only: run it without "
+        raise ValueError("compute() runs the x- and y-polarised (TE) model without autograd "
+                         "(FDTD.misfit_and_gradient_te gives its gradients): run it without "
                          "gradients (torch.no_grad() or detached epsilon and sigma)")
     kind, amp, f0 = source_amplitudes
     if kind != "ricker":

@@ -114,7 +114,8 @@ def test_paper_demo_loop_with_adam_reduces_the_loss():
 @pytest.mark.gpu
 def test_compute_with_x_and_y_polarised_sources():
     """['hertzian', 'x' | 'y'] runs the TE model: the traces are the source component of
-    forward_model_te; asking for gradients is refused (no TE adjoint)."""
+    forward_model_te; asking autograd for gradients is refused (the TE gradient call takes
+    observed traces, not a trace cotangent)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2506_20513_gb300 import FDTD
