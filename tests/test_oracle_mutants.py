@@ -49,6 +49,8 @@ TE_MUTANTS = [
      "traces[((size_t)n * nrec + r) * 3 + 0] = Ex[c + 1];"),
     ("te_source_scale", "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / (dx * dy);",
      "Qy;\n            Q[c] -= wav[(size_t)s * nt + n] / dx;"),
+    ("te_hz_receiver_node", "traces[((size_t)n * nrec + r) * 3 + 2] = Hz[c];",
+     "traces[((size_t)n * nrec + r) * 3 + 2] = Hz[c + nx];"),
     # ... and in its adjoint
     ("te_adj_psi_decay_dropped", "aPHzx[c] = ax.bH[i] * aPHzx[c] - ah;", "aPHzx[c] = -ah;"),
     ("te_adj_transposed_index", "aHz[c - 1] -= aD / dx;", "aHz[c + 1] -= aD / dx;"),
