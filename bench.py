@@ -477,6 +477,12 @@ def fwi_leg(args, fd, wl, eps_t, sig_t, eps0, sig0) -> dict:
 # Ex, Ey and writes Ex, Ey (20 B); Ca, Cb (one plane pair for all shots) stay in L2, the
 # CPML memories are touched in the strips only (not counted).
 TE_BYTES_PER_CELL_STEP = 36.0
+# TE gradient, per cell and step: the forward above plus its Ex, Ey history writes (8 B), and
+# the adjoint's four launches: E reversed (reads aEx, aEy and Ex, Ey of two steps, writes
+# aEx, aEy and two difference cotangents, updates two gradient planes: 56 B), Hz reversed
+# (reads aHz and two cotangent planes, writes aHz and two: 24 B), gather (reads aEx, aEy and
+# two cotangent planes, writes aEx, aEy: 24 B).
+TE_GRAD_BYTES_PER_CELL_STEP = TE_BYTES_PER_CELL_STEP + 8.0 + 56.0 + 24.0 + 24.0
 
 
 def te_leg(args, dev) -> dict:
@@ -505,10 +511,36 @@ def te_leg(args, dev) -> dict:
     ms = ev0.elapsed_time(ev1) / reps
     launches = (fd.lib.gf_kernel_launches(fd.ctx) - l0) // reps
     fd.status()
-    fd.close()
     cell_steps = wl.nshots * g.nt * (g.nx - 1) * (g.ny - 1)   # cells each step updates
     peak, kind = hbm_peak()
     achieved = TE_BYTES_PER_CELL_STEP * cell_steps / (ms / 1e3) / 1e9
+    # the gradient at the smoothed start model for data of the true model (one warm-up call,
+    # two timed); its E history is held by the context (nt x 2 planes per shot)
+    grad = None
+    try:
+        obs = fd.forward_model_te(e, s, wav, 0)[..., 0].contiguous()
+        e0, s0 = t32(wl.eps_init), t32(wl.sig_init)
+        fd.misfit_and_gradient_te(e0, s0, wav, obs, 0)
+        torch.cuda.synchronize(dev)
+        ev0.record()
+        for _ in range(2):
+            J, _, _ = fd.misfit_and_gradient_te(e0, s0, wav, obs, 0)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+        gms = ev0.elapsed_time(ev1) / 2
+        fd.status()
+        ga = TE_GRAD_BYTES_PER_CELL_STEP * cell_steps / (gms / 1e3) / 1e9
+        grad = {"s_per_gradient": gms / 1e3, "misfit": float(J.item()),
+                "gcell_updates_per_s": 2 * wl.nshots * g.nt * g.ncells / gms / 1e6,
+                "history_gb": 2 * g.nt * wl.nshots * g.ny * ((g.nx + 3) // 4 * 4) * 4 / 1e9,
+                "roofline": {"bound": "hbm", "achieved": ga, "peak": peak, "unit": "GB/s",
+                             "frac": ga / peak, "traffic": None,
+                             "kernel": "TE forward with history + four adjoint launches per "
+                                       "step (whole calls)",
+                             "algorithmic_bytes_per_cell_step": TE_GRAD_BYTES_PER_CELL_STEP}}
+    except Exception as ex:  # noqa: BLE001 -- reported in the record, not fatal to the bench
+        grad = {"error": f"{type(ex).__name__}: {ex}"}
+    fd.close()
     return {"workload": f"{wl.name}_te_x", "grid": f"{g.nx}x{g.ny}", "nshots": wl.nshots,
             "nt": g.nt, "nrec": wl.nrec, "polarisation": "x (traces of Ex, Ey, Hz)",
             "ms_per_forward": ms,
@@ -518,7 +550,8 @@ def te_leg(args, dev) -> dict:
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "te_h_kernel + te_e_kernel (whole calls)",
                          "peak_source": f"hbm_gbs of {kind}",
-                         "algorithmic_bytes_per_cell_step": TE_BYTES_PER_CELL_STEP}}
+                         "algorithmic_bytes_per_cell_step": TE_BYTES_PER_CELL_STEP},
+            "gradient": grad}
 
 
 def large_leg(args, dev, sms: int) -> dict:
@@ -736,6 +769,7 @@ def ours(args):
         large = large_leg(args, dev, sms)
     te_rec = None
     if not args.no_te and world == 1 and args.workload == "multishot" and not args.checkpoint:
+        torch.cuda.empty_cache()   # the earlier legs' workspaces: room for the TE history
         te_rec = te_leg(args, dev)
 
     if rank == 0:
