@@ -230,6 +230,14 @@ int gf_misfit_and_gradient_te(gf_ctx* ctx, const float* eps_r, const float* sigm
                               double* misfit, float* g_eps_r, float* g_sigma, float* traces,
                               void* stream);
 
+/* The misfit of gf_misfit_and_gradient_te alone (a line-search evaluation): the TE forward
+ * model and J = 1/2 sum (d - o)^2 over the source component's traces, no history, no
+ * adjoint.  Bit-identical to the J of gf_misfit_and_gradient_te on the same inputs.
+ * observed: device [nshots][nt][nrec]; misfit: device FP64 scalar.  Uses the context's TE
+ * trace buffer (held until gf_destroy). */
+int gf_misfit_te(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,
+                 int polarisation, const float* observed, double* misfit, void* stream);
+
 /* Forward run that also stores the wavefield (mode GF_STORE_FULL) in the workspace for a
  * later gf_adjoint on the same model, wavelet and stream. */
 int gf_forward(gf_ctx* ctx, const float* eps_r, const float* sigma, const float* wavelet,

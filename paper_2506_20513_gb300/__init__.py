@@ -7,7 +7,7 @@ Layout: ``csrc/`` CUDA kernels and the C-ABI runtime (``include/gprfwi.h``), ``_
 Heavy modules are imported lazily so that ``workloads`` can be used without torch/CUDA.
 """
 
-__all__ = ["FDTD", "FDTDBatch", "FDTDFunction", "Tiling", "autotune", "ricker"]
+__all__ = ["FDTD", "FDTDBatch", "FDTDFunction", "TEMode", "Tiling", "autotune", "ricker"]
 
 
 def __getattr__(name):

@@ -35,7 +35,7 @@ ERROR_NAMES = {
 # Every entry point declared in include/gprfwi.h and include/gprfwi_unet.h.
 EXPORTS = (
     "gf_create", "gf_destroy", "gf_last_error", "gf_workspace_size", "gf_set_workspace",
-    "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward_model_fields", "gf_forward_model_te", "gf_misfit_and_gradient_te", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
+    "gf_set_tiling", "gf_set_variant", "gf_set_storage", "gf_get_tiling", "gf_forward_model", "gf_forward_model_fields", "gf_forward_model_te", "gf_misfit_and_gradient_te", "gf_misfit_te", "gf_forward", "gf_adjoint", "gf_misfit_and_gradient",
     "gf_status", "gf_ricker", "gf_version", "gf_kernel_launches", "gf_set_wait_budget", "gf_set_lanes", "gf_profile",
     "gf_profile_read", "gf_profile_read_span", "gf_forward_model_noalloc", "gf_misfit", "gf_tv_scratch_bytes",
     "gf_tv_gradient", "gf_adam_update", "gf_autotune", "gf_batch_create", "gf_batch_destroy",
@@ -109,6 +109,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
             "gf_forward_model_fields": (i, [vp, vp, vp, vp, vp, vp, vp, vp]),
             "gf_forward_model_te": (i, [vp, vp, vp, vp, i, vp, vp]),
             "gf_misfit_and_gradient_te": (i, [vp, vp, vp, vp, i, vp, vp, vp, vp, vp, vp]),
+            "gf_misfit_te": (i, [vp, vp, vp, vp, i, vp, vp, vp]),
             "gf_forward": (i, [vp, vp, vp, vp, vp, vp, i, vp]),
             "gf_adjoint": (i, [vp, vp, vp, vp, vp, vp, vp]),
             "gf_misfit_and_gradient": (i, [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),

@@ -1364,6 +1364,20 @@ static int te_setup(gf_ctx* c, const float* eps_r, const float* sigma, const flo
     return GF_OK;
 }
 
+// The context's TE buffer (E history, traces, residual), grown to `need` bytes.
+static int te_buffer(gf_ctx* c, size_t need) {
+    if (c->te_bytes >= need) return GF_OK;
+    if (c->te_buf) cudaFree(c->te_buf);
+    c->te_buf = nullptr;
+    c->te_bytes = 0;
+    if (cudaMalloc(&c->te_buf, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GF_ENOMEM, "TE model: %zu bytes of history and trace buffers", need);
+    }
+    c->te_bytes = need;
+    return GF_OK;
+}
+
 static int te_forward_steps(gf_ctx* c, const gf::TeParams& p, cudaStream_t st) {
     for (int n = 0; n < c->g.nt; ++n) {
         GF_OP(c, st, GF_KERNEL_FWD, "TE H update", gf::launch_te_h(p, n, s_));
@@ -1386,6 +1400,33 @@ int gf_forward_model_te(gf_ctx* c, const float* eps_r, const float* sigma,
     return te_forward_steps(c, p, st);
 }
 
+int gf_misfit_te(gf_ctx* c, const float* eps_r, const float* sigma, const float* wavelet,
+                 int polarisation, const float* observed, double* misfit, void* stream) {
+    if (!c) return GF_EINVAL;
+    if (!observed || !misfit) return fail(c, GF_EINVAL, "NULL observed or misfit pointer");
+    DeviceGuard guard(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    gf::TeParams p;
+    Layout L;
+    int rc = te_setup(c, eps_r, sigma, wavelet, polarisation, st, p, L);
+    if (rc) return rc;
+    const size_t ntr = (size_t)c->nshots * c->g.nt * c->nrec;
+    rc = te_buffer(c, sizeof(float) * ntr);
+    if (rc) return rc;
+    p.traces_p = c->te_buf;
+    rc = te_forward_steps(c, p, st);
+    if (rc) return rc;
+    double* partial = (double*)(c->ws + L.partial);
+    int* status = (int*)(c->ws + L.status);
+    const float* tp = p.traces_p;
+    GF_OP(c, st, GF_KERNEL_AUX, "TE misfit",
+          gf::launch_residual_misfit(tp, observed, nullptr, (long long)ntr, partial,
+                                     kMisfitBlocks, status, s_));
+    GF_OP(c, st, GF_KERNEL_AUX, "TE misfit",
+          gf::launch_finish_misfit(partial, kMisfitBlocks, misfit, s_));
+    return GF_OK;
+}
+
 int gf_misfit_and_gradient_te(gf_ctx* c, const float* eps_r, const float* sigma,
                               const float* wavelet, int polarisation, const float* observed,
                               double* misfit, float* g_eps_r, float* g_sigma, float* traces,
@@ -1402,17 +1443,8 @@ int gf_misfit_and_gradient_te(gf_ctx* c, const float* eps_r, const float* sigma,
     // library's own (kept for the next call)
     const long long F = p.F;
     const size_t ntr = (size_t)c->nshots * c->g.nt * c->nrec;
-    const size_t need = sizeof(float) * ((size_t)c->g.nt * 2 * (size_t)F + 2 * ntr);
-    if (c->te_bytes < need) {
-        if (c->te_buf) cudaFree(c->te_buf);
-        c->te_buf = nullptr;
-        c->te_bytes = 0;
-        if (cudaMalloc(&c->te_buf, need) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, GF_ENOMEM, "TE gradient: %zu bytes of wavefield history", need);
-        }
-        c->te_bytes = need;
-    }
+    rc = te_buffer(c, sizeof(float) * ((size_t)c->g.nt * 2 * (size_t)F + 2 * ntr));
+    if (rc) return rc;
     p.hist = c->te_buf;
     p.traces_p = c->te_buf + (size_t)c->g.nt * 2 * (size_t)F;
     float* resid = p.traces_p + ntr;

@@ -231,6 +231,22 @@ class FDTD:
         _lib.check(self.lib, self.ctx, rc)
         return (J, ge, gs, tr) if return_traces else (J, ge, gs)
 
+    def misfit_te(self, eps_r, sigma, wavelet, observed, polarisation: int = 0,
+                  out: torch.Tensor | None = None):
+        """TE mode: J = 1/2 sum (d - o)^2 over the source component's traces only (a
+        line-search evaluation), FP64 device scalar."""
+        e, s = self._model(eps_r, sigma)
+        w = self._wavelet(wavelet)
+        o = _dev_f32(observed, self.trace_shape, "observed", self.device)
+        self._workspace(full=False)
+        J = out if out is not None else torch.empty(1, dtype=torch.float64, device=self.device)
+        if J.dtype != torch.float64 or J.device != self.device or J.numel() < 1:
+            raise ValueError("out must be a float64 tensor on the context's device")
+        rc = self.lib.gf_misfit_te(self.ctx, e.data_ptr(), s.data_ptr(), w.data_ptr(),
+                                   int(polarisation), o.data_ptr(), J.data_ptr(), self._stream())
+        _lib.check(self.lib, self.ctx, rc)
+        return J
+
     def misfit_and_gradient(self, eps_r, sigma, wavelet, observed, return_traces: bool = False):
         """J = 1/2 sum (d - o)^2 (FP64 device scalar), dJ/deps_r and dJ/dsigma [ny, nx].
 
@@ -301,6 +317,36 @@ class FDTD:
                                  gs.data_ptr(), self._stream())
         _lib.check(self.lib, self.ctx, rc)
         return ge, gs
+
+
+class TEMode:
+    """An :class:`FDTD` context seen through the TE mode of one source polarisation (0: x,
+    1: y): ``misfit`` and ``misfit_and_gradient`` have the TM signatures and run the TE
+    calls, so that the FWI driver (:class:`~.fwi.FWI`, without a learned preconditioner)
+    inverts the source component's traces.  Everything else is the context's."""
+
+    def __init__(self, fdtd: FDTD, polarisation: int):
+        if polarisation not in (0, 1):
+            raise ValueError("polarisation must be 0 (x) or 1 (y)")
+        self.fd = fdtd
+        self.polarisation = polarisation
+
+    def __getattr__(self, name):
+        if name == "fd":
+            raise AttributeError(name)
+        return getattr(self.fd, name)
+
+    def misfit(self, eps_r, sigma, wavelet, observed, out=None):
+        return self.fd.misfit_te(eps_r, sigma, wavelet, observed, self.polarisation, out=out)
+
+    def misfit_and_gradient(self, eps_r, sigma, wavelet, observed):
+        return self.fd.misfit_and_gradient_te(eps_r, sigma, wavelet, observed, self.polarisation)
+
+    def forward_model(self, eps_r, sigma, wavelet, illumination: bool = False):
+        if illumination:
+            raise ValueError("no TE illumination: the learned preconditioner is TM-only")
+        return self.fd.forward_model_te(eps_r, sigma, wavelet,
+                                        self.polarisation)[..., self.polarisation].contiguous()
 
 
 class FDTDFunction(torch.autograd.Function):

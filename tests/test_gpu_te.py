@@ -232,3 +232,33 @@ def test_gradient_errors(dev):
         fd.misfit_and_gradient_te(e, s, w, obs, 2)
     assert ex.value.code == _lib.GF_EINVAL
     fd.close()
+
+
+def test_misfit_alone_and_fwi_on_the_te_mode(dev):
+    """gf_misfit_te gives the gradient call's J bit for bit; the L-BFGS driver inverts the
+    x-polarised traces through TEMode: its first misfit is the oracle's, and every accepted
+    step lowers it."""
+    from paper_2506_20513_gb300 import FDTD, TEMode
+    from paper_2506_20513_gb300.fwi import FWI, FWIConfig, interior_mask
+    wl = W.small_random(46, nxp=46, nyp=27, npml=6, nt=150, nshots=3, nrec=9)
+    g = wl.grid
+    wav = wavelets(wl, 1)
+    obs = np.stack([O.forward_te_shot(g, wl.eps_true, wl.sig_true, 0, wl.src[k], wav[k],
+                                      wl.rec[k])["traces"][:, :, 0]
+                    for k in range(wl.nshots)])
+    fd = FDTD(g, wl.src, wl.rec, device=dev)
+    e0, s0, w, o = (t32(a, dev) for a in (wl.eps_init, wl.sig_init, wav, obs))
+    J1 = fd.misfit_te(e0, s0, w, o, 0)
+    J2, _, _ = fd.misfit_and_gradient_te(e0, s0, w, o, 0)
+    assert float(J1.item()) == float(J2.item())
+    J64, _, _ = O.misfit_and_gradient_te(g, wl.eps_init, wl.sig_init, 0, wl.src, wav, wl.rec,
+                                         obs)
+    inv = FWI(TEMode(fd, 0), lambda f0: o, interior_mask(g, rows_below_top=2),
+              FWIConfig(bands=((wl.f0, 6),)))
+    eps, sig, hist = inv.run(e0, s0)
+    fd.status()
+    fd.close()
+    assert abs(hist.misfit[0] - J64) <= GRAD_TOL * J64
+    seq = hist.misfit + [hist.final_misfit]
+    assert all(b <= a for a, b in zip(seq, seq[1:]))
+    assert hist.final_misfit < 0.9 * hist.misfit[0]
