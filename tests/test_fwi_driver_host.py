@@ -172,3 +172,36 @@ def test_learned_max_caps_the_kept_updates(no_cuda_sync):
     # two updates kept, then the network is not consulted again in the band
     assert pre.stages == [0, 1]
     assert hist.learned == [True, True, False, False, False]
+
+
+class QuadraticTE(QuadraticFD):
+    """The TE calls of a context, over the same quadratic misfit; records the polarisations."""
+
+    def __init__(self):
+        super().__init__()
+        self.pols = []
+
+    def misfit_te(self, eps, sig, wav, obs, polarisation, out=None):
+        self.pols.append(polarisation)
+        return self.misfit(eps, sig, wav, obs, out=out)
+
+    def misfit_and_gradient_te(self, eps, sig, wav, obs, polarisation):
+        self.pols.append(polarisation)
+        return self.misfit_and_gradient(eps, sig, wav, obs)
+
+
+def test_te_mode_routes_the_driver_to_the_te_calls(no_cuda_sync):
+    from paper_2506_20513_gb300.fdtd import TEMode
+    fd = QuadraticTE()
+    te = TEMode(fd, 1)
+    assert te.shape == fd.shape and te.grid is fd.grid   # everything else is the context's
+    drv = F.FWI(te, lambda f0: None, torch.ones(fd.shape), F.FWIConfig(bands=((4e8, 20),)))
+    eps, _, hist = drv.run(fd.eps_true + 0.5, fd.sig_true * 0.5)
+    # every evaluation went through a TE call with the view's polarisation
+    assert fd.pols and set(fd.pols) == {1}
+    assert len(fd.pols) == fd.calls["misfit"] + fd.calls["gradient"]
+    assert hist.misfit[-1] < 1e-3 * hist.misfit[0]
+    with pytest.raises(ValueError):
+        TEMode(fd, 2)
+    with pytest.raises(ValueError):
+        te.forward_model(eps, eps, None, illumination=True)
